@@ -1,0 +1,412 @@
+"""Seeded synthetic scenes and the stand-in dynamics that feeds each step.
+
+This module produces inputs only: meshes, inverse masses, initial states and
+the target ``x~`` of each step.  It holds none of the collision-handling
+method's arithmetic, and serves both the CUDA path and the CPU oracle.
+
+The paper's own meshes and animations are not available, so every scene is a
+synthetic stand-in shaped like the paper's examples: cloth over a sphere, two
+stacked cloth layers, a pile of volumetric bodies, two interleaved tubes that
+tighten like a knot, and hair strands with sand grains in a bowl.
+
+The stand-in dynamics (not part of the method, which receives ``x~`` as
+input) is explicit inertia ``x~ = x^t + dt v`` with scripted kinematic
+vertices, followed by a few Jacobi sweeps that pull mesh edges toward their
+rest lengths, and the velocity update ``v <- (x^{t+1} - x^t)/dt + dt g`` that
+the paper uses to chain steps.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Scene:
+    name: str
+    inv_mass: np.ndarray            # (n,) float64; 0 = fixed or kinematic
+    tris: np.ndarray                # (T,3) int32 collision triangles
+    edges: np.ndarray               # (E,2) int32 collision edges (edge-edge pairs)
+    len_edges: np.ndarray           # (C,2) int32 edge-length constraints
+    points: np.ndarray              # (Q,) int32 point participants (vertex-vertex pairs)
+    x0: np.ndarray                  # (n,3) float64 initial, intersection-free
+    v0: np.ndarray                  # (n,3) float64 initial velocity
+    dt: float
+    gravity: np.ndarray             # (3,)
+    radius: Optional[np.ndarray] = None     # (n,) or None
+    kin_v: Optional[np.ndarray] = None      # (n,3) scripted velocity of inv_mass==0 vertices
+    rest_len: Optional[np.ndarray] = None   # (C,) rest lengths for the stand-in relaxation
+    relax_sweeps: int = 4
+    steps: int = 30
+    params: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_verts(self) -> int:
+        return int(self.x0.shape[0])
+
+    def counts(self) -> dict:
+        return dict(verts=self.n_verts, tris=len(self.tris), edges=len(self.edges), len_edges=len(self.len_edges),
+                    points=len(self.points))
+
+
+# --------------------------------------------------------------------------
+# mesh builders
+# --------------------------------------------------------------------------
+def unique_edges(tris: np.ndarray) -> np.ndarray:
+    e = np.concatenate([tris[:, [0, 1]], tris[:, [1, 2]], tris[:, [2, 0]]], axis=0)
+    e = np.sort(e, axis=1)
+    e = np.unique(e, axis=0)
+    return e.astype(np.int32)
+
+
+def grid_cloth(n: int, side: float, height: float, center=(0.0, 0.0)):
+    """n x n vertices spanning side x side in the xz plane at y = height."""
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    h = side / (n - 1)
+    x = np.stack([center[0] - side / 2 + i * h, np.full(i.shape, height, dtype=np.float64),
+                  center[1] - side / 2 + j * h], axis=-1).reshape(-1, 3)
+    ii, jj = np.meshgrid(np.arange(n - 1), np.arange(n - 1), indexing="ij")
+    v00 = (ii * n + jj).ravel()
+    v10 = ((ii + 1) * n + jj).ravel()
+    v01 = (ii * n + jj + 1).ravel()
+    v11 = ((ii + 1) * n + jj + 1).ravel()
+    tris = np.concatenate([np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)], 0).astype(np.int32)
+    return x.astype(np.float64), tris
+
+
+def icosphere(subdiv: int, radius: float, center=(0.0, 0.0, 0.0)):
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6),
+         (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10),
+         (8, 6, 7), (9, 8, 1)]
+    verts = [np.array(p, dtype=np.float64) / np.linalg.norm(p) for p in v]
+    faces = list(f)
+    for _ in range(subdiv):
+        cache = {}
+
+        def mid(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[k] = len(verts) - 1
+            return cache[k]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    x = np.array(verts) * radius + np.asarray(center, dtype=np.float64)
+    return x, np.array(faces, dtype=np.int32)
+
+
+def tet_cube(n: int, side: float):
+    """n^3 vertex cube split into 6 Kuhn tetrahedra per cell (centred at 0)."""
+    g = np.arange(n)
+    i, j, k = np.meshgrid(g, g, g, indexing="ij")
+    x = np.stack([i, j, k], -1).reshape(-1, 3).astype(np.float64) * (side / (n - 1)) - side / 2
+
+    def vid(a, b, c):
+        return (a * n + b) * n + c
+
+    tets = []
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    for a in range(n - 1):
+        for b in range(n - 1):
+            for c in range(n - 1):
+                base = np.array([a, b, c])
+                for p in perms:
+                    cur = base.copy()
+                    tet = [vid(*cur)]
+                    for ax in p:
+                        cur = cur.copy()
+                        cur[ax] += 1
+                        tet.append(vid(*cur))
+                    tets.append(tet)
+    tets = np.array(tets, dtype=np.int64)
+    faces = np.concatenate([tets[:, [0, 1, 2]], tets[:, [0, 1, 3]], tets[:, [0, 2, 3]], tets[:, [1, 2, 3]]], 0)
+    fs = np.sort(faces, axis=1)
+    uniq, inv, cnt = np.unique(fs, axis=0, return_inverse=True, return_counts=True)
+    surface = uniq[cnt == 1].astype(np.int32)
+    tet_edges = np.concatenate([tets[:, [a, b]] for a in range(4) for b in range(a + 1, 4)], 0)
+    tet_edges = np.unique(np.sort(tet_edges, axis=1), axis=0).astype(np.int32)
+    return x, tets.astype(np.int32), surface, tet_edges
+
+
+def lumped_tri_mass(x, tris, n, density=1.0):
+    a = x[tris[:, 1]] - x[tris[:, 0]]
+    b = x[tris[:, 2]] - x[tris[:, 0]]
+    area = 0.5 * np.linalg.norm(np.cross(a, b), axis=1)
+    m = np.zeros(n)
+    for k in range(3):
+        m += np.bincount(tris[:, k], weights=area / 3.0 * density, minlength=n)
+    return m
+
+
+def lumped_tet_mass(x, tets, n, density=1.0):
+    a = x[tets[:, 1]] - x[tets[:, 0]]
+    b = x[tets[:, 2]] - x[tets[:, 0]]
+    c = x[tets[:, 3]] - x[tets[:, 0]]
+    vol = np.abs(np.einsum("ij,ij->i", a, np.cross(b, c))) / 6.0
+    m = np.zeros(n)
+    for k in range(4):
+        m += np.bincount(tets[:, k], weights=vol / 4.0 * density, minlength=n)
+    return m
+
+
+def random_rotation(rng) -> np.ndarray:
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def _rest(x, len_edges):
+    return np.linalg.norm(x[len_edges[:, 0]] - x[len_edges[:, 1]], axis=1)
+
+
+# --------------------------------------------------------------------------
+# scenes
+# --------------------------------------------------------------------------
+def cloth_over_sphere(n: int = 32, side: float = 1.0, sphere_subdiv: int = 3, sphere_r: float = 0.3,
+                      gap: float = 0.05, seed: int = 0, noise: float = 0.5, v_down: float = 3.0,
+                      dt: float = 1.0 / 30, steps: int = 30) -> Scene:
+    """Cloth held horizontally `gap` above a fixed icosphere, thrown down onto it."""
+    xc, tc = grid_cloth(n, side, sphere_r + gap)
+    xs, ts = icosphere(sphere_subdiv, sphere_r)
+    nc = len(xc)
+    x = np.concatenate([xc, xs], 0)
+    tris = np.concatenate([tc, ts + nc], 0).astype(np.int32)
+    edges = unique_edges(tris)
+    len_edges = unique_edges(tc)
+    m = lumped_tri_mass(xc, tc, nc)
+    inv_mass = np.concatenate([1.0 / m, np.zeros(len(xs))])
+    rng = np.random.default_rng(seed)
+    v = np.zeros_like(x)
+    v[:nc] = np.array([0.0, -v_down, 0.0]) + rng.normal(0.0, noise, size=(nc, 3))
+    return Scene(f"cloth{n}_sphere{sphere_subdiv}", inv_mass, tris, edges, len_edges, np.zeros(0, np.int32), x, v,
+                 dt, np.array([0.0, -9.8, 0.0]), kin_v=np.zeros_like(x), rest_len=_rest(x, len_edges),
+                 steps=steps, params=dict(max_iters=2048))
+
+
+def two_cloths(n: int = 256, side: float = 2.0, sep: float = 0.01, omega: float = 6.0, noise: float = 0.3,
+               seed: int = 0, dt: float = 1.0 / 30, steps: int = 60) -> Scene:
+    """Two stacked n x n cloth grids `sep` apart; the top one spins about the vertical axis."""
+    xb, tb = grid_cloth(n, side, 0.0)
+    xt, tt = grid_cloth(n, side, sep)
+    nb = len(xb)
+    x = np.concatenate([xb, xt], 0)
+    tris = np.concatenate([tb, tt + nb], 0).astype(np.int32)
+    edges = unique_edges(tris)
+    m = lumped_tri_mass(xb, tb, nb)
+    inv_mass = np.concatenate([1.0 / m, 1.0 / m])
+    rng = np.random.default_rng(seed)
+    v = np.zeros_like(x)
+    rel = xt - np.array([0.0, sep, 0.0])
+    v[nb:, 0] = omega * rel[:, 2]
+    v[nb:, 2] = -omega * rel[:, 0]
+    v[nb:] += rng.normal(0.0, noise, size=(nb, 3))
+    return Scene(f"two_cloths{n}", inv_mass, tris, edges, edges.copy(), np.zeros(0, np.int32), x, v, dt,
+                 np.zeros(3), kin_v=np.zeros_like(x), rest_len=_rest(x, edges), steps=steps,
+                 params=dict(max_iters=2048))
+
+
+def tet_bodies(n_bodies: int = 64, n: int = 8, side: float = 0.2, box: float = 1.5, seed: int = 0,
+               v_sigma: float = 2.0, w_sigma: float = 4.0, dt: float = 1.0 / 20, steps: int = 100) -> Scene:
+    """Cube tet meshes at random orientations on a lattice inside a `box` cube."""
+    xb, tets, surf, tedges = tet_cube(n, side)
+    k = int(math.ceil(n_bodies ** (1.0 / 3.0) - 1e-9))
+    spacing = box / k
+    if spacing < side * math.sqrt(3.0):
+        raise ValueError("bodies would overlap")
+    rng = np.random.default_rng(seed)
+    nb = len(xb)
+    xs, vs, tr, ed, le, tt = [], [], [], [], [], []
+    surf_edges = unique_edges(surf)
+    mb = lumped_tet_mass(xb, tets, nb)
+    for b in range(n_bodies):
+        c = np.array([(b % k + 0.5), ((b // k) % k + 0.5), (b // (k * k) + 0.5)]) * spacing
+        R = random_rotation(rng)
+        xw = xb @ R.T + c
+        vl = rng.normal(0.0, v_sigma, size=3)
+        w = rng.normal(0.0, w_sigma, size=3)
+        xs.append(xw)
+        vs.append(vl + np.cross(w, xw - c))
+        tr.append(surf + b * nb)
+        ed.append(surf_edges + b * nb)
+        le.append(tedges + b * nb)
+        tt.append(tets + b * nb)
+    x = np.concatenate(xs, 0)
+    v = np.concatenate(vs, 0)
+    inv_mass = np.tile(1.0 / mb, n_bodies)
+    len_edges = np.concatenate(le, 0).astype(np.int32)
+    return Scene(f"tets{n_bodies}x{n}", inv_mass, np.concatenate(tr, 0).astype(np.int32),
+                 np.concatenate(ed, 0).astype(np.int32), len_edges, np.zeros(0, np.int32), x, v, dt, np.zeros(3),
+                 kin_v=np.zeros_like(x), rest_len=_rest(x, len_edges), steps=steps, params=dict(max_iters=2048))
+
+
+def tube_knot(around: int = 64, rings: int = 561, r: float = 0.01, helix_r: float = 0.012, pitch: float = 0.04,
+              ring_dz: float = 0.0015, pull: float = 1.0, dt: float = 1.0 / 30, steps: int = 200) -> Scene:
+    """Two open tubes wound around each other as a double helix; the end rings
+    are kinematic and pulled apart along the axis so the twist tightens."""
+    xs, ts = [], []
+    kin = []
+    length = (rings - 1) * ring_dz
+    for s in range(2):
+        phase = math.pi * s
+        zc = np.arange(rings) * ring_dz - length / 2
+        ang = 2 * math.pi * (zc + length / 2) / pitch + phase
+        cx, cy = helix_r * np.cos(ang), helix_r * np.sin(ang)
+        th = 2 * math.pi * np.arange(around) / around
+        px = cx[:, None] + r * np.cos(th)[None, :]
+        py = cy[:, None] + r * np.sin(th)[None, :]
+        pz = np.broadcast_to(zc[:, None], px.shape)
+        x = np.stack([px, py, pz], -1).reshape(-1, 3)
+        a = np.arange(rings - 1)[:, None]
+        b = np.arange(around)[None, :]
+        v00 = a * around + b
+        v01 = a * around + (b + 1) % around
+        v10 = (a + 1) * around + b
+        v11 = (a + 1) * around + (b + 1) % around
+        t = np.concatenate([np.stack([v00, v10, v11], -1).reshape(-1, 3), np.stack([v00, v11, v01], -1).reshape(-1, 3)])
+        base = s * rings * around
+        xs.append(x)
+        ts.append(t + base)
+        kin.append(np.arange(around) + base)
+        kin.append(np.arange((rings - 1) * around, rings * around) + base)
+    x = np.concatenate(xs, 0)
+    tris = np.concatenate(ts, 0).astype(np.int32)
+    edges = unique_edges(tris)
+    n = len(x)
+    m = lumped_tri_mass(x, tris, n)
+    inv_mass = 1.0 / m
+    kin_v = np.zeros_like(x)
+    for s in range(2):
+        lo = s * rings * around
+        kin_v[lo:lo + around, 2] = -pull
+        kin_v[lo + (rings - 1) * around: lo + rings * around, 2] = pull
+        inv_mass[lo:lo + around] = 0.0
+        inv_mass[lo + (rings - 1) * around: lo + rings * around] = 0.0
+    v = kin_v.copy()
+    return Scene(f"knot{around}x{rings}", inv_mass, tris, edges, edges.copy(), np.zeros(0, np.int32), x, v, dt,
+                 np.zeros(3), kin_v=kin_v, rest_len=_rest(x, edges), relax_sweeps=10, steps=steps,
+                 params=dict(max_iters=2048, delta=0.5e-3, d_min=1e-3, d_max=2e-3))
+
+
+def hair_sand(n_strands: int = 10000, segs: int = 32, n_points: int = 100000, grain_r: float = 0.002,
+              bowl_r: float = 0.5, bowl_subdiv: int = 5, seg_len: float = 0.01, seed: int = 0,
+              dt: float = 1.0 / 30, steps: int = 200) -> Scene:
+    """Hair strands and sand grains poured from a lattice above a fixed bowl."""
+    rng = np.random.default_rng(seed)
+    xs_b, ts_b = icosphere(bowl_subdiv, bowl_r)
+    keep = xs_b[:, 1] < 1e-9
+    fk = np.all(keep[ts_b], axis=1)
+    ts_b = ts_b[fk]
+    used = np.unique(ts_b)
+    remap = -np.ones(len(xs_b), np.int64)
+    remap[used] = np.arange(len(used))
+    xb = xs_b[used] + np.array([0.0, bowl_r, 0.0])
+    tb = remap[ts_b].astype(np.int32)
+    # strands hang vertically on a square lattice above the bowl
+    sq = int(math.ceil(math.sqrt(n_strands)))
+    span = 0.6 * bowl_r
+    gx = (np.arange(sq) + 0.5) / sq * 2 * span - span
+    sx, sz = np.meshgrid(gx, gx, indexing="ij")
+    roots = np.stack([sx.ravel(), sz.ravel()], -1)[:n_strands]
+    top = bowl_r + 0.05 + segs * seg_len
+    hx = []
+    for k in range(segs + 1):
+        hx.append(np.stack([roots[:, 0], np.full(len(roots), top - k * seg_len), roots[:, 1]], -1))
+    hx = np.stack(hx, 1).reshape(-1, 3)
+    nh = len(hx)
+    sid = np.arange(n_strands)[:, None] * (segs + 1)
+    se = np.stack([sid + np.arange(segs)[None, :], sid + np.arange(1, segs + 1)[None, :]], -1).reshape(-1, 2)
+    # sand grains on a lattice above the strands
+    pc = int(math.ceil(n_points ** (1.0 / 3.0)))
+    pitch = 3.0 * grain_r
+    g = (np.arange(pc) - (pc - 1) / 2) * pitch
+    px, py, pz = np.meshgrid(g, np.arange(pc) * pitch, g, indexing="ij")
+    pts = np.stack([px.ravel(), py.ravel() + top + 0.02, pz.ravel()], -1)[:n_points]
+    nb = len(xb)
+    x = np.concatenate([xb, hx, pts], 0)
+    n = len(x)
+    tris = tb
+    edges = np.concatenate([unique_edges(tb), se + nb], 0).astype(np.int32)
+    points = (np.arange(len(pts)) + nb + nh).astype(np.int32)
+    inv_mass = np.concatenate([np.zeros(nb), np.full(nh, 1.0 / (seg_len * 1.0)), np.full(len(pts), 1.0)])
+    radius = np.concatenate([np.zeros(nb + nh), np.full(len(pts), grain_r)])
+    v = np.zeros_like(x)
+    v[nb:] = np.array([0.0, -2.0, 0.0]) + rng.normal(0.0, 0.2, size=(n - nb, 3))
+    len_edges = (se + nb).astype(np.int32)
+    return Scene(f"hair{n_strands}x{segs}_sand{n_points}", inv_mass, tris, edges, len_edges, points, x, v, dt,
+                 np.array([0.0, -9.8, 0.0]), radius=radius, kin_v=np.zeros_like(x), rest_len=_rest(x, len_edges),
+                 steps=steps, params=dict(max_iters=2048, delta=0.2e-3, d_min=0.4e-3, d_max=0.8e-3))
+
+
+# --------------------------------------------------------------------------
+# stand-in dynamics that produces x~ for each step
+# --------------------------------------------------------------------------
+def predict(scene: Scene, x: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """x~ = x + dt v, kinematic vertices on their script, then Jacobi
+    sweeps toward rest edge lengths (inverse-mass weighted)."""
+    xt = x + scene.dt * v
+    im = scene.inv_mass
+    fixed = im == 0.0
+    if scene.kin_v is not None:
+        xt[fixed] = x[fixed] + scene.dt * scene.kin_v[fixed]
+    le = scene.len_edges
+    if scene.relax_sweeps and len(le) and scene.rest_len is not None:
+        n = len(x)
+        i, j = le[:, 0], le[:, 1]
+        wi, wj = im[i], im[j]
+        ws = wi + wj
+        ok = ws > 0
+        deg = np.bincount(i[ok], minlength=n) + np.bincount(j[ok], minlength=n)
+        deg = np.maximum(deg, 1).astype(np.float64)
+        for _ in range(scene.relax_sweeps):
+            d = xt[i] - xt[j]
+            L = np.linalg.norm(d, axis=1)
+            L = np.where(L > 0, L, 1.0)
+            corr = np.where(ok, (L - scene.rest_len) / L / np.where(ok, ws, 1.0), 0.0)[:, None] * d
+            dx = np.zeros_like(xt)
+            for k in range(3):
+                dx[:, k] -= np.bincount(i, weights=wi * corr[:, k], minlength=n)
+                dx[:, k] += np.bincount(j, weights=wj * corr[:, k], minlength=n)
+            xt += dx / deg[:, None]
+    return xt
+
+
+def next_velocity(scene: Scene, x_new: np.ndarray, x_old: np.ndarray) -> np.ndarray:
+    v = (x_new - x_old) / scene.dt
+    movable = scene.inv_mass > 0
+    v[movable] += scene.dt * scene.gravity
+    if scene.kin_v is not None:
+        v[~movable] = scene.kin_v[~movable]
+    return v
+
+
+def initial(scene: Scene):
+    """(x^0, x~^0) of the first step."""
+    x = scene.x0.copy()
+    v = scene.v0.copy()
+    v[scene.inv_mass > 0] += scene.dt * scene.gravity
+    return x, predict(scene, x, v), v
+
+
+def by_name(name: str, **kw) -> Scene:
+    table = {
+        "cloth_sphere": cloth_over_sphere,
+        "two_cloths": two_cloths,
+        "tets": tet_bodies,
+        "knot": tube_knot,
+        "hair_sand": hair_sand,
+    }
+    return table[name](**kw)

@@ -1,0 +1,54 @@
+"""P2: closed-form times of impact of the oracle's CCD (the comparison scheme
+of Sec. 5.1, used here as the segment safety check)."""
+import numpy as np
+import pytest
+
+import oracle
+
+TRI = np.array([[0.0, 0, 0], [1.0, 0, 0], [0, 1.0, 0]])
+
+
+@pytest.mark.parametrize("h,v", [(0.3, 1.0), (0.05, 0.2), (1e-3, 0.5), (0.5, 0.75)])
+def test_vertex_onto_static_triangle(h, v):
+    x0 = np.concatenate([[[0.2, 0.2, h]], TRI])
+    x1 = x0.copy()
+    x1[0, 2] -= v
+    hit, toi = oracle.ccd(oracle.VT, x0, x1)
+    assert hit and abs(toi - h / v) < 1e-9
+
+
+@pytest.mark.parametrize("h,u,v", [(0.3, 0.2, 0.5), (0.1, 0.4, 0.4)])
+def test_triangle_rising_to_falling_vertex(h, u, v):
+    x0 = np.concatenate([[[0.25, 0.25, h]], TRI])
+    x1 = x0.copy()
+    x1[0, 2] -= v
+    x1[1:, 2] += u
+    hit, toi = oracle.ccd(oracle.VT, x0, x1)
+    assert hit and abs(toi - h / (u + v)) < 1e-9
+
+
+@pytest.mark.parametrize("h,v", [(0.2, 0.5), (0.01, 0.02)])
+def test_edge_onto_crossing_edge(h, v):
+    x0 = np.array([[-1.0, 0, h], [1.0, 0, h], [0, -1.0, 0], [0, 1.0, 0]])
+    x1 = x0.copy()
+    x1[:2, 2] -= v
+    hit, toi = oracle.ccd(oracle.EE, x0, x1)
+    assert hit and abs(toi - h / v) < 1e-9
+
+
+def test_misses():
+    # vertex outside the triangle's shadow
+    x0 = np.concatenate([[[0.8, 0.8, 0.3]], TRI])
+    x1 = x0.copy()
+    x1[0, 2] -= 1.0
+    assert oracle.ccd(oracle.VT, x0, x1) == (False, None)
+    # vertex stops short
+    x0 = np.concatenate([[[0.2, 0.2, 0.3]], TRI])
+    x1 = x0.copy()
+    x1[0, 2] -= 0.25
+    assert oracle.ccd(oracle.VT, x0, x1) == (False, None)
+    # edges pass beside each other
+    x0 = np.array([[-1.0, 2.0, 0.2], [1.0, 2.0, 0.2], [0, -1.0, 0], [0, 1.0, 0]])
+    x1 = x0.copy()
+    x1[:2, 2] -= 0.5
+    assert oracle.ccd(oracle.EE, x0, x1) == (False, None)
