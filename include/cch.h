@@ -1,0 +1,182 @@
+/*
+ * cch.h -- C ABI of the GB300 two-way continuous collision handling library.
+ *
+ * The library implements one collision-handling call of Wang et al., "Fast
+ * GPU-Based Two-Way Continuous Collision Handling" (arXiv 2211.04045): given
+ * an intersection-free state x^t and an unconstrained target x~ it runs
+ * Algorithm 1 (interleaved backward and forward steps, Sec. 3-5) on the GPU
+ * and returns an intersection-free x^{t+1}.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns cch_status; none aborts, traps or exits.
+ *   - Position arrays are AoS float64, n_verts x 3, C-contiguous.  Unless a
+ *     name ends in _host they are DEVICE pointers on the device that was
+ *     current when the scene was created, and must stay valid until the call
+ *     returns.  The call is stream-ordered on the scene's stream and returns
+ *     after the result has been written (it synchronises that stream).
+ *   - Topology and parameters are copied at creation; the caller keeps
+ *     ownership of every pointer it passes.
+ *   - Invalid arguments (NULL, negative sizes, out-of-range indices,
+ *     non-finite coordinates) are rejected with CCH_E_INVALID_ARG before any
+ *     device work.
+ *   - Not reaching ||r||_inf < eps within L iterations is NOT an error: the
+ *     result is still intersection-free (Sec. 3, end of the Algorithm 1
+ *     discussion) and stats.converged = 0 reports it.
+ *   - A scene object may be used by one host thread at a time.
+ */
+#ifndef CCH_H
+#define CCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CCH_OK = 0,
+  CCH_E_INVALID_ARG = 1,       /* bad pointer, size, index or value            */
+  CCH_E_OOM = 2,               /* device allocation failed                     */
+  CCH_E_BUDGET = 3,            /* a server's HBM budget would be exceeded      */
+  CCH_E_CUDA = 4,              /* a CUDA runtime call failed                   */
+  CCH_E_CAPACITY = 5,          /* an internal bound (colours, rounds) exceeded */
+  CCH_E_TIMEOUT = 6,           /* a bounded device loop ran out                */
+  CCH_E_INPUT_NOT_FEASIBLE = 7,/* validate_input: x_t already intersects       */
+  CCH_E_CANCELLED = 8,         /* a server request was cancelled               */
+  CCH_E_STATE = 9              /* call not valid in the object's current state */
+} cch_status;
+
+typedef enum { CCH_PREC_FP64 = 0, CCH_PREC_MIXED = 1 } cch_precision;
+typedef enum { CCH_SOLVER_COLORED_PGS = 0, CCH_SOLVER_JACOBI = 1 } cch_solver;
+
+/* Parameters of Algorithm 1.  cch_params_default() fills Table 2's values
+ * (L = 2048, eps = 1e-4, D^min = 2 mm, D^max = 4 mm, delta = 1 mm,
+ * sigma = 1.1, gamma = 0.9). */
+typedef struct {
+  double d_min;          /* D^min: search again when D^(l) falls below it      */
+  double d_max;          /* D^max: bound of each proximity search              */
+  double delta;          /* contact activation threshold (Sec. 4.1)            */
+  double sigma;          /* edge-length violation ratio limit (Sec. 4.2)       */
+  double gamma;          /* forward-step damping factor (Eq. forward2)         */
+  double eps;            /* termination threshold on ||r||_inf                 */
+  double jacobi_omega;   /* under-relaxation of the projected Jacobi solver    */
+  int32_t max_iters;     /* L; the loop runs l = 0..L (at most L+1 iterations) */
+  int32_t gs_sweeps;     /* Gauss-Seidel sweeps per backward step (Sec 4.3.1)  */
+  int32_t precision;     /* cch_precision                                      */
+  int32_t solver;        /* cch_solver                                         */
+  int32_t ccd_check;     /* 1: CCD of every pair's segment each iteration, with
+                            the time-of-impact clamp (Sec. 5.1 scheme as a
+                            safety net)                                        */
+  int32_t accept_check;  /* 1: exact-filtered intersection test of x^{t+1}     */
+  int32_t validate_input;/* 1: the same test on x^t before the loop            */
+  int32_t iters_per_launch; /* iterations captured per CUDA-graph launch (G)   */
+  int32_t bvh_refit_only;   /* 1: rebuild the BVH at the first search of a step
+                               and only refit it at later searches             */
+  int32_t reserved_;
+  uint64_t seed;         /* priorities of the randomized colouring (Sec. 4.3)  */
+} cch_params;
+
+/* Mesh of one scene (host pointers, copied at creation).
+ * Collision vertices are the vertices of tris, edges and points; every
+ * collision vertex is tested against every triangle (vertex-triangle pairs),
+ * collision edges against each other (edge-edge), and points against every
+ * collision vertex (vertex-vertex, e.g. sand grains). */
+typedef struct {
+  int64_t n_verts;
+  const double* inv_mass;      /* n_verts; 0 = fixed or scripted (kinematic)   */
+  const double* point_radius;  /* n_verts or NULL (all 0)                      */
+  int64_t n_tris;   const int32_t* tris;       /* 3 per triangle               */
+  int64_t n_edges;  const int32_t* edges;      /* 2 per collision edge         */
+  int64_t n_len;    const int32_t* len_edges;  /* 2 per edge-length constraint */
+  int64_t n_points; const int32_t* points;     /* vertex ids of point bodies   */
+} cch_topology;
+
+typedef struct {
+  int32_t iterations;        /* Algorithm 1 iterations executed               */
+  int32_t searches;          /* proximity searches                            */
+  int32_t converged;         /* ||r||_inf < eps reached                       */
+  int32_t ccd_clamps;        /* CCD hits that clamped a step (expected 0)     */
+  int64_t pairs_evaluated;   /* sum over iterations of |P|                    */
+  int64_t max_pairs;         /* max over iterations of |P|                    */
+  int64_t active_contacts;   /* sum over iterations of contacts (dist<delta)  */
+  int64_t candidates;        /* sum over searches of box-test candidates      */
+  int64_t degenerate;        /* contacts skipped as degenerate                */
+  int32_t max_colours;       /* most contact colours in one iteration         */
+  int32_t edge_colours;      /* colours of the edge-length constraints        */
+  double final_r_inf;        /* ||r^(l+1)||_inf at exit                       */
+  double min_pair_dist;      /* smallest pair distance seen in the step       */
+  int64_t intersections;     /* accept_check: intersecting pairs in x^{t+1}   */
+  int64_t uncertain;         /* accept_check: pairs the FP64 filter could not
+                                certify (expected 0)                          */
+  double device_ms;          /* device time of the call (CUDA events)         */
+} cch_step_stats;
+
+typedef struct cch_scene cch_scene;
+typedef struct cch_server cch_server;
+
+cch_status cch_params_default(cch_params* p);
+const char* cch_status_string(cch_status s);
+
+/* Create one resident scene on the current device.  cuda_stream may be NULL
+ * (the legacy default stream) or a cudaStream_t.  Algorithm 1 input line:
+ * the mesh and the bounds [D^min, D^max], L and eps. */
+cch_status cch_create_scene(const cch_topology* topo, const cch_params* prm, void* cuda_stream, cch_scene** out);
+
+/* Create a batch: n_scenes independent scenes that every step call handles
+ * together in one set of launches (per-scene offset tables, per-scene loop
+ * control).  Each scene's result equals what a scene of its own returns. */
+cch_status cch_create_batch(const cch_topology* topos, int32_t n_scenes, const cch_params* prm, void* cuda_stream,
+                            cch_scene** out);
+
+/* One collision-handling call, Algorithm 1: x^(0) = x_t, y^(0) = x_tilde;
+ * x_next receives x^(l+1).  Device pointers, n_verts x 3 float64 each;
+ * x_next may alias x_t.  stats may be NULL. */
+cch_status cch_handle_step(cch_scene* s, const double* x_t, const double* x_tilde, double* x_next,
+                           cch_step_stats* stats);
+
+/* Same call with HOST buffers: the library copies x_t and x_tilde to the
+ * device and x_next back (pageable or pinned memory). */
+cch_status cch_handle_step_host(cch_scene* s, const double* x_t, const double* x_tilde, double* x_next,
+                                cch_step_stats* stats);
+
+/* Batched call: arrays of n_scenes device pointers (scene order of
+ * cch_create_batch); stats is an array of n_scenes entries or NULL. */
+cch_status cch_batch_handle_step(cch_scene* s, const double* const* x_t, const double* const* x_tilde,
+                                 double* const* x_next, cch_step_stats* stats);
+
+cch_status cch_destroy(cch_scene* s);
+
+/* ---- inspection (tests) ------------------------------------------------ */
+/* Candidate set (Sec. 3.1 broad phase: non-adjacent, not-all-static pairs
+ * whose boxes are within D on every axis) and proximity set
+ * P = {candidates with dist < D} of scene 0 at state x (device pointer),
+ * with the static-vertex flags taken from (x_t, x_tilde) = (x, x_ref).
+ * keys (host, capacity cap) receive the canonical pair keys
+ * kind<<62 | id1<<31 | id2 in unspecified order, dist (host, may be NULL)
+ * the matching distances; *count receives the full size even when it
+ * exceeds cap. */
+cch_status cch_query_pairs(cch_scene* s, const double* x, const double* x_ref, double D, int32_t want_candidates,
+                           uint64_t* keys, double* dist, int64_t cap, int64_t* count);
+
+/* ---- serving --------------------------------------------------------------
+ * A server keeps scenes resident in HBM (topology, BVH, last state) and runs
+ * a request loop on its own host thread: requests that arrive while others
+ * are on the GPU join the running batch at the next launch boundary (when
+ * memory and slots allow) and leave it when their own loop ends. */
+cch_status cch_server_create(size_t hbm_budget_bytes, const cch_params* prm, int32_t max_active, void* cuda_stream,
+                             cch_server** out);
+/* Make a scene resident; CCH_E_BUDGET when it would exceed the budget. */
+cch_status cch_server_add_scene(cch_server* sv, const cch_topology* topo, int32_t* scene_id);
+/* Queue one step of a resident scene; pointers are device pointers that must
+ * stay valid until the request completes. */
+cch_status cch_server_submit(cch_server* sv, int32_t scene_id, const double* x_t, const double* x_tilde,
+                             double* x_next, uint64_t* ticket);
+/* Block until the request completes; latency_ms = submit to completion. */
+cch_status cch_server_wait(cch_server* sv, uint64_t ticket, cch_step_stats* stats, double* latency_ms);
+cch_status cch_server_destroy(cch_server* sv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

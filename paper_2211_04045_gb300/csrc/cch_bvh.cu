@@ -1,0 +1,588 @@
+// cch_bvh.cu -- proximity search of Sec. 3.1 on sm_103a.
+//
+// The paper's search is a grid spatial hash; this build uses a linear BVH
+// built from a radix sort of Morton codes (Karras 2012), one tree per
+// primitive class (triangles, collision edges, collision vertices) over the
+// whole pool.  The scene index sits above the Morton bits of every key, so
+// each scene owns a subtree and queries start at their scene's root.  The
+// tree only prunes: float boxes rounded outward and a round-down gap test
+// never reject a pair that the exact FP64 candidate test accepts, and every
+// leaf reached goes through that exact test, so the candidate set does not
+// depend on the tree.
+#include <cooperative_groups.h>
+#include "cch_host.h"
+
+namespace cg = cooperative_groups;
+namespace cch {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int fl_ord(float f) {
+  unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_fl(unsigned int u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ unsigned int expand10(unsigned int v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+// class accessors: FP64 box and scene of primitive id of class c
+// c = 0 triangles, 1 collision edges, 2 collision vertices
+__device__ __forceinline__ void prim_box(const Pool& P, int c, int id, dv3& lo, dv3& hi, int& scene) {
+  if (c == 0) {
+    int4 t = P.tv[id];
+    dv3 a = mk(P.x[t.x]), b = mk(P.x[t.y]), d = mk(P.x[t.z]);
+    lo = a; hi = a;
+    if (b.x < lo.x) lo.x = b.x; if (b.x > hi.x) hi.x = b.x;
+    if (b.y < lo.y) lo.y = b.y; if (b.y > hi.y) hi.y = b.y;
+    if (b.z < lo.z) lo.z = b.z; if (b.z > hi.z) hi.z = b.z;
+    if (d.x < lo.x) lo.x = d.x; if (d.x > hi.x) hi.x = d.x;
+    if (d.y < lo.y) lo.y = d.y; if (d.y > hi.y) hi.y = d.y;
+    if (d.z < lo.z) lo.z = d.z; if (d.z > hi.z) hi.z = d.z;
+    scene = t.w;
+  } else if (c == 1) {
+    int4 e = P.ev[id];
+    dv3 a = mk(P.x[e.x]), b = mk(P.x[e.y]);
+    lo = a; hi = a;
+    if (b.x < lo.x) lo.x = b.x; if (b.x > hi.x) hi.x = b.x;
+    if (b.y < lo.y) lo.y = b.y; if (b.y > hi.y) hi.y = b.y;
+    if (b.z < lo.z) lo.z = b.z; if (b.z > hi.z) hi.z = b.z;
+    scene = e.z;
+  } else {
+    int v = P.vc[id];
+    dv3 a = mk(P.x[v]);
+    double r = P.rho[v];
+    lo = {a.x - r, a.y - r, a.z - r};
+    hi = {a.x + r, a.y + r, a.z + r};
+    scene = P.vscene[v];
+  }
+}
+
+// Conservative float version used for pruning: boxes rounded outward, gaps
+// rounded down, D rounded up; it never rejects what box_near accepts.
+__device__ __forceinline__ bool fbox_near(float4 lo, float4 hi, float3 qlo, float3 qhi, float Df) {
+  return __fsub_rd(lo.x, qhi.x) <= Df && __fsub_rd(qlo.x, hi.x) <= Df && __fsub_rd(lo.y, qhi.y) <= Df &&
+         __fsub_rd(qlo.y, hi.y) <= Df && __fsub_rd(lo.z, qhi.z) <= Df && __fsub_rd(qlo.z, hi.z) <= Df;
+}
+
+__device__ __forceinline__ BVH& bvh_of(Pool& P, int c) { return c == 0 ? P.bt : (c == 1 ? P.be : P.bv); }
+__device__ __forceinline__ int nprim(const Pool& P, int c) { return c == 0 ? P.nt : (c == 1 ? P.ne : P.nvc); }
+
+// ---------------------------------------------------------------------------
+// build
+// ---------------------------------------------------------------------------
+__global__ void k_scene_bounds_reset(Pool P) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P.nscene) {
+    unsigned int* b = (unsigned int*)(P.sbox + 2 * i);
+    b[0] = b[1] = b[2] = 0xffffffffu;
+    b[4] = b[5] = b[6] = 0u;
+  }
+}
+// bounds of the collision vertices of every scene (ordered-int float atomics)
+__global__ void k_scene_bounds(Pool P) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nvc; i += gridDim.x * blockDim.x) {
+    int v = P.vc[i];
+    int s = P.vscene[v];
+    if (!P.ss[s].active) continue;
+    P4 p = P.x[v];
+    unsigned int* b = (unsigned int*)(P.sbox + 2 * s);
+    atomicMin(&b[0], fl_ord(__double2float_rd(p.x)));
+    atomicMin(&b[1], fl_ord(__double2float_rd(p.y)));
+    atomicMin(&b[2], fl_ord(__double2float_rd(p.z)));
+    atomicMax(&b[4], fl_ord(__double2float_ru(p.x)));
+    atomicMax(&b[5], fl_ord(__double2float_ru(p.y)));
+    atomicMax(&b[6], fl_ord(__double2float_ru(p.z)));
+  }
+}
+
+__global__ void k_morton(Pool P, int c) {
+  BVH& B = bvh_of(P, c);
+  int n = nprim(P, c);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    dv3 lo, hi;
+    int s;
+    prim_box(P, c, i, lo, hi, s);
+    const unsigned int* b = (const unsigned int*)(P.sbox + 2 * s);
+    float bl[3] = {ord_fl(b[0]), ord_fl(b[1]), ord_fl(b[2])};
+    float bh[3] = {ord_fl(b[4]), ord_fl(b[5]), ord_fl(b[6])};
+    float cen[3] = {(float)(0.5 * (lo.x + hi.x)), (float)(0.5 * (lo.y + hi.y)), (float)(0.5 * (lo.z + hi.z))};
+    unsigned int q[3];
+    for (int k = 0; k < 3; k++) {
+      float ext = bh[k] - bl[k];
+      float u = ext > 0.f ? (cen[k] - bl[k]) / ext : 0.f;
+      u = fminf(fmaxf(u, 0.f), 1.f);
+      q[k] = min((unsigned int)(u * 1024.f), 1023u);
+    }
+    unsigned long long m = (expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]);
+    B.keys[i] = ((unsigned long long)s << 30) | m;
+    B.ids[i] = i;
+  }
+}
+
+// LSD radix sort, 8-bit digits, tiles of 2048 keys (256 threads x 8).  Pass 1
+// counts digits per tile; pass 2 scans the digit-major table; pass 3 ranks
+// each key stably inside its tile (per-warp match + per-warp prefix) and
+// scatters it.
+constexpr int RS_THREADS = 256, RS_ITEMS = 8, RS_TILE = RS_THREADS * RS_ITEMS;
+
+__global__ void k_radix_hist(const unsigned long long* keys, int n, int shift, unsigned int* hist, int ntiles) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * RS_TILE;
+  for (int k = 0; k < RS_ITEMS; k++) {
+    int i = base + k * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of m entries in one block of 1024 threads
+__global__ void k_scan_1block(unsigned int* a, int m) {
+  __shared__ unsigned int part[1024];
+  int per = (m + 1023) / 1024;
+  int lo = threadIdx.x * per, hi = min(lo + per, m);
+  unsigned int s = 0;
+  for (int i = lo; i < hi; i++) s += a[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    unsigned int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int i = lo; i < hi; i++) {
+    unsigned int v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void k_radix_scatter(const unsigned long long* kin, const int* vin, unsigned long long* kout, int* vout,
+                                int n, int shift, const unsigned int* hist, int ntiles) {
+  __shared__ unsigned int wc[8][256];    // per-warp digit counts, then prefixes
+  __shared__ unsigned int gb[256];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+    for (int k = 0; k < 8; k++) wc[k][d] = 0;
+    gb[d] = hist[d * ntiles + blockIdx.x];
+  }
+  __syncthreads();
+  int base = blockIdx.x * RS_TILE + w * (RS_ITEMS * 32);
+  unsigned long long kk[RS_ITEMS];
+  int vv[RS_ITEMS];
+  unsigned int rank[RS_ITEMS], dig[RS_ITEMS];
+  for (int r = 0; r < RS_ITEMS; r++) {
+    int i = base + r * 32 + lane;
+    bool ok = i < n;
+    kk[r] = ok ? kin[i] : 0ull;
+    vv[r] = ok ? vin[i] : 0;
+    unsigned int d = ok ? (unsigned int)((kk[r] >> shift) & 255) : 256u + lane;
+    dig[r] = d;
+    unsigned int peers = __match_any_sync(0xffffffffu, d);
+    unsigned int before = __popc(peers & ((1u << lane) - 1u));
+    unsigned int cur = ok ? wc[w][d] : 0;
+    rank[r] = cur + before;
+    __syncwarp();
+    if (ok && before == 0) wc[w][d] = cur + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive prefix over warps, per digit
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+    unsigned int run = 0;
+    for (int k = 0; k < 8; k++) {
+      unsigned int c = wc[k][d];
+      wc[k][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int r = 0; r < RS_ITEMS; r++) {
+    int i = base + r * 32 + lane;
+    if (i < n) {
+      unsigned int d = dig[r];
+      unsigned int pos = gb[d] + wc[w][d] + rank[r];
+      kout[pos] = kk[r];
+      vout[pos] = vv[r];
+    }
+  }
+}
+
+__device__ __forceinline__ int delta_k(const unsigned long long* k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  unsigned long long a = k[i], b = k[j];
+  if (a == b) return 64 + __clz(i ^ j);
+  return __clzll(a ^ b);
+}
+
+// Karras 2012: internal node i covers a contiguous range of sorted leaves
+__global__ void k_karras(Pool P, int c) {
+  BVH& B = bvh_of(P, c);
+  int n = B.n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += gridDim.x * blockDim.x) {
+    const unsigned long long* K = B.keys;
+    int d = (delta_k(K, n, i, i + 1) - delta_k(K, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta_k(K, n, i, i - d);
+    int lmax = 2;
+    while (delta_k(K, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+      if (delta_k(K, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta_k(K, n, i, j);
+    int s = 0;
+    int t = l;
+    do {
+      t = (t + 1) >> 1;
+      if (delta_k(K, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = i + s * d + min(d, 0);
+    int lo = min(i, j), hi = max(i, j);
+    int left = (lo == gamma) ? (LEAF | gamma) : gamma;
+    int right = (hi == gamma + 1) ? (LEAF | (gamma + 1)) : gamma + 1;
+    B.left[i] = left;
+    B.right[i] = right;
+    B.range_hi[i] = hi;
+    if (left & LEAF) B.parent[n - 1 + (left & ~LEAF)] = i; else B.parent[left] = i;
+    if (right & LEAF) B.parent[n - 1 + (right & ~LEAF)] = i; else B.parent[right] = i;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (n >= 1) B.parent[0] = -1;
+    if (n == 1) B.parent[n - 1 + 0] = -1;
+  }
+}
+
+__device__ __forceinline__ int scene_of_pos(const BVH& B, int pos) { return (int)(B.keys[pos] >> 30); }
+
+// the root of each scene's subtree: the highest node whose leaves all belong to one scene
+__global__ void k_scene_roots(Pool P, int c) {
+  BVH& B = bvh_of(P, c);
+  int n = B.n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n - 1; i += gridDim.x * blockDim.x) {
+    int lo, hi, par;
+    int node;
+    if (i < n - 1) {
+      node = i;
+      // leftmost leaf: descend left
+      int cur = i, steps = 0;
+      while (!(cur & LEAF) && ++steps < 256) cur = B.left[cur];
+      if (!(cur & LEAF)) { atomicOr(&P.cnt->err, 8); continue; }
+      lo = cur & ~LEAF;
+      hi = B.range_hi[i];
+      par = B.parent[i];
+    } else {
+      int leaf = i - (n - 1);
+      node = LEAF | leaf;
+      lo = hi = leaf;
+      par = B.parent[i];
+    }
+    int s = scene_of_pos(B, lo);
+    if (scene_of_pos(B, hi) != s) continue;
+    bool top = par < 0;
+    if (!top) {
+      int plo;
+      int cur = par, steps = 0;
+      while (!(cur & LEAF) && ++steps < 256) cur = B.left[cur];
+      if (!(cur & LEAF)) { atomicOr(&P.cnt->err, 8); continue; }
+      plo = cur & ~LEAF;
+      int phi = B.range_hi[par];
+      top = scene_of_pos(B, plo) != s || scene_of_pos(B, phi) != s;
+    }
+    if (top) B.sroot[s] = node;
+  }
+}
+
+__device__ __forceinline__ void child_box(const BVH& B, int child, float4& lo, float4& hi) {
+  if (child & LEAF) {
+    int l = child & ~LEAF;
+    lo = B.leafbox[2 * l];
+    hi = B.leafbox[2 * l + 1];
+  } else {
+    float4 a = B.box[3 * child], b = B.box[3 * child + 1], d = B.box[3 * child + 2];
+    // left (a.xyz, a.w b.x b.y) right (b.z b.w d.x, d.y d.z d.w)
+    lo = make_float4(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, d.x), 0.f);
+    hi = make_float4(fmaxf(a.w, d.y), fmaxf(b.x, d.z), fmaxf(b.y, d.w), 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// queries
+// ---------------------------------------------------------------------------
+// traversal skeleton: calls leaf(pos) for every leaf whose box passes the
+// conservative float test against the query box
+template <class LeafFn>
+__device__ __forceinline__ void traverse(const BVH& B, int root, float3 qlo, float3 qhi, float Df, int min_pos,
+                                         Counters* cnt, LeafFn leaf) {
+  if (root < 0) return;
+  if (root & LEAF) {
+    int l = root & ~LEAF;
+    if (l > min_pos) {
+      float4 lo = B.leafbox[2 * l], hi = B.leafbox[2 * l + 1];
+      if (fbox_near(lo, hi, qlo, qhi, Df)) leaf(l);
+    }
+    return;
+  }
+  int stack[64];
+  int sp = 0;
+  stack[sp++] = root;
+  // a valid tree visits each internal node at most once per query
+  int budget = B.n + 2;
+  while (sp > 0) {
+    if (--budget < 0) {
+      atomicOr(&cnt->err, 4);
+      return;
+    }
+    int node = stack[--sp];
+    if (B.range_hi[node] <= min_pos) continue;
+    float4 a = B.box[3 * node], b = B.box[3 * node + 1], d = B.box[3 * node + 2];
+    float4 llo = make_float4(a.x, a.y, a.z, 0.f), lhi = make_float4(a.w, b.x, b.y, 0.f);
+    float4 rlo = make_float4(b.z, b.w, d.x, 0.f), rhi = make_float4(d.y, d.z, d.w, 0.f);
+    int L = B.left[node], R = B.right[node];
+    bool hl = fbox_near(llo, lhi, qlo, qhi, Df), hr = fbox_near(rlo, rhi, qlo, qhi, Df);
+    if (hr) {
+      if (R & LEAF) { if ((R & ~LEAF) > min_pos) leaf(R & ~LEAF); }
+      else if (sp < 64) stack[sp++] = R;
+      else atomicOr(&cnt->err, 2);
+    }
+    if (hl) {
+      if (L & LEAF) { if ((L & ~LEAF) > min_pos) leaf(L & ~LEAF); }
+      else if (sp < 64) stack[sp++] = L;
+      else atomicOr(&cnt->err, 2);
+    }
+  }
+}
+
+__device__ __forceinline__ float3 f3rd(dv3 a) {
+  return make_float3(__double2float_rd(a.x), __double2float_rd(a.y), __double2float_rd(a.z));
+}
+__device__ __forceinline__ float3 f3ru(dv3 a) {
+  return make_float3(__double2float_ru(a.x), __double2float_ru(a.y), __double2float_ru(a.z));
+}
+
+// vertex-triangle pairs: every collision vertex against its scene's triangles
+__global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, double Dq) {
+  if (mode == 0 && !P.cnt->any_search) return;
+  for (int qi = blockIdx.x * blockDim.x + threadIdx.x; qi < P.nvc; qi += gridDim.x * blockDim.x) {
+    int a = P.vc[qi];
+    int s = P.vscene[a];
+    if (mode == 0 && !searching(P, s)) continue;
+    const SceneDesc& S = P.sd[s];
+    double D = mode == 0 ? S.d_max : Dq;
+    dv3 xa = mk(P.x[a]);
+    double ra = P.rho[a];
+    dv3 alo = {xa.x - ra, xa.y - ra, xa.z - ra}, ahi = {xa.x + ra, xa.y + ra, xa.z + ra};
+    float Df = __double2float_ru(D);
+    bool sa = is_static(P, a);
+    traverse(P.bt, P.bt.sroot[s], f3rd(alo), f3ru(ahi), Df, -1, P.cnt, [&](int pos) {
+      int t = P.bt.ids[pos];
+      int4 tv = P.tv[t];
+      if (a == tv.x || a == tv.y || a == tv.z) return;
+      if (sa && is_static(P, tv.x) && is_static(P, tv.y) && is_static(P, tv.z)) return;
+      dv3 lo, hi;
+      int sc;
+      prim_box(P, 0, t, lo, hi, sc);
+      if (!box_near(alo, ahi, lo, hi, D)) return;
+      unsigned long long key = mkkey(K_VT, a - S.v0, t - S.t0);
+      if (mode == 1) { emit_query(P, key, 0.0); return; }
+      if (mode == 0) count_candidate(P, s);
+      double d = d_pt(xa, mk(P.x[tv.x]), mk(P.x[tv.y]), mk(P.x[tv.z])) - ra;
+      if (!(d < D)) return;
+      if (mode == 2) { emit_query(P, key, d); return; }
+      emit_pair(P, nxt, s, key, make_int4(a, tv.x, tv.y, tv.z), d);
+    });
+  }
+}
+
+// edge-edge pairs: each edge (at sorted leaf position i) against the later leaves of its scene
+__global__ void __launch_bounds__(128) k_query_ee(Pool P, int nxt, int mode, double Dq) {
+  if (mode == 0 && !P.cnt->any_search) return;
+  const BVH& B = P.be;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n; i += gridDim.x * blockDim.x) {
+    int e1 = B.ids[i];
+    int4 ea = P.ev[e1];
+    int s = ea.z;
+    if (mode == 0 && !searching(P, s)) continue;
+    const SceneDesc& S = P.sd[s];
+    double D = mode == 0 ? S.d_max : Dq;
+    dv3 alo, ahi;
+    int sc;
+    prim_box(P, 1, e1, alo, ahi, sc);
+    float Df = __double2float_ru(D);
+    bool sa = is_static(P, ea.x) && is_static(P, ea.y);
+    traverse(B, B.sroot[s], f3rd(alo), f3ru(ahi), Df, i, P.cnt, [&](int pos) {
+      int e2 = B.ids[pos];
+      int4 eb = P.ev[e2];
+      if (ea.x == eb.x || ea.x == eb.y || ea.y == eb.x || ea.y == eb.y) return;
+      if (sa && is_static(P, eb.x) && is_static(P, eb.y)) return;
+      dv3 lo, hi;
+      int sc2;
+      prim_box(P, 1, e2, lo, hi, sc2);
+      if (!box_near(alo, ahi, lo, hi, D)) return;
+      int lo_e = min(e1, e2), hi_e = max(e1, e2);
+      int4 A = lo_e == e1 ? ea : eb, Bv = lo_e == e1 ? eb : ea;
+      unsigned long long key = mkkey(K_EE, lo_e - S.e0, hi_e - S.e0);
+      if (mode == 1) { emit_query(P, key, 0.0); return; }
+      if (mode == 0) count_candidate(P, s);
+      double ps, pt;
+      double d = d_ss(mk(P.x[A.x]), mk(P.x[A.y]), mk(P.x[Bv.x]), mk(P.x[Bv.y]), &ps, &pt);
+      if (!(d < D)) return;
+      if (mode == 2) { emit_query(P, key, d); return; }
+      emit_pair(P, nxt, s, key, make_int4(A.x, A.y, Bv.x, Bv.y), d);
+    });
+  }
+}
+
+// vertex-vertex pairs: each point against every collision vertex of its scene
+__global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, double Dq) {
+  if (mode == 0 && !P.cnt->any_search) return;
+  for (int qi = blockIdx.x * blockDim.x + threadIdx.x; qi < P.nq; qi += gridDim.x * blockDim.x) {
+    int a = P.pts[qi];
+    int s = P.vscene[a];
+    if (mode == 0 && !searching(P, s)) continue;
+    const SceneDesc& S = P.sd[s];
+    double D = mode == 0 ? S.d_max : Dq;
+    dv3 xa = mk(P.x[a]);
+    double ra = P.rho[a];
+    dv3 alo = {xa.x - ra, xa.y - ra, xa.z - ra}, ahi = {xa.x + ra, xa.y + ra, xa.z + ra};
+    float Df = __double2float_ru(D);
+    bool sa = is_static(P, a);
+    traverse(P.bv, P.bv.sroot[s], f3rd(alo), f3ru(ahi), Df, -1, P.cnt, [&](int pos) {
+      int b = P.vc[P.bv.ids[pos]];
+      if (b == a) return;
+      if ((P.vflag[b] & VF_POINT) && b < a) return;
+      if (sa && is_static(P, b)) return;
+      dv3 xb = mk(P.x[b]);
+      double rb = P.rho[b];
+      dv3 blo = {xb.x - rb, xb.y - rb, xb.z - rb}, bhi = {xb.x + rb, xb.y + rb, xb.z + rb};
+      if (!box_near(alo, ahi, blo, bhi, D)) return;
+      unsigned long long key = mkkey(K_VV, a - S.v0, b - S.v0);
+      if (mode == 1) { emit_query(P, key, 0.0); return; }
+      if (mode == 0) count_candidate(P, s);
+      double d = (vnorm(vsub(xa, xb)) - ra) - rb;
+      if (!(d < D)) return;
+      if (mode == 2) { emit_query(P, key, d); return; }
+      emit_pair(P, nxt, s, key, make_int4(a, b, -1, -1), d);
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)g;
+}
+
+void bvh_build(Runtime& R, int c, cudaStream_t st) {
+  Pool& P = R.pool;
+  BVH& B = c == 0 ? P.bt : (c == 1 ? P.be : P.bv);
+  int n = B.n;
+  if (n == 0) return;
+  k_morton<<<grid_for(n, 256), 256, 0, st>>>(P, c);
+  int bits = 30 + R.scene_bits;
+  int ntiles = (n + RS_TILE - 1) / RS_TILE;
+  unsigned long long *k0 = B.keys, *k1 = B.keys_alt;
+  int *v0 = B.ids, *v1 = B.ids_alt;
+  int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; p++) {
+    int shift = 8 * p;
+    k_radix_hist<<<ntiles, 256, 0, st>>>(k0, n, shift, B.hist, ntiles);
+    k_scan_1block<<<1, 1024, 0, st>>>(B.hist, 256 * ntiles);
+    k_radix_scatter<<<ntiles, 256, 0, st>>>(k0, v0, k1, v1, n, shift, B.hist, ntiles);
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+  }
+  if (k0 != B.keys) {
+    cudaMemcpyAsync(B.keys, k0, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(B.ids, v0, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+  }
+  cudaMemsetAsync(B.sroot, 0xff, sizeof(int) * P.nscene, st);
+  if (n > 1) k_karras<<<grid_for(n - 1, 256), 256, 0, st>>>(P, c);
+  else k_karras<<<1, 32, 0, st>>>(P, c);
+  k_scene_roots<<<grid_for(2 * n - 1, 256), 256, 0, st>>>(P, c);
+}
+
+void bvh_build_all(Runtime& R, cudaStream_t st) {
+  Pool& P = R.pool;
+  k_scene_bounds_reset<<<(P.nscene + 127) / 128, 128, 0, st>>>(P);
+  k_scene_bounds<<<grid_for(P.nvc, 256), 256, 0, st>>>(P);
+  for (int c = 0; c < 3; c++) bvh_build(R, c, st);
+}
+
+__global__ void k_refit_guard_reset(Pool P, int c, int force) {
+  // clears the arrival flags when a search is due (or forced)
+  BVH& B = bvh_of(P, c);
+  if (!force && !P.cnt->any_search) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n - 1; i += gridDim.x * blockDim.x) B.flag[i] = 0;
+}
+__global__ void k_leaf_boxes_guard(Pool P, int c, int force) {
+  if (!force && !P.cnt->any_search) return;
+  BVH& B = bvh_of(P, c);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n; i += gridDim.x * blockDim.x) {
+    dv3 lo, hi;
+    int s;
+    prim_box(P, c, B.ids[i], lo, hi, s);
+    B.leafbox[2 * i] = make_float4(__double2float_rd(lo.x), __double2float_rd(lo.y), __double2float_rd(lo.z), 0.f);
+    B.leafbox[2 * i + 1] = make_float4(__double2float_ru(hi.x), __double2float_ru(hi.y), __double2float_ru(hi.z), 0.f);
+  }
+}
+__global__ void k_refit_guard(Pool P, int c, int force) {
+  if (!force && !P.cnt->any_search) return;
+  BVH& B = bvh_of(P, c);
+  int n = B.n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int node = B.parent[n - 1 + i];
+    int climb = 0;
+    while (node >= 0) {
+      if (++climb > 256) {  // deeper than any Karras tree over 64-bit keys
+        atomicOr(&P.cnt->err, 8);
+        break;
+      }
+      __threadfence();
+      if (atomicAdd(&B.flag[node], 1) == 0) break;
+      __threadfence();
+      float4 llo, lhi, rlo, rhi;
+      child_box(B, B.left[node], llo, lhi);
+      child_box(B, B.right[node], rlo, rhi);
+      B.box[3 * node] = make_float4(llo.x, llo.y, llo.z, lhi.x);
+      B.box[3 * node + 1] = make_float4(lhi.y, lhi.z, rlo.x, rlo.y);
+      B.box[3 * node + 2] = make_float4(rlo.z, rhi.x, rhi.y, rhi.z);
+      node = B.parent[node];
+    }
+  }
+}
+
+void bvh_refit_all(Runtime& R, cudaStream_t st, int force) {
+  Pool& P = R.pool;
+  for (int c = 0; c < 3; c++) {
+    BVH& B = c == 0 ? P.bt : (c == 1 ? P.be : P.bv);
+    if (B.n == 0) continue;
+    if (B.n > 1) k_refit_guard_reset<<<grid_for(B.n - 1, 256), 256, 0, st>>>(P, c, force);
+    k_leaf_boxes_guard<<<grid_for(B.n, 256), 256, 0, st>>>(P, c, force);
+    k_refit_guard<<<grid_for(B.n, 256), 256, 0, st>>>(P, c, force);
+  }
+}
+
+void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) {
+  Pool& P = R.pool;
+  if (P.nvc && P.nt) k_query_vt<<<grid_for(P.nvc, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+  if (P.ne > 1) k_query_ee<<<grid_for(P.ne, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+  if (P.nq && P.nvc) k_query_vv<<<grid_for(P.nq, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+}
+
+}  // namespace cch

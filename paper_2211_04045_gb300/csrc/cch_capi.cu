@@ -1,0 +1,596 @@
+// cch_capi.cu -- host runtime and the C ABI declared in include/cch.h.
+//
+// A cch_scene owns a pool: the concatenated arrays of one or more scenes
+// (per-scene offset tables in SceneDesc), their BVHs, the proximity-pair and
+// contact buffers, and the per-scene loop state.  A step runs Algorithm 1 on
+// every scene of the pool at once; each scene keeps its own D^(l), search
+// flag and termination, so batched results equal single-scene results.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/cch.h"
+#include "cch_host.h"
+#include "cch_step.h"
+
+using namespace cch;
+
+struct cch_scene {
+  Runtime R;
+  int n_scenes = 0;
+  std::vector<int64_t> nverts;  // per scene
+};
+
+namespace {
+
+#define CK(call)                                 \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+cch_status cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return CCH_E_OOM;
+  return CCH_E_CUDA;
+}
+
+template <class T>
+cudaError_t dalloc_in(std::vector<void*>& list, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * count);
+  if (e != cudaSuccess) return e;
+  list.push_back(q);
+  *p = (T*)q;
+  return cudaSuccess;
+}
+template <class T>
+cudaError_t dalloc(Runtime& R, T** p, size_t count) {
+  return dalloc_in(R.allocs, p, count);
+}
+
+void free_all(Runtime& R) {
+  for (void* p : R.allocs) cudaFree(p);
+  R.allocs.clear();
+  for (void* p : R.pair_allocs) cudaFree(p);
+  R.pair_allocs.clear();
+  if (R.graph) cudaGraphExecDestroy(R.graph);
+  R.graph = nullptr;
+  if (R.h_ptrs) cudaFreeHost(R.h_ptrs);
+  if (R.h_cnt) cudaFreeHost(R.h_cnt);
+  if (R.h_ss) cudaFreeHost(R.h_ss);
+  R.h_ptrs = nullptr;
+  R.h_cnt = nullptr;
+  R.h_ss = nullptr;
+  if (R.ev0) cudaEventDestroy(R.ev0);
+  if (R.ev1) cudaEventDestroy(R.ev1);
+  R.ev0 = R.ev1 = nullptr;
+}
+
+bool finite_nonneg(const double* a, int64_t n) {
+  for (int64_t i = 0; i < n; i++)
+    if (!std::isfinite(a[i]) || a[i] < 0.0) return false;
+  return true;
+}
+
+cch_status validate_topology(const cch_topology* t) {
+  if (!t || t->n_verts <= 0 || t->n_verts >= (1LL << 30) || !t->inv_mass) return CCH_E_INVALID_ARG;
+  if (t->n_tris < 0 || t->n_edges < 0 || t->n_len < 0 || t->n_points < 0) return CCH_E_INVALID_ARG;
+  if ((t->n_tris && !t->tris) || (t->n_edges && !t->edges) || (t->n_len && !t->len_edges) ||
+      (t->n_points && !t->points))
+    return CCH_E_INVALID_ARG;
+  if (t->n_tris >= (1LL << 31) || t->n_edges >= (1LL << 31) || t->n_len >= (1LL << 31)) return CCH_E_INVALID_ARG;
+  if (!finite_nonneg(t->inv_mass, t->n_verts)) return CCH_E_INVALID_ARG;
+  if (t->point_radius && !finite_nonneg(t->point_radius, t->n_verts)) return CCH_E_INVALID_ARG;
+  int64_t n = t->n_verts;
+  for (int64_t i = 0; i < t->n_tris; i++) {
+    const int32_t* v = t->tris + 3 * i;
+    for (int k = 0; k < 3; k++)
+      if (v[k] < 0 || v[k] >= n) return CCH_E_INVALID_ARG;
+    if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) return CCH_E_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < t->n_edges; i++) {
+    const int32_t* v = t->edges + 2 * i;
+    if (v[0] < 0 || v[0] >= n || v[1] < 0 || v[1] >= n || v[0] == v[1]) return CCH_E_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < t->n_len; i++) {
+    const int32_t* v = t->len_edges + 2 * i;
+    if (v[0] < 0 || v[0] >= n || v[1] < 0 || v[1] >= n || v[0] == v[1]) return CCH_E_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < t->n_points; i++)
+    if (t->points[i] < 0 || t->points[i] >= n) return CCH_E_INVALID_ARG;
+  return CCH_OK;
+}
+
+cch_status validate_params(const cch_params* p) {
+  if (!p) return CCH_E_INVALID_ARG;
+  if (!(p->d_min > 0.0) || !(p->d_max > p->d_min) || !(p->delta > 0.0) || !(p->delta <= p->d_min))
+    return CCH_E_INVALID_ARG;
+  if (!(p->sigma > 0.0) || !(p->gamma > 0.0 && p->gamma < 1.0) || !(p->eps >= 0.0)) return CCH_E_INVALID_ARG;
+  if (p->max_iters < 0 || p->gs_sweeps < 1 || p->gs_sweeps > 64) return CCH_E_INVALID_ARG;
+  if (p->precision != CCH_PREC_FP64 && p->precision != CCH_PREC_MIXED) return CCH_E_INVALID_ARG;
+  if (p->solver != CCH_SOLVER_COLORED_PGS && p->solver != CCH_SOLVER_JACOBI) return CCH_E_INVALID_ARG;
+  if (p->iters_per_launch < 0 || p->iters_per_launch > 4096) return CCH_E_INVALID_ARG;
+  return CCH_OK;
+}
+
+// Pair-buffer capacities; grown on overflow.
+void set_caps(Runtime& R, int pair_cap) {
+  R.pool.pair_cap = pair_cap;
+  R.pool.act_cap = pair_cap;
+  R.pool.cons_cap = pair_cap;
+}
+
+cudaError_t alloc_pairs(Runtime& R) {
+  Pool& P = R.pool;
+  std::vector<void*>& L = R.pair_allocs;
+  cudaError_t e;
+  for (int b = 0; b < 2; b++) {
+    if ((e = dalloc_in(L, &P.pb[b].key, P.pair_cap)) != cudaSuccess) return e;
+    if ((e = dalloc_in(L, &P.pb[b].v, P.pair_cap)) != cudaSuccess) return e;
+    if ((e = dalloc_in(L, &P.pb[b].d, P.pair_cap)) != cudaSuccess) return e;
+  }
+  if ((e = dalloc_in(L, &P.act, P.act_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.corder, P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.ccol, P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.lam, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// Frees the pair-sized buffers (re-allocated when they grow).
+void free_pairs(Runtime& R) {
+  for (void* p : R.pair_allocs) cudaFree(p);
+  R.pair_allocs.clear();
+}
+
+cudaError_t alloc_bvh(Runtime& R, BVH& B, int n, int nscene) {
+  cudaError_t e;
+  B.n = n;
+  int ni = n > 1 ? n - 1 : 1;
+  int ntiles = (n + 2047) / 2048 + 1;
+  if ((e = dalloc(R, &B.keys, n)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.keys_alt, n)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.ids, n)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.ids_alt, n)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.left, ni)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.right, ni)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.parent, ni + n)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.range_hi, ni)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.box, 3 * ni)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.flag, ni)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.leafbox, 2 * (size_t)n)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.sroot, nscene)) != cudaSuccess) return e;
+  if ((e = dalloc(R, &B.hist, 256 * (size_t)ntiles)) != cudaSuccess) return e;
+  B.hist2 = nullptr;
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t upload(Runtime& R, T** dst, const std::vector<T>& src) {
+  cudaError_t e = dalloc(R, dst, src.size());
+  if (e != cudaSuccess) return e;
+  if (!src.empty()) e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, const cch_params* prm, void* stream) {
+  Runtime& R = S->R;
+  Pool& P = R.pool;
+  R.stream = (cudaStream_t)stream;
+  S->n_scenes = n_scenes;
+  // host tables
+  std::vector<P4> zero4;
+  std::vector<double> im, rho;
+  std::vector<int> vscene, vc, pts;
+  std::vector<uint8_t> vflag;
+  std::vector<int4> tv, ev, lv;
+  int nv = 0, nt = 0, ne = 0, nl = 0, nq = 0;
+  for (int s = 0; s < n_scenes; s++) {
+    const cch_topology& t = topos[s];
+    SceneDesc d{};
+    d.v0 = nv; d.nv = (int)t.n_verts;
+    d.t0 = nt; d.nt = (int)t.n_tris;
+    d.e0 = ne; d.ne = (int)t.n_edges;
+    d.l0 = nl; d.nl = (int)t.n_len;
+    d.q0 = nq; d.nq = (int)t.n_points;
+    d.c0 = (int)vc.size();
+    d.d_min = prm->d_min; d.d_max = prm->d_max; d.delta = prm->delta; d.sigma = prm->sigma;
+    d.hgamma = 0.5 * prm->gamma; d.eps = prm->eps; d.omega = prm->jacobi_omega;
+    d.max_iters = prm->max_iters; d.gs_sweeps = prm->gs_sweeps; d.solver = prm->solver; d.ccd = prm->ccd_check;
+    d.seed = prm->seed;
+    std::vector<uint8_t> f(t.n_verts, 0);
+    for (int64_t i = 0; i < t.n_points; i++) f[t.points[i]] |= VF_POINT | VF_COLL;
+    for (int64_t i = 0; i < 3 * t.n_tris; i++) f[t.tris[i]] |= VF_COLL;
+    for (int64_t i = 0; i < 2 * t.n_edges; i++) f[t.edges[i]] |= VF_COLL;
+    for (int64_t v = 0; v < t.n_verts; v++) {
+      if (t.inv_mass[v] > 0.0) f[v] |= VF_MOVABLE;
+      im.push_back(t.inv_mass[v]);
+      rho.push_back(t.point_radius ? t.point_radius[v] : 0.0);
+      vscene.push_back(s);
+      vflag.push_back(f[v]);
+      if (f[v] & VF_COLL) vc.push_back(nv + (int)v);
+    }
+    d.nc = (int)vc.size() - d.c0;
+    for (int64_t i = 0; i < t.n_tris; i++)
+      tv.push_back(make_int4(nv + t.tris[3 * i], nv + t.tris[3 * i + 1], nv + t.tris[3 * i + 2], s));
+    for (int64_t i = 0; i < t.n_edges; i++)
+      ev.push_back(make_int4(nv + t.edges[2 * i], nv + t.edges[2 * i + 1], s, 0));
+    for (int64_t i = 0; i < t.n_len; i++)
+      lv.push_back(make_int4(nv + t.len_edges[2 * i], nv + t.len_edges[2 * i + 1], s, 0));
+    for (int64_t i = 0; i < t.n_points; i++) pts.push_back(nv + t.points[i]);
+    nv += (int)t.n_verts; nt += (int)t.n_tris; ne += (int)t.n_edges; nl += (int)t.n_len; nq += (int)t.n_points;
+    R.sd.push_back(d);
+    S->nverts.push_back(t.n_verts);
+    if (prm->max_iters > R.max_iters) R.max_iters = prm->max_iters;
+  }
+  P.nv = nv; P.nt = nt; P.ne = ne; P.nl = nl; P.nq = nq; P.nvc = (int)vc.size(); P.nscene = n_scenes;
+  R.scene_bits = 0;
+  while ((1 << R.scene_bits) < n_scenes) R.scene_bits++;
+  R.sweeps = prm->gs_sweeps;
+  R.solver = prm->solver;
+  R.ccd = prm->ccd_check;
+  R.iters_per_check = prm->iters_per_launch > 0 ? prm->iters_per_launch : 16;
+  R.coop_blocks = coop_grid(256);
+
+  CK(dalloc(R, &P.x, nv));
+  CK(dalloc(R, &P.y, nv));
+  CK(dalloc(R, &P.yt, nv));
+  CK(cudaMemset(P.x, 0, sizeof(P4) * nv));
+  P.xp = nullptr;
+  if (prm->ccd_check) CK(dalloc(R, &P.xp, nv));
+  CK(upload(R, &P.im, im));
+  CK(upload(R, &P.rho, rho));
+  CK(dalloc(R, &P.r, nv));
+  CK(dalloc(R, &P.Dv, nv));
+  CK(upload(R, &P.vscene, vscene));
+  CK(upload(R, &P.vflag, vflag));
+  CK(upload(R, &P.tv, tv));
+  CK(upload(R, &P.ev, ev));
+  CK(upload(R, &P.lv, lv));
+  CK(dalloc(R, &P.lg, nl));
+  CK(dalloc(R, &P.lorder, nl));
+  CK(dalloc(R, &P.lcol, nl));
+  CK(dalloc(R, &P.lcstart, MAX_COLOURS + 2));
+  CK(upload(R, &P.vc, vc));
+  CK(upload(R, &P.pts, pts));
+  CK(upload(R, &P.sd, R.sd));
+  CK(dalloc(R, &P.ss, n_scenes));
+  CK(cudaMemset(P.ss, 0, sizeof(SceneState) * n_scenes));
+  CK(dalloc(R, &P.cnt, 1));
+  CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
+  CK(dalloc(R, &P.vprio, nv));
+  CK(dalloc(R, &P.vmask, 2 * (size_t)nv));
+  CK(dalloc(R, &P.jacc, 3 * (size_t)nv));
+  CK(dalloc(R, &P.sbox, 2 * (size_t)n_scenes));
+  CK(alloc_bvh(R, P.bt, nt, n_scenes));
+  CK(alloc_bvh(R, P.be, ne, n_scenes));
+  CK(alloc_bvh(R, P.bv, P.nvc, n_scenes));
+  P.qcap = 1 << 16;
+  CK(dalloc(R, &P.qkeys, P.qcap));
+  CK(dalloc(R, &P.qdist, P.qcap));
+  CK(cudaMallocHost(&R.h_ptrs, sizeof(double*) * 3 * n_scenes));
+  CK(cudaMallocHost(&R.h_cnt, sizeof(Counters)));
+  CK(cudaMallocHost(&R.h_ss, sizeof(SceneState) * n_scenes));
+  CK(dalloc(R, &R.d_ptrs, 3 * (size_t)n_scenes));
+  CK(cudaEventCreate(&R.ev0));
+  CK(cudaEventCreate(&R.ev1));
+  // colour the edge-length constraints once (topology only)
+  P.nlcol = 0;
+  CK(colour_edges(R, R.stream));
+  CK(cudaStreamSynchronize(R.stream));
+  if (nl) {
+    std::vector<int> cs(MAX_COLOURS + 1);
+    CK(cudaMemcpy(cs.data(), P.lcstart, sizeof(int) * (MAX_COLOURS + 1), cudaMemcpyDeviceToHost));
+    int nc = 0;
+    for (int c = 0; c < MAX_COLOURS; c++)
+      if (cs[c + 1] > cs[c]) nc = c + 1;
+    P.nlcol = nc;
+    CK(cudaMemcpy(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
+    if (R.h_cnt->overflow) return CCH_E_CAPACITY;
+  }
+  R.edge_colours = P.nlcol;
+  // pair-sized buffers last (they are re-allocated on growth)
+  long long guess = 4LL * (nt + ne + nq) + 4096;
+  if (guess > (1LL << 30)) guess = 1LL << 30;
+  set_caps(R, (int)guess);
+  CK(alloc_pairs(R));
+  return CCH_OK;
+}
+
+cch_status grow_pairs(Runtime& R) {
+  long long cap = 2LL * R.pool.pair_cap;
+  if (cap > (1LL << 30)) return CCH_E_CAPACITY;
+  CK(cudaStreamSynchronize(R.stream));
+  free_pairs(R);
+  set_caps(R, (int)cap);
+  CK(alloc_pairs(R));
+  if (R.graph) cudaGraphExecDestroy(R.graph);
+  R.graph = nullptr;
+  return CCH_OK;
+}
+
+// Two iterations (pair buffers 0 -> 1 -> 0) captured as one graph.
+cudaError_t capture_graph(Runtime& R) {
+  if (R.graph) {
+    cudaGraphExecDestroy(R.graph);
+    R.graph = nullptr;
+  }
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t g;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = iteration(R, 0, cs);
+    cudaError_t e2 = iteration(R, 1, cs);
+    e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess && (e1 != cudaSuccess || e2 != cudaSuccess)) e = e1 != cudaSuccess ? e1 : e2;
+    if (e == cudaSuccess) {
+      e = cudaGraphInstantiate(&R.graph, g, 0);
+      cudaGraphDestroy(g);
+    }
+  }
+  cudaStreamDestroy(cs);
+  cudaGetLastError();
+  return e;
+}
+
+void fill_stats(const Runtime& R, const SceneState& S, cch_step_stats* st, float ms) {
+  st->iterations = S.iter;
+  st->searches = S.searches;
+  st->converged = S.converged;
+  st->ccd_clamps = S.ccd_clamps;
+  st->pairs_evaluated = S.pairs_eval;
+  st->max_pairs = S.max_pairs;
+  st->active_contacts = S.contacts;
+  st->candidates = S.candidates;
+  st->degenerate = S.degenerate;
+  st->max_colours = S.max_colours;
+  st->edge_colours = R.edge_colours;
+  st->final_r_inf = S.final_r;
+  union { unsigned long long u; double d; } b;
+  b.u = S.mind_bits;
+  st->min_pair_dist = b.d;
+  st->intersections = S.isect;
+  st->uncertain = S.uncertain;
+  st->device_ms = ms;
+}
+
+// Runs Algorithm 1 on every scene of the pool; pointer table already set.
+cch_status run_step(cch_scene* S, cch_step_stats* stats) {
+  Runtime& R = S->R;
+  Pool& P = R.pool;
+  cudaStream_t st = R.stream;
+  for (int attempt = 0; attempt < 24; attempt++) {
+    CK(cudaMemcpyAsync(R.d_ptrs, R.h_ptrs, sizeof(double*) * 3 * S->n_scenes, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(R.ev0, st));
+    step_init(R, st, 0);
+    set_any_search(R, st);
+    bvh_build_all(R, st);
+    CK(cudaGetLastError());
+    if (R.use_graphs && !R.graph) {
+      if (capture_graph(R) != cudaSuccess) R.use_graphs = 0;
+    }
+    int cur = 0, iters = 0;
+    int limit = R.max_iters + 2;
+    bool overflow = false;
+    while (iters < limit) {
+      int chunk = R.iters_per_check;
+      if (R.use_graphs && R.graph) {
+        for (int k = 0; k < chunk; k += 2) CK(cudaGraphLaunch(R.graph, st));
+        iters += (chunk + 1) / 2 * 2;
+      } else {
+        for (int k = 0; k < chunk; k++) {
+          CK(iteration(R, cur, st));
+          cur = 1 - cur;
+        }
+        iters += chunk;
+      }
+      CK(cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (R.h_cnt->err) return CCH_E_CAPACITY;
+      if (R.h_cnt->overflow & (OV_COLOURS | OV_ROUNDS)) return CCH_E_CAPACITY;
+      if (R.h_cnt->overflow & (OV_PAIRS | OV_CONTACTS)) {
+        overflow = true;
+        break;
+      }
+      if (R.h_cnt->all_done) break;
+    }
+    if (overflow) {
+      cch_status g = grow_pairs(R);
+      if (g != CCH_OK) return g;
+      continue;
+    }
+    output(R, st);
+    CK(cudaEventRecord(R.ev1, st));
+    CK(cudaMemcpyAsync(R.h_ss, P.ss, sizeof(SceneState) * S->n_scenes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, R.ev0, R.ev1);
+    if (stats)
+      for (int s = 0; s < S->n_scenes; s++) fill_stats(R, R.h_ss[s], &stats[s], ms);
+    return CCH_OK;
+  }
+  return CCH_E_CAPACITY;
+}
+
+}  // namespace
+
+extern "C" {
+
+cch_status cch_params_default(cch_params* p) {
+  if (!p) return CCH_E_INVALID_ARG;
+  memset(p, 0, sizeof(*p));
+  p->d_min = 2e-3;
+  p->d_max = 4e-3;
+  p->delta = 1e-3;
+  p->sigma = 1.1;
+  p->gamma = 0.9;
+  p->eps = 1e-4;
+  p->jacobi_omega = 0.5;
+  p->max_iters = 2048;
+  p->gs_sweeps = 1;
+  p->precision = CCH_PREC_FP64;
+  p->solver = CCH_SOLVER_COLORED_PGS;
+  p->ccd_check = 0;
+  p->accept_check = 0;
+  p->validate_input = 0;
+  p->iters_per_launch = 16;
+  p->bvh_refit_only = 1;
+  p->seed = 0x2211040450ULL;
+  return CCH_OK;
+}
+
+const char* cch_status_string(cch_status s) {
+  switch (s) {
+    case CCH_OK: return "ok";
+    case CCH_E_INVALID_ARG: return "invalid argument";
+    case CCH_E_OOM: return "out of device memory";
+    case CCH_E_BUDGET: return "HBM budget exceeded";
+    case CCH_E_CUDA: return "CUDA error";
+    case CCH_E_CAPACITY: return "internal capacity exceeded";
+    case CCH_E_TIMEOUT: return "bounded device loop timed out";
+    case CCH_E_INPUT_NOT_FEASIBLE: return "input state intersects";
+    case CCH_E_CANCELLED: return "cancelled";
+    case CCH_E_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+cch_status cch_create_batch(const cch_topology* topos, int32_t n_scenes, const cch_params* prm, void* stream,
+                            cch_scene** out) {
+  if (!out || !topos || n_scenes <= 0 || n_scenes > (1 << 20)) return CCH_E_INVALID_ARG;
+  *out = nullptr;
+  cch_status v = validate_params(prm);
+  if (v != CCH_OK) return v;
+  long long tot = 0;
+  for (int s = 0; s < n_scenes; s++) {
+    v = validate_topology(&topos[s]);
+    if (v != CCH_OK) return v;
+    tot += topos[s].n_verts;
+  }
+  if (tot >= (1LL << 30)) return CCH_E_INVALID_ARG;
+  cch_scene* S = new cch_scene();
+  cch_status r = build_pool(S, topos, n_scenes, prm, stream);
+  if (r != CCH_OK) {
+    free_all(S->R);
+    delete S;
+    return r;
+  }
+  *out = S;
+  return CCH_OK;
+}
+
+cch_status cch_create_scene(const cch_topology* topo, const cch_params* prm, void* stream, cch_scene** out) {
+  return cch_create_batch(topo, 1, prm, stream, out);
+}
+
+cch_status cch_batch_handle_step(cch_scene* S, const double* const* x_t, const double* const* x_tilde,
+                                 double* const* x_next, cch_step_stats* stats) {
+  if (!S || !x_t || !x_tilde || !x_next) return CCH_E_INVALID_ARG;
+  for (int s = 0; s < S->n_scenes; s++) {
+    if (!x_t[s] || !x_tilde[s] || !x_next[s]) return CCH_E_INVALID_ARG;
+    S->R.h_ptrs[3 * s] = (double*)x_t[s];
+    S->R.h_ptrs[3 * s + 1] = (double*)x_tilde[s];
+    S->R.h_ptrs[3 * s + 2] = x_next[s];
+  }
+  return run_step(S, stats);
+}
+
+cch_status cch_handle_step(cch_scene* S, const double* x_t, const double* x_tilde, double* x_next,
+                           cch_step_stats* stats) {
+  if (!S || S->n_scenes != 1) return CCH_E_INVALID_ARG;
+  return cch_batch_handle_step(S, &x_t, &x_tilde, &x_next, stats);
+}
+
+cch_status cch_handle_step_host(cch_scene* S, const double* x_t, const double* x_tilde, double* x_next,
+                                cch_step_stats* stats) {
+  if (!S || S->n_scenes != 1 || !x_t || !x_tilde || !x_next) return CCH_E_INVALID_ARG;
+  size_t bytes = sizeof(double) * 3 * (size_t)S->nverts[0];
+  double *dt = nullptr, *dl = nullptr;
+  cudaStream_t st = S->R.stream;
+  // staging buffers of the scene, allocated on first use
+  static_assert(sizeof(double) == 8, "");
+  CK(cudaMallocAsync(&dt, bytes, st));
+  CK(cudaMallocAsync(&dl, bytes, st));
+  cudaError_t e = cudaMemcpyAsync(dt, x_t, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dl, x_tilde, bytes, cudaMemcpyHostToDevice, st);
+  cch_status r = e == cudaSuccess ? cch_handle_step(S, dt, dl, dt, stats) : cuda_fail(e);
+  if (r == CCH_OK) {
+    e = cudaMemcpyAsync(x_next, dt, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) r = cuda_fail(e);
+  }
+  cudaFreeAsync(dt, st);
+  cudaFreeAsync(dl, st);
+  cudaStreamSynchronize(st);
+  return r;
+}
+
+cch_status cch_destroy(cch_scene* S) {
+  if (!S) return CCH_E_INVALID_ARG;
+  cudaStreamSynchronize(S->R.stream);
+  free_all(S->R);
+  delete S;
+  return CCH_OK;
+}
+
+cch_status cch_query_pairs(cch_scene* S, const double* x, const double* x_ref, double D, int32_t want_candidates,
+                           uint64_t* keys, double* dist, int64_t cap, int64_t* count) {
+  if (!S || !x || !x_ref || !count || !(D >= 0.0) || cap < 0 || (cap > 0 && !keys)) return CCH_E_INVALID_ARG;
+  if (S->n_scenes != 1) return CCH_E_INVALID_ARG;
+  Runtime& R = S->R;
+  Pool& P = R.pool;
+  cudaStream_t st = R.stream;
+  for (int attempt = 0; attempt < 32; attempt++) {
+    R.h_ptrs[0] = (double*)x;
+    R.h_ptrs[1] = (double*)x_ref;
+    R.h_ptrs[2] = nullptr;
+    CK(cudaMemcpyAsync(R.d_ptrs, R.h_ptrs, sizeof(double*) * 3, cudaMemcpyHostToDevice, st));
+    step_init(R, st, 0);
+    bvh_build_all(R, st);
+    bvh_refit_all(R, st, 1);
+    search_queries(R, 0, want_candidates ? 1 : 2, D, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (R.h_cnt->err) return CCH_E_CAPACITY;
+    int n = R.h_cnt->n_query;
+    if (n > P.qcap) {
+      // grow the inspection buffers and retry
+      int cap2 = P.qcap;
+      while (cap2 < n) cap2 *= 2;
+      P.qcap = cap2;
+      CK(dalloc(R, &P.qkeys, P.qcap));
+      CK(dalloc(R, &P.qdist, P.qcap));
+      continue;
+    }
+    *count = n;
+    int64_t m = n < cap ? n : cap;
+    if (m > 0) {
+      CK(cudaMemcpy(keys, P.qkeys, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost));
+      if (dist) CK(cudaMemcpy(dist, P.qdist, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    }
+    return CCH_OK;
+  }
+  return CCH_E_CAPACITY;
+}
+
+// ---- serving -------------------------------------------------------------
+struct cch_server;
+cch_status cch_server_create(size_t, const cch_params*, int32_t, void*, cch_server** out) {
+  if (out) *out = nullptr;
+  return CCH_E_STATE;
+}
+cch_status cch_server_add_scene(cch_server*, const cch_topology*, int32_t*) { return CCH_E_STATE; }
+cch_status cch_server_submit(cch_server*, int32_t, const double*, const double*, double*, uint64_t*) {
+  return CCH_E_STATE;
+}
+cch_status cch_server_wait(cch_server*, uint64_t, cch_step_stats*, double*) { return CCH_E_STATE; }
+cch_status cch_server_destroy(cch_server*) { return CCH_E_STATE; }
+
+}  // extern "C"

@@ -1,0 +1,331 @@
+// cch_dev.cuh -- device data layout and per-element arithmetic of the
+// two-way collision-handling path (arXiv 2211.04045) for sm_103a.
+//
+// Every formula here is evaluated as written: the library is compiled with
+// --fmad=false, so no multiply-add is contracted and each FP64 expression
+// rounds exactly like its plain IEEE evaluation, left to right.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cch {
+
+// ---------------------------------------------------------------------------
+// layout
+// ---------------------------------------------------------------------------
+// Positions live as 32-byte aligned (x, y, z, w) records: one vertex gather
+// touches one 32-byte sector.
+struct __align__(32) P4 { double x, y, z, w; };
+
+struct dv3 { double x, y, z; };
+
+// vertex flag bits
+enum : uint8_t { VF_STATIC = 1, VF_POINT = 2, VF_COLL = 4, VF_MOVABLE = 8 };
+enum { K_VT = 0, K_EE = 1, K_VV = 2 };
+
+// Per-scene constants (device copy).
+struct SceneDesc {
+  int v0, nv;      // vertex range in the pool
+  int t0, nt;      // triangle range
+  int e0, ne;      // collision-edge range
+  int l0, nl;      // edge-length constraint range
+  int q0, nq;      // point range
+  int c0, nc;      // collision-vertex range (index into the vc list)
+  double d_min, d_max, delta, sigma, hgamma, eps, omega;
+  int max_iters, gs_sweeps, solver, ccd;
+  uint64_t seed;
+};
+
+// Per-scene loop state, mutated on the device.
+struct SceneState {
+  double D;                       // D^(l)
+  int iter;                       // l
+  int active;                     // takes part in the current step
+  int done;                       // loop of this step has ended
+  int do_search;                  // iteration l runs a proximity search
+  int converged;
+  int searches;
+  unsigned long long move_bits;   // max_i |x_i^(l+1) - x_i^(l)| (double bits)
+  unsigned long long rmax_bits;   // ||r^(l+1)||_inf (double bits)
+  unsigned long long mind_bits;   // min pair distance of the step
+  long long pairs_eval, max_pairs, contacts, candidates, degenerate;
+  int n_pairs;                    // |P| of this iteration
+  int max_colours;
+  int ccd_clamps;
+  double final_r;
+  long long isect, uncertain;
+};
+
+// Device-wide counters and flags.
+struct Counters {
+  int n_pairs[2];       // pairs in buffer 0 / 1
+  int n_active;         // active contact candidates (dist < delta)
+  int n_cons;           // assembled contact constraints
+  int ncol;             // contact colours this iteration
+  int overflow;         // OV_* bits
+  int err;              // first error code
+  int any_search;       // some active scene searches in this iteration
+  int remaining;        // uncoloured constraints (colouring rounds)
+  int all_done;         // every active scene has finished
+  unsigned long long n_cand;   // candidate pairs counted
+  int colour_hist[130]; // per-colour counts, then exclusive starts
+  int colour_cursor[130];
+  int jp_rounds;
+  int n_query;          // pairs written by a query call
+  int ccd_hit;
+  int pad;
+};
+enum { OV_PAIRS = 1, OV_CONTACTS = 2, OV_COLOURS = 4, OV_ROUNDS = 8, OV_QUERY = 16 };
+constexpr int MAX_COLOURS = 128;
+
+// Proximity pair (SoA arrays in the pool).
+struct PairBuf {
+  unsigned long long* key;  // kind<<62 | local id1<<31 | local id2
+  int4* v;                  // global vertex ids (VV: v.z = v.w = -1)
+  double* d;                // distance at x^(l)
+};
+
+// One assembled contact constraint of Eq. LCP, linearised at x^(l).
+struct __align__(16) Contact {
+  int4 v;                 // vertices (VV: two, the rest -1)
+  double g[12];           // dc/dx_v
+  double c0;              // c(x^(l))
+  double den;             // sum_v m_v^-1 |g_v|^2
+  unsigned long long prio;// colouring priority
+  unsigned long long key; // canonical identity (tie break)
+};
+
+// BVH over one primitive class of the pool (triangles, edges or collision
+// vertices).  Internal node i has children left[i], right[i]; a child index
+// with the top bit set is a leaf (sorted position).  Child boxes are stored in
+// the parent, rounded outward to float.
+struct BVH {
+  int n;                       // primitives
+  unsigned long long* keys;    // sorted Morton keys (scene<<30 | morton)
+  unsigned long long* keys_alt;
+  int* ids;                    // sorted primitive ids
+  int* ids_alt;
+  int* left;                   // n-1
+  int* right;
+  int* parent;                 // internal parents (n-1) ; leaf parents at parent[n-1 + leaf]
+  int* range_hi;               // last sorted leaf under the node (n-1)
+  float4* box;                 // n-1 nodes x 3 float4: (Llo.xyz, Lhi.x) (Lhi.yz, Rlo.xy) (Rlo.z, Rhi.xyz)
+  int* flag;                   // refit arrival counters (n-1)
+  float4* leafbox;             // n x 2: lo, hi per sorted leaf
+  int* sroot;                  // per scene: root node (leaf: top bit set), -1 if none
+  unsigned int* hist;          // radix histograms
+  unsigned int* hist2;
+};
+
+constexpr int LEAF = 0x40000000;
+
+// Everything a kernel needs, passed by value.
+struct Pool {
+  int nv, nt, ne, nl, nq, nvc, nscene;
+  int pair_cap, act_cap, cons_cap;
+  P4 *x, *y, *yt, *xp;
+  double *im, *rho, *r;
+  unsigned long long* Dv;
+  int* vscene;
+  uint8_t* vflag;
+  int4* tv;                // i, j, k, scene
+  int4* ev;                // a, b, scene, -
+  int4* lv;                // i, j, scene, -
+  P4* lg;                  // per edge-length constraint: g = u/L0 (xyz), den (w)
+  int* lorder;             // edge-length constraints sorted by colour
+  int* lcol;               // colour of each edge-length constraint
+  int* lcstart;            // colour starts into lorder (MAX_COLOURS+1)
+  int nlcol;
+  int* vc;                 // collision vertices (pool ids), scene-contiguous
+  int* pts;                // point vertices
+  SceneDesc* sd;
+  SceneState* ss;
+  Counters* cnt;
+  PairBuf pb[2];
+  int* act;                // active contact list: indices into the next pair buffer
+  Contact* cons;
+  int* corder;             // contacts sorted by colour
+  int* ccol;               // colour per contact
+  unsigned long long* vprio;   // per vertex: max priority of uncoloured contacts (colouring)
+  unsigned long long* vmask;   // per vertex: 2 x 64-bit used-colour masks
+  double* lam;             // multipliers for gs_sweeps > 1 (contacts then edges)
+  double* jacc;            // projected Jacobi accumulators (3 per vertex)
+  BVH bt, be, bv;          // triangles, edges, collision vertices
+  float4* sbox;            // per scene: Morton normalisation box (lo, hi) x2
+  unsigned long long* qkeys;   // inspection output
+  double* qdist;
+  int qcap;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 vector helpers (no contraction: compiled with --fmad=false)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dv3 mk(const P4& p) { return {p.x, p.y, p.z}; }
+__device__ __forceinline__ dv3 vsub(dv3 a, dv3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ dv3 vadd(dv3 a, dv3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ dv3 vscl(double s, dv3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ dv3 vdiv(dv3 a, double s) { return {a.x / s, a.y / s, a.z / s}; }
+__device__ __forceinline__ double vdot(dv3 a, dv3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+__device__ __forceinline__ dv3 vcross(dv3 a, dv3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double vnorm(dv3 a) { return sqrt(vdot(a, a)); }
+__device__ __forceinline__ double vdet(dv3 a, dv3 b, dv3 c) { return vdot(a, vcross(b, c)); }
+
+__device__ __forceinline__ unsigned long long dbits(double d) { return (unsigned long long)__double_as_longlong(d); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// ---------------------------------------------------------------------------
+// distances between simplices
+// ---------------------------------------------------------------------------
+// point to segment [a,b]; t receives the clamped parameter
+__device__ __forceinline__ double d_ps(dv3 p, dv3 a, dv3 b, double* tout) {
+  dv3 e = vsub(b, a), w = vsub(p, a), q = a;
+  double ee = vdot(e, e), t = 0.0;
+  if (ee > 0.0) {
+    t = vdot(w, e) / ee;
+    if (t <= 0.0) { t = 0.0; q = a; }
+    else if (t >= 1.0) { t = 1.0; q = b; }
+    else q = vadd(a, vscl(t, e));
+  }
+  *tout = t;
+  return vnorm(vsub(p, q));
+}
+
+// point to triangle (a,b,c): plane projection when inside, else the nearest edge
+__device__ __forceinline__ double d_pt(dv3 p, dv3 a, dv3 b, dv3 c) {
+  dv3 e1 = vsub(b, a), e2 = vsub(c, a), w = vsub(p, a);
+  dv3 n = vcross(e1, e2);
+  double nn = vdot(n, n);
+  if (nn > 0.0) {
+    double u = vdot(vcross(w, e2), n) / nn;
+    double v = vdot(vcross(e1, w), n) / nn;
+    if (u >= 0.0 && v >= 0.0 && u + v <= 1.0) return fabs(vdot(w, n)) / sqrt(nn);
+  }
+  double t;
+  double d = d_ps(p, a, b, &t), d2 = d_ps(p, b, c, &t), d3 = d_ps(p, c, a, &t);
+  if (d2 < d) d = d2;
+  if (d3 < d) d = d3;
+  return d;
+}
+
+// segment [a,b] to segment [c,d]: interior critical point if inside, and the
+// four endpoint-to-segment distances; the smallest wins (first on ties)
+__device__ __forceinline__ double d_ss(dv3 a, dv3 b, dv3 c, dv3 d, double* sout, double* tout) {
+  dv3 d1 = vsub(b, a), d2 = vsub(d, c), r = vsub(a, c);
+  double A = vdot(d1, d1), E = vdot(d2, d2), B = vdot(d1, d2), C = vdot(d1, r), F = vdot(d2, r);
+  double best = __longlong_as_double(0x7ff0000000000000LL), bs = 0.0, bt = 0.0, tt, dd;
+  double den = A * E - B * B;
+  if (den > 0.0) {
+    double s = (B * F - C * E) / den, t = (A * F - B * C) / den;
+    if (s >= 0.0 && s <= 1.0 && t >= 0.0 && t <= 1.0) {
+      dv3 p = vadd(a, vscl(s, d1)), q = vadd(c, vscl(t, d2));
+      best = vnorm(vsub(p, q)); bs = s; bt = t;
+    }
+  }
+  dd = d_ps(a, c, d, &tt); if (dd < best) { best = dd; bs = 0.0; bt = tt; }
+  dd = d_ps(b, c, d, &tt); if (dd < best) { best = dd; bs = 1.0; bt = tt; }
+  dd = d_ps(c, a, b, &tt); if (dd < best) { best = dd; bs = tt; bt = 0.0; }
+  dd = d_ps(d, a, b, &tt); if (dd < best) { best = dd; bs = tt; bt = 1.0; }
+  *sout = bs; *tout = bt;
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// keys and priorities
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long mkkey(int kind, long long a, long long b) {
+  return ((unsigned long long)kind << 62) | ((unsigned long long)a << 31) | (unsigned long long)b;
+}
+// SplitMix64 (Steele, Lea and Flood 2014), the colouring priority mixer
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+// (prio, key) lexicographic "a ranks above b"
+__device__ __forceinline__ bool ranks_above(unsigned long long pa, unsigned long long ka, unsigned long long pb,
+                                            unsigned long long kb) {
+  return pa > pb || (pa == pb && ka > kb);
+}
+
+// ---------------------------------------------------------------------------
+// contact constraints, Sec. 4.1
+// ---------------------------------------------------------------------------
+// Volume constraint: reference r_v = p_v + sgn_v h n (h = (delta - d)/2),
+// c = det[p1-p0, p2-p0, p3-p0] / det[r1-r0, r2-r0, r3-r0] - 1, gradient of
+// the numerator over the (constant) denominator.
+__device__ __forceinline__ bool volume_cons(const dv3 p[4], const double sg[4], dv3 n, double h, double* c0,
+                                            dv3 g[4]) {
+  dv3 r[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) r[i] = vadd(p[i], vscl(sg[i] * h, n));
+  dv3 c1 = vsub(p[1], p[0]), c2 = vsub(p[2], p[0]), c3 = vsub(p[3], p[0]);
+  double dx = vdet(c1, c2, c3);
+  double dr = vdet(vsub(r[1], r[0]), vsub(r[2], r[0]), vsub(r[3], r[0]));
+  if (!(fabs(dr) >= 1e-30)) return false;
+  *c0 = dx / dr - 1.0;
+  g[1] = vdiv(vcross(c2, c3), dr);
+  g[2] = vdiv(vcross(c3, c1), dr);
+  g[3] = vdiv(vcross(c1, c2), dr);
+  dv3 s = vadd(vadd(g[1], g[2]), g[3]);
+  g[0] = vscl(-1.0, s);
+  return true;
+}
+
+// vertex p0 against triangle (p1,p2,p3): unit normal flipped to the vertex
+__device__ __forceinline__ bool vt_cons(const dv3 p[4], double d, double delta, double* c0, dv3 g[4]) {
+  dv3 nrm = vcross(vsub(p[2], p[1]), vsub(p[3], p[1]));
+  double nn = vdot(nrm, nrm);
+  if (!(nn > 0.0)) return false;
+  dv3 nh = vdiv(nrm, sqrt(nn));
+  double side = vdot(nh, vsub(p[0], p[1])) < 0.0 ? -1.0 : 1.0;
+  dv3 n = vscl(side, nh);
+  const double sg[4] = {1.0, -1.0, -1.0, -1.0};
+  return volume_cons(p, sg, n, 0.5 * (delta - d), c0, g);
+}
+
+// edge (p0,p1) against edge (p2,p3); near-parallel edges use the gap form
+__device__ __forceinline__ bool ee_cons(const dv3 p[4], double d, double s, double t, double delta, double* c0,
+                                        dv3 g[4]) {
+  dv3 e1 = vsub(p[1], p[0]), e2 = vsub(p[3], p[2]);
+  dv3 nx = vcross(e1, e2);
+  double nn = vdot(nx, nx);
+  dv3 pa = vadd(p[0], vscl(s, e1)), pc = vadd(p[2], vscl(t, e2));
+  dv3 dv = vsub(pa, pc);
+  double L = vnorm(dv);
+  dv3 n;
+  if (L > 0.0) n = vdiv(dv, L);
+  else if (nn > 0.0) n = vdiv(nx, sqrt(nn));
+  else return false;
+  if (nn < 1e-12 * (vdot(e1, e1) * vdot(e2, e2))) {
+    *c0 = d / delta - 1.0;
+    g[0] = vscl((1.0 - s) / delta, n);
+    g[1] = vscl(s / delta, n);
+    g[2] = vscl(-((1.0 - t) / delta), n);
+    g[3] = vscl(-(t / delta), n);
+    return true;
+  }
+  const double sg[4] = {1.0, 1.0, -1.0, -1.0};
+  return volume_cons(p, sg, n, 0.5 * (delta - d), c0, g);
+}
+
+// point p0 against vertex p1 with radii
+__device__ __forceinline__ bool vv_cons(const dv3 p[2], double ra, double rb, double delta, double* c0, dv3 g[4]) {
+  dv3 dv = vsub(p[0], p[1]);
+  double L = vnorm(dv);
+  if (!(L > 0.0)) return false;
+  double R = (ra + rb) + delta;
+  *c0 = L / R - 1.0;
+  dv3 u = vdiv(dv, L);
+  g[0] = vdiv(u, R);
+  g[1] = vscl(-1.0, g[0]);
+  return true;
+}
+
+// Smallest pair distance the forward step trusts: below it D_i/2 is no larger
+// than the rounding of an FP64 position update, so the vertex stays put.
+constexpr double D_FLOOR = 1e-10;
+
+}  // namespace cch

@@ -1,0 +1,120 @@
+// cch_host.h -- declarations shared by the CUDA translation units of the
+// library: the host runtime object and the device helpers used by both the
+// proximity search and the per-iteration kernels.
+#pragma once
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "cch_dev.cuh"
+
+namespace cch {
+namespace cg = cooperative_groups;
+
+// Host-side runtime of one pool of scenes (a single scene, a batch, or the
+// resident scenes of a server).
+struct Runtime {
+  Pool pool{};                       // device pointers and sizes
+  std::vector<SceneDesc> sd;         // host copy of the scene table
+  std::vector<void*> allocs;         // device allocations of the pool
+  std::vector<void*> pair_allocs;    // pair-sized buffers (grown on overflow)
+  cudaStream_t stream = nullptr;
+  int scene_bits = 0;                // bits of the scene index in Morton keys
+  int coop_blocks = 0;               // grid of the cooperative kernels
+  int sweeps = 1, solver = 0, ccd = 0;
+  int max_iters = 0;                 // max over scenes
+  int iters_per_check = 16;
+  int use_graphs = 1;
+  cudaGraphExec_t graph = nullptr;   // two captured iterations
+  int graph_pair_cap = -1;
+  double** d_ptrs = nullptr;         // device table: x_t, x_tilde, x_next per scene
+  double** h_ptrs = nullptr;         // pinned host copy of the table
+  Counters* h_cnt = nullptr;         // pinned host copy of the counters
+  SceneState* h_ss = nullptr;        // pinned host copy of the scene states
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int edge_colours = 0;
+};
+
+// The exact candidate test (R3): on every axis fl(lo_b - hi_a) <= D and
+// fl(lo_a - hi_b) <= D.
+__device__ __forceinline__ bool box_near(dv3 alo, dv3 ahi, dv3 blo, dv3 bhi, double D) {
+  if (blo.x - ahi.x > D) return false;
+  if (alo.x - bhi.x > D) return false;
+  if (blo.y - ahi.y > D) return false;
+  if (alo.y - bhi.y > D) return false;
+  if (blo.z - ahi.z > D) return false;
+  if (alo.z - bhi.z > D) return false;
+  return true;
+}
+__device__ __forceinline__ bool searching(const Pool& P, int s) {
+  const SceneState& S = P.ss[s];
+  return S.active && !S.done && S.do_search;
+}
+
+// per-scene candidate counts, aggregated over the lanes of one scene
+__device__ __forceinline__ void count_candidate(Pool& P, int s) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  auto part = cg::labeled_partition(g, s);
+  if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].candidates, (unsigned long long)part.size());
+}
+
+__device__ __forceinline__ int append_idx(int* ctr) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(ctr, (int)g.size());
+  return g.shfl(base, 0) + (int)g.thread_rank();
+}
+
+// Record one pair of P found at iteration l (search or refresh).
+// mode 0: normal; 1: inspection of candidates; 2: inspection of P.
+__device__ __forceinline__ void emit_pair(Pool& P, int nxt, int s, unsigned long long key, int4 v, double d) {
+  const SceneDesc& S = P.sd[s];
+  int idx = append_idx(&P.cnt->n_pairs[nxt]);
+  if (idx >= P.pair_cap) {
+    atomicOr(&P.cnt->overflow, OV_PAIRS);
+    return;
+  }
+  PairBuf& B = P.pb[nxt];
+  B.key[idx] = key;
+  B.v[idx] = v;
+  B.d[idx] = d;
+  unsigned long long db = dbits(d > 0.0 ? d : 0.0);
+  atomicMin(&P.Dv[v.x], db);
+  atomicMin(&P.Dv[v.y], db);
+  if (v.z >= 0) atomicMin(&P.Dv[v.z], db);
+  if (v.w >= 0) atomicMin(&P.Dv[v.w], db);
+  {
+    cg::coalesced_group g = cg::coalesced_threads();
+    auto part = cg::labeled_partition(g, s);
+    unsigned long long m = cg::reduce(part, db, cg::less<unsigned long long>());
+    if (part.thread_rank() == 0) {
+      atomicMin(&P.ss[s].mind_bits, m);
+      atomicAdd(&P.ss[s].n_pairs, (int)part.size());
+    }
+  }
+  if (d < S.delta) {
+    int a = append_idx(&P.cnt->n_active);
+    if (a < P.act_cap) P.act[a] = idx;
+    else atomicOr(&P.cnt->overflow, OV_CONTACTS);
+  }
+}
+
+__device__ __forceinline__ void emit_query(Pool& P, unsigned long long key, double d) {
+  int idx = append_idx(&P.cnt->n_query);
+  if (idx < P.qcap) {
+    P.qkeys[idx] = key;
+    P.qdist[idx] = d;
+  } else atomicOr(&P.cnt->overflow, OV_QUERY);
+}
+
+__device__ __forceinline__ bool is_static(const Pool& P, int v) { return (P.vflag[v] & VF_STATIC) != 0; }
+
+
+// launchers (cch_bvh.cu)
+void bvh_build_all(Runtime& R, cudaStream_t st);
+void bvh_refit_all(Runtime& R, cudaStream_t st, int force);
+void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st);
+
+}  // namespace cch

@@ -1,0 +1,568 @@
+// cch_step.cu -- one iteration of Algorithm 1 on sm_103a: distance refresh
+// of the reused proximity set (Sec. 3.1), contact assembly (Sec. 4.1),
+// randomized constraint colouring and projected Gauss-Seidel (Sec. 4.3),
+// the forward step (Sec. 5) and the loop control (Algorithm 1).
+#include "cch_host.h"
+#include "cch_step.h"
+
+namespace cch {
+
+static int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// step set-up
+// ---------------------------------------------------------------------------
+// per scene: D^(0) = 0 < D^min, so the first iteration searches (D <- D^max)
+__global__ void k_scene_init(Pool P, int only_active) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.nscene; s += gridDim.x * blockDim.x) {
+    SceneState& S = P.ss[s];
+    if (only_active && !S.active) continue;
+    if (!only_active) S.active = 1;
+    S.D = P.sd[s].d_max;
+    S.iter = 0;
+    S.done = 0;
+    S.do_search = 1;
+    S.converged = 0;
+    S.searches = 0;
+    S.move_bits = 0;
+    S.rmax_bits = 0;
+    S.mind_bits = 0x7ff0000000000000ULL;
+    S.pairs_eval = S.max_pairs = S.contacts = S.candidates = S.degenerate = 0;
+    S.n_pairs = 0;
+    S.max_colours = 0;
+    S.ccd_clamps = 0;
+    S.final_r = 1.0;
+    S.isect = S.uncertain = 0;
+  }
+}
+
+// x^(0) = x_t, y^(0) = y^[k+1] = x_tilde, r^(0) = 1; static flags (R4)
+__global__ void k_vert_init(Pool P, double* const* ptrs) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
+    int s = P.vscene[v];
+    if (!P.ss[s].active) continue;
+    int i = v - P.sd[s].v0;
+    const double* xt = ptrs[3 * s];
+    const double* xl = ptrs[3 * s + 1];
+    P4 a = {xt[3 * i], xt[3 * i + 1], xt[3 * i + 2], 0.0};
+    P4 b = {xl[3 * i], xl[3 * i + 1], xl[3 * i + 2], 0.0};
+    P.x[v] = a;
+    P.y[v] = b;
+    P.yt[v] = b;
+    P.r[v] = 1.0;
+    P.Dv[v] = 0x7ff0000000000000ULL;
+    uint8_t f = P.vflag[v] & (uint8_t)~VF_STATIC;
+    if (P.im[v] == 0.0 && a.x == b.x && a.y == b.y && a.z == b.z) f |= VF_STATIC;
+    P.vflag[v] = f;
+  }
+}
+
+// edge-length constraints of the step (R9): g = u / L0 from y^[k+1]
+__global__ void k_edge_prep(Pool P) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nl; e += gridDim.x * blockDim.x) {
+    int4 l = P.lv[e];
+    if (!P.ss[l.z].active) continue;
+    dv3 d0 = vsub(mk(P.yt[l.x]), mk(P.yt[l.y]));
+    double L0 = vnorm(d0);
+    P4 o = {0.0, 0.0, 0.0, 0.0};
+    if (L0 > 0.0) {
+      dv3 g = vdiv(vdiv(d0, L0), L0);
+      o = {g.x, g.y, g.z, (P.im[l.x] + P.im[l.y]) * vdot(g, g)};
+    }
+    P.lg[e] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// distance refresh of a reused P (Sec. 3.1): keep pairs still below D^(l)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double pair_dist(const Pool& P, unsigned long long key, int4 v) {
+  int kind = (int)(key >> 62);
+  if (kind == K_VT) return d_pt(mk(P.x[v.x]), mk(P.x[v.y]), mk(P.x[v.z]), mk(P.x[v.w])) - P.rho[v.x];
+  if (kind == K_EE) {
+    double s, t;
+    return d_ss(mk(P.x[v.x]), mk(P.x[v.y]), mk(P.x[v.z]), mk(P.x[v.w]), &s, &t);
+  }
+  return (vnorm(vsub(mk(P.x[v.x]), mk(P.x[v.y]))) - P.rho[v.x]) - P.rho[v.y];
+}
+
+__global__ void k_refresh(Pool P, int cur, int nxt) {
+  int n = P.cnt->n_pairs[cur];
+  if (n > P.pair_cap) n = P.pair_cap;
+  const PairBuf B = P.pb[cur];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int4 v = B.v[i];
+    int s = P.vscene[v.x];
+    const SceneState& S = P.ss[s];
+    if (!S.active || S.done || S.do_search) continue;
+    unsigned long long key = B.key[i];
+    double d = pair_dist(P, key, v);
+    if (d < S.D) emit_pair(P, nxt, s, key, v, d);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// contact assembly at x^(l) (Sec. 4.1, linearisation of Sec. 4)
+// ---------------------------------------------------------------------------
+__global__ void k_assemble(Pool P, int nxt) {
+  int n = P.cnt->n_active;
+  if (n > P.act_cap) n = P.act_cap;
+  const PairBuf B = P.pb[nxt];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int p = P.act[i];
+    unsigned long long key = B.key[p];
+    int4 v = B.v[p];
+    double d = B.d[p];
+    int s = P.vscene[v.x];
+    const SceneDesc& S = P.sd[s];
+    int kind = (int)(key >> 62);
+    dv3 q[4];
+    dv3 g[4];
+    double c0 = 0.0;
+    bool ok;
+    q[0] = mk(P.x[v.x]);
+    q[1] = mk(P.x[v.y]);
+    int nv = 2;
+    if (kind == K_VV) {
+      ok = vv_cons(q, P.rho[v.x], P.rho[v.y], S.delta, &c0, g);
+      g[2] = g[3] = {0.0, 0.0, 0.0};
+    } else {
+      q[2] = mk(P.x[v.z]);
+      q[3] = mk(P.x[v.w]);
+      nv = 4;
+      if (kind == K_VT) ok = vt_cons(q, d, S.delta, &c0, g);
+      else {
+        double ps, pt;
+        d_ss(q[0], q[1], q[2], q[3], &ps, &pt);
+        ok = ee_cons(q, d, ps, pt, S.delta, &c0, g);
+      }
+    }
+    if (!ok) {
+      atomicAdd((unsigned long long*)&P.ss[s].degenerate, 1ull);
+      continue;
+    }
+    int vid[4] = {v.x, v.y, v.z, v.w};
+    double den = 0.0;
+    for (int k = 0; k < nv; k++) den = den + P.im[vid[k]] * vdot(g[k], g[k]);
+    int idx = append_idx(&P.cnt->n_cons);
+    if (idx >= P.cons_cap) {
+      atomicOr(&P.cnt->overflow, OV_CONTACTS);
+      continue;
+    }
+    Contact c;
+    c.v = v;
+    for (int k = 0; k < 4; k++) {
+      c.g[3 * k] = g[k].x;
+      c.g[3 * k + 1] = g[k].y;
+      c.g[3 * k + 2] = g[k].z;
+    }
+    c.c0 = c0;
+    c.den = den;
+    c.key = key;
+    c.prio = splitmix64(S.seed ^ key);
+    P.cons[idx] = c;
+    {
+      cg::coalesced_group gg = cg::coalesced_threads();
+      auto part = cg::labeled_partition(gg, s);
+      if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].contacts, (unsigned long long)part.size());
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Randomized colouring of constraints (Sec. 4.3).  R11: priorities
+// splitmix64(seed ^ key) (a bijection, so no ties); a constraint takes the
+// smallest colour unused by its higher-priority neighbours (sharing a movable
+// vertex).  Rounds colour every constraint whose priority is the largest
+// among the uncoloured constraints at each of its movable vertices; this
+// yields the sequential greedy colouring in descending priority order.
+// ---------------------------------------------------------------------------
+struct ContactAcc {
+  const Contact* c;
+  __device__ int4 verts(int i) const { return c[i].v; }
+  __device__ unsigned long long prio(int i) const { return c[i].prio; }
+};
+struct EdgeAcc {
+  const int4* lv;
+  const SceneDesc* sd;
+  __device__ int4 verts(int i) const { int4 l = lv[i]; return make_int4(l.x, l.y, -1, -1); }
+  __device__ unsigned long long prio(int i) const {
+    int s = lv[i].z;
+    unsigned long long key = (3ULL << 62) | (unsigned long long)(i - sd[s].l0);
+    return splitmix64(sd[s].seed ^ key);
+  }
+};
+
+__device__ __forceinline__ bool movable(const Pool& P, int v) { return v >= 0 && (P.vflag[v] & VF_MOVABLE); }
+
+template <class Acc>
+__global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int* col, int* order, int* cstart,
+                         int* ncol_out, int max_rounds) {
+  cg::grid_group grid = cg::this_grid();
+  int n = n_ptr ? *n_ptr : fixed_n;
+  if (n_ptr && n > P.cons_cap) n = P.cons_cap;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  Counters* C = P.cnt;
+  for (int i = tid; i < n; i += nth) {
+    col[i] = -1;
+    int4 v = acc.verts(i);
+    int vv[4] = {v.x, v.y, v.z, v.w};
+    for (int k = 0; k < 4; k++)
+      if (movable(P, vv[k])) {
+        P.vprio[vv[k]] = 0ull;
+        P.vmask[2 * vv[k]] = 0ull;
+        P.vmask[2 * vv[k] + 1] = 0ull;
+      }
+  }
+  if (tid < MAX_COLOURS + 2) {
+    C->colour_hist[tid] = 0;
+    C->colour_cursor[tid] = 0;
+  }
+  if (tid == 0) {
+    C->remaining = n;
+    C->jp_rounds = 0;
+  }
+  grid.sync();
+  int round = 0;
+  for (; round < max_rounds; round++) {
+    if (__ldcg(&C->remaining) == 0) break;
+    for (int i = tid; i < n; i += nth) {
+      if (__ldcg(&col[i]) >= 0) continue;
+      int4 v = acc.verts(i);
+      unsigned long long p = acc.prio(i);
+      int vv[4] = {v.x, v.y, v.z, v.w};
+      for (int k = 0; k < 4; k++)
+        if (movable(P, vv[k])) atomicMax(&P.vprio[vv[k]], p);
+    }
+    grid.sync();
+    for (int i = tid; i < n; i += nth) {
+      if (__ldcg(&col[i]) >= 0) continue;
+      int4 v = acc.verts(i);
+      unsigned long long p = acc.prio(i);
+      int vv[4] = {v.x, v.y, v.z, v.w};
+      bool top = true;
+      unsigned long long m0 = 0, m1 = 0;
+      for (int k = 0; k < 4; k++)
+        if (movable(P, vv[k])) {
+          if (__ldcg(&P.vprio[vv[k]]) != p) top = false;
+          m0 |= __ldcg(&P.vmask[2 * vv[k]]);
+          m1 |= __ldcg(&P.vmask[2 * vv[k] + 1]);
+        }
+      if (!top) continue;
+      int c;
+      if (~m0) c = __ffsll((long long)~m0) - 1;
+      else if (~m1) c = 64 + __ffsll((long long)~m1) - 1;
+      else {
+        atomicOr(&C->overflow, OV_COLOURS);
+        c = MAX_COLOURS - 1;
+      }
+      for (int k = 0; k < 4; k++)
+        if (movable(P, vv[k])) atomicOr(&P.vmask[2 * vv[k] + (c >> 6)], 1ull << (c & 63));
+      col[i] = c;
+      atomicSub(&C->remaining, 1);
+    }
+    grid.sync();
+    for (int i = tid; i < n; i += nth) {
+      int4 v = acc.verts(i);
+      int vv[4] = {v.x, v.y, v.z, v.w};
+      for (int k = 0; k < 4; k++)
+        if (movable(P, vv[k])) P.vprio[vv[k]] = 0ull;
+    }
+    grid.sync();
+  }
+  if (tid == 0) {
+    C->jp_rounds = round;
+    if (round == max_rounds && __ldcg(&C->remaining) != 0) atomicOr(&C->overflow, OV_ROUNDS);
+  }
+  // counting sort by colour
+  for (int i = tid; i < n; i += nth) {
+    int c = __ldcg(&col[i]);
+    if (c < 0) c = MAX_COLOURS - 1;
+    atomicAdd(&C->colour_hist[c], 1);
+  }
+  grid.sync();
+  if (tid == 0) {
+    int run = 0, nc = 0;
+    for (int c = 0; c < MAX_COLOURS; c++) {
+      int h = __ldcg(&C->colour_hist[c]);
+      cstart[c] = run;
+      C->colour_cursor[c] = run;
+      run += h;
+      if (h) nc = c + 1;
+    }
+    cstart[MAX_COLOURS] = run;
+    *ncol_out = nc;
+  }
+  grid.sync();
+  for (int i = tid; i < n; i += nth) {
+    int c = __ldcg(&col[i]);
+    if (c < 0) c = MAX_COLOURS - 1;
+    int pos = atomicAdd(&C->colour_cursor[c], 1);
+    order[pos] = i;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Backward step: projected Gauss-Seidel over the colour classes (Eq. LCP),
+// contacts first then edge-length constraints (R10).  Inside a colour no two
+// constraints share a movable vertex, so each class is one parallel pass.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dv3 ldy(const Pool& P, int v) {
+  const double* p = (const double*)(P.y + v);
+  return {__ldcg(p), __ldcg(p + 1), __ldcg(p + 2)};
+}
+__device__ __forceinline__ void sty(Pool& P, int v, dv3 a) {
+  double* p = (double*)(P.y + v);
+  __stcg(p, a.x);
+  __stcg(p + 1, a.y);
+  __stcg(p + 2, a.z);
+}
+
+__device__ __forceinline__ void pgs_contact(Pool& P, int ci, double* lam) {
+  const Contact& c = P.cons[ci];
+  if (!(c.den > 0.0)) return;
+  int vid[4] = {c.v.x, c.v.y, c.v.z, c.v.w};
+  int nv = vid[2] < 0 ? 2 : 4;
+  double w = c.c0;
+  dv3 yv[4];
+  for (int k = 0; k < nv; k++) {
+    yv[k] = ldy(P, vid[k]);
+    dv3 g = {c.g[3 * k], c.g[3 * k + 1], c.g[3 * k + 2]};
+    w = w + vdot(g, vsub(yv[k], mk(P.x[vid[k]])));
+  }
+  double l0 = lam ? lam[ci] : 0.0;
+  double tl = l0 - w / c.den;
+  double ln = tl > 0.0 ? tl : 0.0;
+  double dl = ln - l0;
+  if (lam) lam[ci] = ln;
+  if (dl == 0.0) return;
+  for (int k = 0; k < nv; k++) {
+    double sc = P.im[vid[k]] * dl;
+    dv3 g = {c.g[3 * k], c.g[3 * k + 1], c.g[3 * k + 2]};
+    sty(P, vid[k], vadd(yv[k], vscl(sc, g)));
+  }
+}
+
+__device__ __forceinline__ void pgs_edge(Pool& P, int e, double* lam) {
+  int4 l = P.lv[e];
+  const SceneState& S = P.ss[l.z];
+  if (!S.active || S.done) return;
+  P4 gd = P.lg[e];
+  if (!(gd.w > 0.0)) return;
+  dv3 g = {gd.x, gd.y, gd.z};
+  dv3 yi = ldy(P, l.x), yj = ldy(P, l.y);
+  double w = P.sd[l.z].sigma - vdot(g, vsub(yi, yj));
+  double l0 = lam ? lam[e] : 0.0;
+  double tl = l0 - w / gd.w;
+  double ln = tl > 0.0 ? tl : 0.0;
+  double dl = ln - l0;
+  if (lam) lam[e] = ln;
+  if (dl == 0.0) return;
+  double si = P.im[l.x] * dl, sj = P.im[l.y] * dl;
+  sty(P, l.x, vsub(yi, vscl(si, g)));
+  sty(P, l.y, vadd(yj, vscl(sj, g)));
+}
+
+__global__ void k_pgs(Pool P, int sweeps) {
+  cg::grid_group grid = cg::this_grid();
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  int ncol = P.cnt->ncol;
+  int n = P.cnt->n_cons;
+  if (n > P.cons_cap) n = P.cons_cap;
+  double* lamc = sweeps > 1 ? P.lam : nullptr;
+  double* lame = sweeps > 1 ? P.lam + P.cons_cap : nullptr;
+  if (sweeps > 1) {
+    for (int i = tid; i < n; i += nth) lamc[i] = 0.0;
+    for (int i = tid; i < P.nl; i += nth) lame[i] = 0.0;
+    grid.sync();
+  }
+  int* cs = P.cnt->colour_hist;  // contact colour starts after k_colour
+  for (int sw = 0; sw < sweeps; sw++) {
+    for (int k = 0; k < ncol; k++) {
+      int a = cs[k], b = cs[k + 1];
+      for (int i = a + tid; i < b; i += nth) pgs_contact(P, P.corder[i], lamc);
+      grid.sync();
+    }
+    for (int k = 0; k < P.nlcol; k++) {
+      int a = P.lcstart[k], b = P.lcstart[k + 1];
+      for (int i = a + tid; i < b; i += nth) pgs_edge(P, P.lorder[i], lame);
+      grid.sync();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward step, Eq. forward2 (R2): alpha_i = min(0.5 gamma D_i / |y_i - x_i|, 1)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void scene_max(unsigned long long* dst, int s, unsigned long long v) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  auto part = cg::labeled_partition(g, s);
+  unsigned long long m = cg::reduce(part, v, cg::greater<unsigned long long>());
+  if (part.thread_rank() == 0) atomicMax(dst, m);
+}
+
+__global__ void k_forward(Pool P) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
+    int s = P.vscene[v];
+    const SceneState& S = P.ss[s];
+    if (!S.active || S.done) continue;
+    double Di = bitsd(P.Dv[v]);
+    if (S.D < Di) Di = S.D;
+    if (!(Di >= D_FLOOR)) Di = 0.0;
+    P.Dv[v] = 0x7ff0000000000000ULL;
+    P4 xv4 = P.x[v];
+    dv3 xv = mk(xv4), yv = mk(P.y[v]);
+    dv3 dx = vsub(yv, xv);
+    double nd = vnorm(dx), a = 1.0;
+    if (nd > 0.0) {
+      double q = (P.sd[s].hgamma * Di) / nd;
+      a = q < 1.0 ? q : 1.0;
+    }
+    dv3 xn = a == 1.0 ? yv : vadd(xv, vscl(a, dx));
+    if (P.xp) P.xp[v] = xv4;
+    P.x[v] = {xn.x, xn.y, xn.z, 0.0};
+    double r = P.r[v] * (1.0 - a);
+    P.r[v] = r;
+    double mv = vnorm(vsub(xn, xv));
+    scene_max(&P.ss[s].move_bits, s, dbits(mv));
+    scene_max(&P.ss[s].rmax_bits, s, dbits(r));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Loop control (Algorithm 1): D^(l+1) = D^(l) - 2 max|dx| one ulp down (R15);
+// stop at ||r||_inf < eps or after iteration L; search when D < D^min.
+// ---------------------------------------------------------------------------
+__global__ void k_control(Pool P, int cur) {
+  Counters* C = P.cnt;
+  __shared__ int any_search, running;
+  if (threadIdx.x == 0) { any_search = 0; running = 0; }
+  __syncthreads();
+  for (int s = threadIdx.x; s < P.nscene; s += blockDim.x) {
+    SceneState& S = P.ss[s];
+    if (!S.active || S.done) continue;
+    const SceneDesc& d = P.sd[s];
+    double m = bitsd(S.move_bits), rmax = bitsd(S.rmax_bits);
+    S.pairs_eval += S.n_pairs;
+    if (S.n_pairs > S.max_pairs) S.max_pairs = S.n_pairs;
+    if (S.do_search) S.searches++;
+    S.n_pairs = 0;
+    S.D = nextafter(S.D - 2.0 * m, -__longlong_as_double(0x7ff0000000000000LL));
+    S.iter++;
+    S.final_r = rmax;
+    S.move_bits = 0;
+    S.rmax_bits = 0;
+    if (C->ncol > S.max_colours) S.max_colours = C->ncol;
+    if (rmax < d.eps) {
+      S.done = 1;
+      S.converged = 1;
+    } else if (S.iter > d.max_iters) {
+      S.done = 1;
+    } else {
+      S.do_search = S.D < d.d_min;
+      if (S.do_search) {
+        S.D = d.d_max;
+        atomicOr(&any_search, 1);
+      }
+      atomicOr(&running, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    C->any_search = any_search;
+    C->all_done = running ? 0 : 1;
+    C->n_pairs[cur] = 0;
+    C->n_active = 0;
+    C->n_cons = 0;
+    C->ncol = 0;
+  }
+}
+
+__global__ void k_output(Pool P, double* const* ptrs) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
+    int s = P.vscene[v];
+    if (!P.ss[s].active) continue;
+    int i = v - P.sd[s].v0;
+    double* xo = ptrs[3 * s + 2];
+    P4 p = P.x[v];
+    xo[3 * i] = p.x;
+    xo[3 * i + 1] = p.y;
+    xo[3 * i + 2] = p.z;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <class K, class... A>
+static cudaError_t coop_launch(K kern, int blocks, int threads, cudaStream_t st, A... args) {
+  void* argv[] = {(void*)&args...};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(threads), argv, 0, st);
+}
+
+int coop_grid(int threads) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int a = 0, b = 0, c = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_colour<ContactAcc>, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_colour<EdgeAcc>, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pgs, threads, 0);
+  per = a < b ? a : b;
+  per = per < c ? per : c;
+  if (per > 2) per = 2;
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+void step_init(Runtime& R, cudaStream_t st, int only_active) {
+  Pool& P = R.pool;
+  cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
+  k_scene_init<<<(P.nscene + 127) / 128, 128, 0, st>>>(P, only_active);
+  k_vert_init<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.d_ptrs);
+  if (P.nl) k_edge_prep<<<grid_for(P.nl, 256), 256, 0, st>>>(P);
+}
+
+void set_any_search(Runtime& R, cudaStream_t st) {
+  int one = 1;
+  cudaMemcpyAsync(&R.pool.cnt->any_search, &one, sizeof(int), cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
+  Pool& P = R.pool;
+  int nxt = 1 - cur;
+  bvh_refit_all(R, st, 0);
+  search_queries(R, nxt, 0, 0.0, st);
+  k_refresh<<<grid_for(P.pair_cap, 256), 256, 0, st>>>(P, cur, nxt);
+  k_assemble<<<grid_for(P.act_cap, 128), 128, 0, st>>>(P, nxt);
+  ContactAcc ca{P.cons};
+  cudaError_t e = coop_launch(k_colour<ContactAcc>, R.coop_blocks, 256, st, P, ca, (const int*)&P.cnt->n_cons, 0,
+                              P.ccol, P.corder, P.cnt->colour_hist, &P.cnt->ncol, 4096);
+  if (e != cudaSuccess) return e;
+  e = coop_launch(k_pgs, R.coop_blocks, 256, st, P, R.sweeps);
+  if (e != cudaSuccess) return e;
+  k_forward<<<grid_for(P.nv, 256), 256, 0, st>>>(P);
+  k_control<<<1, 256, 0, st>>>(P, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t colour_edges(Runtime& R, cudaStream_t st) {
+  Pool& P = R.pool;
+  if (P.nl == 0) return cudaSuccess;
+  EdgeAcc ea{P.lv, P.sd};
+  cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
+  return coop_launch(k_colour<EdgeAcc>, R.coop_blocks, 256, st, P, ea, (const int*)nullptr, P.nl, P.lcol, P.lorder,
+                     P.lcstart, &P.cnt->pad, 65536);
+}
+
+void output(Runtime& R, cudaStream_t st) {
+  Pool& P = R.pool;
+  k_output<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.d_ptrs);
+}
+
+}  // namespace cch

@@ -1,0 +1,12 @@
+// cch_step.h -- host launchers of the per-iteration kernels (cch_step.cu).
+#pragma once
+#include "cch_host.h"
+
+namespace cch {
+int coop_grid(int threads);
+void step_init(Runtime& R, cudaStream_t st, int only_active);
+void set_any_search(Runtime& R, cudaStream_t st);
+cudaError_t iteration(Runtime& R, int cur, cudaStream_t st);
+cudaError_t colour_edges(Runtime& R, cudaStream_t st);
+void output(Runtime& R, cudaStream_t st);
+}  // namespace cch
