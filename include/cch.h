@@ -110,6 +110,7 @@ typedef struct {
   int64_t uncertain;         /* accept_check: pairs the FP64 filter could not
                                 certify (expected 0)                          */
   double device_ms;          /* device time of the call (CUDA events)         */
+  int64_t kernel_launches;   /* kernels this call launched (graph nodes count) */
 } cch_step_stats;
 
 typedef struct cch_scene cch_scene;
@@ -158,6 +159,18 @@ cch_status cch_destroy(cch_scene* s);
  * exceeds cap. */
 cch_status cch_query_pairs(cch_scene* s, const double* x, const double* x_ref, double D, int32_t want_candidates,
                            uint64_t* keys, double* dist, int64_t cap, int64_t* count);
+
+/* ---- profiling -----------------------------------------------------------
+ * With profiling on, steps launch kernels directly (no CUDA graphs) and
+ * record CUDA events on the scene's stream around each kernel group:
+ * 0 BVH refit, 1 vertex-triangle query, 2 edge-edge query, 3 vertex-vertex
+ * query, 4 distance refresh, 5 contact assembly, 6 colouring, 7 Gauss-Seidel
+ * sweeps, 8 forward step, 9 loop control, 10 step set-up (inputs, BVH
+ * build), 11 output.  cch_set_profiling resets the accumulators;
+ * cch_get_profile returns, per group, the summed milliseconds and the number
+ * of timed launches (n entries). */
+cch_status cch_set_profiling(cch_scene* s, int32_t on);
+cch_status cch_get_profile(cch_scene* s, double* ms, int64_t* count, int32_t n);
 
 /* ---- serving --------------------------------------------------------------
  * A server keeps scenes resident in HBM (topology, BVH, last state) and runs

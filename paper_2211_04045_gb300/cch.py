@@ -53,7 +53,7 @@ class StepStats(C.Structure):
                 ("active_contacts", C.c_int64), ("candidates", C.c_int64), ("degenerate", C.c_int64),
                 ("max_colours", C.c_int32), ("edge_colours", C.c_int32), ("final_r_inf", C.c_double),
                 ("min_pair_dist", C.c_double), ("intersections", C.c_int64), ("uncertain", C.c_int64),
-                ("device_ms", C.c_double)]
+                ("device_ms", C.c_double), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,10 +91,12 @@ def lib():
             L.cch_server_submit.argtypes = [p, i32, p, p, p, C.POINTER(C.c_uint64)]
             L.cch_server_wait.argtypes = [p, C.c_uint64, C.POINTER(StepStats), C.POINTER(d)]
             L.cch_server_destroy.argtypes = [p]
+            L.cch_set_profiling.argtypes = [p, i32]
+            L.cch_get_profile.argtypes = [p, p, p, i32]
             for f in ("cch_params_default", "cch_create_scene", "cch_create_batch", "cch_handle_step",
                       "cch_handle_step_host", "cch_batch_handle_step", "cch_destroy", "cch_query_pairs",
                       "cch_server_create", "cch_server_add_scene", "cch_server_submit", "cch_server_wait",
-                      "cch_server_destroy"):
+                      "cch_server_destroy", "cch_set_profiling", "cch_get_profile"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -230,6 +232,20 @@ class Scene:
                                      C.c_void_p(dist.ctypes.data), m, C.byref(cnt)), "cch_query_pairs")
         o = np.argsort(keys[:m], kind="stable")
         return keys[:m][o], dist[:m][o]
+
+    PROFILE_GROUPS = ("refit", "query_vt", "query_ee", "query_vv", "refresh", "assemble", "colour", "pgs",
+                      "forward", "control", "setup", "output")
+
+    def set_profiling(self, on: bool):
+        _check(lib().cch_set_profiling(self.h, int(bool(on))), "cch_set_profiling")
+
+    def profile(self):
+        n = len(self.PROFILE_GROUPS)
+        ms = np.zeros(n)
+        cnt = np.zeros(n, np.int64)
+        _check(lib().cch_get_profile(self.h, C.c_void_p(ms.ctypes.data), C.c_void_p(cnt.ctypes.data), n),
+               "cch_get_profile")
+        return {g: (float(ms[i]), int(cnt[i])) for i, g in enumerate(self.PROFILE_GROUPS)}
 
     def close(self):
         if getattr(self, "h", None):

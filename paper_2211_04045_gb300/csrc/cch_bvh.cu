@@ -371,6 +371,14 @@ __device__ __forceinline__ float3 f3ru(dv3 a) {
   return make_float3(__double2float_ru(a.x), __double2float_ru(a.y), __double2float_ru(a.z));
 }
 
+__device__ __forceinline__ void add_candidates(Pool& P, int s, long long n) {
+  if (n == 0) return;
+  cg::coalesced_group g = cg::coalesced_threads();
+  auto part = cg::labeled_partition(g, s);
+  long long t = cg::reduce(part, n, cg::plus<long long>());
+  if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].candidates, (unsigned long long)t);
+}
+
 // vertex-triangle pairs: every collision vertex against its scene's triangles
 __global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, double Dq) {
   if (mode == 0 && !P.cnt->any_search) return;
@@ -384,24 +392,37 @@ __global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, dou
     double ra = P.rho[a];
     dv3 alo = {xa.x - ra, xa.y - ra, xa.z - ra}, ahi = {xa.x + ra, xa.y + ra, xa.z + ra};
     float Df = __double2float_ru(D);
+    float raf = __double2float_rd(ra);
+    fv3 fa = fk(P.xf[a]);
     bool sa = is_static(P, a);
+    long long ncand = 0;
     traverse(P.bt, P.bt.sroot[s], f3rd(alo), f3ru(ahi), Df, -1, P.cnt, [&](int pos) {
       int t = P.bt.ids[pos];
       int4 tv = P.tv[t];
       if (a == tv.x || a == tv.y || a == tv.z) return;
       if (sa && is_static(P, tv.x) && is_static(P, tv.y) && is_static(P, tv.z)) return;
+      unsigned long long key = mkkey(K_VT, a - S.v0, t - S.t0);
+      if (mode == 1) {
+        dv3 lo, hi;
+        int sc;
+        prim_box(P, 0, t, lo, hi, sc);
+        if (box_near(alo, ahi, lo, hi, D)) emit_query(P, key, 0.0);
+        return;
+      }
+      ncand++;
+      fv3 f1 = fk(P.xf[tv.x]), f2 = fk(P.xf[tv.y]), f3 = fk(P.xf[tv.z]);
+      float lower = __fsub_rd(__fsub_rd(f_pt(fa, f1, f2, f3), raf), ftol(fa, f1, f2, f3));
+      if (lower >= Df) return;
+      double d = d_pt(xa, mk(P.x[tv.x]), mk(P.x[tv.y]), mk(P.x[tv.z])) - ra;
+      if (!(d < D)) return;
       dv3 lo, hi;
       int sc;
       prim_box(P, 0, t, lo, hi, sc);
       if (!box_near(alo, ahi, lo, hi, D)) return;
-      unsigned long long key = mkkey(K_VT, a - S.v0, t - S.t0);
-      if (mode == 1) { emit_query(P, key, 0.0); return; }
-      if (mode == 0) count_candidate(P, s);
-      double d = d_pt(xa, mk(P.x[tv.x]), mk(P.x[tv.y]), mk(P.x[tv.z])) - ra;
-      if (!(d < D)) return;
       if (mode == 2) { emit_query(P, key, d); return; }
       emit_pair(P, nxt, s, key, make_int4(a, tv.x, tv.y, tv.z), d);
     });
+    if (mode == 0) add_candidates(P, s, ncand);
   }
 }
 
@@ -421,26 +442,38 @@ __global__ void __launch_bounds__(128) k_query_ee(Pool P, int nxt, int mode, dou
     prim_box(P, 1, e1, alo, ahi, sc);
     float Df = __double2float_ru(D);
     bool sa = is_static(P, ea.x) && is_static(P, ea.y);
+    fv3 fa0 = fk(P.xf[ea.x]), fa1 = fk(P.xf[ea.y]);
+    long long ncand = 0;
     traverse(B, B.sroot[s], f3rd(alo), f3ru(ahi), Df, i, P.cnt, [&](int pos) {
       int e2 = B.ids[pos];
       int4 eb = P.ev[e2];
       if (ea.x == eb.x || ea.x == eb.y || ea.y == eb.x || ea.y == eb.y) return;
       if (sa && is_static(P, eb.x) && is_static(P, eb.y)) return;
+      int lo_e = min(e1, e2), hi_e = max(e1, e2);
+      unsigned long long key = mkkey(K_EE, lo_e - S.e0, hi_e - S.e0);
+      if (mode == 1) {
+        dv3 lo, hi;
+        int sc2;
+        prim_box(P, 1, e2, lo, hi, sc2);
+        if (box_near(alo, ahi, lo, hi, D)) emit_query(P, key, 0.0);
+        return;
+      }
+      ncand++;
+      fv3 fb0 = fk(P.xf[eb.x]), fb1 = fk(P.xf[eb.y]);
+      float lower = __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
+      if (lower >= Df) return;
+      int4 A = lo_e == e1 ? ea : eb, Bv = lo_e == e1 ? eb : ea;
+      double ps, pt;
+      double d = d_ss(mk(P.x[A.x]), mk(P.x[A.y]), mk(P.x[Bv.x]), mk(P.x[Bv.y]), &ps, &pt);
+      if (!(d < D)) return;
       dv3 lo, hi;
       int sc2;
       prim_box(P, 1, e2, lo, hi, sc2);
       if (!box_near(alo, ahi, lo, hi, D)) return;
-      int lo_e = min(e1, e2), hi_e = max(e1, e2);
-      int4 A = lo_e == e1 ? ea : eb, Bv = lo_e == e1 ? eb : ea;
-      unsigned long long key = mkkey(K_EE, lo_e - S.e0, hi_e - S.e0);
-      if (mode == 1) { emit_query(P, key, 0.0); return; }
-      if (mode == 0) count_candidate(P, s);
-      double ps, pt;
-      double d = d_ss(mk(P.x[A.x]), mk(P.x[A.y]), mk(P.x[Bv.x]), mk(P.x[Bv.y]), &ps, &pt);
-      if (!(d < D)) return;
       if (mode == 2) { emit_query(P, key, d); return; }
       emit_pair(P, nxt, s, key, make_int4(A.x, A.y, Bv.x, Bv.y), d);
     });
+    if (mode == 0) add_candidates(P, s, ncand);
   }
 }
 
@@ -458,6 +491,7 @@ __global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, dou
     dv3 alo = {xa.x - ra, xa.y - ra, xa.z - ra}, ahi = {xa.x + ra, xa.y + ra, xa.z + ra};
     float Df = __double2float_ru(D);
     bool sa = is_static(P, a);
+    long long ncand = 0;
     traverse(P.bv, P.bv.sroot[s], f3rd(alo), f3ru(ahi), Df, -1, P.cnt, [&](int pos) {
       int b = P.vc[P.bv.ids[pos]];
       if (b == a) return;
@@ -466,15 +500,19 @@ __global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, dou
       dv3 xb = mk(P.x[b]);
       double rb = P.rho[b];
       dv3 blo = {xb.x - rb, xb.y - rb, xb.z - rb}, bhi = {xb.x + rb, xb.y + rb, xb.z + rb};
-      if (!box_near(alo, ahi, blo, bhi, D)) return;
       unsigned long long key = mkkey(K_VV, a - S.v0, b - S.v0);
-      if (mode == 1) { emit_query(P, key, 0.0); return; }
-      if (mode == 0) count_candidate(P, s);
+      if (mode == 1) {
+        if (box_near(alo, ahi, blo, bhi, D)) emit_query(P, key, 0.0);
+        return;
+      }
+      ncand++;
       double d = (vnorm(vsub(xa, xb)) - ra) - rb;
       if (!(d < D)) return;
+      if (!box_near(alo, ahi, blo, bhi, D)) return;
       if (mode == 2) { emit_query(P, key, d); return; }
       emit_pair(P, nxt, s, key, make_int4(a, b, -1, -1), d);
     });
+    if (mode == 0) add_candidates(P, s, ncand);
   }
 }
 
@@ -494,6 +532,7 @@ void bvh_build(Runtime& R, int c, cudaStream_t st) {
   int n = B.n;
   if (n == 0) return;
   k_morton<<<grid_for(n, 256), 256, 0, st>>>(P, c);
+  R.launches++;
   int bits = 30 + R.scene_bits;
   int ntiles = (n + RS_TILE - 1) / RS_TILE;
   unsigned long long *k0 = B.keys, *k1 = B.keys_alt;
@@ -504,6 +543,7 @@ void bvh_build(Runtime& R, int c, cudaStream_t st) {
     k_radix_hist<<<ntiles, 256, 0, st>>>(k0, n, shift, B.hist, ntiles);
     k_scan_1block<<<1, 1024, 0, st>>>(B.hist, 256 * ntiles);
     k_radix_scatter<<<ntiles, 256, 0, st>>>(k0, v0, k1, v1, n, shift, B.hist, ntiles);
+    R.launches += 3;
     std::swap(k0, k1);
     std::swap(v0, v1);
   }
@@ -515,12 +555,14 @@ void bvh_build(Runtime& R, int c, cudaStream_t st) {
   if (n > 1) k_karras<<<grid_for(n - 1, 256), 256, 0, st>>>(P, c);
   else k_karras<<<1, 32, 0, st>>>(P, c);
   k_scene_roots<<<grid_for(2 * n - 1, 256), 256, 0, st>>>(P, c);
+  R.launches += 2;
 }
 
 void bvh_build_all(Runtime& R, cudaStream_t st) {
   Pool& P = R.pool;
   k_scene_bounds_reset<<<(P.nscene + 127) / 128, 128, 0, st>>>(P);
   k_scene_bounds<<<grid_for(P.nvc, 256), 256, 0, st>>>(P);
+  R.launches += 2;
   for (int c = 0; c < 3; c++) bvh_build(R, c, st);
 }
 
@@ -572,17 +614,34 @@ void bvh_refit_all(Runtime& R, cudaStream_t st, int force) {
   for (int c = 0; c < 3; c++) {
     BVH& B = c == 0 ? P.bt : (c == 1 ? P.be : P.bv);
     if (B.n == 0) continue;
-    if (B.n > 1) k_refit_guard_reset<<<grid_for(B.n - 1, 256), 256, 0, st>>>(P, c, force);
+    if (B.n > 1) {
+      k_refit_guard_reset<<<grid_for(B.n - 1, 256), 256, 0, st>>>(P, c, force);
+      R.launches++;
+    }
     k_leaf_boxes_guard<<<grid_for(B.n, 256), 256, 0, st>>>(P, c, force);
     k_refit_guard<<<grid_for(B.n, 256), 256, 0, st>>>(P, c, force);
+    R.launches += 2;
+  }
+}
+
+void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t st) {
+  Pool& P = R.pool;
+  if (c == 0 && P.nvc && P.nt) {
+    k_query_vt<<<grid_for(P.nvc, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+    R.launches++;
+  }
+  if (c == 1 && P.ne > 1) {
+    k_query_ee<<<grid_for(P.ne, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+    R.launches++;
+  }
+  if (c == 2 && P.nq && P.nvc) {
+    k_query_vv<<<grid_for(P.nq, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+    R.launches++;
   }
 }
 
 void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) {
-  Pool& P = R.pool;
-  if (P.nvc && P.nt) k_query_vt<<<grid_for(P.nvc, 128), 128, 0, st>>>(P, nxt, mode, Dq);
-  if (P.ne > 1) k_query_ee<<<grid_for(P.ne, 128), 128, 0, st>>>(P, nxt, mode, Dq);
-  if (P.nq && P.nvc) k_query_vv<<<grid_for(P.nq, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+  for (int c = 0; c < 3; c++) query_class(R, c, nxt, mode, Dq, st);
 }
 
 }  // namespace cch

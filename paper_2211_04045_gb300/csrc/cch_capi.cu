@@ -7,6 +7,7 @@
 // flag and termination, so batched results equal single-scene results.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -64,6 +65,12 @@ void free_all(Runtime& R) {
   R.h_ptrs = nullptr;
   R.h_cnt = nullptr;
   R.h_ss = nullptr;
+  for (int g = 0; g < PG_N; g++)
+    for (int k = 0; k < 2; k++)
+      if (R.pev[g][k]) {
+        cudaEventDestroy(R.pev[g][k]);
+        R.pev[g][k] = nullptr;
+      }
   if (R.ev0) cudaEventDestroy(R.ev0);
   if (R.ev1) cudaEventDestroy(R.ev1);
   R.ev0 = R.ev1 = nullptr;
@@ -239,6 +246,8 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(dalloc(R, &P.y, nv));
   CK(dalloc(R, &P.yt, nv));
   CK(cudaMemset(P.x, 0, sizeof(P4) * nv));
+  CK(dalloc(R, &P.xf, nv));
+  CK(cudaMemset(P.xf, 0, sizeof(float4) * nv));
   P.xp = nullptr;
   if (prm->ccd_check) CK(dalloc(R, &P.xp, nv));
   CK(upload(R, &P.im, im));
@@ -262,7 +271,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(dalloc(R, &P.cnt, 1));
   CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
   CK(dalloc(R, &P.vprio, nv));
-  CK(dalloc(R, &P.vmask, 2 * (size_t)nv));
+  CK(dalloc(R, &P.vmask, (size_t)MASK_WORDS * nv));
   CK(dalloc(R, &P.jacc, 3 * (size_t)nv));
   CK(dalloc(R, &P.sbox, 2 * (size_t)n_scenes));
   CK(alloc_bvh(R, P.bt, nt, n_scenes));
@@ -322,10 +331,13 @@ cudaError_t capture_graph(Runtime& R) {
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return e;
   cudaGraph_t g;
+  long long before = R.launches;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t e1 = iteration(R, 0, cs);
     cudaError_t e2 = iteration(R, 1, cs);
+    R.graph_launches = R.launches - before;
+    R.launches = before;
     e = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess && (e1 != cudaSuccess || e2 != cudaSuccess)) e = e1 != cudaSuccess ? e1 : e2;
     if (e == cudaSuccess) {
@@ -359,6 +371,21 @@ void fill_stats(const Runtime& R, const SceneState& S, cch_step_stats* st, float
   st->device_ms = ms;
 }
 
+// Accumulates the event times of the kernel groups recorded since the last call.
+void prof_collect(Runtime& R) {
+  if (!R.profiling || !R.prof_used) return;
+  for (int g = 0; g < PG_N; g++)
+    if (R.prof_used & (1u << g)) {
+      cudaEventSynchronize(R.pev[g][1]);
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, R.pev[g][0], R.pev[g][1]) == cudaSuccess) {
+        R.prof_ms[g] += ms;
+        R.prof_n[g]++;
+      }
+    }
+  R.prof_used = 0;
+}
+
 // Runs Algorithm 1 on every scene of the pool; pointer table already set.
 cch_status run_step(cch_scene* S, cch_step_stats* stats) {
   Runtime& R = S->R;
@@ -366,12 +393,16 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
   cudaStream_t st = R.stream;
   for (int attempt = 0; attempt < 24; attempt++) {
     CK(cudaMemcpyAsync(R.d_ptrs, R.h_ptrs, sizeof(double*) * 3 * S->n_scenes, cudaMemcpyHostToDevice, st));
+    long long launches0 = R.launches;
     CK(cudaEventRecord(R.ev0, st));
+    prof_mark(R, PG_SETUP, 0, st);
     step_init(R, st, 0);
     set_any_search(R, st);
     bvh_build_all(R, st);
+    prof_mark(R, PG_SETUP, 1, st);
+    prof_collect(R);
     CK(cudaGetLastError());
-    if (R.use_graphs && !R.graph) {
+    if (R.use_graphs && !R.profiling && !R.graph) {
       if (capture_graph(R) != cudaSuccess) R.use_graphs = 0;
     }
     int cur = 0, iters = 0;
@@ -379,18 +410,26 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
     bool overflow = false;
     while (iters < limit) {
       int chunk = R.iters_per_check;
-      if (R.use_graphs && R.graph) {
-        for (int k = 0; k < chunk; k += 2) CK(cudaGraphLaunch(R.graph, st));
+      if (R.use_graphs && !R.profiling && R.graph) {
+        for (int k = 0; k < chunk; k += 2) {
+          CK(cudaGraphLaunch(R.graph, st));
+          R.launches += R.graph_launches;
+        }
         iters += (chunk + 1) / 2 * 2;
       } else {
         for (int k = 0; k < chunk; k++) {
           CK(iteration(R, cur, st));
+          prof_collect(R);
           cur = 1 - cur;
         }
         iters += chunk;
       }
       CK(cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
+      if ((R.h_cnt->err || (R.h_cnt->overflow & (OV_COLOURS | OV_ROUNDS))) && getenv("CCH_DEBUG"))
+        fprintf(stderr, "cch: iteration %d err=%d overflow=%d ncol=%d rounds=%d n_cons=%d pairs=%d/%d\n", iters,
+                R.h_cnt->err, R.h_cnt->overflow, R.h_cnt->ncol, R.h_cnt->jp_rounds, R.h_cnt->n_cons,
+                R.h_cnt->n_pairs[0], R.h_cnt->n_pairs[1]);
       if (R.h_cnt->err) return CCH_E_CAPACITY;
       if (R.h_cnt->overflow & (OV_COLOURS | OV_ROUNDS)) return CCH_E_CAPACITY;
       if (R.h_cnt->overflow & (OV_PAIRS | OV_CONTACTS)) {
@@ -404,15 +443,21 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
       if (g != CCH_OK) return g;
       continue;
     }
+    prof_mark(R, PG_OUTPUT, 0, st);
     output(R, st);
+    prof_mark(R, PG_OUTPUT, 1, st);
     CK(cudaEventRecord(R.ev1, st));
     CK(cudaMemcpyAsync(R.h_ss, P.ss, sizeof(SceneState) * S->n_scenes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    prof_collect(R);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, R.ev0, R.ev1);
     if (stats)
-      for (int s = 0; s < S->n_scenes; s++) fill_stats(R, R.h_ss[s], &stats[s], ms);
+      for (int s = 0; s < S->n_scenes; s++) {
+        fill_stats(R, R.h_ss[s], &stats[s], ms);
+        stats[s].kernel_launches = R.launches - launches0;
+      }
     return CCH_OK;
   }
   return CCH_E_CAPACITY;
@@ -578,6 +623,30 @@ cch_status cch_query_pairs(cch_scene* S, const double* x, const double* x_ref, d
     return CCH_OK;
   }
   return CCH_E_CAPACITY;
+}
+
+cch_status cch_set_profiling(cch_scene* S, int32_t on) {
+  if (!S) return CCH_E_INVALID_ARG;
+  Runtime& R = S->R;
+  if (on && !R.pev[0][0])
+    for (int g = 0; g < PG_N; g++)
+      for (int k = 0; k < 2; k++) CK(cudaEventCreate(&R.pev[g][k]));
+  R.profiling = on ? 1 : 0;
+  for (int g = 0; g < PG_N; g++) {
+    R.prof_ms[g] = 0.0;
+    R.prof_n[g] = 0;
+  }
+  R.prof_used = 0;
+  return CCH_OK;
+}
+
+cch_status cch_get_profile(cch_scene* S, double* ms, int64_t* count, int32_t n) {
+  if (!S || !ms || !count || n < 0) return CCH_E_INVALID_ARG;
+  for (int g = 0; g < n && g < PG_N; g++) {
+    ms[g] = S->R.prof_ms[g];
+    count[g] = S->R.prof_n[g];
+  }
+  return CCH_OK;
 }
 
 // ---- serving -------------------------------------------------------------

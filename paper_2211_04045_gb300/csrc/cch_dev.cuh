@@ -68,15 +68,19 @@ struct Counters {
   int remaining;        // uncoloured constraints (colouring rounds)
   int all_done;         // every active scene has finished
   unsigned long long n_cand;   // candidate pairs counted
-  int colour_hist[130]; // per-colour counts, then exclusive starts
-  int colour_cursor[130];
+  int colour_hist[520]; // per-colour counts, then exclusive starts
+  int colour_cursor[520];
   int jp_rounds;
   int n_query;          // pairs written by a query call
   int ccd_hit;
   int pad;
 };
 enum { OV_PAIRS = 1, OV_CONTACTS = 2, OV_COLOURS = 4, OV_ROUNDS = 8, OV_QUERY = 16 };
-constexpr int MAX_COLOURS = 128;
+constexpr int MASK_WORDS = 8;
+constexpr int MAX_COLOURS = 64 * MASK_WORDS;  // 512
+// constraint counts up to this are coloured and swept by one thread block
+// (block barriers instead of grid barriers)
+constexpr int SMALL_WORK = 16384;
 
 // Proximity pair (SoA arrays in the pool).
 struct PairBuf {
@@ -124,6 +128,7 @@ struct Pool {
   int nv, nt, ne, nl, nq, nvc, nscene;
   int pair_cap, act_cap, cons_cap;
   P4 *x, *y, *yt, *xp;
+  float4* xf;              // x rounded to float (the FP32 distance pre-filter)
   double *im, *rho, *r;
   unsigned long long* Dv;
   int* vscene;
@@ -147,7 +152,7 @@ struct Pool {
   int* corder;             // contacts sorted by colour
   int* ccol;               // colour per contact
   unsigned long long* vprio;   // per vertex: max priority of uncoloured contacts (colouring)
-  unsigned long long* vmask;   // per vertex: 2 x 64-bit used-colour masks
+  unsigned long long* vmask;   // per vertex: MASK_WORDS x 64-bit used-colour masks
   double* lam;             // multipliers for gs_sweeps > 1 (contacts then edges)
   double* jacc;            // projected Jacobi accumulators (3 per vertex)
   BVH bt, be, bv;          // triangles, edges, collision vertices
@@ -322,6 +327,60 @@ __device__ __forceinline__ bool vv_cons(const dv3 p[2], double ra, double rb, do
   g[0] = vdiv(u, R);
   g[1] = vscl(-1.0, g[0]);
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 distance pre-filter.  The distances below are evaluated on float
+// copies of the positions; their error is below FILTER_TOL * (|x|max + extent)
+// (coordinate rounding 2^-24 |x| plus a few dozen float operations on vectors
+// of the primitives' extent).  A pair is sent to the exact FP64 distance
+// unless d32 - tol >= D, so the set of pairs closer than D is unchanged.
+// ---------------------------------------------------------------------------
+constexpr float FILTER_TOL = 4e-6f;
+struct fv3 { float x, y, z; };
+__device__ __forceinline__ fv3 fk(float4 p) { return {p.x, p.y, p.z}; }
+__device__ __forceinline__ fv3 fsub(fv3 a, fv3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ float fdot(fv3 a, fv3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ fv3 fcross(fv3 a, fv3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float fmaxabs(fv3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
+__device__ __forceinline__ float f_ps(fv3 p, fv3 a, fv3 b) {
+  fv3 e = fsub(b, a), w = fsub(p, a);
+  float ee = fdot(e, e), t = 0.f;
+  if (ee > 0.f) t = fminf(fmaxf(fdot(w, e) / ee, 0.f), 1.f);
+  fv3 q = {w.x - t * e.x, w.y - t * e.y, w.z - t * e.z};
+  return sqrtf(fdot(q, q));
+}
+__device__ __forceinline__ float f_pt(fv3 p, fv3 a, fv3 b, fv3 c) {
+  fv3 e1 = fsub(b, a), e2 = fsub(c, a), w = fsub(p, a);
+  fv3 n = fcross(e1, e2);
+  float nn = fdot(n, n);
+  if (nn > 0.f) {
+    float u = fdot(fcross(w, e2), n) / nn, v = fdot(fcross(e1, w), n) / nn;
+    if (u >= 0.f && v >= 0.f && u + v <= 1.f) return fabsf(fdot(w, n)) * rsqrtf(nn);
+  }
+  return fminf(f_ps(p, a, b), fminf(f_ps(p, b, c), f_ps(p, c, a)));
+}
+__device__ __forceinline__ float f_ss(fv3 a, fv3 b, fv3 c, fv3 d) {
+  fv3 d1 = fsub(b, a), d2 = fsub(d, c), r = fsub(a, c);
+  float A = fdot(d1, d1), E = fdot(d2, d2), B = fdot(d1, d2), C = fdot(d1, r), F = fdot(d2, r);
+  float best = fminf(fminf(f_ps(a, c, d), f_ps(b, c, d)), fminf(f_ps(c, a, b), f_ps(d, a, b)));
+  float den = A * E - B * B;
+  if (den > 0.f) {
+    float s = (B * F - C * E) / den, t = (A * F - B * C) / den;
+    if (s >= 0.f && s <= 1.f && t >= 0.f && t <= 1.f) {
+      fv3 q = {r.x + s * d1.x - t * d2.x, r.y + s * d1.y - t * d2.y, r.z + s * d1.z - t * d2.z};
+      best = fminf(best, sqrtf(fdot(q, q)));
+    }
+  }
+  return best;
+}
+// error margin of a float distance over these points
+__device__ __forceinline__ float ftol(fv3 a, fv3 b, fv3 c, fv3 d) {
+  float X = fmaxf(fmaxf(fmaxabs(a), fmaxabs(b)), fmaxf(fmaxabs(c), fmaxabs(d)));
+  float M = fmaxf(fmaxf(fmaxabs(fsub(b, a)), fmaxabs(fsub(c, a))), fmaxabs(fsub(d, a)));
+  return FILTER_TOL * (X + M) + 1e-30f;
 }
 
 // Smallest pair distance the forward step trusts: below it D_i/2 is no larger

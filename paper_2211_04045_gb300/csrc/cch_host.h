@@ -13,6 +13,12 @@
 namespace cch {
 namespace cg = cooperative_groups;
 
+// Kernel groups timed by the profiling mode (CUDA events on the stream).
+enum ProfGroup {
+  PG_REFIT, PG_VT, PG_EE, PG_VV, PG_REFRESH, PG_ASSEMBLE, PG_COLOUR, PG_PGS, PG_FORWARD, PG_CONTROL, PG_SETUP,
+  PG_OUTPUT, PG_N
+};
+
 // Host-side runtime of one pool of scenes (a single scene, a batch, or the
 // resident scenes of a server).
 struct Runtime {
@@ -35,7 +41,20 @@ struct Runtime {
   SceneState* h_ss = nullptr;        // pinned host copy of the scene states
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int edge_colours = 0;
+  long long launches = 0;            // kernels launched by this runtime
+  long long graph_launches = 0;      // kernels in one captured graph
+  int profiling = 0;                 // time kernel groups with events
+  unsigned prof_used = 0;
+  cudaEvent_t pev[PG_N][2] = {};
+  double prof_ms[PG_N] = {};
+  long long prof_n[PG_N] = {};
 };
+
+inline void prof_mark(Runtime& R, int g, int which, cudaStream_t st) {
+  if (!R.profiling) return;
+  cudaEventRecord(R.pev[g][which], st);
+  R.prof_used |= 1u << g;
+}
 
 // The exact candidate test (R3): on every axis fl(lo_b - hi_a) <= D and
 // fl(lo_a - hi_b) <= D.
@@ -116,5 +135,6 @@ __device__ __forceinline__ bool is_static(const Pool& P, int v) { return (P.vfla
 void bvh_build_all(Runtime& R, cudaStream_t st);
 void bvh_refit_all(Runtime& R, cudaStream_t st, int force);
 void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st);
+void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t st);
 
 }  // namespace cch

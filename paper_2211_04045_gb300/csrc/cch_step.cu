@@ -52,6 +52,7 @@ __global__ void k_vert_init(Pool P, double* const* ptrs) {
     P4 a = {xt[3 * i], xt[3 * i + 1], xt[3 * i + 2], 0.0};
     P4 b = {xl[3 * i], xl[3 * i + 1], xl[3 * i + 2], 0.0};
     P.x[v] = a;
+    P.xf[v] = make_float4((float)a.x, (float)a.y, (float)a.z, 0.f);
     P.y[v] = b;
     P.yt[v] = b;
     P.r[v] = 1.0;
@@ -91,6 +92,20 @@ __device__ __forceinline__ double pair_dist(const Pool& P, unsigned long long ke
   return (vnorm(vsub(mk(P.x[v.x]), mk(P.x[v.y]))) - P.rho[v.x]) - P.rho[v.y];
 }
 
+// FP32 lower bound of a pair's distance (see FILTER_TOL)
+__device__ __forceinline__ float pair_lower32(const Pool& P, unsigned long long key, int4 v) {
+  int kind = (int)(key >> 62);
+  fv3 a = fk(P.xf[v.x]), b = fk(P.xf[v.y]);
+  if (kind == K_VV) {
+    fv3 d = fsub(a, b);
+    float r = __double2float_ru(P.rho[v.x] + P.rho[v.y]);
+    return __fsub_rd(__fsub_rd(sqrtf(fdot(d, d)), r), ftol(a, b, b, b));
+  }
+  fv3 c = fk(P.xf[v.z]), d = fk(P.xf[v.w]);
+  float dd = kind == K_VT ? __fsub_rd(f_pt(a, b, c, d), __double2float_ru(P.rho[v.x])) : f_ss(a, b, c, d);
+  return __fsub_rd(dd, ftol(a, b, c, d));
+}
+
 __global__ void k_refresh(Pool P, int cur, int nxt) {
   int n = P.cnt->n_pairs[cur];
   if (n > P.pair_cap) n = P.pair_cap;
@@ -101,6 +116,7 @@ __global__ void k_refresh(Pool P, int cur, int nxt) {
     const SceneState& S = P.ss[s];
     if (!S.active || S.done || S.do_search) continue;
     unsigned long long key = B.key[i];
+    if (pair_lower32(P, key, v) >= __double2float_ru(S.D)) continue;
     double d = pair_dist(P, key, v);
     if (d < S.D) emit_pair(P, nxt, s, key, v, d);
   }
@@ -200,13 +216,19 @@ struct EdgeAcc {
 
 __device__ __forceinline__ bool movable(const Pool& P, int v) { return v >= 0 && (P.vflag[v] & VF_MOVABLE); }
 
-template <class Acc>
-__global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int* col, int* order, int* cstart,
-                         int* ncol_out, int max_rounds) {
-  cg::grid_group grid = cg::this_grid();
-  int n = n_ptr ? *n_ptr : fixed_n;
-  if (n_ptr && n > P.cons_cap) n = P.cons_cap;
-  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+struct GridSync {
+  cg::grid_group g;
+  __device__ void operator()() { g.sync(); }
+};
+struct BlockSync {
+  __device__ void operator()() { __syncthreads(); }
+};
+
+// The colouring rounds for n constraints with the threads (tid, nth) and the
+// barrier of either the whole grid or one block.
+template <class Acc, class Sync>
+__device__ void colour_body(Pool& P, const Acc& acc, int n, int* col, int* order, int* cstart, int* ncol_out,
+                            int max_rounds, int tid, int nth, Sync sync) {
   Counters* C = P.cnt;
   for (int i = tid; i < n; i += nth) {
     col[i] = -1;
@@ -215,19 +237,18 @@ __global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int* co
     for (int k = 0; k < 4; k++)
       if (movable(P, vv[k])) {
         P.vprio[vv[k]] = 0ull;
-        P.vmask[2 * vv[k]] = 0ull;
-        P.vmask[2 * vv[k] + 1] = 0ull;
+        for (int w = 0; w < MASK_WORDS; w++) P.vmask[MASK_WORDS * vv[k] + w] = 0ull;
       }
   }
-  if (tid < MAX_COLOURS + 2) {
-    C->colour_hist[tid] = 0;
-    C->colour_cursor[tid] = 0;
+  for (int c = tid; c < MAX_COLOURS + 2; c += nth) {
+    C->colour_hist[c] = 0;
+    C->colour_cursor[c] = 0;
   }
   if (tid == 0) {
     C->remaining = n;
     C->jp_rounds = 0;
   }
-  grid.sync();
+  sync();
   int round = 0;
   for (; round < max_rounds; round++) {
     if (__ldcg(&C->remaining) == 0) break;
@@ -239,41 +260,40 @@ __global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int* co
       for (int k = 0; k < 4; k++)
         if (movable(P, vv[k])) atomicMax(&P.vprio[vv[k]], p);
     }
-    grid.sync();
+    sync();
     for (int i = tid; i < n; i += nth) {
       if (__ldcg(&col[i]) >= 0) continue;
       int4 v = acc.verts(i);
       unsigned long long p = acc.prio(i);
       int vv[4] = {v.x, v.y, v.z, v.w};
       bool top = true;
-      unsigned long long m0 = 0, m1 = 0;
       for (int k = 0; k < 4; k++)
-        if (movable(P, vv[k])) {
-          if (__ldcg(&P.vprio[vv[k]]) != p) top = false;
-          m0 |= __ldcg(&P.vmask[2 * vv[k]]);
-          m1 |= __ldcg(&P.vmask[2 * vv[k] + 1]);
-        }
+        if (movable(P, vv[k]) && __ldcg(&P.vprio[vv[k]]) != p) top = false;
       if (!top) continue;
-      int c;
-      if (~m0) c = __ffsll((long long)~m0) - 1;
-      else if (~m1) c = 64 + __ffsll((long long)~m1) - 1;
-      else {
+      int c = -1;
+      for (int w = 0; w < MASK_WORDS && c < 0; w++) {
+        unsigned long long m = 0;
+        for (int k = 0; k < 4; k++)
+          if (movable(P, vv[k])) m |= __ldcg(&P.vmask[MASK_WORDS * vv[k] + w]);
+        if (~m) c = 64 * w + __ffsll((long long)~m) - 1;
+      }
+      if (c < 0) {
         atomicOr(&C->overflow, OV_COLOURS);
         c = MAX_COLOURS - 1;
       }
       for (int k = 0; k < 4; k++)
-        if (movable(P, vv[k])) atomicOr(&P.vmask[2 * vv[k] + (c >> 6)], 1ull << (c & 63));
+        if (movable(P, vv[k])) atomicOr(&P.vmask[MASK_WORDS * vv[k] + (c >> 6)], 1ull << (c & 63));
       col[i] = c;
       atomicSub(&C->remaining, 1);
     }
-    grid.sync();
+    sync();
     for (int i = tid; i < n; i += nth) {
       int4 v = acc.verts(i);
       int vv[4] = {v.x, v.y, v.z, v.w};
       for (int k = 0; k < 4; k++)
         if (movable(P, vv[k])) P.vprio[vv[k]] = 0ull;
     }
-    grid.sync();
+    sync();
   }
   if (tid == 0) {
     C->jp_rounds = round;
@@ -285,7 +305,7 @@ __global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int* co
     if (c < 0) c = MAX_COLOURS - 1;
     atomicAdd(&C->colour_hist[c], 1);
   }
-  grid.sync();
+  sync();
   if (tid == 0) {
     int run = 0, nc = 0;
     for (int c = 0; c < MAX_COLOURS; c++) {
@@ -298,13 +318,28 @@ __global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int* co
     cstart[MAX_COLOURS] = run;
     *ncol_out = nc;
   }
-  grid.sync();
+  sync();
   for (int i = tid; i < n; i += nth) {
     int c = __ldcg(&col[i]);
     if (c < 0) c = MAX_COLOURS - 1;
     int pos = atomicAdd(&C->colour_cursor[c], 1);
     order[pos] = i;
   }
+}
+
+template <class Acc>
+__global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int* col, int* order, int* cstart,
+                         int* ncol_out, int max_rounds) {
+  int n = n_ptr ? *n_ptr : fixed_n;
+  if (n_ptr && n > P.cons_cap) n = P.cons_cap;
+  if (n <= SMALL_WORK) {
+    // few constraints: one block, block barriers
+    if (blockIdx.x == 0)
+      colour_body(P, acc, n, col, order, cstart, ncol_out, max_rounds, threadIdx.x, blockDim.x, BlockSync{});
+    return;
+  }
+  colour_body(P, acc, n, col, order, cstart, ncol_out, max_rounds, blockIdx.x * blockDim.x + threadIdx.x,
+              gridDim.x * blockDim.x, GridSync{cg::this_grid()});
 }
 
 // ---------------------------------------------------------------------------
@@ -368,32 +403,39 @@ __device__ __forceinline__ void pgs_edge(Pool& P, int e, double* lam) {
   sty(P, l.y, vadd(yj, vscl(sj, g)));
 }
 
-__global__ void k_pgs(Pool P, int sweeps) {
-  cg::grid_group grid = cg::this_grid();
-  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+template <class Sync>
+__device__ void pgs_body(Pool& P, int sweeps, int n, int tid, int nth, Sync sync) {
   int ncol = P.cnt->ncol;
-  int n = P.cnt->n_cons;
-  if (n > P.cons_cap) n = P.cons_cap;
   double* lamc = sweeps > 1 ? P.lam : nullptr;
   double* lame = sweeps > 1 ? P.lam + P.cons_cap : nullptr;
   if (sweeps > 1) {
     for (int i = tid; i < n; i += nth) lamc[i] = 0.0;
     for (int i = tid; i < P.nl; i += nth) lame[i] = 0.0;
-    grid.sync();
+    sync();
   }
-  int* cs = P.cnt->colour_hist;  // contact colour starts after k_colour
+  const int* cs = P.cnt->colour_hist;  // contact colour starts after k_colour
   for (int sw = 0; sw < sweeps; sw++) {
     for (int k = 0; k < ncol; k++) {
       int a = cs[k], b = cs[k + 1];
       for (int i = a + tid; i < b; i += nth) pgs_contact(P, P.corder[i], lamc);
-      grid.sync();
+      sync();
     }
     for (int k = 0; k < P.nlcol; k++) {
       int a = P.lcstart[k], b = P.lcstart[k + 1];
       for (int i = a + tid; i < b; i += nth) pgs_edge(P, P.lorder[i], lame);
-      grid.sync();
+      sync();
     }
   }
+}
+
+__global__ void k_pgs(Pool P, int sweeps) {
+  int n = P.cnt->n_cons;
+  if (n > P.cons_cap) n = P.cons_cap;
+  if (n + P.nl <= SMALL_WORK) {
+    if (blockIdx.x == 0) pgs_body(P, sweeps, n, threadIdx.x, blockDim.x, BlockSync{});
+    return;
+  }
+  pgs_body(P, sweeps, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, GridSync{cg::this_grid()});
 }
 
 // ---------------------------------------------------------------------------
@@ -426,6 +468,7 @@ __global__ void k_forward(Pool P) {
     dv3 xn = a == 1.0 ? yv : vadd(xv, vscl(a, dx));
     if (P.xp) P.xp[v] = xv4;
     P.x[v] = {xn.x, xn.y, xn.z, 0.0};
+    P.xf[v] = make_float4((float)xn.x, (float)xn.y, (float)xn.z, 0.f);
     double r = P.r[v] * (1.0 - a);
     P.r[v] = r;
     double mv = vnorm(vsub(xn, xv));
@@ -525,7 +568,11 @@ void step_init(Runtime& R, cudaStream_t st, int only_active) {
   cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
   k_scene_init<<<(P.nscene + 127) / 128, 128, 0, st>>>(P, only_active);
   k_vert_init<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.d_ptrs);
-  if (P.nl) k_edge_prep<<<grid_for(P.nl, 256), 256, 0, st>>>(P);
+  R.launches += 2;
+  if (P.nl) {
+    k_edge_prep<<<grid_for(P.nl, 256), 256, 0, st>>>(P);
+    R.launches++;
+  }
 }
 
 void set_any_search(Runtime& R, cudaStream_t st) {
@@ -536,18 +583,37 @@ void set_any_search(Runtime& R, cudaStream_t st) {
 cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   Pool& P = R.pool;
   int nxt = 1 - cur;
+  prof_mark(R, PG_REFIT, 0, st);
   bvh_refit_all(R, st, 0);
-  search_queries(R, nxt, 0, 0.0, st);
+  prof_mark(R, PG_REFIT, 1, st);
+  for (int c = 0; c < 3; c++) {
+    prof_mark(R, PG_VT + c, 0, st);
+    query_class(R, c, nxt, 0, 0.0, st);
+    prof_mark(R, PG_VT + c, 1, st);
+  }
+  prof_mark(R, PG_REFRESH, 0, st);
   k_refresh<<<grid_for(P.pair_cap, 256), 256, 0, st>>>(P, cur, nxt);
+  prof_mark(R, PG_REFRESH, 1, st);
+  prof_mark(R, PG_ASSEMBLE, 0, st);
   k_assemble<<<grid_for(P.act_cap, 128), 128, 0, st>>>(P, nxt);
+  prof_mark(R, PG_ASSEMBLE, 1, st);
   ContactAcc ca{P.cons};
+  prof_mark(R, PG_COLOUR, 0, st);
   cudaError_t e = coop_launch(k_colour<ContactAcc>, R.coop_blocks, 256, st, P, ca, (const int*)&P.cnt->n_cons, 0,
                               P.ccol, P.corder, P.cnt->colour_hist, &P.cnt->ncol, 4096);
+  prof_mark(R, PG_COLOUR, 1, st);
   if (e != cudaSuccess) return e;
+  prof_mark(R, PG_PGS, 0, st);
   e = coop_launch(k_pgs, R.coop_blocks, 256, st, P, R.sweeps);
+  prof_mark(R, PG_PGS, 1, st);
   if (e != cudaSuccess) return e;
+  prof_mark(R, PG_FORWARD, 0, st);
   k_forward<<<grid_for(P.nv, 256), 256, 0, st>>>(P);
+  prof_mark(R, PG_FORWARD, 1, st);
+  prof_mark(R, PG_CONTROL, 0, st);
   k_control<<<1, 256, 0, st>>>(P, cur);
+  prof_mark(R, PG_CONTROL, 1, st);
+  R.launches += 6;
   return cudaGetLastError();
 }
 
@@ -563,6 +629,7 @@ cudaError_t colour_edges(Runtime& R, cudaStream_t st) {
 void output(Runtime& R, cudaStream_t st) {
   Pool& P = R.pool;
   k_output<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.d_ptrs);
+  R.launches++;
 }
 
 }  // namespace cch

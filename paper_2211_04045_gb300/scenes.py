@@ -410,3 +410,58 @@ def by_name(name: str, **kw) -> Scene:
         "hair_sand": hair_sand,
     }
     return table[name](**kw)
+
+
+# --------------------------------------------------------------------------
+# the same stand-in dynamics on the GPU (torch), used by the benchmark to
+# chain steps without host round trips
+# --------------------------------------------------------------------------
+class TorchDynamics:
+    def __init__(self, scene: Scene, device):
+        import torch
+        self.torch = torch
+        self.sc = scene
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=device)  # noqa: E731
+        self.im = f(scene.inv_mass)
+        self.fixed = self.im == 0.0
+        self.kin_v = f(scene.kin_v if scene.kin_v is not None else np.zeros_like(scene.x0))
+        self.g = f(scene.gravity)
+        le = scene.len_edges
+        self.relax = bool(scene.relax_sweeps and len(le) and scene.rest_len is not None)
+        if self.relax:
+            self.i = f(le[:, 0].astype(np.int64))
+            self.j = f(le[:, 1].astype(np.int64))
+            wi, wj = self.im[self.i], self.im[self.j]
+            ws = wi + wj
+            self.ok = ws > 0
+            self.wi, self.wj = wi, wj
+            self.ws = torch.where(self.ok, ws, torch.ones_like(ws))
+            n = scene.n_verts
+            deg = torch.zeros(n, device=device, dtype=torch.float64)
+            deg.index_add_(0, self.i[self.ok], torch.ones_like(ws[self.ok]))
+            deg.index_add_(0, self.j[self.ok], torch.ones_like(ws[self.ok]))
+            self.deg = torch.clamp(deg, min=1.0)[:, None]
+            self.rest = f(scene.rest_len)
+
+    def predict(self, x, v):
+        torch = self.torch
+        sc = self.sc
+        xt = x + sc.dt * v
+        xt = torch.where(self.fixed[:, None], x + sc.dt * self.kin_v, xt)
+        if self.relax:
+            for _ in range(sc.relax_sweeps):
+                d = xt[self.i] - xt[self.j]
+                L = torch.linalg.norm(d, dim=1)
+                L = torch.where(L > 0, L, torch.ones_like(L))
+                c = torch.where(self.ok, (L - self.rest) / L / self.ws, torch.zeros_like(L))[:, None] * d
+                dx = torch.zeros_like(xt)
+                dx.index_add_(0, self.i, -self.wi[:, None] * c)
+                dx.index_add_(0, self.j, self.wj[:, None] * c)
+                xt = xt + dx / self.deg
+        return xt
+
+    def next_velocity(self, x_new, x_old):
+        torch = self.torch
+        v = (x_new - x_old) / self.sc.dt
+        v = torch.where(self.fixed[:, None], self.kin_v, v + self.sc.dt * self.g)
+        return v
