@@ -194,6 +194,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ncu-case", type=int, default=0,
+                    help="profiling aid: run one step of the workload capped at this many iterations and exit "
+                         "(prints no bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -210,6 +213,15 @@ def main():
     from paper_2211_04045_gb300 import cch, scenes
     sc, wname = workload(args.config)
     prm = cch.params_for(sc, precision=1 if args.precision == "mixed" else 0)
+    if args.ncu_case:
+        prm.max_iters = args.ncu_case
+        g = cch.Scene(sc, prm)
+        x0, xt0, _ = scenes.initial(sc)
+        _, st = g.step(torch.tensor(x0, device=dev), torch.tensor(xt0, device=dev))
+        torch.cuda.synchronize(dev)
+        sys.stderr.write(f"[bench] ncu case: {st['iterations']} iterations, {st['kernel_launches']} launches\n")
+        g.close()
+        return 0
     stream = torch.cuda.current_stream(dev)
     gpu = cch.Scene(sc, prm, stream=stream.cuda_stream)
     n = sc.n_verts
