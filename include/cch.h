@@ -160,6 +160,32 @@ cch_status cch_destroy(cch_scene* s);
 cch_status cch_query_pairs(cch_scene* s, const double* x, const double* x_ref, double D, int32_t want_candidates,
                            uint64_t* keys, double* dist, int64_t cap, int64_t* count);
 
+/* ---- proximity query without device allocation ----------------------------
+ * The same query as cch_query_pairs for callers that must not allocate device
+ * memory while they run: for example code executing between
+ * cudaStreamBeginCapture and cudaStreamEndCapture (where cudaMalloc is not
+ * allowed), real-time loops that reserve all of their memory up front, or
+ * hosts whose memory manager forbids direct cudaMalloc.  The paper has no
+ * counterpart; this is a deployment variant of the query above.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The pair
+ * list the query kernels produce is written to one fixed array inside the
+ * library (CCH_NOALLOC_MAX_PAIRS pairs, 16 bytes each, 2 MiB per GPU, held by
+ * every GPU that loads the library until the process exits) and copied to
+ * keys/dist from there.  The first call on a device looks the array's device
+ * address up (cudaGetSymbolAddress, once per device, with that device
+ * current); make that first call before any stream capture starts.
+ * Results: as cch_query_pairs.  When more than CCH_NOALLOC_MAX_PAIRS pairs
+ * are found, *count receives the full count and the call returns
+ * CCH_E_CAPACITY without copying.  All calls share the array and it keeps
+ * the previous call's contents; calls whose work overlaps on the GPU (other
+ * host threads, other scenes on other streams) race on it and must be
+ * serialised by the caller. */
+#define CCH_NOALLOC_MAX_PAIRS 131072
+cch_status cch_query_pairs_noalloc(cch_scene* s, const double* x, const double* x_ref, double D,
+                                   int32_t want_candidates, uint64_t* keys, double* dist, int64_t cap,
+                                   int64_t* count);
+
 /* ---- profiling -----------------------------------------------------------
  * With profiling on, steps launch kernels directly (no CUDA graphs) and
  * record CUDA events on the scene's stream around each kernel group:

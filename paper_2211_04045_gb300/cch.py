@@ -91,12 +91,13 @@ def lib():
             L.cch_server_submit.argtypes = [p, i32, p, p, p, C.POINTER(C.c_uint64)]
             L.cch_server_wait.argtypes = [p, C.c_uint64, C.POINTER(StepStats), C.POINTER(d)]
             L.cch_server_destroy.argtypes = [p]
+            L.cch_query_pairs_noalloc.argtypes = [p, p, p, d, i32, p, p, i64, C.POINTER(i64)]
             L.cch_set_profiling.argtypes = [p, i32]
             L.cch_get_profile.argtypes = [p, p, p, i32]
             for f in ("cch_params_default", "cch_create_scene", "cch_create_batch", "cch_handle_step",
                       "cch_handle_step_host", "cch_batch_handle_step", "cch_destroy", "cch_query_pairs",
                       "cch_server_create", "cch_server_add_scene", "cch_server_submit", "cch_server_wait",
-                      "cch_server_destroy", "cch_set_profiling", "cch_get_profile"):
+                      "cch_server_destroy", "cch_set_profiling", "cch_get_profile", "cch_query_pairs_noalloc"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -230,6 +231,26 @@ class Scene:
         _check(lib().cch_query_pairs(self.h, C.c_void_p(_dev_ptr(x, n)), C.c_void_p(_dev_ptr(x_ref, n)), float(D),
                                      int(bool(candidates)), C.c_void_p(keys.ctypes.data),
                                      C.c_void_p(dist.ctypes.data), m, C.byref(cnt)), "cch_query_pairs")
+        o = np.argsort(keys[:m], kind="stable")
+        return keys[:m][o], dist[:m][o]
+
+    NOALLOC_MAX_PAIRS = 131072
+
+    def query_pairs_noalloc(self, x, x_ref, D: float, candidates: bool, cap: int = NOALLOC_MAX_PAIRS):
+        """The allocation-free variant of query_pairs (fixed library-side scratch).
+
+        Returns (keys, dist) sorted by key; raises CchError with code 5
+        (internal capacity exceeded) when more than NOALLOC_MAX_PAIRS pairs
+        are found."""
+        n = self.topos[0].n
+        keys = np.zeros(max(cap, 1), np.uint64)
+        dist = np.zeros(max(cap, 1), np.float64)
+        cnt = C.c_int64(0)
+        _check(lib().cch_query_pairs_noalloc(self.h, C.c_void_p(_dev_ptr(x, n)), C.c_void_p(_dev_ptr(x_ref, n)),
+                                             float(D), int(bool(candidates)), C.c_void_p(keys.ctypes.data),
+                                             C.c_void_p(dist.ctypes.data), cap, C.byref(cnt)),
+               "cch_query_pairs_noalloc")
+        m = min(cnt.value, cap)
         o = np.argsort(keys[:m], kind="stable")
         return keys[:m][o], dist[:m][o]
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/cch.h"
@@ -623,6 +624,76 @@ cch_status cch_query_pairs(cch_scene* S, const double* x, const double* x_ref, d
     return CCH_OK;
   }
   return CCH_E_CAPACITY;
+}
+
+// ---- proximity query without device allocation -----------------------------
+// The pair list that the query kernels write before it is copied to the host
+// lives in this fixed array instead of the scene's growable buffers, so the
+// call below allocates nothing.  Keys occupy the first half, distances the
+// second.  Every GPU that loads the library holds it until the process ends.
+static __device__ __align__(256) unsigned char g_query_scratch[CCH_NOALLOC_MAX_PAIRS * 16];
+
+static std::mutex g_scratch_mu;
+static void* g_scratch_addr[64] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code only sees a stand-in symbol, not the device address).
+static cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_query_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+cch_status cch_query_pairs_noalloc(cch_scene* S, const double* x, const double* x_ref, double D,
+                                   int32_t want_candidates, uint64_t* keys, double* dist, int64_t cap,
+                                   int64_t* count) {
+  if (!S || !x || !x_ref || !count || !(D >= 0.0) || cap < 0 || (cap > 0 && !keys)) return CCH_E_INVALID_ARG;
+  if (S->n_scenes != 1) return CCH_E_INVALID_ARG;
+  Runtime& R = S->R;
+  cudaStream_t st = R.stream;
+  void* scratch = nullptr;
+  CK(scratch_address(&scratch));
+  // run the query kernels with the fixed array as their output buffer
+  Pool saved = R.pool;
+  R.pool.qkeys = (unsigned long long*)scratch;
+  R.pool.qdist = (double*)((unsigned char*)scratch + CCH_NOALLOC_MAX_PAIRS * 8);
+  R.pool.qcap = CCH_NOALLOC_MAX_PAIRS;
+  R.h_ptrs[0] = (double*)x;
+  R.h_ptrs[1] = (double*)x_ref;
+  R.h_ptrs[2] = nullptr;
+  cudaError_t e = cudaMemcpyAsync(R.d_ptrs, R.h_ptrs, sizeof(double*) * 3, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    step_init(R, st, 0);
+    bvh_build_all(R, st);
+    bvh_refit_all(R, st, 1);
+    search_queries(R, 0, want_candidates ? 1 : 2, D, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(R.h_cnt, R.pool.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  Pool used = R.pool;
+  R.pool = saved;
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (R.h_cnt->err) return CCH_E_CAPACITY;
+  int64_t n = R.h_cnt->n_query;
+  *count = n;
+  if (n > CCH_NOALLOC_MAX_PAIRS) return CCH_E_CAPACITY;
+  int64_t m = n < cap ? n : cap;
+  if (m > 0) {
+    CK(cudaMemcpy(keys, used.qkeys, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost));
+    if (dist) CK(cudaMemcpy(dist, used.qdist, sizeof(double) * m, cudaMemcpyDeviceToHost));
+  }
+  return CCH_OK;
 }
 
 cch_status cch_set_profiling(cch_scene* S, int32_t on) {
