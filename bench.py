@@ -194,6 +194,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ncu-warm", type=int, default=0, help="full chain steps before the --ncu-case step")
     ap.add_argument("--ncu-case", type=int, default=0,
                     help="profiling aid: run one step of the workload capped at this many iterations and exit "
                          "(prints no bench line)")
@@ -214,12 +215,28 @@ def main():
     sc, wname = workload(args.config)
     prm = cch.params_for(sc, precision=1 if args.precision == "mixed" else 0)
     if args.ncu_case:
+        x0, xt0, v0 = scenes.initial(sc)
+        x, xt, v = (torch.tensor(a, device=dev) for a in (x0, xt0, v0))
+        if args.ncu_warm:
+            dyn = scenes.TorchDynamics(sc, dev)
+            gw = cch.Scene(sc, prm)
+            for _ in range(args.ncu_warm):
+                out, _ = gw.step(x, xt)
+                v = dyn.next_velocity(out, x)
+                x, xt = out, dyn.predict(out, v)
+            gw.close()
         prm.max_iters = args.ncu_case
         g = cch.Scene(sc, prm)
-        x0, xt0, _ = scenes.initial(sc)
-        _, st = g.step(torch.tensor(x0, device=dev), torch.tensor(xt0, device=dev))
         torch.cuda.synchronize(dev)
-        sys.stderr.write(f"[bench] ncu case: {st['iterations']} iterations, {st['kernel_launches']} launches\n")
+        torch.cuda.profiler.start()  # captures with --profile-from-start off cover this step only
+        _, st = g.step(x, xt)
+        torch.cuda.synchronize(dev)
+        torch.cuda.profiler.stop()
+        torch.cuda.synchronize(dev)
+        sys.stderr.write(f"[bench] ncu case: {st['iterations']} iterations, {st['kernel_launches']} launches, "
+                         f"{st['pairs_evaluated'] / st['iterations']:.0f} pairs/iter, "
+                         f"{st['active_contacts'] / st['iterations']:.0f} contacts/iter, "
+                         f"{st['max_colours']} colours, {st['max_colour_rounds']} colouring rounds\n")
         g.close()
         return 0
     stream = torch.cuda.current_stream(dev)

@@ -111,6 +111,8 @@ typedef struct {
                                 certify (expected 0)                          */
   double device_ms;          /* device time of the call (CUDA events)         */
   int64_t kernel_launches;   /* kernels this call launched (graph nodes count) */
+  int32_t max_colour_rounds; /* most colouring rounds in one iteration        */
+  int32_t reserved_;
 } cch_step_stats;
 
 typedef struct cch_scene cch_scene;
@@ -177,7 +179,9 @@ cch_status cch_query_pairs(cch_scene* s, const double* x, const double* x_ref, d
  * current); make that first call before any stream capture starts.
  * Results: as cch_query_pairs.  When more than CCH_NOALLOC_MAX_PAIRS pairs
  * are found, *count receives the full count and the call returns
- * CCH_E_CAPACITY without copying.  All calls share the array and it keeps
+ * CCH_E_CAPACITY without copying; it returns CCH_E_CAPACITY too when the
+ * query's intermediate pairs outgrow the buffers the scene was created with
+ * (cch_query_pairs would grow them; this call cannot).  All calls share the array and it keeps
  * the previous call's contents; calls whose work overlaps on the GPU (other
  * host threads, other scenes on other streams) race on it and must be
  * serialised by the caller. */
@@ -192,7 +196,7 @@ cch_status cch_query_pairs_noalloc(cch_scene* s, const double* x, const double* 
  * 0 BVH refit, 1 vertex-triangle query, 2 edge-edge query, 3 vertex-vertex
  * query, 4 distance refresh, 5 contact assembly, 6 colouring, 7 Gauss-Seidel
  * sweeps, 8 forward step, 9 loop control, 10 step set-up (inputs, BVH
- * build), 11 output.  cch_set_profiling resets the accumulators;
+ * build), 11 output, 12 exact FP64 stage of the search.  cch_set_profiling resets the accumulators;
  * cch_get_profile returns, per group, the summed milliseconds and the number
  * of timed launches (n entries). */
 cch_status cch_set_profiling(cch_scene* s, int32_t on);

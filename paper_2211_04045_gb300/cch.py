@@ -53,7 +53,8 @@ class StepStats(C.Structure):
                 ("active_contacts", C.c_int64), ("candidates", C.c_int64), ("degenerate", C.c_int64),
                 ("max_colours", C.c_int32), ("edge_colours", C.c_int32), ("final_r_inf", C.c_double),
                 ("min_pair_dist", C.c_double), ("intersections", C.c_int64), ("uncertain", C.c_int64),
-                ("device_ms", C.c_double), ("kernel_launches", C.c_int64)]
+                ("device_ms", C.c_double), ("kernel_launches", C.c_int64), ("max_colour_rounds", C.c_int32),
+                ("reserved_", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -255,7 +256,7 @@ class Scene:
         return keys[:m][o], dist[:m][o]
 
     PROFILE_GROUPS = ("refit", "query_vt", "query_ee", "query_vv", "refresh", "assemble", "colour", "pgs",
-                      "forward", "control", "setup", "output")
+                      "forward", "control", "setup", "output", "finalize")
 
     def set_profiling(self, on: bool):
         _check(lib().cch_set_profiling(self.h, int(bool(on))), "cch_set_profiling")

@@ -371,6 +371,20 @@ __device__ __forceinline__ float3 f3ru(dv3 a) {
   return make_float3(__double2float_ru(a.x), __double2float_ru(a.y), __double2float_ru(a.z));
 }
 
+// A pair that the FP32 filter could not reject; the exact FP64 distance is
+// evaluated later by k_finalize with one pair per thread (full warps instead
+// of the few lanes still active inside a divergent traversal).
+__device__ __forceinline__ void push_survivor(Pool& P, int kind, unsigned long long key, int4 v) {
+  int idx = append_idx(&P.cnt->n_fcand[kind]);
+  if (idx >= P.pair_cap) {
+    atomicOr(&P.cnt->overflow, OV_PAIRS);
+    return;
+  }
+  size_t o = (size_t)kind * P.pair_cap + idx;
+  P.fkey[o] = key;
+  P.fv[o] = v;
+}
+
 __device__ __forceinline__ void add_candidates(Pool& P, int s, long long n) {
   if (n == 0) return;
   cg::coalesced_group g = cg::coalesced_threads();
@@ -413,14 +427,7 @@ __global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, dou
       fv3 f1 = fk(P.xf[tv.x]), f2 = fk(P.xf[tv.y]), f3 = fk(P.xf[tv.z]);
       float lower = __fsub_rd(__fsub_rd(f_pt(fa, f1, f2, f3), raf), ftol(fa, f1, f2, f3));
       if (lower >= Df) return;
-      double d = d_pt(xa, mk(P.x[tv.x]), mk(P.x[tv.y]), mk(P.x[tv.z])) - ra;
-      if (!(d < D)) return;
-      dv3 lo, hi;
-      int sc;
-      prim_box(P, 0, t, lo, hi, sc);
-      if (!box_near(alo, ahi, lo, hi, D)) return;
-      if (mode == 2) { emit_query(P, key, d); return; }
-      emit_pair(P, nxt, s, key, make_int4(a, tv.x, tv.y, tv.z), d);
+      push_survivor(P, K_VT, key, make_int4(a, tv.x, tv.y, tv.z));
     });
     if (mode == 0) add_candidates(P, s, ncand);
   }
@@ -463,15 +470,7 @@ __global__ void __launch_bounds__(128) k_query_ee(Pool P, int nxt, int mode, dou
       float lower = __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
       if (lower >= Df) return;
       int4 A = lo_e == e1 ? ea : eb, Bv = lo_e == e1 ? eb : ea;
-      double ps, pt;
-      double d = d_ss(mk(P.x[A.x]), mk(P.x[A.y]), mk(P.x[Bv.x]), mk(P.x[Bv.y]), &ps, &pt);
-      if (!(d < D)) return;
-      dv3 lo, hi;
-      int sc2;
-      prim_box(P, 1, e2, lo, hi, sc2);
-      if (!box_near(alo, ahi, lo, hi, D)) return;
-      if (mode == 2) { emit_query(P, key, d); return; }
-      emit_pair(P, nxt, s, key, make_int4(A.x, A.y, Bv.x, Bv.y), d);
+      push_survivor(P, K_EE, key, make_int4(A.x, A.y, Bv.x, Bv.y));
     });
     if (mode == 0) add_candidates(P, s, ncand);
   }
@@ -506,13 +505,58 @@ __global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, dou
         return;
       }
       ncand++;
-      double d = (vnorm(vsub(xa, xb)) - ra) - rb;
-      if (!(d < D)) return;
-      if (!box_near(alo, ahi, blo, bhi, D)) return;
-      if (mode == 2) { emit_query(P, key, d); return; }
-      emit_pair(P, nxt, s, key, make_int4(a, b, -1, -1), d);
+      push_survivor(P, K_VV, key, make_int4(a, b, -1, -1));
     });
     if (mode == 0) add_candidates(P, s, ncand);
+  }
+}
+
+// Exact stage of the search: FP64 distance, then the exact FP64 box test of
+// R3 (implied by dist < D up to rounding; evaluated so that P equals the
+// oracle's set), for every FP32-filter survivor.  The three kinds occupy
+// separate regions, so a warp almost always runs one kind's arithmetic.
+__global__ void k_finalize(Pool P, int nxt, int mode, double Dq) {
+  if (mode == 0 && !P.cnt->any_search) return;
+  int n0 = min(P.cnt->n_fcand[0], P.pair_cap), n1 = min(P.cnt->n_fcand[1], P.pair_cap);
+  int n2 = min(P.cnt->n_fcand[2], P.pair_cap);
+  int total = n0 + n1 + n2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int kind = i < n0 ? K_VT : (i < n0 + n1 ? K_EE : K_VV);
+    int j = kind == K_VT ? i : (kind == K_EE ? i - n0 : i - n0 - n1);
+    size_t o = (size_t)kind * P.pair_cap + j;
+    unsigned long long key = P.fkey[o];
+    int4 v = P.fv[o];
+    int s = P.vscene[v.x];
+    double D = mode == 0 ? P.sd[s].d_max : Dq;
+    dv3 a = mk(P.x[v.x]), b = mk(P.x[v.y]);
+    double d;
+    dv3 alo, ahi, blo, bhi;
+    if (kind == K_VV) {
+      double ra = P.rho[v.x], rb = P.rho[v.y];
+      d = (vnorm(vsub(a, b)) - ra) - rb;
+      if (!(d < D)) continue;
+      alo = {a.x - ra, a.y - ra, a.z - ra}; ahi = {a.x + ra, a.y + ra, a.z + ra};
+      blo = {b.x - rb, b.y - rb, b.z - rb}; bhi = {b.x + rb, b.y + rb, b.z + rb};
+    } else {
+      dv3 c = mk(P.x[v.z]), e = mk(P.x[v.w]);
+      if (kind == K_VT) {
+        double ra = P.rho[v.x];
+        d = d_pt(a, b, c, e) - ra;
+        if (!(d < D)) continue;
+        alo = {a.x - ra, a.y - ra, a.z - ra}; ahi = {a.x + ra, a.y + ra, a.z + ra};
+        blo = {fmin(fmin(b.x, c.x), e.x), fmin(fmin(b.y, c.y), e.y), fmin(fmin(b.z, c.z), e.z)};
+        bhi = {fmax(fmax(b.x, c.x), e.x), fmax(fmax(b.y, c.y), e.y), fmax(fmax(b.z, c.z), e.z)};
+      } else {
+        double ps, pt;
+        d = d_ss(a, b, c, e, &ps, &pt);
+        if (!(d < D)) continue;
+        alo = {fmin(a.x, b.x), fmin(a.y, b.y), fmin(a.z, b.z)}; ahi = {fmax(a.x, b.x), fmax(a.y, b.y), fmax(a.z, b.z)};
+        blo = {fmin(c.x, e.x), fmin(c.y, e.y), fmin(c.z, e.z)}; bhi = {fmax(c.x, e.x), fmax(c.y, e.y), fmax(c.z, e.z)};
+      }
+    }
+    if (!box_near(alo, ahi, blo, bhi, D)) continue;
+    if (mode == 2) emit_query(P, key, d);
+    else emit_pair(P, nxt, s, key, v, d);
   }
 }
 
@@ -640,8 +684,15 @@ void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t s
   }
 }
 
+void finalize_search(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) {
+  Pool& P = R.pool;
+  k_finalize<<<grid_for(3LL * P.pair_cap, 256), 256, 0, st>>>(P, nxt, mode, Dq);
+  R.launches++;
+}
+
 void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) {
   for (int c = 0; c < 3; c++) query_class(R, c, nxt, mode, Dq, st);
+  if (mode != 1) finalize_search(R, nxt, mode, Dq, st);
 }
 
 }  // namespace cch

@@ -141,9 +141,12 @@ cudaError_t alloc_pairs(Runtime& R) {
     if ((e = dalloc_in(L, &P.pb[b].d, P.pair_cap)) != cudaSuccess) return e;
   }
   if ((e = dalloc_in(L, &P.act, P.act_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.fkey, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.fv, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.corder, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.ccol, P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.cwork, 2 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.lam, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -289,7 +292,9 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaEventCreate(&R.ev1));
   // colour the edge-length constraints once (topology only)
   P.nlcol = 0;
-  CK(colour_edges(R, R.stream));
+  int* ework = nullptr;
+  CK(dalloc(R, &ework, 2 * (size_t)(nl > 0 ? nl : 1)));
+  CK(colour_edges(R, R.stream, ework));
   CK(cudaStreamSynchronize(R.stream));
   if (nl) {
     std::vector<int> cs(MAX_COLOURS + 1);
@@ -362,6 +367,7 @@ void fill_stats(const Runtime& R, const SceneState& S, cch_step_stats* st, float
   st->candidates = S.candidates;
   st->degenerate = S.degenerate;
   st->max_colours = S.max_colours;
+  st->max_colour_rounds = S.max_rounds;
   st->edge_colours = R.edge_colours;
   st->final_r_inf = S.final_r;
   union { unsigned long long u; double d; } b;
@@ -605,6 +611,12 @@ cch_status cch_query_pairs(cch_scene* S, const double* x, const double* x_ref, d
     CK(cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (R.h_cnt->err) return CCH_E_CAPACITY;
+    if (R.h_cnt->overflow & OV_PAIRS) {
+      // the FP32-filter survivors outgrew the pair-sized buffers
+      cch_status g = grow_pairs(R);
+      if (g != CCH_OK) return g;
+      continue;
+    }
     int n = R.h_cnt->n_query;
     if (n > P.qcap) {
       // grow the inspection buffers and retry
@@ -687,7 +699,8 @@ cch_status cch_query_pairs_noalloc(cch_scene* S, const double* x, const double* 
   if (R.h_cnt->err) return CCH_E_CAPACITY;
   int64_t n = R.h_cnt->n_query;
   *count = n;
-  if (n > CCH_NOALLOC_MAX_PAIRS) return CCH_E_CAPACITY;
+  // more pairs than the array holds, or than the scene's pair buffers hold
+  if (n > CCH_NOALLOC_MAX_PAIRS || (R.h_cnt->overflow & OV_PAIRS)) return CCH_E_CAPACITY;
   int64_t m = n < cap ? n : cap;
   if (m > 0) {
     CK(cudaMemcpy(keys, used.qkeys, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost));

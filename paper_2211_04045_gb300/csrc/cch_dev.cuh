@@ -51,6 +51,7 @@ struct SceneState {
   long long pairs_eval, max_pairs, contacts, candidates, degenerate;
   int n_pairs;                    // |P| of this iteration
   int max_colours;
+  int max_rounds;                 // most colouring rounds in one iteration
   int ccd_clamps;
   double final_r;
   long long isect, uncertain;
@@ -71,7 +72,11 @@ struct Counters {
   int colour_hist[520]; // per-colour counts, then exclusive starts
   int colour_cursor[520];
   int jp_rounds;
+  int wcount[2];        // colouring worklist sizes
+  int wcur;             // current worklist
   int n_query;          // pairs written by a query call
+  int n_fcand[3];       // FP32-filter survivors per pair kind (VT, EE, VV)
+  int any_refresh;      // some active scene reuses P in this iteration
   int ccd_hit;
   int pad;
 };
@@ -148,9 +153,12 @@ struct Pool {
   Counters* cnt;
   PairBuf pb[2];
   int* act;                // active contact list: indices into the next pair buffer
+  unsigned long long* fkey;  // FP32-filter survivors: 3 regions of pair_cap (VT, EE, VV)
+  int4* fv;
   Contact* cons;
   int* corder;             // contacts sorted by colour
   int* ccol;               // colour per contact
+  int* cwork;              // colouring worklists (2 x cons_cap)
   unsigned long long* vprio;   // per vertex: max priority of uncoloured contacts (colouring)
   unsigned long long* vmask;   // per vertex: MASK_WORDS x 64-bit used-colour masks
   double* lam;             // multipliers for gs_sweeps > 1 (contacts then edges)

@@ -16,7 +16,7 @@ namespace cg = cooperative_groups;
 // Kernel groups timed by the profiling mode (CUDA events on the stream).
 enum ProfGroup {
   PG_REFIT, PG_VT, PG_EE, PG_VV, PG_REFRESH, PG_ASSEMBLE, PG_COLOUR, PG_PGS, PG_FORWARD, PG_CONTROL, PG_SETUP,
-  PG_OUTPUT, PG_N
+  PG_OUTPUT, PG_FINAL, PG_N
 };
 
 // Host-side runtime of one pool of scenes (a single scene, a batch, or the
@@ -136,5 +136,6 @@ void bvh_build_all(Runtime& R, cudaStream_t st);
 void bvh_refit_all(Runtime& R, cudaStream_t st, int force);
 void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st);
 void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t st);
+void finalize_search(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st);
 
 }  // namespace cch

@@ -35,6 +35,7 @@ __global__ void k_scene_init(Pool P, int only_active) {
     S.pairs_eval = S.max_pairs = S.contacts = S.candidates = S.degenerate = 0;
     S.n_pairs = 0;
     S.max_colours = 0;
+    S.max_rounds = 0;
     S.ccd_clamps = 0;
     S.final_r = 1.0;
     S.isect = S.uncertain = 0;
@@ -107,6 +108,7 @@ __device__ __forceinline__ float pair_lower32(const Pool& P, unsigned long long 
 }
 
 __global__ void k_refresh(Pool P, int cur, int nxt) {
+  if (!P.cnt->any_refresh) return;
   int n = P.cnt->n_pairs[cur];
   if (n > P.pair_cap) n = P.pair_cap;
   const PairBuf B = P.pb[cur];
@@ -224,14 +226,14 @@ struct BlockSync {
   __device__ void operator()() { __syncthreads(); }
 };
 
-// The colouring rounds for n constraints with the threads (tid, nth) and the
-// barrier of either the whole grid or one block.
+// Colouring state: col[] (-1 = uncoloured) and two worklists of uncoloured
+// constraint indices whose sizes live in Counters::wcount.
 template <class Acc, class Sync>
-__device__ void colour_body(Pool& P, const Acc& acc, int n, int* col, int* order, int* cstart, int* ncol_out,
-                            int max_rounds, int tid, int nth, Sync sync) {
+__device__ void colour_init(Pool& P, const Acc& acc, int n, int* col, int* work, int tid, int nth, Sync sync) {
   Counters* C = P.cnt;
   for (int i = tid; i < n; i += nth) {
     col[i] = -1;
+    work[i] = i;
     int4 v = acc.verts(i);
     int vv[4] = {v.x, v.y, v.z, v.w};
     for (int k = 0; k < 4; k++)
@@ -245,15 +247,38 @@ __device__ void colour_body(Pool& P, const Acc& acc, int n, int* col, int* order
     C->colour_cursor[c] = 0;
   }
   if (tid == 0) {
-    C->remaining = n;
+    C->wcount[0] = n;
+    C->wcount[1] = 0;
+    C->wcur = 0;
     C->jp_rounds = 0;
   }
   sync();
-  int round = 0;
-  for (; round < max_rounds; round++) {
-    if (__ldcg(&C->remaining) == 0) break;
-    for (int i = tid; i < n; i += nth) {
-      if (__ldcg(&col[i]) >= 0) continue;
+}
+
+// Rounds of the colouring.  Each round colours every worklist constraint
+// whose priority is the largest among the uncoloured constraints at each of
+// its movable vertices, with the smallest colour unused by its (already
+// coloured, higher-priority) neighbours; the rest go to the next worklist.
+// Returns when the worklist is empty, or (grid mode) when it has shrunk to
+// `tail` entries so that one block can finish with cheaper barriers.
+template <class Acc, class Sync>
+__device__ void colour_rounds(Pool& P, const Acc& acc, int* col, int* work, int cap, int max_rounds, int tail,
+                              int tid, int nth, Sync sync) {
+  Counters* C = P.cnt;
+  for (;;) {
+    int cur = __ldcg(&C->wcur);
+    int m = __ldcg(&C->wcount[cur]);
+    int rounds = __ldcg(&C->jp_rounds);
+    if (m == 0) return;
+    if (m <= tail) return;
+    if (rounds >= max_rounds) {
+      if (tid == 0) atomicOr(&C->overflow, OV_ROUNDS);
+      return;
+    }
+    int* wc = work + (size_t)cur * cap;
+    int* wn = work + (size_t)(1 - cur) * cap;
+    for (int j = tid; j < m; j += nth) {
+      int i = wc[j];
       int4 v = acc.verts(i);
       unsigned long long p = acc.prio(i);
       int vv[4] = {v.x, v.y, v.z, v.w};
@@ -261,21 +286,24 @@ __device__ void colour_body(Pool& P, const Acc& acc, int n, int* col, int* order
         if (movable(P, vv[k])) atomicMax(&P.vprio[vv[k]], p);
     }
     sync();
-    for (int i = tid; i < n; i += nth) {
-      if (__ldcg(&col[i]) >= 0) continue;
+    for (int j = tid; j < m; j += nth) {
+      int i = wc[j];
       int4 v = acc.verts(i);
       unsigned long long p = acc.prio(i);
       int vv[4] = {v.x, v.y, v.z, v.w};
       bool top = true;
       for (int k = 0; k < 4; k++)
         if (movable(P, vv[k]) && __ldcg(&P.vprio[vv[k]]) != p) top = false;
-      if (!top) continue;
+      if (!top) {
+        wn[append_idx(&C->wcount[1 - cur])] = i;
+        continue;
+      }
       int c = -1;
       for (int w = 0; w < MASK_WORDS && c < 0; w++) {
-        unsigned long long m = 0;
+        unsigned long long msk = 0;
         for (int k = 0; k < 4; k++)
-          if (movable(P, vv[k])) m |= __ldcg(&P.vmask[MASK_WORDS * vv[k] + w]);
-        if (~m) c = 64 * w + __ffsll((long long)~m) - 1;
+          if (movable(P, vv[k])) msk |= __ldcg(&P.vmask[MASK_WORDS * vv[k] + w]);
+        if (~msk) c = 64 * w + __ffsll((long long)~msk) - 1;
       }
       if (c < 0) {
         atomicOr(&C->overflow, OV_COLOURS);
@@ -284,62 +312,85 @@ __device__ void colour_body(Pool& P, const Acc& acc, int n, int* col, int* order
       for (int k = 0; k < 4; k++)
         if (movable(P, vv[k])) atomicOr(&P.vmask[MASK_WORDS * vv[k] + (c >> 6)], 1ull << (c & 63));
       col[i] = c;
-      atomicSub(&C->remaining, 1);
     }
     sync();
-    for (int i = tid; i < n; i += nth) {
+    for (int j = tid; j < m; j += nth) {
+      int i = wc[j];
       int4 v = acc.verts(i);
       int vv[4] = {v.x, v.y, v.z, v.w};
       for (int k = 0; k < 4; k++)
         if (movable(P, vv[k])) P.vprio[vv[k]] = 0ull;
     }
-    sync();
-  }
-  if (tid == 0) {
-    C->jp_rounds = round;
-    if (round == max_rounds && __ldcg(&C->remaining) != 0) atomicOr(&C->overflow, OV_ROUNDS);
-  }
-  // counting sort by colour
-  for (int i = tid; i < n; i += nth) {
-    int c = __ldcg(&col[i]);
-    if (c < 0) c = MAX_COLOURS - 1;
-    atomicAdd(&C->colour_hist[c], 1);
-  }
-  sync();
-  if (tid == 0) {
-    int run = 0, nc = 0;
-    for (int c = 0; c < MAX_COLOURS; c++) {
-      int h = __ldcg(&C->colour_hist[c]);
-      cstart[c] = run;
-      C->colour_cursor[c] = run;
-      run += h;
-      if (h) nc = c + 1;
+    if (tid == 0) {
+      C->wcount[cur] = 0;
+      C->wcur = 1 - cur;
+      C->jp_rounds = rounds + 1;
     }
-    cstart[MAX_COLOURS] = run;
-    *ncol_out = nc;
-  }
-  sync();
-  for (int i = tid; i < n; i += nth) {
-    int c = __ldcg(&col[i]);
-    if (c < 0) c = MAX_COLOURS - 1;
-    int pos = atomicAdd(&C->colour_cursor[c], 1);
-    order[pos] = i;
+    sync();
   }
 }
 
 template <class Acc>
-__global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int* col, int* order, int* cstart,
-                         int* ncol_out, int max_rounds) {
+__global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int cap, int* col, int* work,
+                         int max_rounds) {
   int n = n_ptr ? *n_ptr : fixed_n;
-  if (n_ptr && n > P.cons_cap) n = P.cons_cap;
+  if (n > cap) n = cap;
   if (n <= SMALL_WORK) {
     // few constraints: one block, block barriers
-    if (blockIdx.x == 0)
-      colour_body(P, acc, n, col, order, cstart, ncol_out, max_rounds, threadIdx.x, blockDim.x, BlockSync{});
+    if (blockIdx.x == 0) {
+      colour_init(P, acc, n, col, work, threadIdx.x, blockDim.x, BlockSync{});
+      colour_rounds(P, acc, col, work, cap, max_rounds, 0, threadIdx.x, blockDim.x, BlockSync{});
+    }
     return;
   }
-  colour_body(P, acc, n, col, order, cstart, ncol_out, max_rounds, blockIdx.x * blockDim.x + threadIdx.x,
-              gridDim.x * blockDim.x, GridSync{cg::this_grid()});
+  GridSync gs{cg::this_grid()};
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  colour_init(P, acc, n, col, work, tid, nth, gs);
+  colour_rounds(P, acc, col, work, cap, max_rounds, SMALL_WORK / 4, tid, nth, gs);
+  // the last few uncoloured constraints: one block
+  if (blockIdx.x == 0) colour_rounds(P, acc, col, work, cap, max_rounds, 0, threadIdx.x, blockDim.x, BlockSync{});
+}
+
+// counting sort of the constraints by colour: histogram, scan, scatter
+__global__ void k_colour_hist(Pool P, const int* n_ptr, int fixed_n, int cap, const int* col) {
+  int n = n_ptr ? *n_ptr : fixed_n;
+  if (n > cap) n = cap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c = col[i];
+    if (c < 0) c = MAX_COLOURS - 1;
+    atomicAdd(&P.cnt->colour_hist[c], 1);
+  }
+}
+__global__ void k_colour_scan(Pool P, int* cstart, int* ncol_out) {
+  __shared__ int h[MAX_COLOURS];
+  __shared__ int last;
+  Counters* C = P.cnt;
+  if (threadIdx.x == 0) last = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < MAX_COLOURS; c += blockDim.x) {
+    h[c] = C->colour_hist[c];
+    if (h[c]) atomicMax(&last, c + 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int c = 0; c < MAX_COLOURS; c++) {
+      cstart[c] = run;
+      C->colour_cursor[c] = run;
+      run += h[c];
+    }
+    cstart[MAX_COLOURS] = run;
+    *ncol_out = last;
+  }
+}
+__global__ void k_colour_scatter(Pool P, const int* n_ptr, int fixed_n, int cap, const int* col, int* order) {
+  int n = n_ptr ? *n_ptr : fixed_n;
+  if (n > cap) n = cap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c = col[i];
+    if (c < 0) c = MAX_COLOURS - 1;
+    order[atomicAdd(&P.cnt->colour_cursor[c], 1)] = i;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -483,8 +534,8 @@ __global__ void k_forward(Pool P) {
 // ---------------------------------------------------------------------------
 __global__ void k_control(Pool P, int cur) {
   Counters* C = P.cnt;
-  __shared__ int any_search, running;
-  if (threadIdx.x == 0) { any_search = 0; running = 0; }
+  __shared__ int any_search, running, any_refresh;
+  if (threadIdx.x == 0) { any_search = 0; running = 0; any_refresh = 0; }
   __syncthreads();
   for (int s = threadIdx.x; s < P.nscene; s += blockDim.x) {
     SceneState& S = P.ss[s];
@@ -501,6 +552,7 @@ __global__ void k_control(Pool P, int cur) {
     S.move_bits = 0;
     S.rmax_bits = 0;
     if (C->ncol > S.max_colours) S.max_colours = C->ncol;
+    if (C->jp_rounds > S.max_rounds) S.max_rounds = C->jp_rounds;
     if (rmax < d.eps) {
       S.done = 1;
       S.converged = 1;
@@ -511,6 +563,8 @@ __global__ void k_control(Pool P, int cur) {
       if (S.do_search) {
         S.D = d.d_max;
         atomicOr(&any_search, 1);
+      } else {
+        atomicOr(&any_refresh, 1);
       }
       atomicOr(&running, 1);
     }
@@ -518,6 +572,8 @@ __global__ void k_control(Pool P, int cur) {
   __syncthreads();
   if (threadIdx.x == 0) {
     C->any_search = any_search;
+    C->any_refresh = any_refresh;
+    C->n_fcand[0] = C->n_fcand[1] = C->n_fcand[2] = 0;
     C->all_done = running ? 0 : 1;
     C->n_pairs[cur] = 0;
     C->n_active = 0;
@@ -591,6 +647,9 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     query_class(R, c, nxt, 0, 0.0, st);
     prof_mark(R, PG_VT + c, 1, st);
   }
+  prof_mark(R, PG_FINAL, 0, st);
+  finalize_search(R, nxt, 0, 0.0, st);
+  prof_mark(R, PG_FINAL, 1, st);
   prof_mark(R, PG_REFRESH, 0, st);
   k_refresh<<<grid_for(P.pair_cap, 256), 256, 0, st>>>(P, cur, nxt);
   prof_mark(R, PG_REFRESH, 1, st);
@@ -599,10 +658,15 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   prof_mark(R, PG_ASSEMBLE, 1, st);
   ContactAcc ca{P.cons};
   prof_mark(R, PG_COLOUR, 0, st);
-  cudaError_t e = coop_launch(k_colour<ContactAcc>, R.coop_blocks, 256, st, P, ca, (const int*)&P.cnt->n_cons, 0,
-                              P.ccol, P.corder, P.cnt->colour_hist, &P.cnt->ncol, 4096);
-  prof_mark(R, PG_COLOUR, 1, st);
+  const int* ncp = &P.cnt->n_cons;
+  cudaError_t e = coop_launch(k_colour<ContactAcc>, R.coop_blocks, 256, st, P, ca, ncp, 0, P.cons_cap, P.ccol,
+                              P.cwork, 65536);
   if (e != cudaSuccess) return e;
+  k_colour_hist<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, ncp, 0, P.cons_cap, P.ccol);
+  k_colour_scan<<<1, 512, 0, st>>>(P, P.cnt->colour_hist, &P.cnt->ncol);
+  k_colour_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, ncp, 0, P.cons_cap, P.ccol, P.corder);
+  R.launches += 3;
+  prof_mark(R, PG_COLOUR, 1, st);
   prof_mark(R, PG_PGS, 0, st);
   e = coop_launch(k_pgs, R.coop_blocks, 256, st, P, R.sweeps);
   prof_mark(R, PG_PGS, 1, st);
@@ -617,13 +681,18 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t colour_edges(Runtime& R, cudaStream_t st) {
+cudaError_t colour_edges(Runtime& R, cudaStream_t st, int* work) {
   Pool& P = R.pool;
   if (P.nl == 0) return cudaSuccess;
   EdgeAcc ea{P.lv, P.sd};
   cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
-  return coop_launch(k_colour<EdgeAcc>, R.coop_blocks, 256, st, P, ea, (const int*)nullptr, P.nl, P.lcol, P.lorder,
-                     P.lcstart, &P.cnt->pad, 65536);
+  cudaError_t e = coop_launch(k_colour<EdgeAcc>, R.coop_blocks, 256, st, P, ea, (const int*)nullptr, P.nl, P.nl,
+                              P.lcol, work, 65536);
+  if (e != cudaSuccess) return e;
+  k_colour_hist<<<grid_for(P.nl, 256), 256, 0, st>>>(P, nullptr, P.nl, P.nl, P.lcol);
+  k_colour_scan<<<1, 512, 0, st>>>(P, P.lcstart, &P.cnt->pad);
+  k_colour_scatter<<<grid_for(P.nl, 256), 256, 0, st>>>(P, nullptr, P.nl, P.nl, P.lcol, P.lorder);
+  return cudaGetLastError();
 }
 
 void output(Runtime& R, cudaStream_t st) {
