@@ -146,7 +146,9 @@ cudaError_t alloc_pairs(Runtime& R) {
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.corder, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.ccol, P.cons_cap)) != cudaSuccess) return e;
-  if ((e = dalloc_in(L, &P.cwork, 2 * (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &R.cbuf.iprio, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &R.cbuf.iid, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &R.cbuf.rank, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.lam, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -274,7 +276,6 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaMemset(P.ss, 0, sizeof(SceneState) * n_scenes));
   CK(dalloc(R, &P.cnt, 1));
   CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
-  CK(dalloc(R, &P.vprio, nv));
   CK(dalloc(R, &P.vmask, (size_t)MASK_WORDS * nv));
   CK(dalloc(R, &P.jacc, 3 * (size_t)nv));
   CK(dalloc(R, &P.sbox, 2 * (size_t)n_scenes));
@@ -292,9 +293,14 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaEventCreate(&R.ev1));
   // colour the edge-length constraints once (topology only)
   P.nlcol = 0;
-  int* ework = nullptr;
-  CK(dalloc(R, &ework, 2 * (size_t)(nl > 0 ? nl : 1)));
-  CK(colour_edges(R, R.stream, ework));
+  CK(dalloc(R, &R.cbuf.vstart, (size_t)nv + 1));
+  CK(dalloc(R, &R.cbuf.vfill, nv));
+  CK(dalloc(R, &R.cbuf.vdone, nv));
+  ColourBufs eb = R.cbuf;
+  CK(dalloc(R, &eb.iprio, 4 * (size_t)(nl > 0 ? nl : 1)));
+  CK(dalloc(R, &eb.iid, 4 * (size_t)(nl > 0 ? nl : 1)));
+  CK(dalloc(R, &eb.rank, 4 * (size_t)(nl > 0 ? nl : 1)));
+  CK(colour_edges(R, R.stream, eb));
   CK(cudaStreamSynchronize(R.stream));
   if (nl) {
     std::vector<int> cs(MAX_COLOURS + 1);

@@ -158,8 +158,6 @@ struct Pool {
   Contact* cons;
   int* corder;             // contacts sorted by colour
   int* ccol;               // colour per contact
-  int* cwork;              // colouring worklists (2 x cons_cap)
-  unsigned long long* vprio;   // per vertex: max priority of uncoloured contacts (colouring)
   unsigned long long* vmask;   // per vertex: MASK_WORDS x 64-bit used-colour masks
   double* lam;             // multipliers for gs_sweeps > 1 (contacts then edges)
   double* jacc;            // projected Jacobi accumulators (3 per vertex)

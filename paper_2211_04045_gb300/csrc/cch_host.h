@@ -19,6 +19,16 @@ enum ProfGroup {
   PG_OUTPUT, PG_FINAL, PG_N
 };
 
+// Scratch of the greedy colouring (see cch_step.cu).
+struct ColourBufs {
+  int* vstart;               // N+1: incidence counts, scanned in place to bucket starts
+  int* vfill;                // N: bucket fill cursors
+  int* vdone;                // N: coloured constraints per vertex so far
+  unsigned long long* iprio; // incidences: priority
+  int* iid;                  // incidences: constraint * 4 + slot
+  int* rank;                 // constraint * 4 + slot: rank at that vertex
+};
+
 // Host-side runtime of one pool of scenes (a single scene, a batch, or the
 // resident scenes of a server).
 struct Runtime {
@@ -41,6 +51,7 @@ struct Runtime {
   SceneState* h_ss = nullptr;        // pinned host copy of the scene states
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int edge_colours = 0;
+  ColourBufs cbuf{};                 // colouring scratch for the contacts
   long long launches = 0;            // kernels launched by this runtime
   long long graph_launches = 0;      // kernels in one captured graph
   int profiling = 0;                 // time kernel groups with events

@@ -226,129 +226,135 @@ struct BlockSync {
   __device__ void operator()() { __syncthreads(); }
 };
 
-// Colouring state: col[] (-1 = uncoloured) and two worklists of uncoloured
-// constraint indices whose sizes live in Counters::wcount.
-template <class Acc, class Sync>
-__device__ void colour_init(Pool& P, const Acc& acc, int n, int* col, int* work, int tid, int nth, Sync sync) {
-  Counters* C = P.cnt;
-  for (int i = tid; i < n; i += nth) {
-    col[i] = -1;
-    work[i] = i;
-    int4 v = acc.verts(i);
+// The greedy colouring is computed without rounds.  Each (constraint,
+// movable vertex) incidence gets its rank among that vertex's constraints by
+// descending priority.  A constraint is ready once every one of its vertices
+// has coloured exactly `rank` constraints (all its higher-priority
+// neighbours there); it then takes the smallest colour not used at its
+// vertices, publishes the colour bit, fences, and advances the vertices'
+// counters.  Threads poll their constraints without blocking, so the highest
+// priority uncoloured constraint is always ready and the colouring always
+// progresses; the polls are bounded and report CCH_E_TIMEOUT past the bound.
+
+template <class Acc>
+__global__ void k_ci_count(Pool P, Acc acc, const int* n_ptr, int fixed_n, int cap, int* col, ColourBufs B) {
+  int n = n_ptr ? *n_ptr : fixed_n;
+  if (n > cap) n = cap;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    col[c] = -1;
+    int4 v = acc.verts(c);
     int vv[4] = {v.x, v.y, v.z, v.w};
     for (int k = 0; k < 4; k++)
       if (movable(P, vv[k])) {
-        P.vprio[vv[k]] = 0ull;
+        atomicAdd(&B.vstart[vv[k]], 1);
+        B.vdone[vv[k]] = 0;
         for (int w = 0; w < MASK_WORDS; w++) P.vmask[MASK_WORDS * vv[k] + w] = 0ull;
       }
-  }
-  for (int c = tid; c < MAX_COLOURS + 2; c += nth) {
-    C->colour_hist[c] = 0;
-    C->colour_cursor[c] = 0;
-  }
-  if (tid == 0) {
-    C->wcount[0] = n;
-    C->wcount[1] = 0;
-    C->wcur = 0;
-    C->jp_rounds = 0;
-  }
-  sync();
-}
-
-// Rounds of the colouring.  Each round colours every worklist constraint
-// whose priority is the largest among the uncoloured constraints at each of
-// its movable vertices, with the smallest colour unused by its (already
-// coloured, higher-priority) neighbours; the rest go to the next worklist.
-// Returns when the worklist is empty, or (grid mode) when it has shrunk to
-// `tail` entries so that one block can finish with cheaper barriers.
-template <class Acc, class Sync>
-__device__ void colour_rounds(Pool& P, const Acc& acc, int* col, int* work, int cap, int max_rounds, int tail,
-                              int tid, int nth, Sync sync) {
-  Counters* C = P.cnt;
-  for (;;) {
-    int cur = __ldcg(&C->wcur);
-    int m = __ldcg(&C->wcount[cur]);
-    int rounds = __ldcg(&C->jp_rounds);
-    if (m == 0) return;
-    if (m <= tail) return;
-    if (rounds >= max_rounds) {
-      if (tid == 0) atomicOr(&C->overflow, OV_ROUNDS);
-      return;
-    }
-    int* wc = work + (size_t)cur * cap;
-    int* wn = work + (size_t)(1 - cur) * cap;
-    for (int j = tid; j < m; j += nth) {
-      int i = wc[j];
-      int4 v = acc.verts(i);
-      unsigned long long p = acc.prio(i);
-      int vv[4] = {v.x, v.y, v.z, v.w};
-      for (int k = 0; k < 4; k++)
-        if (movable(P, vv[k])) atomicMax(&P.vprio[vv[k]], p);
-    }
-    sync();
-    for (int j = tid; j < m; j += nth) {
-      int i = wc[j];
-      int4 v = acc.verts(i);
-      unsigned long long p = acc.prio(i);
-      int vv[4] = {v.x, v.y, v.z, v.w};
-      bool top = true;
-      for (int k = 0; k < 4; k++)
-        if (movable(P, vv[k]) && __ldcg(&P.vprio[vv[k]]) != p) top = false;
-      if (!top) {
-        wn[append_idx(&C->wcount[1 - cur])] = i;
-        continue;
-      }
-      int c = -1;
-      for (int w = 0; w < MASK_WORDS && c < 0; w++) {
-        unsigned long long msk = 0;
-        for (int k = 0; k < 4; k++)
-          if (movable(P, vv[k])) msk |= __ldcg(&P.vmask[MASK_WORDS * vv[k] + w]);
-        if (~msk) c = 64 * w + __ffsll((long long)~msk) - 1;
-      }
-      if (c < 0) {
-        atomicOr(&C->overflow, OV_COLOURS);
-        c = MAX_COLOURS - 1;
-      }
-      for (int k = 0; k < 4; k++)
-        if (movable(P, vv[k])) atomicOr(&P.vmask[MASK_WORDS * vv[k] + (c >> 6)], 1ull << (c & 63));
-      col[i] = c;
-    }
-    sync();
-    for (int j = tid; j < m; j += nth) {
-      int i = wc[j];
-      int4 v = acc.verts(i);
-      int vv[4] = {v.x, v.y, v.z, v.w};
-      for (int k = 0; k < 4; k++)
-        if (movable(P, vv[k])) P.vprio[vv[k]] = 0ull;
-    }
-    if (tid == 0) {
-      C->wcount[cur] = 0;
-      C->wcur = 1 - cur;
-      C->jp_rounds = rounds + 1;
-    }
-    sync();
   }
 }
 
 template <class Acc>
-__global__ void k_colour(Pool P, Acc acc, const int* n_ptr, int fixed_n, int cap, int* col, int* work,
-                         int max_rounds) {
+__global__ void k_ci_scatter(Pool P, Acc acc, const int* n_ptr, int fixed_n, int cap, ColourBufs B) {
   int n = n_ptr ? *n_ptr : fixed_n;
   if (n > cap) n = cap;
-  if (n <= SMALL_WORK) {
-    // few constraints: one block, block barriers
-    if (blockIdx.x == 0) {
-      colour_init(P, acc, n, col, work, threadIdx.x, blockDim.x, BlockSync{});
-      colour_rounds(P, acc, col, work, cap, max_rounds, 0, threadIdx.x, blockDim.x, BlockSync{});
-    }
-    return;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    int4 v = acc.verts(c);
+    unsigned long long p = acc.prio(c);
+    int vv[4] = {v.x, v.y, v.z, v.w};
+    for (int k = 0; k < 4; k++)
+      if (movable(P, vv[k])) {
+        int slot = B.vstart[vv[k]] + atomicAdd(&B.vfill[vv[k]], 1);
+        B.iprio[slot] = p;
+        B.iid[slot] = 4 * c + k;
+      }
   }
-  GridSync gs{cg::this_grid()};
+}
+
+template <class Acc>
+__global__ void k_ci_rank(Pool P, Acc acc, ColourBufs B, int nv) {
+  int total = B.vstart[nv];
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
+    int id = B.iid[s];
+    int4 v = acc.verts(id >> 2);
+    int vv[4] = {v.x, v.y, v.z, v.w};
+    int vert = vv[id & 3];
+    int a = B.vstart[vert], b = B.vstart[vert + 1];
+    unsigned long long p = B.iprio[s];
+    int r = 0;
+    for (int t = a; t < b; t++) r += B.iprio[t] > p;
+    B.rank[id] = r;
+  }
+}
+
+template <class Acc>
+__global__ void k_ci_poll(Pool P, Acc acc, const int* n_ptr, int fixed_n, int cap, int* col, ColourBufs B,
+                          int max_polls) {
+  int n = n_ptr ? *n_ptr : fixed_n;
+  if (n > cap) n = cap;
   int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  colour_init(P, acc, n, col, work, tid, nth, gs);
-  colour_rounds(P, acc, col, work, cap, max_rounds, SMALL_WORK / 4, tid, nth, gs);
-  // the last few uncoloured constraints: one block
-  if (blockIdx.x == 0) colour_rounds(P, acc, col, work, cap, max_rounds, 0, threadIdx.x, blockDim.x, BlockSync{});
+  int polls = 0;
+  for (;;) {
+    bool pending = false;
+    for (int c = tid; c < n; c += nth) {
+      if (col[c] >= 0) continue;
+      int4 v = acc.verts(c);
+      int vv[4] = {v.x, v.y, v.z, v.w};
+      bool ready = true;
+      for (int k = 0; k < 4 && ready; k++)
+        if (movable(P, vv[k]) && __ldcg(&B.vdone[vv[k]]) != B.rank[4 * c + k]) ready = false;
+      if (!ready) {
+        pending = true;
+        continue;
+      }
+      __threadfence();  // the neighbours' colour bits were published before their counters
+      int cc = -1;
+      for (int w = 0; w < MASK_WORDS && cc < 0; w++) {
+        unsigned long long m = 0;
+        for (int k = 0; k < 4; k++)
+          if (movable(P, vv[k])) m |= __ldcg(&P.vmask[MASK_WORDS * vv[k] + w]);
+        if (~m) cc = 64 * w + __ffsll((long long)~m) - 1;
+      }
+      if (cc < 0) {
+        atomicOr(&P.cnt->overflow, OV_COLOURS);
+        cc = MAX_COLOURS - 1;
+      }
+      col[c] = cc;
+      for (int k = 0; k < 4; k++)
+        if (movable(P, vv[k])) atomicOr(&P.vmask[MASK_WORDS * vv[k] + (cc >> 6)], 1ull << (cc & 63));
+      __threadfence();
+      for (int k = 0; k < 4; k++)
+        if (movable(P, vv[k])) atomicAdd(&B.vdone[vv[k]], 1);
+    }
+    if (!pending) break;
+    if (++polls > max_polls) {
+      atomicOr(&P.cnt->err, 16);  // bounded wait ran out
+      break;
+    }
+    __nanosleep(64);
+  }
+}
+
+// exclusive scan of m ints, in place, one block of 1024 threads
+__global__ void k_scan_ints(int* a, int m) {
+  __shared__ int part[1024];
+  int per = (m + 1023) / 1024;
+  int lo = threadIdx.x * per, hi = min(lo + per, m);
+  int sum = 0;
+  for (int i = lo; i < hi; i++) sum += a[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int i = lo; i < hi; i++) {
+    int v = a[i];
+    a[i] = run;
+    run += v;
+  }
 }
 
 // counting sort of the constraints by colour: histogram, scan, scatter
@@ -454,39 +460,63 @@ __device__ __forceinline__ void pgs_edge(Pool& P, int e, double* lam) {
   sty(P, l.y, vadd(yj, vscl(sj, g)));
 }
 
-template <class Sync>
-__device__ void pgs_body(Pool& P, int sweeps, int n, int tid, int nth, Sync sync) {
+// Contact colours in ascending order.  Colour classes shrink with the colour
+// index (greedy colouring); once a class has at most PGS_TAIL constraints the
+// remaining classes run in one block with block barriers.
+constexpr int PGS_TAIL = 1024;
+
+__global__ void k_pgs_contacts(Pool P, int sweep) {
+  int n = P.cnt->n_cons;
+  if (n > P.cons_cap) n = P.cons_cap;
   int ncol = P.cnt->ncol;
-  double* lamc = sweeps > 1 ? P.lam : nullptr;
-  double* lame = sweeps > 1 ? P.lam + P.cons_cap : nullptr;
-  if (sweeps > 1) {
-    for (int i = tid; i < n; i += nth) lamc[i] = 0.0;
-    for (int i = tid; i < P.nl; i += nth) lame[i] = 0.0;
-    sync();
+  const int* cs = P.cnt->colour_hist;  // contact colour starts after the colouring
+  double* lam = P.sd[0].gs_sweeps > 1 ? P.lam : nullptr;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  if (lam && sweep == 0)
+    for (int i = tid; i < n; i += nth) lam[i] = 0.0;
+  int k = 0;
+  if (n > SMALL_WORK) {
+    cg::grid_group grid = cg::this_grid();
+    if (lam && sweep == 0) grid.sync();
+    for (; k < ncol && cs[k + 1] - cs[k] > PGS_TAIL; k++) {
+      for (int i = cs[k] + tid; i < cs[k + 1]; i += nth) pgs_contact(P, P.corder[i], lam);
+      grid.sync();
+    }
+  } else if (lam && sweep == 0) {
+    cg::this_grid().sync();
   }
-  const int* cs = P.cnt->colour_hist;  // contact colour starts after k_colour
-  for (int sw = 0; sw < sweeps; sw++) {
-    for (int k = 0; k < ncol; k++) {
-      int a = cs[k], b = cs[k + 1];
-      for (int i = a + tid; i < b; i += nth) pgs_contact(P, P.corder[i], lamc);
-      sync();
-    }
-    for (int k = 0; k < P.nlcol; k++) {
-      int a = P.lcstart[k], b = P.lcstart[k + 1];
-      for (int i = a + tid; i < b; i += nth) pgs_edge(P, P.lorder[i], lame);
-      sync();
-    }
+  if (blockIdx.x != 0) return;
+  for (; k < ncol; k++) {
+    for (int i = cs[k] + threadIdx.x; i < cs[k + 1]; i += blockDim.x) pgs_contact(P, P.corder[i], lam);
+    __syncthreads();
   }
 }
 
-__global__ void k_pgs(Pool P, int sweeps) {
-  int n = P.cnt->n_cons;
-  if (n > P.cons_cap) n = P.cons_cap;
-  if (n + P.nl <= SMALL_WORK) {
-    if (blockIdx.x == 0) pgs_body(P, sweeps, n, threadIdx.x, blockDim.x, BlockSync{});
+// Edge-length constraints, colour by colour (colouring fixed at creation).
+__global__ void k_pgs_edges(Pool P, int sweep) {
+  double* lam = P.sd[0].gs_sweeps > 1 ? P.lam + P.cons_cap : nullptr;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  if (P.nl <= SMALL_WORK) {
+    if (blockIdx.x != 0) return;
+    if (lam && sweep == 0) {
+      for (int i = threadIdx.x; i < P.nl; i += blockDim.x) lam[i] = 0.0;
+      __syncthreads();
+    }
+    for (int k = 0; k < P.nlcol; k++) {
+      for (int i = P.lcstart[k] + threadIdx.x; i < P.lcstart[k + 1]; i += blockDim.x) pgs_edge(P, P.lorder[i], lam);
+      __syncthreads();
+    }
     return;
   }
-  pgs_body(P, sweeps, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, GridSync{cg::this_grid()});
+  cg::grid_group grid = cg::this_grid();
+  if (lam && sweep == 0) {
+    for (int i = tid; i < P.nl; i += nth) lam[i] = 0.0;
+    grid.sync();
+  }
+  for (int k = 0; k < P.nlcol; k++) {
+    for (int i = P.lcstart[k] + tid; i < P.lcstart[k + 1]; i += nth) pgs_edge(P, P.lorder[i], lam);
+    grid.sync();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -609,14 +639,36 @@ int coop_grid(int threads) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int a = 0, b = 0, c = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_colour<ContactAcc>, threads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_colour<EdgeAcc>, threads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pgs, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ci_poll<ContactAcc>, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ci_poll<EdgeAcc>, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pgs_contacts, threads, 0);
   per = a < b ? a : b;
   per = per < c ? per : c;
   if (per > 2) per = 2;
   if (per < 1) per = 1;
   return sms * per;
+}
+
+// Greedy colouring in descending priority of n constraints (count on the
+// device when n_ptr is set), then the counting sort by colour.
+template <class Acc>
+cudaError_t colour_greedy(Runtime& R, Acc acc, const int* n_ptr, int fixed_n, int cap, int* col, int* order,
+                          int* cstart, int* ncol_out, const ColourBufs& B, cudaStream_t st) {
+  Pool& P = R.pool;
+  cudaMemsetAsync(B.vstart, 0, sizeof(int) * ((size_t)P.nv + 1), st);
+  cudaMemsetAsync(B.vfill, 0, sizeof(int) * (size_t)P.nv, st);
+  k_ci_count<<<grid_for(cap, 256), 256, 0, st>>>(P, acc, n_ptr, fixed_n, cap, col, B);
+  k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
+  k_ci_scatter<<<grid_for(cap, 256), 256, 0, st>>>(P, acc, n_ptr, fixed_n, cap, B);
+  k_ci_rank<<<grid_for(4LL * cap, 256), 256, 0, st>>>(P, acc, B, P.nv);
+  cudaError_t e = coop_launch(k_ci_poll<Acc>, R.coop_blocks, 256, st, P, acc, n_ptr, fixed_n, cap, col, B, 1 << 22);
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(P.cnt->colour_hist, 0, sizeof(int) * (MAX_COLOURS + 2), st);
+  k_colour_hist<<<grid_for(cap, 256), 256, 0, st>>>(P, n_ptr, fixed_n, cap, col);
+  k_colour_scan<<<1, 512, 0, st>>>(P, cstart, ncol_out);
+  k_colour_scatter<<<grid_for(cap, 256), 256, 0, st>>>(P, n_ptr, fixed_n, cap, col, order);
+  R.launches += 8;
+  return cudaGetLastError();
 }
 
 void step_init(Runtime& R, cudaStream_t st, int only_active) {
@@ -658,17 +710,16 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   prof_mark(R, PG_ASSEMBLE, 1, st);
   ContactAcc ca{P.cons};
   prof_mark(R, PG_COLOUR, 0, st);
-  const int* ncp = &P.cnt->n_cons;
-  cudaError_t e = coop_launch(k_colour<ContactAcc>, R.coop_blocks, 256, st, P, ca, ncp, 0, P.cons_cap, P.ccol,
-                              P.cwork, 65536);
-  if (e != cudaSuccess) return e;
-  k_colour_hist<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, ncp, 0, P.cons_cap, P.ccol);
-  k_colour_scan<<<1, 512, 0, st>>>(P, P.cnt->colour_hist, &P.cnt->ncol);
-  k_colour_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, ncp, 0, P.cons_cap, P.ccol, P.corder);
-  R.launches += 3;
+  cudaError_t e = colour_greedy(R, ca, &P.cnt->n_cons, 0, P.cons_cap, P.ccol, P.corder, P.cnt->colour_hist,
+                                &P.cnt->ncol, R.cbuf, st);
   prof_mark(R, PG_COLOUR, 1, st);
+  if (e != cudaSuccess) return e;
   prof_mark(R, PG_PGS, 0, st);
-  e = coop_launch(k_pgs, R.coop_blocks, 256, st, P, R.sweeps);
+  for (int sw = 0; sw < R.sweeps && e == cudaSuccess; sw++) {
+    e = coop_launch(k_pgs_contacts, R.coop_blocks, 256, st, P, sw);
+    if (e == cudaSuccess) e = coop_launch(k_pgs_edges, R.coop_blocks, 256, st, P, sw);
+    R.launches += 2;
+  }
   prof_mark(R, PG_PGS, 1, st);
   if (e != cudaSuccess) return e;
   prof_mark(R, PG_FORWARD, 0, st);
@@ -677,22 +728,16 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   prof_mark(R, PG_CONTROL, 0, st);
   k_control<<<1, 256, 0, st>>>(P, cur);
   prof_mark(R, PG_CONTROL, 1, st);
-  R.launches += 6;
+  R.launches += 4;
   return cudaGetLastError();
 }
 
-cudaError_t colour_edges(Runtime& R, cudaStream_t st, int* work) {
+cudaError_t colour_edges(Runtime& R, cudaStream_t st, const ColourBufs& B) {
   Pool& P = R.pool;
   if (P.nl == 0) return cudaSuccess;
   EdgeAcc ea{P.lv, P.sd};
   cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
-  cudaError_t e = coop_launch(k_colour<EdgeAcc>, R.coop_blocks, 256, st, P, ea, (const int*)nullptr, P.nl, P.nl,
-                              P.lcol, work, 65536);
-  if (e != cudaSuccess) return e;
-  k_colour_hist<<<grid_for(P.nl, 256), 256, 0, st>>>(P, nullptr, P.nl, P.nl, P.lcol);
-  k_colour_scan<<<1, 512, 0, st>>>(P, P.lcstart, &P.cnt->pad);
-  k_colour_scatter<<<grid_for(P.nl, 256), 256, 0, st>>>(P, nullptr, P.nl, P.nl, P.lcol, P.lorder);
-  return cudaGetLastError();
+  return colour_greedy(R, ea, nullptr, P.nl, P.nl, P.lcol, P.lorder, P.lcstart, &P.cnt->pad, B, st);
 }
 
 void output(Runtime& R, cudaStream_t st) {

@@ -7,6 +7,6 @@ int coop_grid(int threads);
 void step_init(Runtime& R, cudaStream_t st, int only_active);
 void set_any_search(Runtime& R, cudaStream_t st);
 cudaError_t iteration(Runtime& R, int cur, cudaStream_t st);
-cudaError_t colour_edges(Runtime& R, cudaStream_t st, int* work);
+cudaError_t colour_edges(Runtime& R, cudaStream_t st, const ColourBufs& B);
 void output(Runtime& R, cudaStream_t st);
 }  // namespace cch
