@@ -97,7 +97,7 @@ def lib():
             L.orc_backward_once.restype = C.c_int
             L.orc_backward_once.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, p, p, p]
             L.orc_ccd.restype = C.c_int
-            L.orc_ccd.argtypes = [C.c_int, p, p, p]
+            L.orc_ccd.argtypes = [C.c_int, p, p, p, p]
             L.orc_count_intersections.restype = i64
             L.orc_count_intersections.argtypes = [C.POINTER(Topology), p]
             L.orc_handle_step.restype = C.c_int
@@ -267,9 +267,10 @@ def colour_greedy(verts, nv, movable, prio, key):
     return nc, col
 
 
-def ccd(kind, x0, x1):
+def ccd(kind, x0, x1, rho=None):
     x0 = _f64(x0).reshape(-1)
     x1 = _f64(x1).reshape(-1)
+    r = None if rho is None else _f64(rho).reshape(-1)
     toi = C.c_double(-1.0)
-    hit = lib().orc_ccd(kind, _ptr(x0), _ptr(x1), C.addressof(toi))
+    hit = lib().orc_ccd(kind, _ptr(x0), _ptr(x1), _ptr(r) if r is not None else None, C.addressof(toi))
     return bool(hit), (toi.value if hit else None)

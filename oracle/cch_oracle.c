@@ -1004,13 +1004,21 @@ static int cubic_roots01(const double c[4], double* roots) {
 #define CCD_TOUCH 1e-9
 /* Smallest pair distance the forward step trusts (metres). */
 #define ORC_D_FLOOR 1e-10
-int orc_ccd(int kind, const double* x0, const double* x1, double* toi) {
+/* Vertices 0..3 move linearly from x0 to x1.  VT (a; i,j,k) and EE (a,b;
+ * c,d): the first time in [0,1] at which the four points are coplanar and the
+ * primitives touch (distance <= CCD_TOUCH); a vertex with a radius (rho[0]
+ * > 0) against a triangle is not handled (returns 0).  VV (a, b) with radii:
+ * the first time the centre distance reaches rho_a + rho_b. */
+int orc_ccd(int kind, const double* x0, const double* x1, const double* rho, double* toi) {
   int nv = kind == ORC_VV ? 2 : 4;
   v3 p0[4], d[4];
   for (int i = 0; i < nv; i++) { p0[i] = ld3(x0, i); d[i] = sub3(ld3(x1, i), p0[i]); }
-  /* swept boxes: the pair can only touch if they overlap */
+  double R = 0.0;
+  if (kind == ORC_VV) R = (rho ? rho[0] : 0.0) + (rho ? rho[1] : 0.0);
+  if (kind == ORC_VT && rho && rho[0] > 0.0) return 0;
+  /* swept boxes of the two primitives: they can only touch if these overlap */
   {
-    int na = kind == ORC_VT ? 1 : 2;
+    int na = kind == ORC_EE ? 2 : 1;
     box A, B;
     for (int k = 0; k < 3; k++) { A.lo[k] = INFINITY; A.hi[k] = -INFINITY; B.lo[k] = INFINITY; B.hi[k] = -INFINITY; }
     for (int i = 0; i < nv; i++) {
@@ -1022,16 +1030,19 @@ int orc_ccd(int kind, const double* x0, const double* x1, double* toi) {
           if (q[3 * h + k] > bx->hi[k]) bx->hi[k] = q[3 * h + k];
         }
     }
-    if (!box_near(&A, &B, CCD_TOUCH)) return 0;
+    if (!box_near(&A, &B, CCD_TOUCH + R)) return 0;
   }
   if (kind == ORC_VV) {
-    /* |a + t da - b - t db|^2 = CCD_TOUCH^2 has a root in [0,1]: closest
-     * approach over the segment */
+    /* |r + t v|^2 = R^2: the smaller root in [0,1], if the spheres reach contact */
     v3 r = sub3(p0[0], p0[1]), v = sub3(d[0], d[1]);
-    double vv = dot3(v, v), t = 0.0;
-    if (vv > 0.0) { t = -dot3(r, v) / vv; if (t < 0.0) t = 0.0; if (t > 1.0) t = 1.0; }
-    double m = norm3(add3(r, scl3(t, v)));
-    if (m <= CCD_TOUCH) { *toi = t; return 1; }
+    double rr = dot3(r, r), RR = (R + CCD_TOUCH) * (R + CCD_TOUCH);
+    if (rr <= RR) { *toi = 0.0; return 1; }
+    double vv = dot3(v, v), rv = dot3(r, v);
+    if (!(vv > 0.0) || rv >= 0.0) return 0;
+    double disc = rv * rv - vv * (rr - RR);
+    if (disc < 0.0) return 0;
+    double t = (-rv - sqrt(disc)) / vv;
+    if (t >= 0.0 && t <= 1.0) { *toi = t; return 1; }
     return 0;
   }
   /* coplanarity cubic f(t) = det[a1+t b1, a2+t b2, a3+t b3] */
@@ -1205,9 +1216,9 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
       for (int64_t i = 0; i < P.n; i++) {
         int32_t v4[4];
         int nv = pair_verts(t, P.k[i], v4);
-        double a0[12], a1[12], toi;
+        double a0[12], a1[12], rr[2] = {rho_of(t, v4[0]), nv == 2 ? rho_of(t, v4[1]) : 0.0}, toi;
         for (int k = 0; k < nv; k++) { st3(a0, k, ld3(x, v4[k])); st3(a1, k, ld3(xn, v4[k])); }
-        if (orc_ccd(key_kind(P.k[i]), a0, a1, &toi)) {
+        if (orc_ccd(key_kind(P.k[i]), a0, a1, rr, &toi)) {
           hit_any = 1;
           S.ccd_clamps++;
           for (int k = 0; k < nv; k++)

@@ -122,9 +122,10 @@ int orc_backward_once(const orc_topology* t, const orc_params* prm, const double
                       const double* y_in, const double* y_target, double* y_out);
 
 /* ---- CCD (comparison scheme of Sec. 5.1, used as a safety check) ---- */
-/* Vertices 0..3 move linearly from x0 to x1 (VT: a,i,j,k; EE: a,b,c,d).
- * Returns 1 and the first time of impact in [0,1] if they touch. */
-int orc_ccd(int kind, const double* x0, const double* x1, double* toi);
+/* Vertices 0..3 move linearly from x0 to x1 (VT: a,i,j,k; EE: a,b,c,d; VV:
+ * a,b with radii rho[0..1]; rho may be NULL).  Returns 1 and the first time
+ * of impact in [0,1] if they touch. */
+int orc_ccd(int kind, const double* x0, const double* x1, const double* rho, double* toi);
 
 /* ---- exact acceptance ---- */
 /* Number of intersecting non-adjacent primitive pairs in state x, decided by

@@ -52,3 +52,17 @@ def test_misses():
     x1 = x0.copy()
     x1[:2, 2] -= 0.5
     assert oracle.ccd(oracle.EE, x0, x1) == (False, None)
+
+
+@pytest.mark.parametrize("d0,v,R", [(0.5, 1.0, 0.0), (0.5, 1.0, 0.1), (0.02, 0.05, 0.004)])
+def test_spheres_meeting_head_on(d0, v, R):
+    # two spheres of radii R/2 approaching at relative speed v: contact at (d0 - R)/v
+    x0 = np.array([[0.0, 0, 0], [d0, 0, 0]])
+    x1 = np.array([[0.5 * v, 0, 0], [d0 - 0.5 * v, 0, 0]])
+    hit, toi = oracle.ccd(oracle.VV, x0, x1, [R / 2, R / 2])
+    # contact is registered 1e-9 m early (the touch tolerance): 1e-9 / v in time
+    assert hit and abs(toi - (d0 - R) / v) <= 1e-9 / v + 1e-12
+    # moving apart from a separated start: no contact
+    far = np.array([[0.0, 0, 0], [d0, 0, 0]])
+    apart = np.array([[-0.5 * v, 0, 0], [d0 + 0.5 * v, 0, 0]])
+    assert oracle.ccd(oracle.VV, far, apart, [R / 2, R / 2]) == (False, None)
