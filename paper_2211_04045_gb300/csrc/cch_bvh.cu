@@ -561,6 +561,88 @@ __global__ void k_finalize(Pool P, int nxt, int mode, double Dq) {
 }
 
 // ---------------------------------------------------------------------------
+// Acceptance of x^{t+1}: no non-adjacent edge crosses a triangle, no two
+// non-adjacent edges meet, and no point touches a triangle or another point.
+// Certain hits go to SceneState::isect, undecided pairs to ::uncertain.
+// ---------------------------------------------------------------------------
+constexpr double ACCEPT_TOL = 1e-11;
+
+__device__ __forceinline__ void accept_count(Pool& P, int s, int r) {
+  if (r == 1) atomicAdd((unsigned long long*)&P.ss[s].isect, 1ull);
+  else if (r == 2) atomicAdd((unsigned long long*)&P.ss[s].uncertain, 1ull);
+}
+
+__global__ void __launch_bounds__(128) k_accept_edges(Pool P) {
+  const BVH& B = P.be;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n; i += gridDim.x * blockDim.x) {
+    int e1 = B.ids[i];
+    int4 ea = P.ev[e1];
+    int s = ea.z;
+    if (!P.ss[s].active) continue;
+    dv3 alo, ahi;
+    int sc;
+    prim_box(P, 1, e1, alo, ahi, sc);
+    dv3 p = mk(P.x[ea.x]), q = mk(P.x[ea.y]);
+    // edge against triangles
+    traverse(P.bt, P.bt.sroot[s], f3rd(alo), f3ru(ahi), 0.f, -1, P.cnt, [&](int pos) {
+      int t = P.bt.ids[pos];
+      int4 tv = P.tv[t];
+      if (ea.x == tv.x || ea.x == tv.y || ea.x == tv.z || ea.y == tv.x || ea.y == tv.y || ea.y == tv.z) return;
+      dv3 lo, hi;
+      int sct;
+      prim_box(P, 0, t, lo, hi, sct);
+      if (!box_near(alo, ahi, lo, hi, 0.0)) return;
+      accept_count(P, s, seg_tri_test(p, q, mk(P.x[tv.x]), mk(P.x[tv.y]), mk(P.x[tv.z]), ACCEPT_TOL));
+    });
+    // edge against later edges
+    traverse(B, B.sroot[s], f3rd(alo), f3ru(ahi), 0.f, i, P.cnt, [&](int pos) {
+      int e2 = B.ids[pos];
+      int4 eb = P.ev[e2];
+      if (ea.x == eb.x || ea.x == eb.y || ea.y == eb.x || ea.y == eb.y) return;
+      dv3 lo, hi;
+      int sc2;
+      prim_box(P, 1, e2, lo, hi, sc2);
+      if (!box_near(alo, ahi, lo, hi, 0.0)) return;
+      dv3 c = mk(P.x[eb.x]), d = mk(P.x[eb.y]);
+      int r = 0;
+      if (o3f(p, q, c, d) == 2) {
+        double ps, pt;
+        r = d_ss(p, q, c, d, &ps, &pt) > ACCEPT_TOL ? 0 : 2;
+      }
+      accept_count(P, s, r);
+    });
+  }
+}
+
+__global__ void __launch_bounds__(128) k_accept_points(Pool P) {
+  for (int qi = blockIdx.x * blockDim.x + threadIdx.x; qi < P.nq; qi += gridDim.x * blockDim.x) {
+    int a = P.pts[qi];
+    int s = P.vscene[a];
+    if (!P.ss[s].active) continue;
+    dv3 xa = mk(P.x[a]);
+    double ra = P.rho[a];
+    dv3 alo = {xa.x - ra, xa.y - ra, xa.z - ra}, ahi = {xa.x + ra, xa.y + ra, xa.z + ra};
+    traverse(P.bt, P.bt.sroot[s], f3rd(alo), f3ru(ahi), __double2float_ru(1e-12), -1, P.cnt, [&](int pos) {
+      int t = P.bt.ids[pos];
+      int4 tv = P.tv[t];
+      if (a == tv.x || a == tv.y || a == tv.z) return;
+      double d = d_pt(xa, mk(P.x[tv.x]), mk(P.x[tv.y]), mk(P.x[tv.z]));
+      int r;
+      if (ra > 0.0) r = (d - ra) <= 1e-12 ? 1 : 0;
+      else r = d > ACCEPT_TOL ? 0 : 2;
+      accept_count(P, s, r);
+    });
+    double Dq = ra + P.sd[s].rho_max + 1e-12;
+    traverse(P.bv, P.bv.sroot[s], f3rd(xa), f3ru(xa), __double2float_ru(Dq), -1, P.cnt, [&](int pos) {
+      int b = P.vc[P.bv.ids[pos]];
+      if (b <= a || !(P.vflag[b] & VF_POINT)) return;
+      double g = (vnorm(vsub(xa, mk(P.x[b]))) - ra) - P.rho[b];
+      accept_count(P, s, g <= 1e-12 ? 1 : 0);
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 static int grid_for(long long n, int threads) {
@@ -693,6 +775,18 @@ void finalize_search(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) 
 void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) {
   for (int c = 0; c < 3; c++) query_class(R, c, nxt, mode, Dq, st);
   if (mode != 1) finalize_search(R, nxt, mode, Dq, st);
+}
+
+void accept_queries(Runtime& R, cudaStream_t st) {
+  Pool& P = R.pool;
+  if (P.ne) {
+    k_accept_edges<<<grid_for(P.ne, 128), 128, 0, st>>>(P);
+    R.launches++;
+  }
+  if (P.nq) {
+    k_accept_points<<<grid_for(P.nq, 128), 128, 0, st>>>(P);
+    R.launches++;
+  }
 }
 
 }  // namespace cch

@@ -214,6 +214,10 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
     d.hgamma = 0.5 * prm->gamma; d.eps = prm->eps; d.omega = prm->jacobi_omega;
     d.max_iters = prm->max_iters; d.gs_sweeps = prm->gs_sweeps; d.solver = prm->solver; d.ccd = prm->ccd_check;
     d.seed = prm->seed;
+    d.rho_max = 0.0;
+    if (t.point_radius)
+      for (int64_t v = 0; v < t.n_verts; v++)
+        if (t.point_radius[v] > d.rho_max) d.rho_max = t.point_radius[v];
     std::vector<uint8_t> f(t.n_verts, 0);
     for (int64_t i = 0; i < t.n_points; i++) f[t.points[i]] |= VF_POINT | VF_COLL;
     for (int64_t i = 0; i < 3 * t.n_tris; i++) f[t.tris[i]] |= VF_COLL;
@@ -245,6 +249,8 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   R.sweeps = prm->gs_sweeps;
   R.solver = prm->solver;
   R.ccd = prm->ccd_check;
+  R.accept = prm->accept_check;
+  R.validate = prm->validate_input;
   R.iters_per_check = prm->iters_per_launch > 0 ? prm->iters_per_launch : 16;
   R.coop_blocks = coop_grid(256);
 
@@ -255,7 +261,13 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(dalloc(R, &P.xf, nv));
   CK(cudaMemset(P.xf, 0, sizeof(float4) * nv));
   P.xp = nullptr;
-  if (prm->ccd_check) CK(dalloc(R, &P.xp, nv));
+  P.alpha = nullptr;
+  P.clampb = nullptr;
+  if (prm->ccd_check) {
+    CK(dalloc(R, &P.xp, nv));
+    CK(dalloc(R, &P.alpha, nv));
+    CK(dalloc(R, &P.clampb, nv));
+  }
   CK(upload(R, &P.im, im));
   CK(upload(R, &P.rho, rho));
   CK(dalloc(R, &P.r, nv));
@@ -415,6 +427,16 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
     prof_mark(R, PG_SETUP, 1, st);
     prof_collect(R);
     CK(cudaGetLastError());
+    if (R.validate) {
+      // the method assumes x^t is intersection-free (Sec. 3)
+      bvh_refit_all(R, st, 1);
+      accept_queries(R, st);
+      CK(cudaMemcpyAsync(R.h_ss, P.ss, sizeof(SceneState) * S->n_scenes, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int s = 0; s < S->n_scenes; s++)
+        if (R.h_ss[s].isect > 0) return CCH_E_INPUT_NOT_FEASIBLE;
+      reset_accept(R, st);
+    }
     if (R.use_graphs && !R.profiling && !R.graph) {
       if (capture_graph(R) != cudaSuccess) R.use_graphs = 0;
     }
@@ -455,6 +477,11 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
       cch_status g = grow_pairs(R);
       if (g != CCH_OK) return g;
       continue;
+    }
+    if (R.accept) {
+      // exact-filtered intersection test of x^{t+1}
+      bvh_refit_all(R, st, 1);
+      accept_queries(R, st);
     }
     prof_mark(R, PG_OUTPUT, 0, st);
     output(R, st);

@@ -32,6 +32,7 @@ struct SceneDesc {
   int q0, nq;      // point range
   int c0, nc;      // collision-vertex range (index into the vc list)
   double d_min, d_max, delta, sigma, hgamma, eps, omega;
+  double rho_max;  // largest point radius of the scene
   int max_iters, gs_sweeps, solver, ccd;
   uint64_t seed;
 };
@@ -133,6 +134,8 @@ struct Pool {
   int nv, nt, ne, nl, nq, nvc, nscene;
   int pair_cap, act_cap, cons_cap;
   P4 *x, *y, *yt, *xp;
+  double* alpha;           // CCD mode: step size of the forward step
+  unsigned long long* clampb;  // CCD mode: per-vertex clamp factor (double bits)
   float4* xf;              // x rounded to float (the FP32 distance pre-filter)
   double *im, *rho, *r;
   unsigned long long* Dv;
@@ -387,6 +390,160 @@ __device__ __forceinline__ float ftol(fv3 a, fv3 b, fv3 c, fv3 d) {
   float X = fmaxf(fmaxf(fmaxabs(a), fmaxabs(b)), fmaxf(fmaxabs(c), fmaxabs(d)));
   float M = fmaxf(fmaxf(fmaxabs(fsub(b, a)), fmaxabs(fsub(c, a))), fmaxabs(fsub(d, a)));
   return FILTER_TOL * (X + M) + 1e-30f;
+}
+
+// The exact candidate test (R3): on every axis fl(lo_b - hi_a) <= D and
+// fl(lo_a - hi_b) <= D.
+__device__ __forceinline__ bool box_near(dv3 alo, dv3 ahi, dv3 blo, dv3 bhi, double D) {
+  if (blo.x - ahi.x > D) return false;
+  if (alo.x - bhi.x > D) return false;
+  if (blo.y - ahi.y > D) return false;
+  if (alo.y - bhi.y > D) return false;
+  if (blo.z - ahi.z > D) return false;
+  if (alo.z - bhi.z > D) return false;
+  return true;
+}
+// ---------------------------------------------------------------------------
+// CCD of a linearly moving pair (the comparison scheme of Sec. 5.1, here the
+// per-iteration safety check).  Same arithmetic as the oracle's CCD.
+// ---------------------------------------------------------------------------
+constexpr double CCD_TOUCH = 1e-9;
+
+__device__ __forceinline__ double cubic_at(const double c[4], double t) {
+  return ((c[3] * t + c[2]) * t + c[1]) * t + c[0];
+}
+// roots of the coplanarity cubic in [0,1], ascending: the interval is cut at
+// the derivative's roots and sign changes on monotone pieces are bisected
+__device__ __forceinline__ int cubic_roots01(const double c[4], double* roots) {
+  double cuts[4];
+  int nc = 0;
+  cuts[nc++] = 0.0;
+  double A = 3.0 * c[3], B = 2.0 * c[2], C = c[1];
+  double crit[2];
+  int ncr = 0;
+  if (A != 0.0) {
+    double disc = B * B - 4.0 * A * C;
+    if (disc >= 0.0) {
+      double sq = sqrt(disc);
+      double r1 = (-B - sq) / (2.0 * A), r2 = (-B + sq) / (2.0 * A);
+      if (r1 > r2) { double tmp = r1; r1 = r2; r2 = tmp; }
+      crit[ncr++] = r1;
+      crit[ncr++] = r2;
+    }
+  } else if (B != 0.0) crit[ncr++] = -C / B;
+  for (int i = 0; i < ncr; i++)
+    if (crit[i] > 0.0 && crit[i] < 1.0 && crit[i] > cuts[nc - 1]) cuts[nc++] = crit[i];
+  cuts[nc++] = 1.0;
+  int nr = 0;
+  for (int i = 0; i + 1 < nc; i++) {
+    double a = cuts[i], b = cuts[i + 1], fa = cubic_at(c, a), fb = cubic_at(c, b);
+    if (fa == 0.0) { if (nr == 0 || roots[nr - 1] != a) roots[nr++] = a; continue; }
+    if (fb == 0.0) { roots[nr++] = b; continue; }
+    if ((fa < 0.0) == (fb < 0.0)) continue;
+    for (int it = 0; it < 80; it++) {
+      double m = 0.5 * (a + b), fm = cubic_at(c, m);
+      if (fm == 0.0) { a = b = m; break; }
+      if ((fm < 0.0) == (fa < 0.0)) { a = m; fa = fm; } else b = m;
+    }
+    roots[nr++] = 0.5 * (a + b);
+  }
+  return nr;
+}
+
+// kind VT (a; i,j,k) / EE (a,b; c,d) / VV (a,b) moving from p0 to p1
+__device__ __forceinline__ bool ccd_pair(int kind, const dv3* p0, const dv3* p1, double ra, double rb, double* toi) {
+  int nv = kind == K_VV ? 2 : 4;
+  dv3 d[4];
+  for (int i = 0; i < nv; i++) d[i] = vsub(p1[i], p0[i]);
+  double R = kind == K_VV ? ra + rb : 0.0;
+  if (kind == K_VT && ra > 0.0) return false;
+  {
+    int na = kind == K_EE ? 2 : 1;
+    dv3 alo = p0[0], ahi = p0[0], blo = p0[na], bhi = p0[na];
+    for (int i = 0; i < nv; i++) {
+      dv3 q[2] = {p0[i], p1[i]};
+      for (int h = 0; h < 2; h++) {
+        dv3& lo = i < na ? alo : blo;
+        dv3& hi = i < na ? ahi : bhi;
+        if (q[h].x < lo.x) lo.x = q[h].x; if (q[h].x > hi.x) hi.x = q[h].x;
+        if (q[h].y < lo.y) lo.y = q[h].y; if (q[h].y > hi.y) hi.y = q[h].y;
+        if (q[h].z < lo.z) lo.z = q[h].z; if (q[h].z > hi.z) hi.z = q[h].z;
+      }
+    }
+    if (!box_near(alo, ahi, blo, bhi, CCD_TOUCH + R)) return false;
+  }
+  if (kind == K_VV) {
+    dv3 r = vsub(p0[0], p0[1]), v = vsub(d[0], d[1]);
+    double rr = vdot(r, r), RR = (R + CCD_TOUCH) * (R + CCD_TOUCH);
+    if (rr <= RR) { *toi = 0.0; return true; }
+    double vv = vdot(v, v), rv = vdot(r, v);
+    if (!(vv > 0.0) || rv >= 0.0) return false;
+    double disc = rv * rv - vv * (rr - RR);
+    if (disc < 0.0) return false;
+    double t = (-rv - sqrt(disc)) / vv;
+    if (t >= 0.0 && t <= 1.0) { *toi = t; return true; }
+    return false;
+  }
+  dv3 a[3], b[3];
+  for (int k = 0; k < 3; k++) { a[k] = vsub(p0[k + 1], p0[0]); b[k] = vsub(d[k + 1], d[0]); }
+  double c[4];
+  c[0] = vdet(a[0], a[1], a[2]);
+  c[1] = (vdet(b[0], a[1], a[2]) + vdet(a[0], b[1], a[2])) + vdet(a[0], a[1], b[2]);
+  c[2] = (vdet(a[0], b[1], b[2]) + vdet(b[0], a[1], b[2])) + vdet(b[0], b[1], a[2]);
+  c[3] = vdet(b[0], b[1], b[2]);
+  double roots[16];
+  int nr;
+  if (c[0] == 0.0 && c[1] == 0.0 && c[2] == 0.0 && c[3] == 0.0) {
+    nr = 0;
+    for (int i = 0; i <= 8; i++) roots[nr++] = i / 8.0;
+  } else nr = cubic_roots01(c, roots);
+  for (int r = 0; r < nr; r++) {
+    double t = roots[r];
+    dv3 q[4];
+    for (int i = 0; i < 4; i++) q[i] = vadd(p0[i], vscl(t, d[i]));
+    double s, u;
+    double dist = kind == K_VT ? d_pt(q[0], q[1], q[2], q[3]) : d_ss(q[0], q[1], q[2], q[3], &s, &u);
+    if (dist <= CCD_TOUCH) { *toi = t; return true; }
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// acceptance: FP64 orientation with an error bound (45 ulps of the
+// permanent); 2 = the sign is not certain
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int o3f(dv3 a, dv3 b, dv3 c, dv3 d) {
+  dv3 u = vsub(b, a), v = vsub(c, a), w = vsub(d, a);
+  double det = vdet(u, v, w);
+  double perm = fabs(u.x) * (fabs(v.y * w.z) + fabs(v.z * w.y)) + fabs(u.y) * (fabs(v.x * w.z) + fabs(v.z * w.x)) +
+                fabs(u.z) * (fabs(v.x * w.y) + fabs(v.y * w.x));
+  double bound = 5e-15 * perm;
+  if (det > bound) return 1;
+  if (det < -bound) return -1;
+  return 2;
+}
+// 1: segment [p,q] meets triangle (a,b,c); 0: disjoint; 2: not decided.
+// When an orientation is uncertain the pair is (nearly) coplanar or passes
+// near the triangle's boundary, and then it is disjoint if the segment stays
+// more than tol from the triangle's edges and the endpoints from the triangle.
+__device__ __forceinline__ int seg_tri_test(dv3 p, dv3 q, dv3 a, dv3 b, dv3 c, double tol) {
+  int s1 = o3f(a, b, c, p), s2 = o3f(a, b, c, q);
+  bool unsure = s1 == 2 || s2 == 2;
+  if (!unsure) {
+    if (s1 == s2) return 0;
+    int t1 = o3f(p, q, a, b), t2 = o3f(p, q, b, c), t3 = o3f(p, q, c, a);
+    if (t1 != 2 && t2 != 2 && t3 != 2) {
+      int pos = (t1 > 0) + (t2 > 0) + (t3 > 0), neg = (t1 < 0) + (t2 < 0) + (t3 < 0);
+      return (pos && neg) ? 0 : 1;
+    }
+  }
+  double s, t;
+  double m = d_pt(p, a, b, c);
+  m = fmin(m, d_pt(q, a, b, c));
+  m = fmin(m, d_ss(p, q, a, b, &s, &t));
+  m = fmin(m, d_ss(p, q, b, c, &s, &t));
+  m = fmin(m, d_ss(p, q, c, a, &s, &t));
+  return m > tol ? 0 : 2;
 }
 
 // Smallest pair distance the forward step trusts: below it D_i/2 is no larger

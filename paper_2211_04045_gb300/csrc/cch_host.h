@@ -39,7 +39,7 @@ struct Runtime {
   cudaStream_t stream = nullptr;
   int scene_bits = 0;                // bits of the scene index in Morton keys
   int coop_blocks = 0;               // grid of the cooperative kernels
-  int sweeps = 1, solver = 0, ccd = 0;
+  int sweeps = 1, solver = 0, ccd = 0, accept = 0, validate = 0;
   int max_iters = 0;                 // max over scenes
   int iters_per_check = 16;
   int use_graphs = 1;
@@ -67,17 +67,6 @@ inline void prof_mark(Runtime& R, int g, int which, cudaStream_t st) {
   R.prof_used |= 1u << g;
 }
 
-// The exact candidate test (R3): on every axis fl(lo_b - hi_a) <= D and
-// fl(lo_a - hi_b) <= D.
-__device__ __forceinline__ bool box_near(dv3 alo, dv3 ahi, dv3 blo, dv3 bhi, double D) {
-  if (blo.x - ahi.x > D) return false;
-  if (alo.x - bhi.x > D) return false;
-  if (blo.y - ahi.y > D) return false;
-  if (alo.y - bhi.y > D) return false;
-  if (blo.z - ahi.z > D) return false;
-  if (alo.z - bhi.z > D) return false;
-  return true;
-}
 __device__ __forceinline__ bool searching(const Pool& P, int s) {
   const SceneState& S = P.ss[s];
   return S.active && !S.done && S.do_search;
@@ -147,6 +136,7 @@ void bvh_build_all(Runtime& R, cudaStream_t st);
 void bvh_refit_all(Runtime& R, cudaStream_t st, int force);
 void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st);
 void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t st);
+void accept_queries(Runtime& R, cudaStream_t st);
 void finalize_search(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st);
 
 }  // namespace cch

@@ -58,6 +58,7 @@ __global__ void k_vert_init(Pool P, double* const* ptrs) {
     P.yt[v] = b;
     P.r[v] = 1.0;
     P.Dv[v] = 0x7ff0000000000000ULL;
+    if (P.clampb) P.clampb[v] = 0x3ff0000000000000ULL;
     uint8_t f = P.vflag[v] & (uint8_t)~VF_STATIC;
     if (P.im[v] == 0.0 && a.x == b.x && a.y == b.y && a.z == b.z) f |= VF_STATIC;
     P.vflag[v] = f;
@@ -547,9 +548,68 @@ __global__ void k_forward(Pool P) {
       a = q < 1.0 ? q : 1.0;
     }
     dv3 xn = a == 1.0 ? yv : vadd(xv, vscl(a, dx));
-    if (P.xp) P.xp[v] = xv4;
     P.x[v] = {xn.x, xn.y, xn.z, 0.0};
     P.xf[v] = make_float4((float)xn.x, (float)xn.y, (float)xn.z, 0.f);
+    if (P.alpha) {
+      // CCD mode: tentative x; k_ccd_fix applies the clamps, r and the reductions
+      P.xp[v] = xv4;
+      P.alpha[v] = a;
+      continue;
+    }
+    double r = P.r[v] * (1.0 - a);
+    P.r[v] = r;
+    double mv = vnorm(vsub(xn, xv));
+    scene_max(&P.ss[s].move_bits, s, dbits(mv));
+    scene_max(&P.ss[s].rmax_bits, s, dbits(r));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Segment safety check (CCD mode): every pair of P is tested over its segment
+// x^(l) -> x^(l+1); a contact at time t* scales the step of the pair's
+// vertices by t*/2 (minimum over the pairs).
+// ---------------------------------------------------------------------------
+__global__ void k_ccd_pairs(Pool P, int nxt) {
+  int n = min(P.cnt->n_pairs[nxt], P.pair_cap);
+  const PairBuf B = P.pb[nxt];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int4 v = B.v[i];
+    int s = P.vscene[v.x];
+    const SceneState& S = P.ss[s];
+    if (!S.active || S.done) continue;
+    int kind = (int)(B.key[i] >> 62);
+    int vid[4] = {v.x, v.y, v.z, v.w};
+    int nv = kind == K_VV ? 2 : 4;
+    dv3 p0[4], p1[4];
+    for (int k = 0; k < nv; k++) {
+      p0[k] = mk(P.xp[vid[k]]);
+      p1[k] = mk(P.x[vid[k]]);
+    }
+    double toi;
+    if (ccd_pair(kind, p0, p1, P.rho[v.x], kind == K_VV ? P.rho[v.y] : 0.0, &toi)) {
+      unsigned long long cb = dbits(0.5 * toi);
+      for (int k = 0; k < nv; k++) atomicMin(&P.clampb[vid[k]], cb);
+      atomicAdd(&P.ss[s].ccd_clamps, 1);
+    }
+  }
+}
+
+__global__ void k_ccd_fix(Pool P) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
+    int s = P.vscene[v];
+    const SceneState& S = P.ss[s];
+    if (!S.active || S.done) continue;
+    double a = P.alpha[v];
+    double c = bitsd(P.clampb[v]);
+    dv3 xv = mk(P.xp[v]);
+    dv3 xn = mk(P.x[v]);
+    if (c < 1.0) {
+      a = c * a;
+      xn = vadd(xv, vscl(a, vsub(mk(P.y[v]), xv)));
+      P.x[v] = {xn.x, xn.y, xn.z, 0.0};
+      P.xf[v] = make_float4((float)xn.x, (float)xn.y, (float)xn.z, 0.f);
+      P.clampb[v] = dbits(1.0);
+    }
     double r = P.r[v] * (1.0 - a);
     P.r[v] = r;
     double mv = vnorm(vsub(xn, xv));
@@ -724,6 +784,11 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   prof_mark(R, PG_FORWARD, 0, st);
   k_forward<<<grid_for(P.nv, 256), 256, 0, st>>>(P);
+  if (P.alpha) {
+    k_ccd_pairs<<<grid_for(P.pair_cap, 128), 128, 0, st>>>(P, nxt);
+    k_ccd_fix<<<grid_for(P.nv, 256), 256, 0, st>>>(P);
+    R.launches += 2;
+  }
   prof_mark(R, PG_FORWARD, 1, st);
   prof_mark(R, PG_CONTROL, 0, st);
   k_control<<<1, 256, 0, st>>>(P, cur);
@@ -738,6 +803,15 @@ cudaError_t colour_edges(Runtime& R, cudaStream_t st, const ColourBufs& B) {
   EdgeAcc ea{P.lv, P.sd};
   cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
   return colour_greedy(R, ea, nullptr, P.nl, P.nl, P.lcol, P.lorder, P.lcstart, &P.cnt->pad, B, st);
+}
+
+__global__ void k_reset_accept(Pool P) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < P.nscene) P.ss[s].isect = P.ss[s].uncertain = 0;
+}
+void reset_accept(Runtime& R, cudaStream_t st) {
+  k_reset_accept<<<(R.pool.nscene + 127) / 128, 128, 0, st>>>(R.pool);
+  R.launches++;
 }
 
 void output(Runtime& R, cudaStream_t st) {
