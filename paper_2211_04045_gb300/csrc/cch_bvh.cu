@@ -427,7 +427,8 @@ __global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, dou
       fv3 f1 = fk(P.xf[tv.x]), f2 = fk(P.xf[tv.y]), f3 = fk(P.xf[tv.z]);
       float lower = __fsub_rd(__fsub_rd(f_pt(fa, f1, f2, f3), raf), ftol(fa, f1, f2, f3));
       if (lower >= Df) return;
-      push_survivor(P, K_VT, key, make_int4(a, tv.x, tv.y, tv.z));
+      if (P.mixed && mode == 0) emit_pair(P, nxt, s, key, make_int4(a, tv.x, tv.y, tv.z), (double)lower);
+      else push_survivor(P, K_VT, key, make_int4(a, tv.x, tv.y, tv.z));
     });
     if (mode == 0) add_candidates(P, s, ncand);
   }
@@ -470,7 +471,8 @@ __global__ void __launch_bounds__(128) k_query_ee(Pool P, int nxt, int mode, dou
       float lower = __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
       if (lower >= Df) return;
       int4 A = lo_e == e1 ? ea : eb, Bv = lo_e == e1 ? eb : ea;
-      push_survivor(P, K_EE, key, make_int4(A.x, A.y, Bv.x, Bv.y));
+      if (P.mixed && mode == 0) emit_pair(P, nxt, s, key, make_int4(A.x, A.y, Bv.x, Bv.y), (double)lower);
+      else push_survivor(P, K_EE, key, make_int4(A.x, A.y, Bv.x, Bv.y));
     });
     if (mode == 0) add_candidates(P, s, ncand);
   }
@@ -505,7 +507,12 @@ __global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, dou
         return;
       }
       ncand++;
-      push_survivor(P, K_VV, key, make_int4(a, b, -1, -1));
+      if (P.mixed && mode == 0) {
+        fv3 fa = fk(P.xf[a]), fb = fk(P.xf[b]);
+        fv3 dd = fsub(fa, fb);
+        float lower = __fsub_rd(__fsub_rd(sqrtf(fdot(dd, dd)), __double2float_ru(ra + rb)), ftol(fa, fb, fb, fb));
+        if (lower < Df) emit_pair(P, nxt, s, key, make_int4(a, b, -1, -1), (double)lower);
+      } else push_survivor(P, K_VV, key, make_int4(a, b, -1, -1));
     });
     if (mode == 0) add_candidates(P, s, ncand);
   }
@@ -516,7 +523,7 @@ __global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, dou
 // oracle's set), for every FP32-filter survivor.  The three kinds occupy
 // separate regions, so a warp almost always runs one kind's arithmetic.
 __global__ void k_finalize(Pool P, int nxt, int mode, double Dq) {
-  if (mode == 0 && !P.cnt->any_search) return;
+  if (mode == 0 && (!P.cnt->any_search || P.mixed)) return;
   int n0 = min(P.cnt->n_fcand[0], P.pair_cap), n1 = min(P.cnt->n_fcand[1], P.pair_cap);
   int n2 = min(P.cnt->n_fcand[2], P.pair_cap);
   int total = n0 + n1 + n2;

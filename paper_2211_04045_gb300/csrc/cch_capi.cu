@@ -260,6 +260,13 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaMemset(P.x, 0, sizeof(P4) * nv));
   CK(dalloc(R, &P.xf, nv));
   CK(cudaMemset(P.xf, 0, sizeof(float4) * nv));
+  P.mixed = prm->precision == CCH_PREC_MIXED;
+  P.yf = nullptr;
+  P.lgf = nullptr;
+  if (P.mixed) {
+    CK(dalloc(R, &P.yf, nv));
+    CK(dalloc(R, &P.lgf, nl));
+  }
   P.xp = nullptr;
   P.alpha = nullptr;
   P.clampb = nullptr;

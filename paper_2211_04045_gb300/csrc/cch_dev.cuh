@@ -105,6 +105,14 @@ struct __align__(16) Contact {
   unsigned long long key; // canonical identity (tie break)
 };
 
+// The same constraint in FP32 (mixed precision).
+struct __align__(16) ContactF {
+  int4 v;
+  float g[12];
+  float c0, den;
+  unsigned long long prio, key;
+};
+
 // BVH over one primitive class of the pool (triangles, edges or collision
 // vertices).  Internal node i has children left[i], right[i]; a child index
 // with the top bit set is a leaf (sorted position).  Child boxes are stored in
@@ -134,6 +142,9 @@ struct Pool {
   int nv, nt, ne, nl, nq, nvc, nscene;
   int pair_cap, act_cap, cons_cap;
   P4 *x, *y, *yt, *xp;
+  int mixed;               // 1: FP32 distances, contacts and projection (CCH_PREC_MIXED)
+  float4* yf;              // mixed: y in float
+  float4* lgf;             // mixed: edge-length constraint g (xyz), den (w) in float
   double* alpha;           // CCD mode: step size of the forward step
   unsigned long long* clampb;  // CCD mode: per-vertex clamp factor (double bits)
   float4* xf;              // x rounded to float (the FP32 distance pre-filter)
@@ -544,6 +555,100 @@ __device__ __forceinline__ int seg_tri_test(dv3 p, dv3 q, dv3 a, dv3 b, dv3 c, d
   m = fmin(m, d_ss(p, q, b, c, &s, &t));
   m = fmin(m, d_ss(p, q, c, a, &s, &t));
   return m > tol ? 0 : 2;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 versions of the contact constraints (mixed precision): the same
+// formulas as vt_cons / ee_cons / vv_cons evaluated in float.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ fv3 fadd3(fv3 a, fv3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ fv3 fscl3(float s, fv3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ fv3 fdiv3(fv3 a, float s) { return {a.x / s, a.y / s, a.z / s}; }
+__device__ __forceinline__ float fdet3(fv3 a, fv3 b, fv3 c) { return fdot(a, fcross(b, c)); }
+__device__ __forceinline__ float f_ps_t(fv3 p, fv3 a, fv3 b, float* tout) {
+  fv3 e = fsub(b, a), w = fsub(p, a), q = a;
+  float ee = fdot(e, e), t = 0.f;
+  if (ee > 0.f) {
+    t = fdot(w, e) / ee;
+    if (t <= 0.f) { t = 0.f; q = a; }
+    else if (t >= 1.f) { t = 1.f; q = b; }
+    else q = fadd3(a, fscl3(t, e));
+  }
+  *tout = t;
+  fv3 r = fsub(p, q);
+  return sqrtf(fdot(r, r));
+}
+__device__ __forceinline__ void f_ss_st(fv3 a, fv3 b, fv3 c, fv3 d, float* sout, float* tout) {
+  fv3 d1 = fsub(b, a), d2 = fsub(d, c), r = fsub(a, c);
+  float A = fdot(d1, d1), E = fdot(d2, d2), B = fdot(d1, d2), C = fdot(d1, r), F = fdot(d2, r);
+  float best = 3.4e38f, bs = 0.f, bt = 0.f, tt, dd;
+  float den = A * E - B * B;
+  if (den > 0.f) {
+    float s = (B * F - C * E) / den, t = (A * F - B * C) / den;
+    if (s >= 0.f && s <= 1.f && t >= 0.f && t <= 1.f) {
+      fv3 q = fsub(fadd3(a, fscl3(s, d1)), fadd3(c, fscl3(t, d2)));
+      best = sqrtf(fdot(q, q)); bs = s; bt = t;
+    }
+  }
+  dd = f_ps_t(a, c, d, &tt); if (dd < best) { best = dd; bs = 0.f; bt = tt; }
+  dd = f_ps_t(b, c, d, &tt); if (dd < best) { best = dd; bs = 1.f; bt = tt; }
+  dd = f_ps_t(c, a, b, &tt); if (dd < best) { best = dd; bs = tt; bt = 0.f; }
+  dd = f_ps_t(d, a, b, &tt); if (dd < best) { best = dd; bs = tt; bt = 1.f; }
+  *sout = bs; *tout = bt;
+}
+__device__ __forceinline__ bool volume_cons_f(const fv3 p[4], const float sg[4], fv3 n, float h, float* c0, fv3 g[4]) {
+  fv3 r[4];
+  for (int i = 0; i < 4; i++) r[i] = fadd3(p[i], fscl3(sg[i] * h, n));
+  fv3 c1 = fsub(p[1], p[0]), c2 = fsub(p[2], p[0]), c3 = fsub(p[3], p[0]);
+  float dx = fdet3(c1, c2, c3);
+  float dr = fdet3(fsub(r[1], r[0]), fsub(r[2], r[0]), fsub(r[3], r[0]));
+  if (!(fabsf(dr) >= 1e-30f)) return false;
+  *c0 = dx / dr - 1.f;
+  g[1] = fdiv3(fcross(c2, c3), dr);
+  g[2] = fdiv3(fcross(c3, c1), dr);
+  g[3] = fdiv3(fcross(c1, c2), dr);
+  g[0] = fscl3(-1.f, fadd3(fadd3(g[1], g[2]), g[3]));
+  return true;
+}
+__device__ __forceinline__ bool vt_cons_f(const fv3 p[4], float d, float delta, float* c0, fv3 g[4]) {
+  fv3 nrm = fcross(fsub(p[2], p[1]), fsub(p[3], p[1]));
+  float nn = fdot(nrm, nrm);
+  if (!(nn > 0.f)) return false;
+  fv3 nh = fdiv3(nrm, sqrtf(nn));
+  float side = fdot(nh, fsub(p[0], p[1])) < 0.f ? -1.f : 1.f;
+  const float sg[4] = {1.f, -1.f, -1.f, -1.f};
+  return volume_cons_f(p, sg, fscl3(side, nh), 0.5f * (delta - d), c0, g);
+}
+__device__ __forceinline__ bool ee_cons_f(const fv3 p[4], float d, float s, float t, float delta, float* c0, fv3 g[4]) {
+  fv3 e1 = fsub(p[1], p[0]), e2 = fsub(p[3], p[2]);
+  fv3 nx = fcross(e1, e2);
+  float nn = fdot(nx, nx);
+  fv3 dv = fsub(fadd3(p[0], fscl3(s, e1)), fadd3(p[2], fscl3(t, e2)));
+  float L = sqrtf(fdot(dv, dv));
+  fv3 n;
+  if (L > 0.f) n = fdiv3(dv, L);
+  else if (nn > 0.f) n = fdiv3(nx, sqrtf(nn));
+  else return false;
+  if (nn < 1e-12f * (fdot(e1, e1) * fdot(e2, e2))) {
+    *c0 = d / delta - 1.f;
+    g[0] = fscl3((1.f - s) / delta, n);
+    g[1] = fscl3(s / delta, n);
+    g[2] = fscl3(-((1.f - t) / delta), n);
+    g[3] = fscl3(-(t / delta), n);
+    return true;
+  }
+  const float sg[4] = {1.f, 1.f, -1.f, -1.f};
+  return volume_cons_f(p, sg, n, 0.5f * (delta - d), c0, g);
+}
+__device__ __forceinline__ bool vv_cons_f(const fv3 p[2], float ra, float rb, float delta, float* c0, fv3 g[4]) {
+  fv3 dv = fsub(p[0], p[1]);
+  float L = sqrtf(fdot(dv, dv));
+  if (!(L > 0.f)) return false;
+  float R = (ra + rb) + delta;
+  *c0 = L / R - 1.f;
+  g[0] = fdiv3(fdiv3(dv, L), R);
+  g[1] = fscl3(-1.f, g[0]);
+  return true;
 }
 
 // Smallest pair distance the forward step trusts: below it D_i/2 is no larger

@@ -56,6 +56,7 @@ __global__ void k_vert_init(Pool P, double* const* ptrs) {
     P.xf[v] = make_float4((float)a.x, (float)a.y, (float)a.z, 0.f);
     P.y[v] = b;
     P.yt[v] = b;
+    if (P.yf) P.yf[v] = make_float4((float)b.x, (float)b.y, (float)b.z, 0.f);
     P.r[v] = 1.0;
     P.Dv[v] = 0x7ff0000000000000ULL;
     if (P.clampb) P.clampb[v] = 0x3ff0000000000000ULL;
@@ -78,6 +79,7 @@ __global__ void k_edge_prep(Pool P) {
       o = {g.x, g.y, g.z, (P.im[l.x] + P.im[l.y]) * vdot(g, g)};
     }
     P.lg[e] = o;
+    if (P.lgf) P.lgf[e] = make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.w);
   }
 }
 
@@ -119,7 +121,13 @@ __global__ void k_refresh(Pool P, int cur, int nxt) {
     const SceneState& S = P.ss[s];
     if (!S.active || S.done || S.do_search) continue;
     unsigned long long key = B.key[i];
-    if (pair_lower32(P, key, v) >= __double2float_ru(S.D)) continue;
+    float lower = pair_lower32(P, key, v);
+    if (lower >= __double2float_ru(S.D)) continue;
+    if (P.mixed) {
+      // mixed precision: the FP32 lower bound is the pair's distance
+      if ((double)lower < S.D) emit_pair(P, nxt, s, key, v, (double)lower);
+      continue;
+    }
     double d = pair_dist(P, key, v);
     if (d < S.D) emit_pair(P, nxt, s, key, v, d);
   }
@@ -128,6 +136,59 @@ __global__ void k_refresh(Pool P, int cur, int nxt) {
 // ---------------------------------------------------------------------------
 // contact assembly at x^(l) (Sec. 4.1, linearisation of Sec. 4)
 // ---------------------------------------------------------------------------
+// mixed precision: the constraint in FP32 from the float positions
+__device__ __forceinline__ void assemble_f(Pool& P, int s, const SceneDesc& S, int kind, unsigned long long key,
+                                           int4 v, float d) {
+  fv3 q[4], g[4];
+  float c0 = 0.f;
+  bool ok;
+  q[0] = fk(P.xf[v.x]);
+  q[1] = fk(P.xf[v.y]);
+  int nv = 2;
+  float delta = (float)S.delta;
+  if (kind == K_VV) {
+    ok = vv_cons_f(q, (float)P.rho[v.x], (float)P.rho[v.y], delta, &c0, g);
+    g[2] = g[3] = {0.f, 0.f, 0.f};
+  } else {
+    q[2] = fk(P.xf[v.z]);
+    q[3] = fk(P.xf[v.w]);
+    nv = 4;
+    if (kind == K_VT) ok = vt_cons_f(q, d, delta, &c0, g);
+    else {
+      float ps, pt;
+      f_ss_st(q[0], q[1], q[2], q[3], &ps, &pt);
+      ok = ee_cons_f(q, d, ps, pt, delta, &c0, g);
+    }
+  }
+  if (!ok) {
+    atomicAdd((unsigned long long*)&P.ss[s].degenerate, 1ull);
+    return;
+  }
+  int vid[4] = {v.x, v.y, v.z, v.w};
+  float den = 0.f;
+  for (int k = 0; k < nv; k++) den = den + (float)P.im[vid[k]] * fdot(g[k], g[k]);
+  int idx = append_idx(&P.cnt->n_cons);
+  if (idx >= P.cons_cap) {
+    atomicOr(&P.cnt->overflow, OV_CONTACTS);
+    return;
+  }
+  ContactF c;
+  c.v = v;
+  for (int k = 0; k < 4; k++) {
+    c.g[3 * k] = g[k].x;
+    c.g[3 * k + 1] = g[k].y;
+    c.g[3 * k + 2] = g[k].z;
+  }
+  c.c0 = c0;
+  c.den = den;
+  c.key = key;
+  c.prio = splitmix64(S.seed ^ key);
+  ((ContactF*)P.cons)[idx] = c;
+  cg::coalesced_group gg = cg::coalesced_threads();
+  auto part = cg::labeled_partition(gg, s);
+  if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].contacts, (unsigned long long)part.size());
+}
+
 __global__ void k_assemble(Pool P, int nxt) {
   int n = P.cnt->n_active;
   if (n > P.act_cap) n = P.act_cap;
@@ -140,6 +201,10 @@ __global__ void k_assemble(Pool P, int nxt) {
     int s = P.vscene[v.x];
     const SceneDesc& S = P.sd[s];
     int kind = (int)(key >> 62);
+    if (P.mixed) {
+      assemble_f(P, s, S, kind, key, v, (float)d);
+      continue;
+    }
     dv3 q[4];
     dv3 g[4];
     double c0 = 0.0;
@@ -203,6 +268,11 @@ __global__ void k_assemble(Pool P, int nxt) {
 // ---------------------------------------------------------------------------
 struct ContactAcc {
   const Contact* c;
+  __device__ int4 verts(int i) const { return c[i].v; }
+  __device__ unsigned long long prio(int i) const { return c[i].prio; }
+};
+struct ContactFAcc {
+  const ContactF* c;
   __device__ int4 verts(int i) const { return c[i].v; }
   __device__ unsigned long long prio(int i) const { return c[i].prio; }
 };
@@ -441,6 +511,51 @@ __device__ __forceinline__ void pgs_contact(Pool& P, int ci, double* lam) {
   }
 }
 
+// mixed precision: the same updates in FP32 on the float copy of y
+__device__ __forceinline__ float4 ldyf(const Pool& P, int v) { return __ldcg(P.yf + v); }
+__device__ __forceinline__ void pgs_contact_f(Pool& P, int ci, double* lam) {
+  const ContactF& c = ((const ContactF*)P.cons)[ci];
+  if (!(c.den > 0.f)) return;
+  int vid[4] = {c.v.x, c.v.y, c.v.z, c.v.w};
+  int nv = vid[2] < 0 ? 2 : 4;
+  float w = c.c0;
+  float4 yv[4];
+  for (int k = 0; k < nv; k++) {
+    yv[k] = ldyf(P, vid[k]);
+    float4 xv = P.xf[vid[k]];
+    w = w + (c.g[3 * k] * (yv[k].x - xv.x) + c.g[3 * k + 1] * (yv[k].y - xv.y) + c.g[3 * k + 2] * (yv[k].z - xv.z));
+  }
+  float l0 = lam ? (float)lam[ci] : 0.f;
+  float tl = l0 - w / c.den;
+  float ln = tl > 0.f ? tl : 0.f;
+  float dl = ln - l0;
+  if (lam) lam[ci] = ln;
+  if (dl == 0.f) return;
+  for (int k = 0; k < nv; k++) {
+    float sc = (float)P.im[vid[k]] * dl;
+    float4 o = make_float4(yv[k].x + sc * c.g[3 * k], yv[k].y + sc * c.g[3 * k + 1], yv[k].z + sc * c.g[3 * k + 2], 0.f);
+    __stcg(P.yf + vid[k], o);
+  }
+}
+__device__ __forceinline__ void pgs_edge_f(Pool& P, int e, double* lam) {
+  int4 l = P.lv[e];
+  const SceneState& S = P.ss[l.z];
+  if (!S.active || S.done) return;
+  float4 gd = P.lgf[e];
+  if (!(gd.w > 0.f)) return;
+  float4 yi = ldyf(P, l.x), yj = ldyf(P, l.y);
+  float w = (float)P.sd[l.z].sigma - (gd.x * (yi.x - yj.x) + gd.y * (yi.y - yj.y) + gd.z * (yi.z - yj.z));
+  float l0 = lam ? (float)lam[e] : 0.f;
+  float tl = l0 - w / gd.w;
+  float ln = tl > 0.f ? tl : 0.f;
+  float dl = ln - l0;
+  if (lam) lam[e] = ln;
+  if (dl == 0.f) return;
+  float si = (float)P.im[l.x] * dl, sj = (float)P.im[l.y] * dl;
+  __stcg(P.yf + l.x, make_float4(yi.x - si * gd.x, yi.y - si * gd.y, yi.z - si * gd.z, 0.f));
+  __stcg(P.yf + l.y, make_float4(yj.x + sj * gd.x, yj.y + sj * gd.y, yj.z + sj * gd.z, 0.f));
+}
+
 __device__ __forceinline__ void pgs_edge(Pool& P, int e, double* lam) {
   int4 l = P.lv[e];
   const SceneState& S = P.ss[l.z];
@@ -480,7 +595,10 @@ __global__ void k_pgs_contacts(Pool P, int sweep) {
     cg::grid_group grid = cg::this_grid();
     if (lam && sweep == 0) grid.sync();
     for (; k < ncol && cs[k + 1] - cs[k] > PGS_TAIL; k++) {
-      for (int i = cs[k] + tid; i < cs[k + 1]; i += nth) pgs_contact(P, P.corder[i], lam);
+      for (int i = cs[k] + tid; i < cs[k + 1]; i += nth) {
+        if (P.mixed) pgs_contact_f(P, P.corder[i], lam);
+        else pgs_contact(P, P.corder[i], lam);
+      }
       grid.sync();
     }
   } else if (lam && sweep == 0) {
@@ -488,7 +606,10 @@ __global__ void k_pgs_contacts(Pool P, int sweep) {
   }
   if (blockIdx.x != 0) return;
   for (; k < ncol; k++) {
-    for (int i = cs[k] + threadIdx.x; i < cs[k + 1]; i += blockDim.x) pgs_contact(P, P.corder[i], lam);
+    for (int i = cs[k] + threadIdx.x; i < cs[k + 1]; i += blockDim.x) {
+      if (P.mixed) pgs_contact_f(P, P.corder[i], lam);
+      else pgs_contact(P, P.corder[i], lam);
+    }
     __syncthreads();
   }
 }
@@ -504,7 +625,10 @@ __global__ void k_pgs_edges(Pool P, int sweep) {
       __syncthreads();
     }
     for (int k = 0; k < P.nlcol; k++) {
-      for (int i = P.lcstart[k] + threadIdx.x; i < P.lcstart[k + 1]; i += blockDim.x) pgs_edge(P, P.lorder[i], lam);
+      for (int i = P.lcstart[k] + threadIdx.x; i < P.lcstart[k + 1]; i += blockDim.x) {
+        if (P.mixed) pgs_edge_f(P, P.lorder[i], lam);
+        else pgs_edge(P, P.lorder[i], lam);
+      }
       __syncthreads();
     }
     return;
@@ -515,7 +639,10 @@ __global__ void k_pgs_edges(Pool P, int sweep) {
     grid.sync();
   }
   for (int k = 0; k < P.nlcol; k++) {
-    for (int i = P.lcstart[k] + tid; i < P.lcstart[k + 1]; i += nth) pgs_edge(P, P.lorder[i], lam);
+    for (int i = P.lcstart[k] + tid; i < P.lcstart[k + 1]; i += nth) {
+      if (P.mixed) pgs_edge_f(P, P.lorder[i], lam);
+      else pgs_edge(P, P.lorder[i], lam);
+    }
     grid.sync();
   }
 }
@@ -540,7 +667,12 @@ __global__ void k_forward(Pool P) {
     if (!(Di >= D_FLOOR)) Di = 0.0;
     P.Dv[v] = 0x7ff0000000000000ULL;
     P4 xv4 = P.x[v];
-    dv3 xv = mk(xv4), yv = mk(P.y[v]);
+    dv3 yv;
+    if (P.yf) {
+      float4 f = P.yf[v];
+      yv = {(double)f.x, (double)f.y, (double)f.z};
+    } else yv = mk(P.y[v]);
+    dv3 xv = mk(xv4);
     dv3 dx = vsub(yv, xv);
     double nd = vnorm(dx), a = 1.0;
     if (nd > 0.0) {
@@ -605,7 +737,12 @@ __global__ void k_ccd_fix(Pool P) {
     dv3 xn = mk(P.x[v]);
     if (c < 1.0) {
       a = c * a;
-      xn = vadd(xv, vscl(a, vsub(mk(P.y[v]), xv)));
+      dv3 yv;
+      if (P.yf) {
+        float4 f = P.yf[v];
+        yv = {(double)f.x, (double)f.y, (double)f.z};
+      } else yv = mk(P.y[v]);
+      xn = vadd(xv, vscl(a, vsub(yv, xv)));
       P.x[v] = {xn.x, xn.y, xn.z, 0.0};
       P.xf[v] = make_float4((float)xn.x, (float)xn.y, (float)xn.z, 0.f);
       P.clampb[v] = dbits(1.0);
@@ -700,6 +837,9 @@ int coop_grid(int threads) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int a = 0, b = 0, c = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ci_poll<ContactAcc>, threads, 0);
+  int a2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, k_ci_poll<ContactFAcc>, threads, 0);
+  if (a2 < a) a = a2;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ci_poll<EdgeAcc>, threads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pgs_contacts, threads, 0);
   per = a < b ? a : b;
@@ -768,10 +908,14 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   prof_mark(R, PG_ASSEMBLE, 0, st);
   k_assemble<<<grid_for(P.act_cap, 128), 128, 0, st>>>(P, nxt);
   prof_mark(R, PG_ASSEMBLE, 1, st);
-  ContactAcc ca{P.cons};
   prof_mark(R, PG_COLOUR, 0, st);
-  cudaError_t e = colour_greedy(R, ca, &P.cnt->n_cons, 0, P.cons_cap, P.ccol, P.corder, P.cnt->colour_hist,
-                                &P.cnt->ncol, R.cbuf, st);
+  cudaError_t e;
+  if (P.mixed)
+    e = colour_greedy(R, ContactFAcc{(const ContactF*)P.cons}, &P.cnt->n_cons, 0, P.cons_cap, P.ccol, P.corder,
+                      P.cnt->colour_hist, &P.cnt->ncol, R.cbuf, st);
+  else
+    e = colour_greedy(R, ContactAcc{P.cons}, &P.cnt->n_cons, 0, P.cons_cap, P.ccol, P.corder, P.cnt->colour_hist,
+                      &P.cnt->ncol, R.cbuf, st);
   prof_mark(R, PG_COLOUR, 1, st);
   if (e != cudaSuccess) return e;
   prof_mark(R, PG_PGS, 0, st);
