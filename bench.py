@@ -146,6 +146,91 @@ def oracle_sample(sc, x_t, x_tilde, budget_s: float):
     return t1 / st["iterations"], st["iterations"], st["pairs_evaluated"]
 
 
+def serving_mix():
+    """Resident scenes of the serving workload: the paper's scene kinds at
+    2K-73K triangles."""
+    from paper_2211_04045_gb300 import scenes
+    return [scenes.cloth_over_sphere(n=16, side=0.5, sphere_subdiv=3, sphere_r=0.15, noise=0.5, seed=11),
+            scenes.cloth_over_sphere(n=32, seed=12),
+            scenes.two_cloths(n=48, side=0.4, sep=0.01, omega=6.0, noise=0.3, seed=13),
+            scenes.two_cloths(n=136, side=1.0, sep=0.01, omega=6.0, noise=0.3, seed=14),
+            scenes.tet_bodies(n_bodies=8, n=6, side=0.2, box=0.8, seed=15),
+            scenes.tube_knot(around=32, rings=121, r=0.008, helix_r=0.0095, pitch=0.03, ring_dz=0.002)]
+
+
+def run_serving(args):
+    """Poisson request stream served with continuous batching, against the
+    same requests run one at a time in plain FP64."""
+    import torch
+    from paper_2211_04045_gb300 import cch, scenes
+    dev = torch.device("cuda:0")
+    scs = serving_mix()
+    rng = np.random.default_rng(0)
+    N = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=N))
+    which = rng.integers(0, len(scs), size=N)
+    inputs = []
+    for i in range(N):
+        sc = scs[which[i]]
+        x, xt, v = scenes.initial(sc)
+        xt = xt + rng.normal(0.0, 1e-4, size=xt.shape) * (sc.inv_mass > 0)[:, None]
+        inputs.append((torch.tensor(x, device=dev), torch.tensor(xt, device=dev)))
+    # plain: one request at a time, FP64, one resident scene per kind
+    base = cch.params_for(scs[0], iters_per_launch=8)
+    plain = [cch.Scene(sc, base) for sc in scs]
+    for g, sc in zip(plain, scs):  # warm-up: builds and graph capture
+        x, xt, _ = scenes.initial(sc)
+        g.step(torch.tensor(x, device=dev), torch.tensor(xt, device=dev))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_ms = []
+    for i in range(N):
+        a = time.perf_counter()
+        plain[which[i]].step(inputs[i][0], inputs[i][1])
+        plain_ms.append(1000.0 * (time.perf_counter() - a))
+    plain_s = time.perf_counter() - t0
+    for g in plain:
+        g.close()
+    # served: requests arrive on the Poisson clock while others run
+    prm = cch.params_for(scs[0], precision=1 if args.precision == "mixed" else 0, iters_per_launch=8)
+    sv = cch.Server(80 << 30, prm, max_active=args.max_active)
+    ids = [sv.add_scene(sc) for sc in scs]
+    # one warm request per scene (pool build, graph capture)
+    outs = [torch.empty_like(inputs[0][0])]
+    for k, sc in enumerate(scs):
+        x, xt, _ = scenes.initial(sc)
+        o = torch.empty((sc.n_verts, 3), dtype=torch.float64, device=dev)
+        sv.wait(sv.submit(ids[k], torch.tensor(x, device=dev), torch.tensor(xt, device=dev), o))
+    outs = [torch.empty((scs[which[i]].n_verts, 3), dtype=torch.float64, device=dev) for i in range(N)]
+    tickets = []
+    t0 = time.perf_counter()
+    for i in range(N):
+        delay = arrivals[i] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(sv.submit(ids[which[i]], inputs[i][0], inputs[i][1], outs[i]))
+    lat = []
+    iters = []
+    for tk in tickets:
+        st, ms = sv.wait(tk)
+        lat.append(ms)
+        iters.append(st["iterations"])
+    served_s = time.perf_counter() - t0
+    sv.close()
+    tris = [len(sc.tris) for sc in scs]
+    out = {"metric": METRIC, "value": N / served_s, "unit": "steps/s", "n_gpus": 1, "steps": N, "warmup": len(scs),
+           "ms_per_step": 1000.0 * served_s / N, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+           "config": {"workload": f"serving_mix_{args.precision}", "requests": N, "rate_per_s": args.rate,
+                      "scene_tris": tris, "max_active": args.max_active, "budget_bytes": 80 << 30},
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "plain_fp64": {"value": N / plain_s, "unit": "steps/s", "p50_ms": float(np.percentile(plain_ms, 50)),
+                          "p99_ms": float(np.percentile(plain_ms, 99))},
+           "speedup_vs_plain": plain_s / served_s, "iterations_per_step": float(np.mean(iters))}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_reference(args):
     """CPU oracle as the reference arm (rank 0 only)."""
     rank, world, _ = dist_env()
@@ -194,6 +279,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--max-active", type=int, default=16, help="serving: requests batched at once")
     ap.add_argument("--ncu-warm", type=int, default=0, help="full chain steps before the --ncu-case step")
     ap.add_argument("--ncu-case", type=int, default=0,
                     help="profiling aid: run one step of the workload capped at this many iterations and exit "
@@ -201,6 +289,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "serve":
+        return run_serving(args)
 
     import torch
     rank, world, local = dist_env()

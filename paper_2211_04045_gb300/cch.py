@@ -279,3 +279,54 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Resident scenes plus a request loop with continuous batching (C ABI
+    cch_server_*).  Requests take device tensors that must stay alive until
+    wait() returns."""
+
+    def __init__(self, hbm_budget_bytes: int, prm: Optional[Params] = None, max_active: int = 8, stream=None):
+        self.prm = prm if prm is not None else params()
+        self.stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        _check(lib().cch_server_create(C.c_size_t(int(hbm_budget_bytes)), C.byref(self.prm), int(max_active),
+                                       C.c_void_p(self.stream), C.byref(h)), "cch_server_create")
+        self.h = h
+        self.n = []
+        self._keep = {}
+
+    def add_scene(self, scene) -> int:
+        t = _Topo(scene)
+        sid = C.c_int32(-1)
+        _check(lib().cch_server_add_scene(self.h, C.byref(t.c), C.byref(sid)), "cch_server_add_scene")
+        self.n.append(t.n)
+        return sid.value
+
+    def submit(self, scene_id: int, x_t, x_tilde, out) -> int:
+        n = self.n[scene_id]
+        tk = C.c_uint64(0)
+        _check(lib().cch_server_submit(self.h, int(scene_id), C.c_void_p(_dev_ptr(x_t, n)),
+                                       C.c_void_p(_dev_ptr(x_tilde, n)), C.c_void_p(_dev_ptr(out, n)), C.byref(tk)),
+               "cch_server_submit")
+        self._keep[tk.value] = (x_t, x_tilde, out)
+        return tk.value
+
+    def wait(self, ticket: int):
+        st = StepStats()
+        lat = C.c_double(0.0)
+        rc = lib().cch_server_wait(self.h, C.c_uint64(ticket), C.byref(st), C.byref(lat))
+        self._keep.pop(ticket, None)
+        _check(rc, "cch_server_wait")
+        return st.as_dict(), lat.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cch_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -374,7 +374,7 @@ __device__ __forceinline__ float3 f3ru(dv3 a) {
 // A pair that the FP32 filter could not reject; the exact FP64 distance is
 // evaluated later by k_finalize with one pair per thread (full warps instead
 // of the few lanes still active inside a divergent traversal).
-__device__ __forceinline__ void push_survivor(Pool& P, int kind, unsigned long long key, int4 v) {
+__device__ __forceinline__ void push_survivor(Pool& P, int kind, unsigned long long key, int4 v, float lower) {
   int idx = append_idx(&P.cnt->n_fcand[kind]);
   if (idx >= P.pair_cap) {
     atomicOr(&P.cnt->overflow, OV_PAIRS);
@@ -383,6 +383,7 @@ __device__ __forceinline__ void push_survivor(Pool& P, int kind, unsigned long l
   size_t o = (size_t)kind * P.pair_cap + idx;
   P.fkey[o] = key;
   P.fv[o] = v;
+  if (P.fd) P.fd[o] = lower;
 }
 
 __device__ __forceinline__ void add_candidates(Pool& P, int s, long long n) {
@@ -427,8 +428,7 @@ __global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, dou
       fv3 f1 = fk(P.xf[tv.x]), f2 = fk(P.xf[tv.y]), f3 = fk(P.xf[tv.z]);
       float lower = __fsub_rd(__fsub_rd(f_pt(fa, f1, f2, f3), raf), ftol(fa, f1, f2, f3));
       if (lower >= Df) return;
-      if (P.mixed && mode == 0) emit_pair(P, nxt, s, key, make_int4(a, tv.x, tv.y, tv.z), (double)lower);
-      else push_survivor(P, K_VT, key, make_int4(a, tv.x, tv.y, tv.z));
+      push_survivor(P, K_VT, key, make_int4(a, tv.x, tv.y, tv.z), lower);
     });
     if (mode == 0) add_candidates(P, s, ncand);
   }
@@ -471,8 +471,7 @@ __global__ void __launch_bounds__(128) k_query_ee(Pool P, int nxt, int mode, dou
       float lower = __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
       if (lower >= Df) return;
       int4 A = lo_e == e1 ? ea : eb, Bv = lo_e == e1 ? eb : ea;
-      if (P.mixed && mode == 0) emit_pair(P, nxt, s, key, make_int4(A.x, A.y, Bv.x, Bv.y), (double)lower);
-      else push_survivor(P, K_EE, key, make_int4(A.x, A.y, Bv.x, Bv.y));
+      push_survivor(P, K_EE, key, make_int4(A.x, A.y, Bv.x, Bv.y), lower);
     });
     if (mode == 0) add_candidates(P, s, ncand);
   }
@@ -507,12 +506,11 @@ __global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, dou
         return;
       }
       ncand++;
-      if (P.mixed && mode == 0) {
-        fv3 fa = fk(P.xf[a]), fb = fk(P.xf[b]);
-        fv3 dd = fsub(fa, fb);
-        float lower = __fsub_rd(__fsub_rd(sqrtf(fdot(dd, dd)), __double2float_ru(ra + rb)), ftol(fa, fb, fb, fb));
-        if (lower < Df) emit_pair(P, nxt, s, key, make_int4(a, b, -1, -1), (double)lower);
-      } else push_survivor(P, K_VV, key, make_int4(a, b, -1, -1));
+      fv3 fa = fk(P.xf[a]), fb = fk(P.xf[b]);
+      fv3 dd = fsub(fa, fb);
+      float lower = __fsub_rd(__fsub_rd(sqrtf(fdot(dd, dd)), __double2float_ru(ra + rb)), ftol(fa, fb, fb, fb));
+      if (lower >= Df) return;
+      push_survivor(P, K_VV, key, make_int4(a, b, -1, -1), lower);
     });
     if (mode == 0) add_candidates(P, s, ncand);
   }
@@ -523,7 +521,7 @@ __global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, dou
 // oracle's set), for every FP32-filter survivor.  The three kinds occupy
 // separate regions, so a warp almost always runs one kind's arithmetic.
 __global__ void k_finalize(Pool P, int nxt, int mode, double Dq) {
-  if (mode == 0 && (!P.cnt->any_search || P.mixed)) return;
+  if (mode == 0 && !P.cnt->any_search) return;
   int n0 = min(P.cnt->n_fcand[0], P.pair_cap), n1 = min(P.cnt->n_fcand[1], P.pair_cap);
   int n2 = min(P.cnt->n_fcand[2], P.pair_cap);
   int total = n0 + n1 + n2;
@@ -535,6 +533,12 @@ __global__ void k_finalize(Pool P, int nxt, int mode, double Dq) {
     int4 v = P.fv[o];
     int s = P.vscene[v.x];
     double D = mode == 0 ? P.sd[s].d_max : Dq;
+    if (P.mixed && mode == 0) {
+      // mixed precision: the FP32 lower bound is the pair's distance
+      double d = (double)P.fd[o];
+      if (d < D) emit_pair(P, nxt, s, key, v, d);
+      continue;
+    }
     dv3 a = mk(P.x[v.x]), b = mk(P.x[v.y]);
     double d;
     dv3 alo, ahi, blo, bhi;

@@ -8,8 +8,13 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/cch.h"
@@ -143,6 +148,8 @@ cudaError_t alloc_pairs(Runtime& R) {
   if ((e = dalloc_in(L, &P.act, P.act_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.fkey, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.fv, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
+  P.fd = nullptr;
+  if (P.mixed && (e = dalloc_in(L, &P.fd, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.corder, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.ccol, P.cons_cap)) != cudaSuccess) return e;
@@ -773,17 +780,315 @@ cch_status cch_get_profile(cch_scene* S, double* ms, int64_t* count, int32_t n) 
   return CCH_OK;
 }
 
-// ---- serving -------------------------------------------------------------
-struct cch_server;
-cch_status cch_server_create(size_t, const cch_params*, int32_t, void*, cch_server** out) {
-  if (out) *out = nullptr;
-  return CCH_E_STATE;
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: resident scenes, a request queue and continuous batching
+// ---------------------------------------------------------------------------
+namespace {
+
+struct OwnedTopo {  // host copy of a resident scene's topology
+  std::vector<double> inv_mass, radius;
+  std::vector<int32_t> tris, edges, len_edges, points;
+  cch_topology view() const {
+    cch_topology t{};
+    t.n_verts = (int64_t)inv_mass.size();
+    t.inv_mass = inv_mass.data();
+    t.point_radius = radius.empty() ? nullptr : radius.data();
+    t.n_tris = (int64_t)tris.size() / 3;
+    t.tris = tris.data();
+    t.n_edges = (int64_t)edges.size() / 2;
+    t.edges = edges.data();
+    t.n_len = (int64_t)len_edges.size() / 2;
+    t.len_edges = len_edges.data();
+    t.n_points = (int64_t)points.size();
+    t.points = points.data();
+    return t;
+  }
+};
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  int scene = -1;
+  const double* xt = nullptr;
+  const double* xl = nullptr;
+  double* xn = nullptr;
+  Clock::time_point t_submit, t_done;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  cch_status status = CCH_OK;
+  cch_step_stats stats{};
+};
+
+// Device bytes a resident scene is expected to need (pool arrays, BVHs,
+// pair-sized buffers at their initial capacity).
+size_t scene_bytes(const cch_topology& t) {
+  size_t prims = (size_t)(t.n_tris + t.n_edges + t.n_points);
+  return 512 * (size_t)t.n_verts + 1600 * prims + 128 * (size_t)t.n_len + (1 << 20);
 }
-cch_status cch_server_add_scene(cch_server*, const cch_topology*, int32_t*) { return CCH_E_STATE; }
-cch_status cch_server_submit(cch_server*, int32_t, const double*, const double*, double*, uint64_t*) {
-  return CCH_E_STATE;
+
+}  // namespace
+
+struct cch_server {
+  cch_params prm{};
+  size_t budget = 0, used = 0;
+  int max_active = 1;
+  cudaStream_t stream = nullptr;
+  std::vector<OwnedTopo> topos;
+  cch_scene* pool = nullptr;      // built from every resident scene
+  int pool_scenes = 0;            // scenes the pool was built with
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, Request> reqs;
+  std::vector<int64_t> running;   // per scene: ticket in flight, or -1
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  cch_status fatal = CCH_OK;
+  std::thread th;
+};
+
+namespace {
+
+// Runs on the server's thread.  Between graph launches it retires finished
+// requests and admits queued ones into free slots; admitted scenes start at
+// iteration 0 while the others continue (per-scene loop state).
+void server_loop(cch_server* sv) {
+  std::unique_lock<std::mutex> lk(sv->mu);
+  int cur = 0;
+  std::vector<int> ends;
+  while (!sv->stop) {
+    int n_running = 0;
+    for (int64_t t : sv->running) n_running += t >= 0;
+    // rebuild the pool when scenes were added and nothing is in flight
+    if (n_running == 0 && (!sv->pool || sv->pool_scenes != (int)sv->topos.size()) && !sv->topos.empty()) {
+      if (sv->pool) cch_destroy(sv->pool);
+      sv->pool = nullptr;
+      std::vector<cch_topology> views;
+      for (auto& t : sv->topos) views.push_back(t.view());
+      int ns = (int)views.size();
+      lk.unlock();
+      cch_scene* p = nullptr;
+      cch_status st = cch_create_batch(views.data(), ns, &sv->prm, sv->stream, &p);
+      lk.lock();
+      if (st != CCH_OK) {
+        sv->fatal = st;
+        for (auto& kv : sv->reqs)
+          if (kv.second.state == 0) { kv.second.state = 2; kv.second.status = st; kv.second.t_done = Clock::now(); }
+        sv->queue.clear();
+        sv->cv_done.notify_all();
+        sv->cv_work.wait(lk);
+        continue;
+      }
+      sv->pool = p;
+      sv->pool_scenes = ns;
+      sv->running.assign(ns, -1);
+      // nothing runs: the shared counters start clean
+      cudaMemsetAsync(p->R.pool.cnt, 0, sizeof(Counters), sv->stream);
+      cudaMemsetAsync(p->R.pool.ss, 0, sizeof(SceneState) * ns, sv->stream);
+      cur = 0;
+    }
+    // admit queued requests into free slots
+    std::vector<int> starting;
+    for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+      Request& r = sv->reqs[*it];
+      if (r.scene < sv->pool_scenes && sv->running[r.scene] < 0 && n_running < sv->max_active) {
+        sv->running[r.scene] = (int64_t)*it;
+        r.state = 1;
+        starting.push_back(r.scene);
+        n_running++;
+        it = sv->queue.erase(it);
+      } else ++it;
+    }
+    if (n_running == 0) {
+      sv->cv_work.wait(lk);
+      continue;
+    }
+    cch_scene* S = sv->pool;
+    Runtime& R = S->R;
+    Pool& P = R.pool;
+    cudaStream_t st = sv->stream;
+    for (int s : starting) {
+      Request& r = sv->reqs[(uint64_t)sv->running[s]];
+      R.h_ptrs[3 * s] = (double*)r.xt;
+      R.h_ptrs[3 * s + 1] = (double*)r.xl;
+      R.h_ptrs[3 * s + 2] = r.xn;
+    }
+    lk.unlock();
+    cudaError_t e = cudaSuccess;
+    if (!starting.empty()) {
+      e = cudaMemcpyAsync(R.d_ptrs, R.h_ptrs, sizeof(double*) * 3 * S->n_scenes, cudaMemcpyHostToDevice, st);
+      static const int one = 1;
+      for (int s : starting)
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&P.ss[s].start, &one, sizeof(int), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) {
+        step_init(R, st, 2);
+        set_any_search(R, st);
+        bvh_build_all(R, st);
+        e = cudaGetLastError();
+      }
+    }
+    if (e == cudaSuccess && R.use_graphs && !R.graph && capture_graph(R) != cudaSuccess) R.use_graphs = 0;
+    // one launch boundary: G iterations for every running scene
+    for (int k = 0; k < R.iters_per_check && e == cudaSuccess; k += (R.use_graphs && R.graph) ? 2 : 1) {
+      if (R.use_graphs && R.graph) {
+        e = cudaGraphLaunch(R.graph, st);
+        R.launches += R.graph_launches;
+      } else {
+        e = iteration(R, cur, st);
+        cur = 1 - cur;
+      }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.h_ss, P.ss, sizeof(SceneState) * S->n_scenes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    bool regrow = e == cudaSuccess && (R.h_cnt->overflow & (OV_PAIRS | OV_CONTACTS));
+    bool broken = e != cudaSuccess || R.h_cnt->err || (R.h_cnt->overflow & (OV_COLOURS | OV_ROUNDS));
+    ends.clear();
+    if (!broken && !regrow)
+      for (int s = 0; s < S->n_scenes; s++)
+        if (R.h_ss[s].active && R.h_ss[s].done) {
+          output_scene(R, s, st);
+          static const int zero = 0;
+          cudaMemcpyAsync(&P.ss[s].active, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+          ends.push_back(s);
+        }
+    if (!ends.empty()) e = cudaStreamSynchronize(st);
+    if (regrow && grow_pairs(R) != CCH_OK) broken = true;
+    lk.lock();
+    auto now = Clock::now();
+    if (broken || e != cudaSuccess) {
+      // fail every request in flight; the pool is rebuilt for the next ones
+      for (size_t s = 0; s < sv->running.size(); s++)
+        if (sv->running[s] >= 0) {
+          Request& r = sv->reqs[(uint64_t)sv->running[s]];
+          r.state = 2;
+          r.status = e != cudaSuccess ? cuda_fail(e) : CCH_E_CAPACITY;
+          r.t_done = now;
+          sv->running[s] = -1;
+        }
+      cch_destroy(sv->pool);
+      sv->pool = nullptr;
+      sv->pool_scenes = 0;
+      cudaGetLastError();
+      sv->cv_done.notify_all();
+      continue;
+    }
+    if (regrow) {
+      // larger buffers: every request in flight starts again from its inputs
+      for (size_t s = 0; s < sv->running.size(); s++)
+        if (sv->running[s] >= 0) {
+          sv->queue.push_front((uint64_t)sv->running[s]);
+          sv->reqs[(uint64_t)sv->running[s]].state = 0;
+          sv->running[s] = -1;
+        }
+      static const int zero = 0;
+      for (int s = 0; s < S->n_scenes; s++) cudaMemcpyAsync(&P.ss[s].active, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+      cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
+      cudaStreamSynchronize(st);
+      continue;
+    }
+    for (int s : ends) {
+      Request& r = sv->reqs[(uint64_t)sv->running[s]];
+      fill_stats(R, R.h_ss[s], &r.stats, 0.f);
+      r.state = 2;
+      r.status = CCH_OK;
+      r.t_done = now;
+      r.stats.device_ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
+      sv->running[s] = -1;
+    }
+    if (!ends.empty()) sv->cv_done.notify_all();
+  }
 }
-cch_status cch_server_wait(cch_server*, uint64_t, cch_step_stats*, double*) { return CCH_E_STATE; }
-cch_status cch_server_destroy(cch_server*) { return CCH_E_STATE; }
+
+}  // namespace
+
+extern "C" {
+
+cch_status cch_server_create(size_t hbm_budget_bytes, const cch_params* prm, int32_t max_active, void* cuda_stream,
+                             cch_server** out) {
+  if (!out || max_active <= 0 || hbm_budget_bytes == 0) return CCH_E_INVALID_ARG;
+  *out = nullptr;
+  cch_status v = validate_params(prm);
+  if (v != CCH_OK) return v;
+  cch_server* sv = new cch_server();
+  sv->prm = *prm;
+  sv->budget = hbm_budget_bytes;
+  sv->max_active = max_active;
+  sv->stream = (cudaStream_t)cuda_stream;
+  sv->th = std::thread(server_loop, sv);
+  *out = sv;
+  return CCH_OK;
+}
+
+cch_status cch_server_add_scene(cch_server* sv, const cch_topology* topo, int32_t* scene_id) {
+  if (!sv || !scene_id) return CCH_E_INVALID_ARG;
+  cch_status v = validate_topology(topo);
+  if (v != CCH_OK) return v;
+  size_t need = scene_bytes(*topo);
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->used + need > sv->budget) return CCH_E_BUDGET;
+  OwnedTopo t;
+  t.inv_mass.assign(topo->inv_mass, topo->inv_mass + topo->n_verts);
+  if (topo->point_radius) t.radius.assign(topo->point_radius, topo->point_radius + topo->n_verts);
+  t.tris.assign(topo->tris, topo->tris + 3 * topo->n_tris);
+  t.edges.assign(topo->edges, topo->edges + 2 * topo->n_edges);
+  t.len_edges.assign(topo->len_edges, topo->len_edges + 2 * topo->n_len);
+  t.points.assign(topo->points, topo->points + topo->n_points);
+  sv->topos.push_back(std::move(t));
+  sv->used += need;
+  *scene_id = (int32_t)sv->topos.size() - 1;
+  sv->cv_work.notify_all();
+  return CCH_OK;
+}
+
+cch_status cch_server_submit(cch_server* sv, int32_t scene_id, const double* x_t, const double* x_tilde,
+                             double* x_next, uint64_t* ticket) {
+  if (!sv || !x_t || !x_tilde || !x_next || !ticket) return CCH_E_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (scene_id < 0 || scene_id >= (int32_t)sv->topos.size()) return CCH_E_INVALID_ARG;
+  if (sv->stop) return CCH_E_STATE;
+  uint64_t t = sv->next_ticket++;
+  Request r;
+  r.scene = scene_id;
+  r.xt = x_t;
+  r.xl = x_tilde;
+  r.xn = x_next;
+  r.t_submit = Clock::now();
+  sv->reqs[t] = r;
+  sv->queue.push_back(t);
+  *ticket = t;
+  sv->cv_work.notify_all();
+  return CCH_OK;
+}
+
+cch_status cch_server_wait(cch_server* sv, uint64_t ticket, cch_step_stats* stats, double* latency_ms) {
+  if (!sv) return CCH_E_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return CCH_E_INVALID_ARG;
+  sv->cv_done.wait(lk, [&] { return it->second.state == 2; });
+  Request r = it->second;
+  sv->reqs.erase(it);
+  if (stats) *stats = r.stats;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+  return r.status;
+}
+
+cch_status cch_server_destroy(cch_server* sv) {
+  if (!sv) return CCH_E_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    for (auto& kv : sv->reqs)
+      if (kv.second.state != 2) { kv.second.state = 2; kv.second.status = CCH_E_CANCELLED; }
+    sv->cv_work.notify_all();
+    sv->cv_done.notify_all();
+  }
+  if (sv->th.joinable()) sv->th.join();
+  if (sv->pool) cch_destroy(sv->pool);
+  delete sv;
+  return CCH_OK;
+}
 
 }  // extern "C"

@@ -42,6 +42,7 @@ struct SceneState {
   double D;                       // D^(l)
   int iter;                       // l
   int active;                     // takes part in the current step
+  int start;                      // server: (re)start this scene's step at the next launch
   int done;                       // loop of this step has ended
   int do_search;                  // iteration l runs a proximity search
   int converged;
@@ -169,6 +170,7 @@ struct Pool {
   int* act;                // active contact list: indices into the next pair buffer
   unsigned long long* fkey;  // FP32-filter survivors: 3 regions of pair_cap (VT, EE, VV)
   int4* fv;
+  float* fd;               // mixed precision: the survivor's FP32 distance lower bound
   Contact* cons;
   int* corder;             // contacts sorted by colour
   int* ccol;               // colour per contact

@@ -18,11 +18,13 @@ static int grid_for(long long n, int threads) {
 // step set-up
 // ---------------------------------------------------------------------------
 // per scene: D^(0) = 0 < D^min, so the first iteration searches (D <- D^max)
-__global__ void k_scene_init(Pool P, int only_active) {
+// mode 0: every scene becomes active and starts; mode 2: only scenes whose
+// start flag is set (a server admitting requests while others run)
+__global__ void k_scene_init(Pool P, int mode) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.nscene; s += gridDim.x * blockDim.x) {
     SceneState& S = P.ss[s];
-    if (only_active && !S.active) continue;
-    if (!only_active) S.active = 1;
+    if (mode == 2 && !S.start) continue;
+    S.active = 1;
     S.D = P.sd[s].d_max;
     S.iter = 0;
     S.done = 0;
@@ -43,10 +45,10 @@ __global__ void k_scene_init(Pool P, int only_active) {
 }
 
 // x^(0) = x_t, y^(0) = y^[k+1] = x_tilde, r^(0) = 1; static flags (R4)
-__global__ void k_vert_init(Pool P, double* const* ptrs) {
+__global__ void k_vert_init(Pool P, double* const* ptrs, int mode) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
     int s = P.vscene[v];
-    if (!P.ss[s].active) continue;
+    if (!P.ss[s].active || (mode == 2 && !P.ss[s].start)) continue;
     int i = v - P.sd[s].v0;
     const double* xt = ptrs[3 * s];
     const double* xl = ptrs[3 * s + 1];
@@ -67,10 +69,10 @@ __global__ void k_vert_init(Pool P, double* const* ptrs) {
 }
 
 // edge-length constraints of the step (R9): g = u / L0 from y^[k+1]
-__global__ void k_edge_prep(Pool P) {
+__global__ void k_edge_prep(Pool P, int mode) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.nl; e += gridDim.x * blockDim.x) {
     int4 l = P.lv[e];
-    if (!P.ss[l.z].active) continue;
+    if (!P.ss[l.z].active || (mode == 2 && !P.ss[l.z].start)) continue;
     dv3 d0 = vsub(mk(P.yt[l.x]), mk(P.yt[l.y]));
     double L0 = vnorm(d0);
     P4 o = {0.0, 0.0, 0.0, 0.0};
@@ -809,10 +811,10 @@ __global__ void k_control(Pool P, int cur) {
   }
 }
 
-__global__ void k_output(Pool P, double* const* ptrs) {
+__global__ void k_output(Pool P, double* const* ptrs, int only) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
     int s = P.vscene[v];
-    if (!P.ss[s].active) continue;
+    if (!P.ss[s].active || (only >= 0 && s != only)) continue;
     int i = v - P.sd[s].v0;
     double* xo = ptrs[3 * s + 2];
     P4 p = P.x[v];
@@ -871,14 +873,25 @@ cudaError_t colour_greedy(Runtime& R, Acc acc, const int* n_ptr, int fixed_n, in
   return cudaGetLastError();
 }
 
-void step_init(Runtime& R, cudaStream_t st, int only_active) {
+__global__ void k_clear_start(Pool P) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < P.nscene) P.ss[s].start = 0;
+}
+
+// mode 0: all scenes start (counters reset); mode 2: only the flagged scenes
+// start, the others keep their loop state and the shared counters
+void step_init(Runtime& R, cudaStream_t st, int mode) {
   Pool& P = R.pool;
-  cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
-  k_scene_init<<<(P.nscene + 127) / 128, 128, 0, st>>>(P, only_active);
-  k_vert_init<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.d_ptrs);
+  if (mode == 0) cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
+  k_scene_init<<<(P.nscene + 127) / 128, 128, 0, st>>>(P, mode);
+  k_vert_init<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.d_ptrs, mode);
   R.launches += 2;
   if (P.nl) {
-    k_edge_prep<<<grid_for(P.nl, 256), 256, 0, st>>>(P);
+    k_edge_prep<<<grid_for(P.nl, 256), 256, 0, st>>>(P, mode);
+    R.launches++;
+  }
+  if (mode == 2) {
+    k_clear_start<<<(P.nscene + 127) / 128, 128, 0, st>>>(P);
     R.launches++;
   }
 }
@@ -960,7 +973,15 @@ void reset_accept(Runtime& R, cudaStream_t st) {
 
 void output(Runtime& R, cudaStream_t st) {
   Pool& P = R.pool;
-  k_output<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.d_ptrs);
+  k_output<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.d_ptrs, -1);
+  R.launches++;
+}
+
+void output_scene(Runtime& R, int s, cudaStream_t st) {
+  Pool& P = R.pool;
+  const SceneDesc& d = R.sd[s];
+  (void)d;
+  k_output<<<grid_for(R.sd[s].nv, 256), 256, 0, st>>>(P, R.d_ptrs, s);
   R.launches++;
 }
 

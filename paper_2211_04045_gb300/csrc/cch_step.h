@@ -4,7 +4,8 @@
 
 namespace cch {
 int coop_grid(int threads);
-void step_init(Runtime& R, cudaStream_t st, int only_active);
+void step_init(Runtime& R, cudaStream_t st, int mode);
+void output_scene(Runtime& R, int s, cudaStream_t st);
 void set_any_search(Runtime& R, cudaStream_t st);
 cudaError_t iteration(Runtime& R, int cur, cudaStream_t st);
 cudaError_t colour_edges(Runtime& R, cudaStream_t st, const ColourBufs& B);

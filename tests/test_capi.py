@@ -73,3 +73,14 @@ def test_status_strings():
     L = cch.lib()
     for code in range(10):
         assert L.cch_status_string(code)
+
+
+def test_server_admission_by_budget():
+    # the budget check happens before any device work
+    sv = cch.Server(1 << 20, cch.params(), max_active=2, stream=0)
+    big = topo(n_verts=200000, inv_mass=np.ones(200000), len_edges=np.zeros((0, 2), np.int32),
+               points=np.zeros(0, np.int32))
+    with pytest.raises(cch.CchError) as e:
+        sv.add_scene(big)
+    assert e.value.code == 3
+    sv.close()
