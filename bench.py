@@ -409,16 +409,26 @@ def main():
 
     nvc = int(np.count_nonzero(np.isin(np.arange(n), np.concatenate([sc.tris.ravel(), sc.edges.ravel(),
                                                                         np.asarray(sc.points).ravel()]))))
-    T, E = len(sc.tris), len(sc.edges)
+    T, E, NL = len(sc.tris), len(sc.edges), len(sc.len_edges)
     searches = sum(s["searches"] for s in pstats)
     p_pairs = sum(s["pairs_evaluated"] for s in pstats)
+    p_cons = sum(s["active_contacts"] for s in pstats)
     p_iters = sum(s["iterations"] for s in pstats)
-    pairs_per_iter = p_pairs / max(1, p_iters)
-    # algorithmic bytes per kernel group over the profiled steps
+    ppi = p_pairs / max(1, p_iters)      # |P| per iteration
+    cpi = p_cons / max(1, p_iters)       # contacts per iteration
+    fp = 8 if args.precision == "fp64" else 4
+    # algorithmic bytes of each kernel group over the profiled step: what the
+    # method must read and write at least (positions 24 B per vertex in FP64,
+    # pair records 32 B, contact records 144 B in FP64 / 96 B mixed)
+    crec = 144 if args.precision == "fp64" else 96
     algo = {
-        "query_vt": searches * (24.0 * nvc + 12.0 * T) + 0.5 * 32.0 * pairs_per_iter * searches,
-        "query_ee": searches * (24.0 * nvc + 8.0 * E) + 0.5 * 32.0 * pairs_per_iter * searches,
-        "refresh": (p_iters - searches) * (32.0 * pairs_per_iter * 2 + 24.0 * min(n, 4 * pairs_per_iter)),
+        "query_vt": searches * (16.0 * nvc + 12.0 * T + 16.0 * nvc),
+        "query_ee": searches * (8.0 * E + 32.0 * nvc),
+        "finalize": p_iters * ppi * (24.0 + 96.0 + 32.0) * (searches / max(1, p_iters)),
+        "refresh": (p_iters - searches) * (32.0 * ppi * 2 + 24.0 * min(n, 4 * ppi)),
+        "assemble": p_iters * cpi * (4.0 + 32.0 + 4 * 3 * fp + crec),
+        "colour": p_iters * cpi * (24.0 * 4 + 48.0 * 3 + 16.0),
+        "pgs": p_iters * (cpi * (crec + 4 * 3 * (3 * fp)) + NL * (8.0 + 4 * fp + 4 * 3 * fp)),
         "forward": p_iters * 96.0 * n,
         "refit": searches * (24.0 * n + 12.0 * T + 8.0 * E),
     }
@@ -463,11 +473,12 @@ def main():
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        spi, its, pe = oracle_sample(sc, hx[0][0], hx[0][1], args.cpu_budget)
+        spi, its, pe = oracle_sample(sc, x0, xt0, args.cpu_budget)
         mean_it = float(np.mean(iters))
         cpu = {"value": 1.0 / (spi * mean_it), "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {its} iterations of timed step 0 ({spi * its:.1f} s), seconds per iteration "
-                         f"times the {mean_it:.1f} iterations per step of the timed run"}
+               "sample": f"first {its} iterations of the chain's first step ({spi * its:.1f} s), seconds per "
+                         f"iteration times the {mean_it:.1f} iterations per step of the timed run (later steps "
+                         f"hold more pairs, so this favours the oracle)"}
 
     if rank == 0:
         out = {"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
