@@ -761,11 +761,11 @@ int32_t orc_colour_greedy(int64_t n_c, const int32_t* verts, const int32_t* nv, 
 }
 
 static void colour_cons(cons* cs, int64_t n, const uint8_t* movable, int32_t* ncol_out) {
-  int32_t* verts = (int32_t*)malloc(sizeof(int32_t) * 4 * ((size_t)n + 1));
-  int32_t* nv = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
-  uint64_t* pr = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
-  uint64_t* ky = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
-  int32_t* col = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+  int32_t* verts = (int32_t*)calloc(4 * ((size_t)n + 1), sizeof(int32_t));
+  int32_t* nv = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+  uint64_t* pr = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+  uint64_t* ky = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+  int32_t* col = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
   for (int64_t i = 0; i < n; i++) {
     for (int k = 0; k < 4; k++) verts[4 * i + k] = cs[i].v[k];
     nv[i] = cs[i].nv; pr[i] = cs[i].prio; ky[i] = cs[i].key;
@@ -816,9 +816,18 @@ static void pgs_edge(cons* c, double sigma, double* y, const double* im) {
   st3(y, c->v[1], add3(ld3(y, c->v[1]), scl3(sj, c->g[0])));
 }
 
-/* Projected Jacobi (Sec. 4.3.2, R12): every multiplier from the same y; the
- * per-vertex sums taken in canonical constraint order (contacts by key,
- * then edges by index), scaled by omega. */
+static int cmp_cons_key(const void* a, const void* b) {
+  uint64_t ka = ((const cons*)a)->key, kb = ((const cons*)b)->key;
+  return ka < kb ? -1 : ka > kb;
+}
+
+/* Projected Jacobi (Sec. 4.3.2, R12).  Every change of multiplier is
+ * computed from the same y with the update of Eq. LCP,
+ * dl = max(0, lambda - w / den) - lambda, and the multiplier advances by
+ * omega * dl so that y - y^[start] stays the sum of m^-1 g lambda.  Each
+ * vertex sums m^-1 dl g over its constraints in canonical order: contacts by
+ * ascending pair key, then edge-length constraints by ascending edge index;
+ * then y += omega * sum.  The caller passes cc and ce sorted by key. */
 static void jacobi_sweep(cons* cc, int64_t nc, cons* ce, int64_t ne, double sigma, double omega,
                          const double* x, double* y, const double* im, int64_t n) {
   double* acc = (double*)calloc(3 * (size_t)n + 3, sizeof(double));
@@ -829,19 +838,20 @@ static void jacobi_sweep(cons* cc, int64_t nc, cons* ce, int64_t ne, double sigm
     if (!(c->den > 0.0)) continue;
     double w = c->c0;
     for (int k = 0; k < c->nv; k++) w = w + dot3(c->g[k], sub3(ld3(y, c->v[k]), ld3(x, c->v[k])));
-    double tl = 0.0 - w / c->den;
-    dls[i] = tl > 0.0 ? tl : 0.0;
+    double tl = c->lambda - w / c->den;
+    dls[i] = (tl > 0.0 ? tl : 0.0) - c->lambda;
   }
   for (int64_t i = 0; i < ne; i++) {
     cons* c = &ce[i];
     dls[nc + i] = 0.0;
     if (!(c->den > 0.0)) continue;
     double w = sigma - dot3(c->g[0], sub3(ld3(y, c->v[0]), ld3(y, c->v[1])));
-    double tl = 0.0 - w / c->den;
-    dls[nc + i] = tl > 0.0 ? tl : 0.0;
+    double tl = c->lambda - w / c->den;
+    dls[nc + i] = (tl > 0.0 ? tl : 0.0) - c->lambda;
   }
   for (int64_t i = 0; i < nc; i++) {
     if (dls[i] == 0.0) continue;
+    cc[i].lambda = cc[i].lambda + omega * dls[i];
     for (int k = 0; k < cc[i].nv; k++) {
       int32_t v = cc[i].v[k];
       st3(acc, v, add3(ld3(acc, v), scl3(im[v] * dls[i], cc[i].g[k])));
@@ -849,6 +859,7 @@ static void jacobi_sweep(cons* cc, int64_t nc, cons* ce, int64_t ne, double sigm
   }
   for (int64_t i = 0; i < ne; i++) {
     if (dls[nc + i] == 0.0) continue;
+    ce[i].lambda = ce[i].lambda + omega * dls[nc + i];
     int32_t a = ce[i].v[0], b = ce[i].v[1];
     st3(acc, a, sub3(ld3(acc, a), scl3(im[a] * dls[nc + i], ce[i].g[0])));
     st3(acc, b, add3(ld3(acc, b), scl3(im[b] * dls[nc + i], ce[i].g[0])));
@@ -929,6 +940,8 @@ static void backward(const orc_topology* t, const orc_params* prm, cons* cc, int
   for (int64_t i = 0; i < nc; i++) cc[i].lambda = 0.0;
   for (int64_t i = 0; i < ne; i++) ce[i].lambda = 0.0;
   if (prm->solver == 1) {
+    qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_key);
+    qsort(ce, (size_t)ne, sizeof(cons), cmp_cons_key);
     for (int s = 0; s < prm->gs_sweeps; s++)
       jacobi_sweep(cc, nc, ce, ne, prm->sigma, prm->jacobi_omega, x, y, t->inv_mass, t->n_verts);
     return;
