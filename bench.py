@@ -128,18 +128,18 @@ def min_iterations(x_t, x_tilde, d_max, gamma):
     return max(1, math.ceil(far / (0.5 * gamma * d_max)))
 
 
-def oracle_sample(sc, x_t, x_tilde, budget_s: float):
+def oracle_sample(sc, x_t, x_tilde, budget_s: float, solver: int = 0):
     """Times the oracle, as it stands, on the first iterations of one step.
     Returns (seconds per iteration, iterations timed, pairs evaluated)."""
     import oracle
     osc = oracle.OracleScene(sc)
-    prm = oracle.params_for(sc, max_iters=0)
+    prm = oracle.params_for(sc, max_iters=0, solver=solver)
     t0 = time.perf_counter()
     _, st, _ = oracle.handle_step(osc, prm, x_t, x_tilde)
     t1 = time.perf_counter() - t0
     m = int(max(1, min(64, budget_s / max(t1, 1e-6))))
     if m > 1:
-        prm = oracle.params_for(sc, max_iters=m - 1)
+        prm = oracle.params_for(sc, max_iters=m - 1, solver=solver)
         t0 = time.perf_counter()
         _, st, _ = oracle.handle_step(osc, prm, x_t, x_tilde)
         t1 = time.perf_counter() - t0
@@ -276,6 +276,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="two_cloths")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--solver", default="pgs", choices=["pgs", "jacobi"],
+                    help="backward step: coloured projected Gauss-Seidel or projected Jacobi (omega 0.5)")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
@@ -303,7 +305,8 @@ def main():
 
     from paper_2211_04045_gb300 import cch, scenes
     sc, wname = workload(args.config)
-    prm = cch.params_for(sc, precision=1 if args.precision == "mixed" else 0)
+    prm = cch.params_for(sc, precision=1 if args.precision == "mixed" else 0,
+                         solver=1 if args.solver == "jacobi" else 0)
     if args.ncu_case:
         x0, xt0, v0 = scenes.initial(sc)
         x, xt, v = (torch.tensor(a, device=dev) for a in (x0, xt0, v0))
@@ -473,7 +476,7 @@ def main():
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        spi, its, pe = oracle_sample(sc, x0, xt0, args.cpu_budget)
+        spi, its, pe = oracle_sample(sc, x0, xt0, args.cpu_budget, 1 if args.solver == "jacobi" else 0)
         mean_it = float(np.mean(iters))
         cpu = {"value": 1.0 / (spi * mean_it), "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": f"first {its} iterations of the chain's first step ({spi * its:.1f} s), seconds per "
@@ -484,7 +487,7 @@ def main():
         out = {"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-               "config": {"workload": f"{wname}_{args.precision}", "verts": n, "tris": T, "edges": E,
+               "config": {"workload": f"{wname}_{args.precision}" + ("_jacobi" if args.solver == "jacobi" else ""), "verts": n, "tris": T, "edges": E,
                           "len_edges": len(sc.len_edges), "dt": sc.dt, "l2": "flushed between steps (256 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single"},
                "contact_pairs_per_sec": world * pairs / (total_ms / 1000.0),

@@ -16,9 +16,11 @@
  *     after the result has been written (it synchronises that stream).
  *   - Topology and parameters are copied at creation; the caller keeps
  *     ownership of every pointer it passes.
- *   - Invalid arguments (NULL, negative sizes, out-of-range indices,
- *     non-finite coordinates) are rejected with CCH_E_INVALID_ARG before any
- *     device work.
+ *   - Invalid arguments (NULL, negative sizes, out-of-range indices) are
+ *     rejected with CCH_E_INVALID_ARG before any device work.  Non-finite
+ *     coordinates in x_t or x_tilde are detected on the device when the step
+ *     starts: that scene runs no iteration and the call (or the server
+ *     request) returns CCH_E_INVALID_ARG, x_next then being unspecified.
  *   - Not reaching ||r||_inf < eps within L iterations is NOT an error: the
  *     result is still intersection-free (Sec. 3, end of the Algorithm 1
  *     discussion) and stats.converged = 0 reports it.

@@ -28,6 +28,14 @@ static void st3(double* p, int64_t i, v3 v) { p[3 * i] = v.x; p[3 * i + 1] = v.y
 static v3 sub3(v3 a, v3 b) { v3 r = {a.x - b.x, a.y - b.y, a.z - b.z}; return r; }
 static v3 add3(v3 a, v3 b) { v3 r = {a.x + b.x, a.y + b.y, a.z + b.z}; return r; }
 static v3 scl3(double s, v3 a) { v3 r = {s * a.x, s * a.y, s * a.z}; return r; }
+/* x + a (y - x), the forward step of Eq. forward2: y itself at a = 1 and x
+ * itself at a = 0 (a vertex that does not move keeps its position exactly,
+ * even when y is not finite, R2c). */
+static v3 step_to(v3 x, v3 y, double a) {
+  if (a == 1.0) return y;
+  if (a == 0.0) return x;
+  return add3(x, scl3(a, sub3(y, x)));
+}
 static v3 div3(v3 a, double s) { v3 r = {a.x / s, a.y / s, a.z / s}; return r; }
 static double dot3(v3 a, v3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
 static v3 cross3(v3 a, v3 b) {
@@ -821,51 +829,67 @@ static int cmp_cons_key(const void* a, const void* b) {
   return ka < kb ? -1 : ka > kb;
 }
 
-/* Projected Jacobi (Sec. 4.3.2, R12).  Every change of multiplier is
- * computed from the same y with the update of Eq. LCP,
- * dl = max(0, lambda - w / den) - lambda, and the multiplier advances by
- * omega * dl so that y - y^[start] stays the sum of m^-1 g lambda.  Each
- * vertex sums m^-1 dl g over its constraints in canonical order: contacts by
- * ascending pair key, then edge-length constraints by ascending edge index;
- * then y += omega * sum.  The caller passes cc and ce sorted by key. */
+/* Projected Jacobi (Sec. 4.3.2, R12).  The paper notes that this variant
+ * needs under-relaxation to converge; summing the corrections of every
+ * constraint at a vertex overshoots by up to the number of constraints
+ * there.  The relaxation is therefore per constraint: omega_c = omega /
+ * n_max(c), where n_max(c) is the largest number of constraints (with a
+ * positive denominator) at any movable vertex of c, so that every vertex
+ * moves by at most omega times a convex combination of single-constraint
+ * corrections.  Every multiplier change comes from the same y with the
+ * update of Eq. LCP, dl = max(0, lambda - w / den) - lambda; the applied
+ * change is s_c = omega_c * dl and lambda advances by s_c, so that y stays
+ * its start plus the sum of m^-1 g lambda.  Each vertex sums m^-1 s_c g over
+ * its constraints in canonical order (contacts by ascending pair key, then
+ * edge-length constraints by ascending edge index) and adds the sum to y.
+ * The caller passes cc and ce sorted by key and the per-vertex counts. */
+static double jacobi_relax(const cons* c, double omega, const int32_t* nvc, const double* im) {
+  int32_t m = 0;
+  for (int k = 0; k < c->nv; k++)
+    if (im[c->v[k]] > 0.0 && nvc[c->v[k]] > m) m = nvc[c->v[k]];
+  return omega / (double)(m > 0 ? m : 1);
+}
+
 static void jacobi_sweep(cons* cc, int64_t nc, cons* ce, int64_t ne, double sigma, double omega,
-                         const double* x, double* y, const double* im, int64_t n) {
+                         const int32_t* nvc, const double* x, double* y, const double* im, int64_t n) {
   double* acc = (double*)calloc(3 * (size_t)n + 3, sizeof(double));
-  double* dls = (double*)malloc(sizeof(double) * ((size_t)(nc + ne) + 1));
+  double* sc = (double*)malloc(sizeof(double) * ((size_t)(nc + ne) + 1));
   for (int64_t i = 0; i < nc; i++) {
     cons* c = &cc[i];
-    dls[i] = 0.0;
+    sc[i] = 0.0;
     if (!(c->den > 0.0)) continue;
     double w = c->c0;
     for (int k = 0; k < c->nv; k++) w = w + dot3(c->g[k], sub3(ld3(y, c->v[k]), ld3(x, c->v[k])));
     double tl = c->lambda - w / c->den;
-    dls[i] = (tl > 0.0 ? tl : 0.0) - c->lambda;
+    double dl = (tl > 0.0 ? tl : 0.0) - c->lambda;
+    sc[i] = jacobi_relax(c, omega, nvc, im) * dl;
   }
   for (int64_t i = 0; i < ne; i++) {
     cons* c = &ce[i];
-    dls[nc + i] = 0.0;
+    sc[nc + i] = 0.0;
     if (!(c->den > 0.0)) continue;
     double w = sigma - dot3(c->g[0], sub3(ld3(y, c->v[0]), ld3(y, c->v[1])));
     double tl = c->lambda - w / c->den;
-    dls[nc + i] = (tl > 0.0 ? tl : 0.0) - c->lambda;
+    double dl = (tl > 0.0 ? tl : 0.0) - c->lambda;
+    sc[nc + i] = jacobi_relax(c, omega, nvc, im) * dl;
   }
   for (int64_t i = 0; i < nc; i++) {
-    if (dls[i] == 0.0) continue;
-    cc[i].lambda = cc[i].lambda + omega * dls[i];
+    if (sc[i] == 0.0) continue;
+    cc[i].lambda = cc[i].lambda + sc[i];
     for (int k = 0; k < cc[i].nv; k++) {
       int32_t v = cc[i].v[k];
-      st3(acc, v, add3(ld3(acc, v), scl3(im[v] * dls[i], cc[i].g[k])));
+      st3(acc, v, add3(ld3(acc, v), scl3(im[v] * sc[i], cc[i].g[k])));
     }
   }
   for (int64_t i = 0; i < ne; i++) {
-    if (dls[nc + i] == 0.0) continue;
-    ce[i].lambda = ce[i].lambda + omega * dls[nc + i];
+    if (sc[nc + i] == 0.0) continue;
+    ce[i].lambda = ce[i].lambda + sc[nc + i];
     int32_t a = ce[i].v[0], b = ce[i].v[1];
-    st3(acc, a, sub3(ld3(acc, a), scl3(im[a] * dls[nc + i], ce[i].g[0])));
-    st3(acc, b, add3(ld3(acc, b), scl3(im[b] * dls[nc + i], ce[i].g[0])));
+    st3(acc, a, sub3(ld3(acc, a), scl3(im[a] * sc[nc + i], ce[i].g[0])));
+    st3(acc, b, add3(ld3(acc, b), scl3(im[b] * sc[nc + i], ce[i].g[0])));
   }
-  for (int64_t v = 0; v < n; v++) st3(y, v, add3(ld3(y, v), scl3(omega, ld3(acc, v))));
-  free(acc); free(dls);
+  for (int64_t v = 0; v < n; v++) st3(y, v, add3(ld3(y, v), ld3(acc, v)));
+  free(acc); free(sc);
 }
 
 /* Edge-length constraints for the step (R9): every listed edge, u and L0
@@ -942,8 +966,19 @@ static void backward(const orc_topology* t, const orc_params* prm, cons* cc, int
   if (prm->solver == 1) {
     qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_key);
     qsort(ce, (size_t)ne, sizeof(cons), cmp_cons_key);
+    /* constraints with a positive denominator at each movable vertex */
+    int32_t* nvc = (int32_t*)calloc((size_t)t->n_verts + 1, sizeof(int32_t));
+    for (int64_t i = 0; i < nc; i++)
+      if (cc[i].den > 0.0)
+        for (int k = 0; k < cc[i].nv; k++)
+          if (t->inv_mass[cc[i].v[k]] > 0.0) nvc[cc[i].v[k]]++;
+    for (int64_t i = 0; i < ne; i++)
+      if (ce[i].den > 0.0)
+        for (int k = 0; k < 2; k++)
+          if (t->inv_mass[ce[i].v[k]] > 0.0) nvc[ce[i].v[k]]++;
     for (int s = 0; s < prm->gs_sweeps; s++)
-      jacobi_sweep(cc, nc, ce, ne, prm->sigma, prm->jacobi_omega, x, y, t->inv_mass, t->n_verts);
+      jacobi_sweep(cc, nc, ce, ne, prm->sigma, prm->jacobi_omega, nvc, x, y, t->inv_mass, t->n_verts);
+    free(nvc);
     return;
   }
   for (int s = 0; s < prm->gs_sweeps; s++) {
@@ -1217,9 +1252,11 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
       if (nd > 0.0) {
         double q = (hg * Di[v]) / nd;
         a = q < 1.0 ? q : 1.0;
+      } else if (nd != 0.0) {
+        a = 0.0; /* R2c: y not finite, the vertex does not move */
       }
       alpha[v] = a;
-      st3(xn, v, a == 1.0 ? yv : add3(xv, scl3(a, dx)));
+      st3(xn, v, step_to(xv, yv, a));
     }
     /* optional CCD safety check on each pair's segment; a hit scales the
      * step of the pair's vertices by half the time of impact */
@@ -1242,8 +1279,7 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
         for (int64_t v = 0; v < n; v++)
           if (clampf[v] < 1.0) {
             alpha[v] = clampf[v] * alpha[v];
-            v3 xv = ld3(x, v);
-            st3(xn, v, add3(xv, scl3(alpha[v], sub3(ld3(y, v), xv))));
+            st3(xn, v, step_to(ld3(x, v), ld3(y, v), alpha[v]));
           }
     }
     double mmax = 0.0, rmax = 0.0;

@@ -375,8 +375,8 @@ __device__ __forceinline__ float3 f3ru(dv3 a) {
 // evaluated later by k_finalize with one pair per thread (full warps instead
 // of the few lanes still active inside a divergent traversal).
 __device__ __forceinline__ void push_survivor(Pool& P, int kind, unsigned long long key, int4 v, float lower) {
-  int idx = append_idx(&P.cnt->n_fcand[kind]);
-  if (idx >= P.pair_cap) {
+  int idx = claim(&P.cnt->n_fcand[kind], P.pair_cap);
+  if (idx < 0) {
     atomicOr(&P.cnt->overflow, OV_PAIRS);
     return;
   }

@@ -157,6 +157,9 @@ cudaError_t alloc_pairs(Runtime& R) {
   if ((e = dalloc_in(L, &R.cbuf.iid, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.cbuf.rank, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.lam, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
+  P.jdl = nullptr;
+  if (R.solver == CCH_SOLVER_JACOBI && (e = dalloc_in(L, &P.jdl, (size_t)P.cons_cap + P.nl)) != cudaSuccess)
+    return e;
   return cudaSuccess;
 }
 
@@ -303,7 +306,25 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(dalloc(R, &P.cnt, 1));
   CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
   CK(dalloc(R, &P.vmask, (size_t)MASK_WORDS * nv));
-  CK(dalloc(R, &P.jacc, 3 * (size_t)nv));
+  P.vlstart = nullptr;
+  P.vllist = nullptr;
+  if (R.solver == CCH_SOLVER_JACOBI) {
+    // per-vertex lists of edge-length constraints in ascending edge order
+    // (the canonical summation order of the Jacobi update)
+    std::vector<int> vls((size_t)nv + 1, 0), vll(2 * (size_t)nl);
+    for (int e = 0; e < nl; e++) {
+      vls[lv[e].x + 1]++;
+      vls[lv[e].y + 1]++;
+    }
+    for (int v = 0; v < nv; v++) vls[v + 1] += vls[v];
+    std::vector<int> fill(vls.begin(), vls.end() - 1);
+    for (int e = 0; e < nl; e++) {
+      vll[fill[lv[e].x]++] = 2 * e;
+      vll[fill[lv[e].y]++] = 2 * e + 1;
+    }
+    CK(upload(R, &P.vlstart, vls));
+    CK(upload(R, &P.vllist, vll));
+  }
   CK(dalloc(R, &P.sbox, 2 * (size_t)n_scenes));
   CK(alloc_bvh(R, P.bt, nt, n_scenes));
   CK(alloc_bvh(R, P.be, ne, n_scenes));
@@ -505,6 +526,8 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
     prof_collect(R);
+    for (int s = 0; s < S->n_scenes; s++)
+      if (R.h_ss[s].bad_input) return CCH_E_INVALID_ARG;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, R.ev0, R.ev1);
     if (stats)
@@ -665,6 +688,7 @@ cch_status cch_query_pairs(cch_scene* S, const double* x, const double* x_ref, d
       continue;
     }
     int n = R.h_cnt->n_query;
+    if (n < 0) return CCH_E_CAPACITY;  // more than 2^31 results
     if (n > P.qcap) {
       // grow the inspection buffers and retry
       int cap2 = P.qcap;
@@ -745,6 +769,7 @@ cch_status cch_query_pairs_noalloc(cch_scene* S, const double* x, const double* 
   if (e != cudaSuccess) return cuda_fail(e);
   if (R.h_cnt->err) return CCH_E_CAPACITY;
   int64_t n = R.h_cnt->n_query;
+  if (n < 0) n = (int64_t)1 << 31;  // the counter passed 2^31
   *count = n;
   // more pairs than the array holds, or than the scene's pair buffers hold
   if (n > CCH_NOALLOC_MAX_PAIRS || (R.h_cnt->overflow & OV_PAIRS)) return CCH_E_CAPACITY;
@@ -992,7 +1017,7 @@ void server_loop(cch_server* sv) {
       Request& r = sv->reqs[(uint64_t)sv->running[s]];
       fill_stats(R, R.h_ss[s], &r.stats, 0.f);
       r.state = 2;
-      r.status = CCH_OK;
+      r.status = R.h_ss[s].bad_input ? CCH_E_INVALID_ARG : CCH_OK;
       r.t_done = now;
       r.stats.device_ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
       sv->running[s] = -1;

@@ -57,6 +57,8 @@ struct SceneState {
   int ccd_clamps;
   double final_r;
   long long isect, uncertain;
+  int bad_input;                  // x_t or x~ held a non-finite coordinate
+  int pad_;
 };
 
 // Device-wide counters and flags.
@@ -176,7 +178,9 @@ struct Pool {
   int* ccol;               // colour per contact
   unsigned long long* vmask;   // per vertex: MASK_WORDS x 64-bit used-colour masks
   double* lam;             // multipliers for gs_sweeps > 1 (contacts then edges)
-  double* jacc;            // projected Jacobi accumulators (3 per vertex)
+  double* jdl;             // projected Jacobi: dl per contact, then per edge (cons_cap + nl)
+  int* vlstart;            // projected Jacobi: per vertex, start into vllist (nv + 1)
+  int* vllist;             // its edge-length constraints, ascending: edge * 2 + end (0 = i, 1 = j)
   BVH bt, be, bv;          // triangles, edges, collision vertices
   float4* sbox;            // per scene: Morton normalisation box (lo, hi) x2
   unsigned long long* qkeys;   // inspection output

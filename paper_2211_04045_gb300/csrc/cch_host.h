@@ -86,12 +86,24 @@ __device__ __forceinline__ int append_idx(int* ctr) {
   return g.shfl(base, 0) + (int)g.thread_rank();
 }
 
+// Claims a slot below cap in an append counter, or returns -1 once the
+// buffer is full.  The counter is read before the atomic add, so it stops
+// growing soon after it reaches cap (only warps already past the read still
+// add) and can never wrap around, whatever the number of appends.
+__device__ __forceinline__ int claim(int* ctr, int cap) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = cap;
+  if (g.thread_rank() == 0 && *(volatile int*)ctr < cap) base = atomicAdd(ctr, (int)g.size());
+  int idx = g.shfl(base, 0) + (int)g.thread_rank();
+  return idx < cap ? idx : -1;
+}
+
 // Record one pair of P found at iteration l (search or refresh).
 // mode 0: normal; 1: inspection of candidates; 2: inspection of P.
 __device__ __forceinline__ void emit_pair(Pool& P, int nxt, int s, unsigned long long key, int4 v, double d) {
   const SceneDesc& S = P.sd[s];
-  int idx = append_idx(&P.cnt->n_pairs[nxt]);
-  if (idx >= P.pair_cap) {
+  int idx = claim(&P.cnt->n_pairs[nxt], P.pair_cap);
+  if (idx < 0) {
     atomicOr(&P.cnt->overflow, OV_PAIRS);
     return;
   }
@@ -114,15 +126,15 @@ __device__ __forceinline__ void emit_pair(Pool& P, int nxt, int s, unsigned long
     }
   }
   if (d < S.delta) {
-    int a = append_idx(&P.cnt->n_active);
-    if (a < P.act_cap) P.act[a] = idx;
+    int a = claim(&P.cnt->n_active, P.act_cap);
+    if (a >= 0) P.act[a] = idx;
     else atomicOr(&P.cnt->overflow, OV_CONTACTS);
   }
 }
 
 __device__ __forceinline__ void emit_query(Pool& P, unsigned long long key, double d) {
   int idx = append_idx(&P.cnt->n_query);
-  if (idx < P.qcap) {
+  if ((unsigned)idx < (unsigned)P.qcap) {
     P.qkeys[idx] = key;
     P.qdist[idx] = d;
   } else atomicOr(&P.cnt->overflow, OV_QUERY);

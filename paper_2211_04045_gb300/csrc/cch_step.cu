@@ -41,6 +41,7 @@ __global__ void k_scene_init(Pool P, int mode) {
     S.ccd_clamps = 0;
     S.final_r = 1.0;
     S.isect = S.uncertain = 0;
+    S.bad_input = 0;
   }
 }
 
@@ -54,6 +55,11 @@ __global__ void k_vert_init(Pool P, double* const* ptrs, int mode) {
     const double* xl = ptrs[3 * s + 1];
     P4 a = {xt[3 * i], xt[3 * i + 1], xt[3 * i + 2], 0.0};
     P4 b = {xl[3 * i], xl[3 * i + 1], xl[3 * i + 2], 0.0};
+    if (!(isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(b.x) && isfinite(b.y) && isfinite(b.z))) {
+      // the scene's step is not run; the call reports CCH_E_INVALID_ARG
+      P.ss[s].bad_input = 1;
+      P.ss[s].done = 1;
+    }
     P.x[v] = a;
     P.xf[v] = make_float4((float)a.x, (float)a.y, (float)a.z, 0.f);
     P.y[v] = b;
@@ -169,8 +175,8 @@ __device__ __forceinline__ void assemble_f(Pool& P, int s, const SceneDesc& S, i
   int vid[4] = {v.x, v.y, v.z, v.w};
   float den = 0.f;
   for (int k = 0; k < nv; k++) den = den + (float)P.im[vid[k]] * fdot(g[k], g[k]);
-  int idx = append_idx(&P.cnt->n_cons);
-  if (idx >= P.cons_cap) {
+  int idx = claim(&P.cnt->n_cons, P.cons_cap);
+  if (idx < 0) {
     atomicOr(&P.cnt->overflow, OV_CONTACTS);
     return;
   }
@@ -235,8 +241,8 @@ __global__ void k_assemble(Pool P, int nxt) {
     int vid[4] = {v.x, v.y, v.z, v.w};
     double den = 0.0;
     for (int k = 0; k < nv; k++) den = den + P.im[vid[k]] * vdot(g[k], g[k]);
-    int idx = append_idx(&P.cnt->n_cons);
-    if (idx >= P.cons_cap) {
+    int idx = claim(&P.cnt->n_cons, P.cons_cap);
+    if (idx < 0) {
       atomicOr(&P.cnt->overflow, OV_CONTACTS);
       continue;
     }
@@ -650,6 +656,252 @@ __global__ void k_pgs_edges(Pool P, int sweep) {
 }
 
 // ---------------------------------------------------------------------------
+// Backward step, projected Jacobi variant (Sec. 4.3.2, R12).  Every
+// multiplier change dl = max(0, lambda - w/den) - lambda is computed from the
+// same y.  Constraint c is under-relaxed by omega_c = omega / n_max(c), the
+// largest number of constraints at one of its movable vertices, so that a
+// vertex moves by at most omega times a convex combination of the
+// single-constraint corrections (an unrelaxed sum overshoots by up to the
+// vertex's constraint count and diverges).  The applied change
+// s_c = omega_c * dl also advances the multiplier.  Each vertex sums
+// m^-1 s_c g over its constraints in canonical order (contacts by ascending
+// pair key, then edge-length constraints by ascending index) and adds the sum
+// to y.  The per-vertex sums are segmented reductions over a vertex-major
+// incidence list sorted by key, so the result does not depend on the order in
+// which contacts were appended.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool scene_running(const Pool& P, int s) {
+  const SceneState& S = P.ss[s];
+  return S.active && !S.done;
+}
+
+// incidences (contact, movable vertex) of every contact that can move y
+__global__ void k_jac_count(Pool P, ColourBufs B) {
+  int n = min(P.cnt->n_cons, P.cons_cap);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    int4 v;
+    bool live;
+    if (P.mixed) {
+      const ContactF& cf = ((const ContactF*)P.cons)[c];
+      v = cf.v;
+      live = cf.den > 0.f;
+    } else {
+      v = P.cons[c].v;
+      live = P.cons[c].den > 0.0;
+    }
+    if (!live) continue;
+    int vv[4] = {v.x, v.y, v.z, v.w};
+    for (int k = 0; k < 4; k++)
+      if (movable(P, vv[k])) atomicAdd(&B.vstart[vv[k]], 1);
+  }
+}
+__global__ void k_jac_scatter(Pool P, ColourBufs B) {
+  int n = min(P.cnt->n_cons, P.cons_cap);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    int4 v;
+    unsigned long long key;
+    bool live;
+    if (P.mixed) {
+      const ContactF& cf = ((const ContactF*)P.cons)[c];
+      v = cf.v;
+      key = cf.key;
+      live = cf.den > 0.f;
+    } else {
+      v = P.cons[c].v;
+      key = P.cons[c].key;
+      live = P.cons[c].den > 0.0;
+    }
+    if (!live) continue;
+    int vv[4] = {v.x, v.y, v.z, v.w};
+    for (int k = 0; k < 4; k++)
+      if (movable(P, vv[k])) {
+        int slot = B.vstart[vv[k]] + atomicAdd(&B.vfill[vv[k]], 1);
+        B.iprio[slot] = key;
+        B.iid[slot] = 4 * c + k;
+      }
+  }
+}
+// place each incidence at its key rank inside its vertex's segment
+// (B.rank becomes the key-sorted incidence list; pair keys are unique)
+__global__ void k_jac_rank(Pool P, ColourBufs B) {
+  int total = B.vstart[P.nv];
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
+    int id = B.iid[s];
+    int4 v = P.mixed ? ((const ContactF*)P.cons)[id >> 2].v : P.cons[id >> 2].v;
+    int vv[4] = {v.x, v.y, v.z, v.w};
+    int vert = vv[id & 3];
+    int a = B.vstart[vert], b = B.vstart[vert + 1];
+    unsigned long long key = B.iprio[s];
+    int r = 0;
+    for (int t = a; t < b; t++) r += B.iprio[t] < key;
+    B.rank[a + r] = id;
+  }
+}
+
+// constraints at each movable vertex: its contacts (the scattered count in
+// vfill) plus its edge-length constraints with a positive denominator
+__global__ void k_jac_nv(Pool P, ColourBufs B) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
+    int m = 0;
+    if (P.vflag[v] & VF_MOVABLE) {
+      m = B.vfill[v];
+      for (int j = P.vlstart[v]; j < P.vlstart[v + 1]; j++) {
+        int e = P.vllist[j] >> 1;
+        m += P.mixed ? (P.lgf[e].w > 0.f) : (P.lg[e].w > 0.0);
+      }
+    }
+    B.vdone[v] = m;
+  }
+}
+__device__ __forceinline__ int nmax_at(const Pool& P, const ColourBufs& B, int v, int m) {
+  return (v >= 0 && (P.vflag[v] & VF_MOVABLE) && B.vdone[v] > m) ? B.vdone[v] : m;
+}
+__device__ __forceinline__ double relax(double omega, int m) { return omega / (double)(m > 0 ? m : 1); }
+
+// s = omega_c dl of every contact and edge-length constraint from the same y
+__global__ void k_jac_dl(Pool P, ColourBufs B, int sweep) {
+  int n = min(P.cnt->n_cons, P.cons_cap);
+  double* lam = P.sd[0].gs_sweeps > 1 ? P.lam : nullptr;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int ci = tid; ci < n; ci += nth) {
+    if (P.mixed) {
+      const ContactF& c = ((const ContactF*)P.cons)[ci];
+      float dl = 0.f;
+      if (c.den > 0.f) {
+        int vid[4] = {c.v.x, c.v.y, c.v.z, c.v.w};
+        int nv = vid[2] < 0 ? 2 : 4;
+        float w = c.c0;
+        for (int k = 0; k < nv; k++) {
+          float4 yv = P.yf[vid[k]], xv = P.xf[vid[k]];
+          w = w + (c.g[3 * k] * (yv.x - xv.x) + c.g[3 * k + 1] * (yv.y - xv.y) + c.g[3 * k + 2] * (yv.z - xv.z));
+        }
+        float l0 = lam && sweep > 0 ? (float)lam[ci] : 0.f;
+        float tl = l0 - w / c.den;
+        int m = 0;
+        for (int k = 0; k < nv; k++) m = nmax_at(P, B, vid[k], m);
+        dl = (float)P.sd[P.vscene[vid[0]]].omega / (float)(m > 0 ? m : 1) * ((tl > 0.f ? tl : 0.f) - l0);
+        if (lam) lam[ci] = (double)(l0 + dl);
+      }
+      P.jdl[ci] = (double)dl;
+      continue;
+    }
+    const Contact& c = P.cons[ci];
+    double dl = 0.0;
+    if (c.den > 0.0) {
+      int vid[4] = {c.v.x, c.v.y, c.v.z, c.v.w};
+      int nv = vid[2] < 0 ? 2 : 4;
+      double w = c.c0;
+      for (int k = 0; k < nv; k++) {
+        dv3 g = {c.g[3 * k], c.g[3 * k + 1], c.g[3 * k + 2]};
+        w = w + vdot(g, vsub(mk(P.y[vid[k]]), mk(P.x[vid[k]])));
+      }
+      double l0 = lam && sweep > 0 ? lam[ci] : 0.0;
+      double tl = l0 - w / c.den;
+      int m = 0;
+      for (int k = 0; k < nv; k++) m = nmax_at(P, B, vid[k], m);
+      dl = relax(P.sd[P.vscene[vid[0]]].omega, m) * ((tl > 0.0 ? tl : 0.0) - l0);
+      if (lam) lam[ci] = l0 + dl;
+    }
+    P.jdl[ci] = dl;
+  }
+  double* elam = lam ? lam + P.cons_cap : nullptr;
+  double* edl = P.jdl + P.cons_cap;
+  for (int e = tid; e < P.nl; e += nth) {
+    int4 l = P.lv[e];
+    double dl = 0.0;
+    if (!scene_running(P, l.z)) {
+      edl[e] = 0.0;
+      continue;
+    }
+    if (P.mixed) {
+      float4 gd = P.lgf[e];
+      float dlf = 0.f;
+      if (gd.w > 0.f) {
+        float4 yi = P.yf[l.x], yj = P.yf[l.y];
+        float w = (float)P.sd[l.z].sigma - (gd.x * (yi.x - yj.x) + gd.y * (yi.y - yj.y) + gd.z * (yi.z - yj.z));
+        float l0 = elam && sweep > 0 ? (float)elam[e] : 0.f;
+        float tl = l0 - w / gd.w;
+        int m = nmax_at(P, B, l.y, nmax_at(P, B, l.x, 0));
+        dlf = (float)P.sd[l.z].omega / (float)(m > 0 ? m : 1) * ((tl > 0.f ? tl : 0.f) - l0);
+        if (elam) elam[e] = (double)(l0 + dlf);
+      }
+      edl[e] = (double)dlf;
+      continue;
+    }
+    P4 gd = P.lg[e];
+    if (gd.w > 0.0) {
+      dv3 g = {gd.x, gd.y, gd.z};
+      double w = P.sd[l.z].sigma - vdot(g, vsub(mk(P.y[l.x]), mk(P.y[l.y])));
+      double l0 = elam && sweep > 0 ? elam[e] : 0.0;
+      double tl = l0 - w / gd.w;
+      int m = nmax_at(P, B, l.y, nmax_at(P, B, l.x, 0));
+      dl = relax(P.sd[l.z].omega, m) * ((tl > 0.0 ? tl : 0.0) - l0);
+      if (elam) elam[e] = l0 + dl;
+    }
+    edl[e] = dl;
+  }
+}
+
+// per-vertex segmented sum in canonical order, then y += omega * sum
+__global__ void k_jac_apply(Pool P, ColourBufs B) {
+  const double* edl = P.jdl + P.cons_cap;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
+    int s = P.vscene[v];
+    if (!scene_running(P, s)) continue;
+    double im = P.im[v];
+    int a = B.vstart[v], b = B.vstart[v + 1];
+    int ea = P.vlstart[v], eb = P.vlstart[v + 1];
+    if (!(P.vflag[v] & VF_MOVABLE)) a = b = ea = eb = 0;
+    if (P.mixed) {
+      float imf = (float)im;
+      float ax = 0.f, ay = 0.f, az = 0.f;
+      for (int j = a; j < b; j++) {
+        int id = B.rank[j];
+        float dl = (float)P.jdl[id >> 2];
+        if (dl == 0.f) continue;
+        const float* g = ((const ContactF*)P.cons)[id >> 2].g + 3 * (id & 3);
+        float sc = imf * dl;
+        ax = ax + sc * g[0];
+        ay = ay + sc * g[1];
+        az = az + sc * g[2];
+      }
+      for (int j = ea; j < eb; j++) {
+        int ent = P.vllist[j];
+        float dl = (float)edl[ent >> 1];
+        if (dl == 0.f) continue;
+        float4 g = P.lgf[ent >> 1];
+        float sc = (ent & 1) ? imf * dl : -(imf * dl);
+        ax = ax + sc * g.x;
+        ay = ay + sc * g.y;
+        az = az + sc * g.z;
+      }
+      float4 y = P.yf[v];
+      P.yf[v] = make_float4(y.x + ax, y.y + ay, y.z + az, 0.f);
+      continue;
+    }
+    dv3 acc = {0.0, 0.0, 0.0};
+    for (int j = a; j < b; j++) {
+      int id = B.rank[j];
+      double dl = P.jdl[id >> 2];
+      if (dl == 0.0) continue;
+      const double* g = P.cons[id >> 2].g + 3 * (id & 3);
+      acc = vadd(acc, vscl(im * dl, dv3{g[0], g[1], g[2]}));
+    }
+    for (int j = ea; j < eb; j++) {
+      int ent = P.vllist[j];
+      double dl = edl[ent >> 1];
+      if (dl == 0.0) continue;
+      P4 g = P.lg[ent >> 1];
+      dv3 t = vscl(im * dl, dv3{g.x, g.y, g.z});
+      acc = (ent & 1) ? vadd(acc, t) : vsub(acc, t);
+    }
+    P4 y = P.y[v];
+    dv3 yn = vadd(mk(y), acc);
+    P.y[v] = {yn.x, yn.y, yn.z, 0.0};
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Forward step, Eq. forward2 (R2): alpha_i = min(0.5 gamma D_i / |y_i - x_i|, 1)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void scene_max(unsigned long long* dst, int s, unsigned long long v) {
@@ -657,6 +909,14 @@ __device__ __forceinline__ void scene_max(unsigned long long* dst, int s, unsign
   auto part = cg::labeled_partition(g, s);
   unsigned long long m = cg::reduce(part, v, cg::greater<unsigned long long>());
   if (part.thread_rank() == 0) atomicMax(dst, m);
+}
+
+// x + a (y - x): y itself at a = 1, x itself at a = 0 (a vertex that does
+// not move keeps its position exactly, even when y is not finite)
+__device__ __forceinline__ dv3 step_to(dv3 x, dv3 y, double a) {
+  if (a == 1.0) return y;
+  if (a == 0.0) return x;
+  return vadd(x, vscl(a, vsub(y, x)));
 }
 
 __global__ void k_forward(Pool P) {
@@ -675,13 +935,14 @@ __global__ void k_forward(Pool P) {
       yv = {(double)f.x, (double)f.y, (double)f.z};
     } else yv = mk(P.y[v]);
     dv3 xv = mk(xv4);
-    dv3 dx = vsub(yv, xv);
-    double nd = vnorm(dx), a = 1.0;
+    double nd = vnorm(vsub(yv, xv)), a = 1.0;
     if (nd > 0.0) {
       double q = (P.sd[s].hgamma * Di) / nd;
       a = q < 1.0 ? q : 1.0;
+    } else if (nd != 0.0) {
+      a = 0.0;  // R2c: y not finite, the vertex does not move
     }
-    dv3 xn = a == 1.0 ? yv : vadd(xv, vscl(a, dx));
+    dv3 xn = step_to(xv, yv, a);
     P.x[v] = {xn.x, xn.y, xn.z, 0.0};
     P.xf[v] = make_float4((float)xn.x, (float)xn.y, (float)xn.z, 0.f);
     if (P.alpha) {
@@ -744,7 +1005,7 @@ __global__ void k_ccd_fix(Pool P) {
         float4 f = P.yf[v];
         yv = {(double)f.x, (double)f.y, (double)f.z};
       } else yv = mk(P.y[v]);
-      xn = vadd(xv, vscl(a, vsub(yv, xv)));
+      xn = step_to(xv, yv, a);
       P.x[v] = {xn.x, xn.y, xn.z, 0.0};
       P.xf[v] = make_float4((float)xn.x, (float)xn.y, (float)xn.z, 0.f);
       P.clampb[v] = dbits(1.0);
@@ -923,6 +1184,25 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   prof_mark(R, PG_ASSEMBLE, 1, st);
   prof_mark(R, PG_COLOUR, 0, st);
   cudaError_t e;
+  if (R.solver == 1) {  // projected Jacobi
+    const ColourBufs& B = R.cbuf;
+    cudaMemsetAsync(B.vstart, 0, sizeof(int) * ((size_t)P.nv + 1), st);
+    cudaMemsetAsync(B.vfill, 0, sizeof(int) * (size_t)P.nv, st);
+    k_jac_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, B);
+    k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
+    k_jac_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, B);
+    k_jac_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, B);
+    k_jac_nv<<<grid_for(P.nv, 256), 256, 0, st>>>(P, B);
+    prof_mark(R, PG_COLOUR, 1, st);
+    prof_mark(R, PG_PGS, 0, st);
+    for (int sw = 0; sw < R.sweeps; sw++) {
+      k_jac_dl<<<grid_for((long long)P.cons_cap + P.nl, 256), 256, 0, st>>>(P, B, sw);
+      k_jac_apply<<<grid_for(P.nv, 256), 256, 0, st>>>(P, B);
+    }
+    prof_mark(R, PG_PGS, 1, st);
+    R.launches += 5 + 2 * R.sweeps;
+    e = cudaGetLastError();
+  } else {
   if (P.mixed)
     e = colour_greedy(R, ContactFAcc{(const ContactF*)P.cons}, &P.cnt->n_cons, 0, P.cons_cap, P.ccol, P.corder,
                       P.cnt->colour_hist, &P.cnt->ncol, R.cbuf, st);
@@ -938,6 +1218,7 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     R.launches += 2;
   }
   prof_mark(R, PG_PGS, 1, st);
+  }
   if (e != cudaSuccess) return e;
   prof_mark(R, PG_FORWARD, 0, st);
   k_forward<<<grid_for(P.nv, 256), 256, 0, st>>>(P);

@@ -86,3 +86,22 @@ def test_acceptance_counts_match_oracle_on_intersecting_state(cuda):
     assert st["uncertain"] == 0
     assert st["intersections"] == expected
     gpu.close()
+
+
+def test_non_finite_input_rejected(cuda):
+    # a NaN or infinite coordinate is detected on the device: no iteration
+    # runs and the call returns CCH_E_INVALID_ARG; the scene stays usable
+    sc = scenes.two_cloths(n=12, side=0.11, sep=0.004, omega=3.0, noise=0.2, seed=6)
+    x, xt, _ = scenes.initial(sc)
+    gpu = cch.Scene(sc, cch.params_for(sc))
+    for which, k, val in (("x_tilde", 7, np.nan), ("x_t", 30, np.inf), ("x_tilde", 100, -np.inf)):
+        a, b = x.copy(), xt.copy()
+        (b if which == "x_tilde" else a)[k, 1] = val
+        with pytest.raises(cch.CchError) as e:
+            gpu.step(T(a, cuda), T(b, cuda))
+        assert e.value.code == 1, which
+    out, st = gpu.step(T(x, cuda), T(xt, cuda))
+    xo, so, _ = oracle.handle_step(oracle.OracleScene(sc), oracle.params_for(sc), x, xt)
+    assert np.max(np.abs(out.cpu().numpy() - xo)) <= 1e-9 * max(1.0, np.max(np.abs(xo)))
+    assert st["iterations"] == so["iterations"]
+    gpu.close()

@@ -1,18 +1,19 @@
 """Closed-form pins of the oracle's projected Jacobi variant (Sec. 4.3.2).
 
-Jacobi computes every multiplier change from the same y and applies
-omega times the per-vertex sum.  These pins fix the parts that a wrong
-implementation would change:
-  * one constraint alone: omega = 1 gives the Gauss-Seidel result exactly
-    (so the update itself is Eq. LCP's), omega scales the move linearly;
-  * a chain of two stretched edges: Jacobi moves both ends by half the
-    excess each while the shared middle vertex stays put (Gauss-Seidel would
-    move it), so the sum really is taken from one y;
-  * two copies of one edge on a vertex pinned at the other end: the excess
-    obeys e_{s+1} = (1 - 2 omega) e_s sweep after sweep, which holds only if
-    the multipliers accumulate (lambda += omega dl) and a negative dl can
-    pull back; with omega = 1 the multipliers hit the projection at zero and
-    the length alternates between two values.
+Jacobi computes every multiplier change from the same y; constraint c is
+under-relaxed by omega_c = omega / n_max(c), n_max(c) being the largest
+number of constraints at a movable vertex of c.  These pins fix the parts
+that a wrong implementation would change:
+  * one constraint alone (n = 1): omega = 1 gives the Gauss-Seidel result
+    exactly (so the update itself is Eq. LCP's), omega scales the move;
+  * a chain of two stretched edges (n = 1, 2, 1): each edge is relaxed by
+    omega / 2, both ends move by a quarter of omega times the excess, and the
+    shared middle vertex stays put (Gauss-Seidel would move it), so the sum
+    really is taken from one y;
+  * two copies of one edge on a vertex pinned at the other end (n = 2): the
+    excess obeys e_{s+1} = (1 - omega) e_s sweep after sweep, which holds
+    only if the multipliers accumulate (lambda += omega_c dl); omega = 1.5
+    overshoots, so every second sweep has dl < 0 and pulls back.
 """
 from types import SimpleNamespace as NS
 
@@ -58,7 +59,7 @@ def test_chain_moves_ends_not_middle(omega, sigma):
     y = np.array([0.0, 1.5, 3.0])[:, None] * L0 * U         # both edges at 1.5 L0
     sc = mini([1.0, 1.0, 1.0], len_edges=[[0, 1], [1, 2]])
     out = oracle.backward_once(oracle.OracleScene(sc), jacobi(sigma=sigma, jacobi_omega=omega), y0, y, y0)
-    move = 0.5 * omega * (1.5 - sigma) * L0
+    move = 0.25 * omega * (1.5 - sigma) * L0
     expect = np.array([move, 1.5 * L0, 3.0 * L0 - move])[:, None] * U
     assert np.max(np.abs(out - expect)) <= 1e-17
     # Gauss-Seidel differs: the middle vertex moves
@@ -66,7 +67,8 @@ def test_chain_moves_ends_not_middle(omega, sigma):
     assert np.linalg.norm(gs[1] - y[1]) > 1e-4 * L0
 
 
-@pytest.mark.parametrize("omega,sweeps", [(0.5, 1), (0.5, 3), (0.75, 1), (0.75, 2), (0.75, 4), (0.3, 3)])
+@pytest.mark.parametrize("omega,sweeps", [(0.5, 1), (0.5, 3), (1.0, 1), (1.0, 3), (1.5, 1), (1.5, 2), (1.5, 4),
+                                          (0.3, 3)])
 def test_duplicate_edge_excess_recurrence(omega, sweeps):
     sigma = 1.1
     y0 = np.array([[0.0, 0, 0], L0 * U])
@@ -74,19 +76,7 @@ def test_duplicate_edge_excess_recurrence(omega, sweeps):
     sc = mini([0.0, 1.0], len_edges=[[0, 1], [0, 1]])
     prm = jacobi(sigma=sigma, jacobi_omega=omega, gs_sweeps=sweeps)
     out = oracle.backward_once(oracle.OracleScene(sc), prm, y0, y, y0)
-    excess = (1.5 - sigma) * (1.0 - 2.0 * omega) ** sweeps
+    excess = (1.5 - sigma) * (1.0 - omega) ** sweeps
     assert np.array_equal(out[0], y[0])
     assert abs(np.linalg.norm(out[1]) - (sigma + excess) * L0) <= 1e-16
     assert np.allclose(np.cross(out[1], U), 0.0, atol=1e-17)
-
-
-@pytest.mark.parametrize("sweeps,length", [(1, 0.7), (2, 1.5), (3, 0.7), (4, 1.5)])
-def test_duplicate_edge_omega_one_alternates(sweeps, length):
-    # omega = 1: both copies correct the full excess, the vertex overshoots to
-    # 0.7 L0; the next sweep's dl = -lambda releases both (projection at 0)
-    y0 = np.array([[0.0, 0, 0], L0 * U])
-    y = np.array([[0.0, 0, 0], 1.5 * L0 * U])
-    sc = mini([0.0, 1.0], len_edges=[[0, 1], [0, 1]])
-    prm = jacobi(sigma=1.1, jacobi_omega=1.0, gs_sweeps=sweeps)
-    out = oracle.backward_once(oracle.OracleScene(sc), prm, y0, y, y0)
-    assert abs(np.linalg.norm(out[1]) - length * L0) <= 1e-16

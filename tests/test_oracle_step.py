@@ -6,6 +6,9 @@ P3: with no active constraint the forward step walks straight to the target,
     0.5 gamma D^max per iteration.
 P4: moves below 0.45 D^max with no pair closer than D^max: one iteration and
     x^{t+1} == x~ bitwise.
+P4b (R2c): a vertex whose target is not finite keeps its position exactly
+    while the others reach theirs; the step never converges (r of that
+    vertex stays 1) and stops after L + 1 iterations.
 P5: safety of every forward step (|dx_i| < D_i/2, Sec. 5), the reuse bound of
     Eq. relationship_P (P contains every pair closer than D^(l)), no CCD hit
     on any segment of the path, and an intersection-free result.
@@ -54,6 +57,23 @@ def test_p4_one_iteration_exact():
     xn, st, _ = oracle.handle_step(oracle.OracleScene(sc), oracle.params(), x0, xt)
     assert st["iterations"] == 1 and st["converged"] == 1 and st["searches"] == 1
     assert np.array_equal(xn, xt)
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_p4b_non_finite_target_does_not_move(solver, bad):
+    sc = free_cloth()
+    rng = np.random.default_rng(4)
+    x0 = sc.x0
+    xt = x0 + rng.uniform(-1, 1, size=x0.shape) * (0.4 * 4e-3 / np.sqrt(3.0))
+    k = 37
+    xt[k] = [bad, 0.0, bad]
+    prm = oracle.params(max_iters=5, solver=solver)
+    xn, st, _ = oracle.handle_step(oracle.OracleScene(sc), prm, x0, xt)
+    assert np.array_equal(xn[k], x0[k])
+    others = np.arange(len(x0)) != k
+    assert np.array_equal(xn[others], xt[others])
+    assert st["converged"] == 0 and st["iterations"] == prm.max_iters + 1
 
 
 def colliding_cases():
