@@ -276,8 +276,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="two_cloths")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--solver", default="pgs", choices=["pgs", "jacobi"],
-                    help="backward step: coloured projected Gauss-Seidel or projected Jacobi (omega 0.5)")
+    ap.add_argument("--solver", default="gs", choices=["gs", "jacobi"],
+                    help="backward step: projected Gauss-Seidel (the paper's) or projected Jacobi (omega 0.5)")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
@@ -329,7 +329,7 @@ def main():
         sys.stderr.write(f"[bench] ncu case: {st['iterations']} iterations, {st['kernel_launches']} launches, "
                          f"{st['pairs_evaluated'] / st['iterations']:.0f} pairs/iter, "
                          f"{st['active_contacts'] / st['iterations']:.0f} contacts/iter, "
-                         f"{st['max_colours']} colours, {st['max_colour_rounds']} colouring rounds\n")
+                         f"{st['max_vertex_contacts']} contacts at one vertex, sweep depth {st['gs_depth']}\n")
         g.close()
         return 0
     stream = torch.cuda.current_stream(dev)
@@ -430,8 +430,8 @@ def main():
         "finalize": p_iters * ppi * (24.0 + 96.0 + 32.0) * (searches / max(1, p_iters)),
         "refresh": (p_iters - searches) * (32.0 * ppi * 2 + 24.0 * min(n, 4 * ppi)),
         "assemble": p_iters * cpi * (4.0 + 32.0 + 4 * 3 * fp + crec),
-        "colour": p_iters * cpi * (24.0 * 4 + 48.0 * 3 + 16.0),
-        "pgs": p_iters * (cpi * (crec + 4 * 3 * (3 * fp)) + NL * (8.0 + 4 * fp + 4 * 3 * fp)),
+        "order": p_iters * cpi * (24.0 * 4 + 48.0 * 3 + 16.0),
+        "sweep": p_iters * (cpi * (crec + 4 * 3 * (3 * fp)) + NL * (8.0 + 4 * fp + 4 * 3 * fp)),
         "forward": p_iters * 96.0 * n,
         "refit": searches * (24.0 * n + 12.0 * T + 8.0 * E),
     }
@@ -493,6 +493,8 @@ def main():
                "contact_pairs_per_sec": world * pairs / (total_ms / 1000.0),
                "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                "iterations_per_step": float(np.mean(iters)), "converged_steps": int(sum(s["converged"] for s in stats)),
+               "sweep_depth": int(max(s["gs_depth"] for s in stats)),
+               "max_vertex_contacts": int(max(s["max_vertex_contacts"] for s in stats)),
                "deterministic_replay": bool(deterministic and e2e_same),
                "roofline": roof, "kernel_groups": groups, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": launches}

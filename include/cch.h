@@ -42,7 +42,8 @@ typedef enum {
   CCH_E_OOM = 2,               /* device allocation failed                     */
   CCH_E_BUDGET = 3,            /* a server's HBM budget would be exceeded      */
   CCH_E_CUDA = 4,              /* a CUDA runtime call failed                   */
-  CCH_E_CAPACITY = 5,          /* an internal bound (colours, rounds) exceeded */
+  CCH_E_CAPACITY = 5,          /* an internal bound was exceeded (buffers past
+                                  2^30 pairs, BVH traversal or sweep bounds)   */
   CCH_E_TIMEOUT = 6,           /* a bounded device loop ran out                */
   CCH_E_INPUT_NOT_FEASIBLE = 7,/* validate_input: x_t already intersects       */
   CCH_E_CANCELLED = 8,         /* a server request was cancelled               */
@@ -50,7 +51,11 @@ typedef enum {
 } cch_status;
 
 typedef enum { CCH_PREC_FP64 = 0, CCH_PREC_MIXED = 1 } cch_precision;
-typedef enum { CCH_SOLVER_COLORED_PGS = 0, CCH_SOLVER_JACOBI = 1 } cch_solver;
+/* Backward step (Sec. 4.3): one projected Gauss-Seidel sweep per iteration
+ * (contacts, then edge-length constraints, each by descending priority), or
+ * the projected Jacobi variant (Sec. 4.3.2) with per-constraint
+ * under-relaxation jacobi_omega / (most constraints at one of its vertices). */
+typedef enum { CCH_SOLVER_GAUSS_SEIDEL = 0, CCH_SOLVER_JACOBI = 1 } cch_solver;
 
 /* Parameters of Algorithm 1.  cch_params_default() fills Table 2's values
  * (L = 2048, eps = 1e-4, D^min = 2 mm, D^max = 4 mm, delta = 1 mm,
@@ -76,7 +81,7 @@ typedef struct {
   int32_t bvh_refit_only;   /* 1: rebuild the BVH at the first search of a step
                                and only refit it at later searches             */
   int32_t reserved_;
-  uint64_t seed;         /* priorities of the randomized colouring (Sec. 4.3)  */
+  uint64_t seed;         /* priorities of the randomized sweep order (Sec. 4.3) */
 } cch_params;
 
 /* Mesh of one scene (host pointers, copied at creation).
@@ -104,8 +109,10 @@ typedef struct {
   int64_t active_contacts;   /* sum over iterations of contacts (dist<delta)  */
   int64_t candidates;        /* sum over searches of box-test candidates      */
   int64_t degenerate;        /* contacts skipped as degenerate                */
-  int32_t max_colours;       /* most contact colours in one iteration         */
-  int32_t edge_colours;      /* colours of the edge-length constraints        */
+  int32_t max_vertex_contacts; /* most contacts at one movable vertex in an
+                                iteration (a lower bound on the colours of
+                                any colouring of them)                        */
+  int32_t max_vertex_edges;  /* most edge-length constraints at one vertex    */
   double final_r_inf;        /* ||r^(l+1)||_inf at exit                       */
   double min_pair_dist;      /* smallest pair distance seen in the step       */
   int64_t intersections;     /* accept_check: intersecting pairs in x^{t+1}   */
@@ -113,7 +120,10 @@ typedef struct {
                                 certify (expected 0)                          */
   double device_ms;          /* device time of the call (CUDA events)         */
   int64_t kernel_launches;   /* kernels this call launched (graph nodes count) */
-  int32_t max_colour_rounds; /* most colouring rounds in one iteration        */
+  int32_t gs_depth;          /* longest chain of constraints in one
+                                Gauss-Seidel backward step, each applied after
+                                the previous one at a shared vertex: the
+                                sweep's critical path                         */
   int32_t reserved_;
 } cch_step_stats;
 
@@ -196,9 +206,10 @@ cch_status cch_query_pairs_noalloc(cch_scene* s, const double* x, const double* 
  * With profiling on, steps launch kernels directly (no CUDA graphs) and
  * record CUDA events on the scene's stream around each kernel group:
  * 0 BVH refit, 1 vertex-triangle query, 2 edge-edge query, 3 vertex-vertex
- * query, 4 distance refresh, 5 contact assembly, 6 colouring, 7 Gauss-Seidel
- * sweeps, 8 forward step, 9 loop control, 10 step set-up (inputs, BVH
- * build), 11 output, 12 exact FP64 stage of the search.  cch_set_profiling resets the accumulators;
+ * query, 4 distance refresh, 5 contact assembly, 6 sweep order (per-vertex
+ * ranks), 7 backward sweeps (Gauss-Seidel or Jacobi), 8 forward step, 9 loop
+ * control, 10 step set-up (inputs, BVH build), 11 output, 12 exact FP64 stage
+ * of the search.  cch_set_profiling resets the accumulators;
  * cch_get_profile returns, per group, the summed milliseconds and the number
  * of timed launches (n entries). */
 cch_status cch_set_profiling(cch_scene* s, int32_t on);

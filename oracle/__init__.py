@@ -54,7 +54,7 @@ class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("searches", C.c_int32), ("converged", C.c_int32),
                 ("ccd_clamps", C.c_int32), ("pairs_evaluated", C.c_int64), ("max_pairs", C.c_int64),
                 ("active_contacts", C.c_int64), ("candidates", C.c_int64), ("degenerate", C.c_int64),
-                ("max_colours", C.c_int32), ("edge_colours", C.c_int32), ("final_r_inf", C.c_double),
+                ("max_vertex_contacts", C.c_int32), ("max_vertex_edges", C.c_int32), ("final_r_inf", C.c_double),
                 ("min_pair_dist", C.c_double)]
 
     def as_dict(self):
@@ -92,8 +92,6 @@ def lib():
             L.orc_proximity.argtypes = [C.POINTER(Topology), p, p, d, i32, p, p, i64]
             L.orc_contact_constraint.restype = C.c_int
             L.orc_contact_constraint.argtypes = [C.c_int, p, p, d, p, p]
-            L.orc_colour_greedy.restype = i32
-            L.orc_colour_greedy.argtypes = [i64, p, p, p, p, p, p]
             L.orc_backward_once.restype = C.c_int
             L.orc_backward_once.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, p, p, p]
             L.orc_ccd.restype = C.c_int
@@ -254,17 +252,6 @@ def contact_constraint(kind, pos, rho, delta):
     ok = lib().orc_contact_constraint(kind, _ptr(pos), _ptr(rho), delta, C.addressof(c0), _ptr(g))
     nv = 2 if kind == VV else 4
     return bool(ok), c0.value, g.reshape(4, 3)[:nv]
-
-
-def colour_greedy(verts, nv, movable, prio, key):
-    verts = _i32(verts).reshape(-1, 4)
-    nv = _i32(nv)
-    movable = np.ascontiguousarray(movable, dtype=np.uint8)
-    prio = np.ascontiguousarray(prio, dtype=np.uint64)
-    key = np.ascontiguousarray(key, dtype=np.uint64)
-    col = np.zeros(len(nv), np.int32)
-    nc = lib().orc_colour_greedy(len(nv), _ptr(verts), _ptr(nv), _ptr(movable), _ptr(prio), _ptr(key), _ptr(col))
-    return nc, col
 
 
 def ccd(kind, x0, x1, rho=None):

@@ -47,7 +47,7 @@ static double det3(v3 a, v3 b, v3 c) { return dot3(a, cross3(b, c)); }
 static int eq3(v3 a, v3 b) { return a.x == b.x && a.y == b.y && a.z == b.z; }
 
 /* SplitMix64 (Steele, Lea, Flood 2014): the counter-based mixer that gives
- * the "randomized" colouring of Sec. 4.3 its priorities. */
+ * the random sweep order of Sec. 4.3 its priorities. */
 uint64_t orc_splitmix64(uint64_t x) {
   uint64_t z = x + 0x9e3779b97f4a7c15ULL;
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
@@ -708,87 +708,34 @@ typedef struct {
   v3 g[4];        /* dc/dx_v ; edges: g[0] = u/L0                              */
   double den;     /* sum_v m_v^-1 |g_v|^2                                       */
   uint64_t key;   /* canonical identity                                          */
-  uint64_t prio;  /* colouring priority                                          */
-  int32_t colour;
+  uint64_t prio;  /* sweep priority (R11)                                        */
   double lambda;
 } cons;
 
-/* Colouring of Sec. 4.3 with colours on constraints.  R11: priorities
- * splitmix64(seed ^ key), ties by key; visiting constraints by descending
- * priority, each takes the smallest colour not used by an already coloured
- * constraint sharing a movable vertex with it. */
-typedef struct { int64_t i; uint64_t prio, key; } pord;
-static int cmp_pord_desc(const void* a, const void* b) {
-  const pord *x = (const pord*)a, *y = (const pord*)b;
-  if (x->prio != y->prio) return x->prio > y->prio ? -1 : 1;
-  if (x->key != y->key) return x->key > y->key ? -1 : 1;
-  return 0;
-}
-int32_t orc_colour_greedy(int64_t n_c, const int32_t* verts, const int32_t* nv, const uint8_t* movable,
-                          const uint64_t* prio, const uint64_t* key, int32_t* colour) {
-  if (n_c == 0) return 0;
-  int32_t vmax = 0;
-  for (int64_t c = 0; c < n_c; c++)
-    for (int k = 0; k < nv[c]; k++) if (verts[4 * c + k] > vmax) vmax = verts[4 * c + k];
-  /* per vertex: list of colours already taken by its constraints */
-  int64_t nvtx = (int64_t)vmax + 1;
-  int32_t** used = (int32_t**)calloc((size_t)nvtx, sizeof(int32_t*));
-  int32_t* nused = (int32_t*)calloc((size_t)nvtx, sizeof(int32_t));
-  int32_t* capu = (int32_t*)calloc((size_t)nvtx, sizeof(int32_t));
-  pord* ord = (pord*)malloc(sizeof(pord) * (size_t)n_c);
-  for (int64_t c = 0; c < n_c; c++) { ord[c].i = c; ord[c].prio = prio[c]; ord[c].key = key[c]; }
-  qsort(ord, (size_t)n_c, sizeof(pord), cmp_pord_desc);
-  int32_t ncol = 0;
-  uint8_t* taken = (uint8_t*)calloc((size_t)n_c + 2, 1); /* colours never exceed n_c */
-  for (int64_t oi = 0; oi < n_c; oi++) {
-    int64_t c = ord[oi].i;
-    int32_t maxc = 0;
-    for (int k = 0; k < nv[c]; k++) {
-      int32_t v = verts[4 * c + k];
-      if (!movable[v]) continue;
-      for (int32_t u = 0; u < nused[v]; u++) { taken[used[v][u]] = 1; if (used[v][u] + 1 > maxc) maxc = used[v][u] + 1; }
-    }
-    int32_t col = 0;
-    while (col < maxc && taken[col]) col++;
-    memset(taken, 0, (size_t)maxc + 1);
-    colour[c] = col;
-    if (col + 1 > ncol) ncol = col + 1;
-    for (int k = 0; k < nv[c]; k++) {
-      int32_t v = verts[4 * c + k];
-      if (!movable[v]) continue;
-      if (nused[v] == capu[v]) {
-        capu[v] = capu[v] ? 2 * capu[v] : 8;
-        used[v] = (int32_t*)realloc(used[v], sizeof(int32_t) * (size_t)capu[v]);
-      }
-      used[v][nused[v]++] = col;
-    }
-  }
-  for (int64_t v = 0; v < nvtx; v++) free(used[v]);
-  free(used); free(nused); free(capu); free(ord); free(taken);
-  return ncol;
+/* Order of the projected Gauss-Seidel sweep (Sec. 4.3, reading R11).  The
+ * paper sweeps colour classes of a randomized colouring; what the colouring
+ * fixes is the order in which constraints sharing a vertex are applied, and
+ * that order is random.  Here it is a random priority order: priorities
+ * splitmix64(seed ^ key) (a bijection of the unique keys, so no ties) and the
+ * sweep visits constraints by descending priority.  A parallel sweep that
+ * applies a constraint once every higher-priority constraint at each of its
+ * movable vertices has been applied gives exactly this sequential result. */
+static int cmp_cons_prio_desc(const void* a, const void* b) {
+  uint64_t pa = ((const cons*)a)->prio, pb = ((const cons*)b)->prio;
+  return pa > pb ? -1 : pa < pb;
 }
 
-static void colour_cons(cons* cs, int64_t n, const uint8_t* movable, int32_t* ncol_out) {
-  int32_t* verts = (int32_t*)calloc(4 * ((size_t)n + 1), sizeof(int32_t));
-  int32_t* nv = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
-  uint64_t* pr = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
-  uint64_t* ky = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
-  int32_t* col = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
-  for (int64_t i = 0; i < n; i++) {
-    for (int k = 0; k < 4; k++) verts[4 * i + k] = cs[i].v[k];
-    nv[i] = cs[i].nv; pr[i] = cs[i].prio; ky[i] = cs[i].key;
-  }
-  *ncol_out = orc_colour_greedy(n, verts, nv, movable, pr, ky, col);
-  for (int64_t i = 0; i < n; i++) cs[i].colour = col[i];
-  free(verts); free(nv); free(pr); free(ky); free(col);
-}
-
-/* Stable order: by colour, then by key. */
-static int cmp_cons_colour(const void* a, const void* b) {
-  const cons *x = (const cons*)a, *y = (const cons*)b;
-  if (x->colour != y->colour) return x->colour < y->colour ? -1 : 1;
-  if (x->key != y->key) return x->key < y->key ? -1 : 1;
-  return 0;
+/* Largest number of constraints at one movable vertex (statistics). */
+static int32_t max_vertex_degree(const cons* cs, int64_t n, const uint8_t* movable, int64_t nverts) {
+  int32_t* deg = (int32_t*)calloc((size_t)nverts + 1, sizeof(int32_t));
+  int32_t m = 0;
+  for (int64_t i = 0; i < n; i++)
+    for (int k = 0; k < cs[i].nv; k++) {
+      int32_t v = cs[i].v[k];
+      if (movable[v] && ++deg[v] > m) m = deg[v];
+    }
+  free(deg);
+  return m;
 }
 
 /* One projected Gauss-Seidel update of a contact constraint linearised at
@@ -894,7 +841,7 @@ static void jacobi_sweep(cons* cc, int64_t nc, cons* ce, int64_t ne, double sigm
 
 /* Edge-length constraints for the step (R9): every listed edge, u and L0
  * from the target y^[k+1]; an edge with L0 = 0 gets a zero denominator and
- * is skipped by the sweep.  The colouring depends on the topology only. */
+ * is skipped by the sweep.  Sweep order: descending priority (R11). */
 static int64_t build_edges(const orc_topology* t, const orc_params* prm, const double* ytgt, const uint8_t* movable,
                            cons** out, int32_t* ncol) {
   cons* ce = (cons*)calloc((size_t)t->n_len + 1, sizeof(cons));
@@ -916,8 +863,8 @@ static int64_t build_edges(const orc_topology* t, const orc_params* prm, const d
     c->key = (3ULL << 62) | (uint64_t)e;
     c->prio = orc_splitmix64(prm->seed ^ c->key);
   }
-  colour_cons(ce, ne, movable, ncol);
-  qsort(ce, (size_t)ne, sizeof(cons), cmp_cons_colour);
+  *ncol = max_vertex_degree(ce, ne, movable, t->n_verts);
+  qsort(ce, (size_t)ne, sizeof(cons), cmp_cons_prio_desc);
   *out = ce;
   return ne;
 }
@@ -950,15 +897,15 @@ static int64_t build_contacts(const orc_topology* t, const orc_params* prm, cons
     c->prio = orc_splitmix64(prm->seed ^ key);
     nc++;
   }
-  colour_cons(cc, nc, movable, ncol);
-  qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_colour);
+  *ncol = max_vertex_degree(cc, nc, movable, t->n_verts);
+  qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_prio_desc);
   *out = cc;
   return nc;
 }
 
 /* Backward step (Sec. 4): y^(l+1) from y^(l) by gs_sweeps projected
- * Gauss-Seidel sweeps, contacts by colour then edges by colour (R10), each
- * backward step starting its multipliers at zero. */
+ * Gauss-Seidel sweeps, contacts then edges (R10), each by descending priority
+ * (R11), each backward step starting its multipliers at zero. */
 static void backward(const orc_topology* t, const orc_params* prm, cons* cc, int64_t nc, cons* ce, int64_t ne,
                      const double* x, double* y) {
   for (int64_t i = 0; i < nc; i++) cc[i].lambda = 0.0;
@@ -1197,7 +1144,7 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
   cons* ce;
   int32_t nce;
   int64_t ne = build_edges(t, prm, x_tilde, movable, &ce, &nce);
-  S.edge_colours = nce;
+  S.max_vertex_edges = nce;
   const double hg = 0.5 * prm->gamma;
   if (tr && tr->x) memcpy(tr->x, x, sizeof(double) * 3 * (size_t)n);
 
@@ -1240,7 +1187,7 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
     int32_t ncc;
     int64_t nc = build_contacts(t, prm, &P, x, movable, &cc, &ncc, &S.degenerate);
     S.active_contacts += nc;
-    if (ncc > S.max_colours) S.max_colours = ncc;
+    if (ncc > S.max_vertex_contacts) S.max_vertex_contacts = ncc;
     backward(t, prm, cc, nc, ce, ne, x, y);
     free(cc);
 

@@ -45,11 +45,11 @@ typedef struct {
   double jacobi_omega;   /* under-relaxation of the projected Jacobi variant */
   int32_t max_iters;     /* L (the loop runs l = 0..L inclusive)            */
   int32_t gs_sweeps;     /* projected Gauss-Seidel sweeps per backward step  */
-  int32_t solver;        /* 0 = coloured PGS, 1 = projected Jacobi           */
+  int32_t solver;        /* 0 = projected Gauss-Seidel, 1 = projected Jacobi */
   int32_t ccd_check;     /* 1 = run the segment CCD safety check each iter   */
   int32_t search_mode;   /* 0 = all pairs, 1 = sorted-axis window, 2 = auto  */
   int32_t pad_;
-  uint64_t seed;         /* colouring priorities                              */
+  uint64_t seed;         /* sweep priorities (R11)                            */
 } orc_params;
 
 typedef struct {
@@ -59,8 +59,9 @@ typedef struct {
   int64_t active_contacts;   /* sum over iterations of active contacts        */
   int64_t candidates;        /* sum over searches of box-test candidates      */
   int64_t degenerate;        /* contacts skipped as degenerate                */
-  int32_t max_colours;       /* max contact colours in one iteration          */
-  int32_t edge_colours;
+  int32_t max_vertex_contacts; /* most contacts at one movable vertex (max over */
+                               /* iterations): a lower bound on any colouring   */
+  int32_t max_vertex_edges;    /* most edge-length constraints at one vertex    */
   double final_r_inf;
   double min_pair_dist;      /* min pair distance seen over the whole step    */
 } orc_stats;
@@ -107,17 +108,9 @@ int64_t orc_proximity(const orc_topology* t, const double* x, const double* x_ti
 int orc_contact_constraint(int kind, const double* p, const double* rho, double delta,
                            double* c0, double* g);
 
-/* ---- colouring (Sec. 4.3) ---- */
-/* Greedy colouring in descending priority; nv[c] vertices per constraint in
- * verts[4c..]; a vertex with movable[v]==0 creates no conflict.  Returns the
- * number of colours. */
-int32_t orc_colour_greedy(int64_t n_c, const int32_t* verts, const int32_t* nv,
-                          const uint8_t* movable, const uint64_t* prio, const uint64_t* key,
-                          int32_t* colour);
-
 /* ---- one backward step (Sec. 4), used by single-constraint pins ---- */
 /* Runs a search at D^max on x, assembles contacts and edge constraints,
- * colours and sweeps once, starting from y_in.  y_out receives y^(l+1). */
+ * sweeps once, starting from y_in.  y_out receives y^(l+1). */
 int orc_backward_once(const orc_topology* t, const orc_params* prm, const double* x,
                       const double* y_in, const double* y_target, double* y_out);
 

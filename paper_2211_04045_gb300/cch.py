@@ -51,9 +51,9 @@ class StepStats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("searches", C.c_int32), ("converged", C.c_int32),
                 ("ccd_clamps", C.c_int32), ("pairs_evaluated", C.c_int64), ("max_pairs", C.c_int64),
                 ("active_contacts", C.c_int64), ("candidates", C.c_int64), ("degenerate", C.c_int64),
-                ("max_colours", C.c_int32), ("edge_colours", C.c_int32), ("final_r_inf", C.c_double),
+                ("max_vertex_contacts", C.c_int32), ("max_vertex_edges", C.c_int32), ("final_r_inf", C.c_double),
                 ("min_pair_dist", C.c_double), ("intersections", C.c_int64), ("uncertain", C.c_int64),
-                ("device_ms", C.c_double), ("kernel_launches", C.c_int64), ("max_colour_rounds", C.c_int32),
+                ("device_ms", C.c_double), ("kernel_launches", C.c_int64), ("gs_depth", C.c_int32),
                 ("reserved_", C.c_int32)]
 
     def as_dict(self):
@@ -255,7 +255,7 @@ class Scene:
         o = np.argsort(keys[:m], kind="stable")
         return keys[:m][o], dist[:m][o]
 
-    PROFILE_GROUPS = ("refit", "query_vt", "query_ee", "query_vv", "refresh", "assemble", "colour", "pgs",
+    PROFILE_GROUPS = ("refit", "query_vt", "query_ee", "query_vv", "refresh", "assemble", "order", "sweep",
                       "forward", "control", "setup", "output", "finalize")
 
     def set_profiling(self, on: bool):

@@ -5,6 +5,7 @@
 // contact buffers, and the per-scene loop state.  A step runs Algorithm 1 on
 // every scene of the pool at once; each scene keeps its own D^(l), search
 // flag and termination, so batched results equal single-scene results.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -15,6 +16,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/cch.h"
@@ -124,7 +126,7 @@ cch_status validate_params(const cch_params* p) {
   if (!(p->sigma > 0.0) || !(p->gamma > 0.0 && p->gamma < 1.0) || !(p->eps >= 0.0)) return CCH_E_INVALID_ARG;
   if (p->max_iters < 0 || p->gs_sweeps < 1 || p->gs_sweeps > 64) return CCH_E_INVALID_ARG;
   if (p->precision != CCH_PREC_FP64 && p->precision != CCH_PREC_MIXED) return CCH_E_INVALID_ARG;
-  if (p->solver != CCH_SOLVER_COLORED_PGS && p->solver != CCH_SOLVER_JACOBI) return CCH_E_INVALID_ARG;
+  if (p->solver != CCH_SOLVER_GAUSS_SEIDEL && p->solver != CCH_SOLVER_JACOBI) return CCH_E_INVALID_ARG;
   if (p->iters_per_launch < 0 || p->iters_per_launch > 4096) return CCH_E_INVALID_ARG;
   return CCH_OK;
 }
@@ -151,11 +153,10 @@ cudaError_t alloc_pairs(Runtime& R) {
   P.fd = nullptr;
   if (P.mixed && (e = dalloc_in(L, &P.fd, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
-  if ((e = dalloc_in(L, &P.corder, P.cons_cap)) != cudaSuccess) return e;
-  if ((e = dalloc_in(L, &P.ccol, P.cons_cap)) != cudaSuccess) return e;
-  if ((e = dalloc_in(L, &R.cbuf.iprio, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
-  if ((e = dalloc_in(L, &R.cbuf.iid, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
-  if ((e = dalloc_in(L, &R.cbuf.rank, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.fdone, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &R.obuf.iprio, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &R.obuf.iid, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &R.obuf.rank, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.lam, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
   P.jdl = nullptr;
   if (R.solver == CCH_SOLVER_JACOBI && (e = dalloc_in(L, &P.jdl, (size_t)P.cons_cap + P.nl)) != cudaSuccess)
@@ -295,9 +296,6 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(upload(R, &P.ev, ev));
   CK(upload(R, &P.lv, lv));
   CK(dalloc(R, &P.lg, nl));
-  CK(dalloc(R, &P.lorder, nl));
-  CK(dalloc(R, &P.lcol, nl));
-  CK(dalloc(R, &P.lcstart, MAX_COLOURS + 2));
   CK(upload(R, &P.vc, vc));
   CK(upload(R, &P.pts, pts));
   CK(upload(R, &P.sd, R.sd));
@@ -305,7 +303,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaMemset(P.ss, 0, sizeof(SceneState) * n_scenes));
   CK(dalloc(R, &P.cnt, 1));
   CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
-  CK(dalloc(R, &P.vmask, (size_t)MASK_WORDS * nv));
+  CK(dalloc(R, &P.vlevel, nv));
   P.vlstart = nullptr;
   P.vllist = nullptr;
   if (R.solver == CCH_SOLVER_JACOBI) {
@@ -338,28 +336,43 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(dalloc(R, &R.d_ptrs, 3 * (size_t)n_scenes));
   CK(cudaEventCreate(&R.ev0));
   CK(cudaEventCreate(&R.ev1));
-  // colour the edge-length constraints once (topology only)
-  P.nlcol = 0;
-  CK(dalloc(R, &R.cbuf.vstart, (size_t)nv + 1));
-  CK(dalloc(R, &R.cbuf.vfill, nv));
-  CK(dalloc(R, &R.cbuf.vdone, nv));
-  ColourBufs eb = R.cbuf;
-  CK(dalloc(R, &eb.iprio, 4 * (size_t)(nl > 0 ? nl : 1)));
-  CK(dalloc(R, &eb.iid, 4 * (size_t)(nl > 0 ? nl : 1)));
-  CK(dalloc(R, &eb.rank, 4 * (size_t)(nl > 0 ? nl : 1)));
-  CK(colour_edges(R, R.stream, eb));
-  CK(cudaStreamSynchronize(R.stream));
-  if (nl) {
-    std::vector<int> cs(MAX_COLOURS + 1);
-    CK(cudaMemcpy(cs.data(), P.lcstart, sizeof(int) * (MAX_COLOURS + 1), cudaMemcpyDeviceToHost));
-    int nc = 0;
-    for (int c = 0; c < MAX_COLOURS; c++)
-      if (cs[c + 1] > cs[c]) nc = c + 1;
-    P.nlcol = nc;
-    CK(cudaMemcpy(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost));
-    if (R.h_cnt->overflow) return CCH_E_CAPACITY;
+  CK(dalloc(R, &R.obuf.vstart, (size_t)nv + 1));
+  CK(dalloc(R, &R.obuf.vfill, nv));
+  CK(dalloc(R, &R.obuf.vdone, nv));
+  {
+    // sweep order of the edge-length constraints (topology only): the rank
+    // of each edge among the edges of each of its vertices, by descending
+    // priority splitmix64(seed ^ key), key = 3 << 62 | local edge index
+    std::vector<int> edeg(nv, 0), estart((size_t)nv + 1, 0), elist(2 * (size_t)nl);
+    std::vector<unsigned long long> eprio(nl);
+    for (int e = 0; e < nl; e++) {
+      const SceneDesc& d = R.sd[lv[e].z];
+      eprio[e] = splitmix64(d.seed ^ ((3ULL << 62) | (unsigned long long)(e - d.l0)));
+      edeg[lv[e].x]++;
+      edeg[lv[e].y]++;
+    }
+    for (int v = 0; v < nv; v++) estart[v + 1] = estart[v] + edeg[v];
+    std::vector<int> fill(estart.begin(), estart.end() - 1);
+    for (int e = 0; e < nl; e++) {
+      elist[fill[lv[e].x]++] = 2 * e;
+      elist[fill[lv[e].y]++] = 2 * e + 1;
+    }
+    std::vector<int2> erank(nl);
+    R.max_vedges = 0;
+    for (int v = 0; v < nv; v++) {
+      int a = estart[v], b = estart[v + 1];
+      std::sort(elist.begin() + a, elist.begin() + b,
+                [&](int p, int q) { return eprio[p >> 1] > eprio[q >> 1]; });
+      for (int r = 0; r < b - a; r++) {
+        int ent = elist[a + r];
+        if (ent & 1) erank[ent >> 1].y = r;
+        else erank[ent >> 1].x = r;
+      }
+      if ((vflag[v] & VF_MOVABLE) && b - a > R.max_vedges) R.max_vedges = b - a;
+    }
+    CK(upload(R, &P.edeg, edeg));
+    CK(upload(R, &P.erank, erank));
   }
-  R.edge_colours = P.nlcol;
   // pair-sized buffers last (they are re-allocated on growth)
   long long guess = 4LL * (nt + ne + nq) + 4096;
   if (guess > (1LL << 30)) guess = 1LL << 30;
@@ -419,9 +432,9 @@ void fill_stats(const Runtime& R, const SceneState& S, cch_step_stats* st, float
   st->active_contacts = S.contacts;
   st->candidates = S.candidates;
   st->degenerate = S.degenerate;
-  st->max_colours = S.max_colours;
-  st->max_colour_rounds = S.max_rounds;
-  st->edge_colours = R.edge_colours;
+  st->max_vertex_contacts = S.max_vcontacts;
+  st->max_vertex_edges = R.max_vedges;
+  st->gs_depth = S.max_depth;
   st->final_r_inf = S.final_r;
   union { unsigned long long u; double d; } b;
   b.u = S.mind_bits;
@@ -496,12 +509,11 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
       }
       CK(cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      if ((R.h_cnt->err || (R.h_cnt->overflow & (OV_COLOURS | OV_ROUNDS))) && getenv("CCH_DEBUG"))
-        fprintf(stderr, "cch: iteration %d err=%d overflow=%d ncol=%d rounds=%d n_cons=%d pairs=%d/%d\n", iters,
-                R.h_cnt->err, R.h_cnt->overflow, R.h_cnt->ncol, R.h_cnt->jp_rounds, R.h_cnt->n_cons,
+      if (R.h_cnt->err && getenv("CCH_DEBUG"))
+        fprintf(stderr, "cch: iteration %d err=%d overflow=%d n_cons=%d pairs=%d/%d\n", iters,
+                R.h_cnt->err, R.h_cnt->overflow, R.h_cnt->n_cons,
                 R.h_cnt->n_pairs[0], R.h_cnt->n_pairs[1]);
       if (R.h_cnt->err) return CCH_E_CAPACITY;
-      if (R.h_cnt->overflow & (OV_COLOURS | OV_ROUNDS)) return CCH_E_CAPACITY;
       if (R.h_cnt->overflow & (OV_PAIRS | OV_CONTACTS)) {
         overflow = true;
         break;
@@ -557,7 +569,7 @@ cch_status cch_params_default(cch_params* p) {
   p->max_iters = 2048;
   p->gs_sweeps = 1;
   p->precision = CCH_PREC_FP64;
-  p->solver = CCH_SOLVER_COLORED_PGS;
+  p->solver = CCH_SOLVER_GAUSS_SEIDEL;
   p->ccd_check = 0;
   p->accept_check = 0;
   p->validate_input = 0;
@@ -968,7 +980,7 @@ void server_loop(cch_server* sv) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     bool regrow = e == cudaSuccess && (R.h_cnt->overflow & (OV_PAIRS | OV_CONTACTS));
-    bool broken = e != cudaSuccess || R.h_cnt->err || (R.h_cnt->overflow & (OV_COLOURS | OV_ROUNDS));
+    bool broken = e != cudaSuccess || R.h_cnt->err;
     ends.clear();
     if (!broken && !regrow)
       for (int s = 0; s < S->n_scenes; s++)

@@ -52,8 +52,8 @@ struct SceneState {
   unsigned long long mind_bits;   // min pair distance of the step
   long long pairs_eval, max_pairs, contacts, candidates, degenerate;
   int n_pairs;                    // |P| of this iteration
-  int max_colours;
-  int max_rounds;                 // most colouring rounds in one iteration
+  int max_vcontacts;              // most contacts at one movable vertex in an iteration
+  int max_depth;                  // longest dependency chain of one backward step
   int ccd_clamps;
   double final_r;
   long long isect, uncertain;
@@ -66,30 +66,22 @@ struct Counters {
   int n_pairs[2];       // pairs in buffer 0 / 1
   int n_active;         // active contact candidates (dist < delta)
   int n_cons;           // assembled contact constraints
-  int ncol;             // contact colours this iteration
+  int vcontacts;        // most contacts at one movable vertex (this iteration)
+  int depth;            // longest dependency chain of this backward step
   int overflow;         // OV_* bits
   int err;              // first error code
   int any_search;       // some active scene searches in this iteration
-  int remaining;        // uncoloured constraints (colouring rounds)
   int all_done;         // every active scene has finished
   unsigned long long n_cand;   // candidate pairs counted
-  int colour_hist[520]; // per-colour counts, then exclusive starts
-  int colour_cursor[520];
-  int jp_rounds;
-  int wcount[2];        // colouring worklist sizes
-  int wcur;             // current worklist
   int n_query;          // pairs written by a query call
   int n_fcand[3];       // FP32-filter survivors per pair kind (VT, EE, VV)
   int any_refresh;      // some active scene reuses P in this iteration
   int ccd_hit;
   int pad;
 };
-enum { OV_PAIRS = 1, OV_CONTACTS = 2, OV_COLOURS = 4, OV_ROUNDS = 8, OV_QUERY = 16 };
-constexpr int MASK_WORDS = 8;
-constexpr int MAX_COLOURS = 64 * MASK_WORDS;  // 512
-// constraint counts up to this are coloured and swept by one thread block
-// (block barriers instead of grid barriers)
-constexpr int SMALL_WORK = 16384;
+enum { OV_PAIRS = 1, OV_CONTACTS = 2, OV_QUERY = 16 };
+// error bits of Counters::err
+enum { ERR_STACK = 2, ERR_BUDGET = 4, ERR_TREE = 8, ERR_POLL = 16 };
 
 // Proximity pair (SoA arrays in the pool).
 struct PairBuf {
@@ -104,8 +96,8 @@ struct __align__(16) Contact {
   double g[12];           // dc/dx_v
   double c0;              // c(x^(l))
   double den;             // sum_v m_v^-1 |g_v|^2
-  unsigned long long prio;// colouring priority
-  unsigned long long key; // canonical identity (tie break)
+  unsigned long long prio;// Gauss-Seidel priority (R11)
+  unsigned long long key; // canonical identity
 };
 
 // The same constraint in FP32 (mixed precision).
@@ -159,10 +151,9 @@ struct Pool {
   int4* ev;                // a, b, scene, -
   int4* lv;                // i, j, scene, -
   P4* lg;                  // per edge-length constraint: g = u/L0 (xyz), den (w)
-  int* lorder;             // edge-length constraints sorted by colour
-  int* lcol;               // colour of each edge-length constraint
-  int* lcstart;            // colour starts into lorder (MAX_COLOURS+1)
-  int nlcol;
+  int* edeg;               // per vertex: edge-length constraints at it
+  int2* erank;             // per edge-length constraint: its rank at vertex i and
+                           // at vertex j among that vertex's edges, by descending priority
   int* vc;                 // collision vertices (pool ids), scene-contiguous
   int* pts;                // point vertices
   SceneDesc* sd;
@@ -174,9 +165,8 @@ struct Pool {
   int4* fv;
   float* fd;               // mixed precision: the survivor's FP32 distance lower bound
   Contact* cons;
-  int* corder;             // contacts sorted by colour
-  int* ccol;               // colour per contact
-  unsigned long long* vmask;   // per vertex: MASK_WORDS x 64-bit used-colour masks
+  unsigned char* fdone;    // Gauss-Seidel sweep: applied flags (cons_cap + nl)
+  int* vlevel;             // per vertex: chain length of its last applied constraint
   double* lam;             // multipliers for gs_sweeps > 1 (contacts then edges)
   double* jdl;             // projected Jacobi: dl per contact, then per edge (cons_cap + nl)
   int* vlstart;            // projected Jacobi: per vertex, start into vllist (nv + 1)
@@ -268,17 +258,12 @@ __device__ __forceinline__ double d_ss(dv3 a, dv3 b, dv3 c, dv3 d, double* sout,
 __device__ __forceinline__ unsigned long long mkkey(int kind, long long a, long long b) {
   return ((unsigned long long)kind << 62) | ((unsigned long long)a << 31) | (unsigned long long)b;
 }
-// SplitMix64 (Steele, Lea and Flood 2014), the colouring priority mixer
+// SplitMix64 (Steele, Lea and Flood 2014), the mixer of the sweep priorities
 __host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
   unsigned long long z = x + 0x9e3779b97f4a7c15ULL;
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
   return z ^ (z >> 31);
-}
-// (prio, key) lexicographic "a ranks above b"
-__device__ __forceinline__ bool ranks_above(unsigned long long pa, unsigned long long ka, unsigned long long pb,
-                                            unsigned long long kb) {
-  return pa > pb || (pa == pb && ka > kb);
 }
 
 // ---------------------------------------------------------------------------

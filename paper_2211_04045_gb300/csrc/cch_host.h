@@ -15,16 +15,17 @@ namespace cg = cooperative_groups;
 
 // Kernel groups timed by the profiling mode (CUDA events on the stream).
 enum ProfGroup {
-  PG_REFIT, PG_VT, PG_EE, PG_VV, PG_REFRESH, PG_ASSEMBLE, PG_COLOUR, PG_PGS, PG_FORWARD, PG_CONTROL, PG_SETUP,
+  PG_REFIT, PG_VT, PG_EE, PG_VV, PG_REFRESH, PG_ASSEMBLE, PG_ORDER, PG_SWEEP, PG_FORWARD, PG_CONTROL, PG_SETUP,
   PG_OUTPUT, PG_FINAL, PG_N
 };
 
-// Scratch of the greedy colouring (see cch_step.cu).
-struct ColourBufs {
+// Per-vertex incidence lists of the contacts of one iteration (see
+// cch_step.cu): the order of the backward step's sweep at each vertex.
+struct OrderBufs {
   int* vstart;               // N+1: incidence counts, scanned in place to bucket starts
   int* vfill;                // N: bucket fill cursors
-  int* vdone;                // N: coloured constraints per vertex so far
-  unsigned long long* iprio; // incidences: priority
+  int* vdone;                // N: constraints applied at the vertex so far
+  unsigned long long* iprio; // incidences: priority (Jacobi: key)
   int* iid;                  // incidences: constraint * 4 + slot
   int* rank;                 // constraint * 4 + slot: rank at that vertex
 };
@@ -38,7 +39,7 @@ struct Runtime {
   std::vector<void*> pair_allocs;    // pair-sized buffers (grown on overflow)
   cudaStream_t stream = nullptr;
   int scene_bits = 0;                // bits of the scene index in Morton keys
-  int coop_blocks = 0;               // grid of the cooperative kernels
+  int coop_blocks = 0;               // grid of the cooperative sweep kernel
   int sweeps = 1, solver = 0, ccd = 0, accept = 0, validate = 0;
   int max_iters = 0;                 // max over scenes
   int iters_per_check = 16;
@@ -50,8 +51,8 @@ struct Runtime {
   Counters* h_cnt = nullptr;         // pinned host copy of the counters
   SceneState* h_ss = nullptr;        // pinned host copy of the scene states
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  int edge_colours = 0;
-  ColourBufs cbuf{};                 // colouring scratch for the contacts
+  int max_vedges = 0;                // most edge-length constraints at one movable vertex
+  OrderBufs obuf{};                  // sweep order of the contacts
   long long launches = 0;            // kernels launched by this runtime
   long long graph_launches = 0;      // kernels in one captured graph
   int profiling = 0;                 // time kernel groups with events

@@ -1,6 +1,6 @@
 // cch_step.cu -- one iteration of Algorithm 1 on sm_103a: distance refresh
 // of the reused proximity set (Sec. 3.1), contact assembly (Sec. 4.1),
-// randomized constraint colouring and projected Gauss-Seidel (Sec. 4.3),
+// the projected Gauss-Seidel or Jacobi backward step (Sec. 4.3),
 // the forward step (Sec. 5) and the loop control (Algorithm 1).
 #include "cch_host.h"
 #include "cch_step.h"
@@ -36,8 +36,8 @@ __global__ void k_scene_init(Pool P, int mode) {
     S.mind_bits = 0x7ff0000000000000ULL;
     S.pairs_eval = S.max_pairs = S.contacts = S.candidates = S.degenerate = 0;
     S.n_pairs = 0;
-    S.max_colours = 0;
-    S.max_rounds = 0;
+    S.max_vcontacts = 0;
+    S.max_depth = 0;
     S.ccd_clamps = 0;
     S.final_r = 1.0;
     S.isect = S.uncertain = 0;
@@ -267,12 +267,13 @@ __global__ void k_assemble(Pool P, int nxt) {
 }
 
 // ---------------------------------------------------------------------------
-// Randomized colouring of constraints (Sec. 4.3).  R11: priorities
-// splitmix64(seed ^ key) (a bijection, so no ties); a constraint takes the
-// smallest colour unused by its higher-priority neighbours (sharing a movable
-// vertex).  Rounds colour every constraint whose priority is the largest
-// among the uncoloured constraints at each of its movable vertices; this
-// yields the sequential greedy colouring in descending priority order.
+// Order of the backward step's sweep (Sec. 4.3, readings R10 and R11):
+// contacts, then edge-length constraints, each by descending priority
+// splitmix64(seed ^ key).  Every constraint's rank among the constraints at
+// each of its movable vertices is all the sweep needs: per-vertex incidence
+// lists of the contacts are built each iteration (count, scan, scatter,
+// rank); the ranks of the edge-length constraints depend on the topology
+// only and are computed once per scene.
 // ---------------------------------------------------------------------------
 struct ContactAcc {
   const Contact* c;
@@ -284,58 +285,23 @@ struct ContactFAcc {
   __device__ int4 verts(int i) const { return c[i].v; }
   __device__ unsigned long long prio(int i) const { return c[i].prio; }
 };
-struct EdgeAcc {
-  const int4* lv;
-  const SceneDesc* sd;
-  __device__ int4 verts(int i) const { int4 l = lv[i]; return make_int4(l.x, l.y, -1, -1); }
-  __device__ unsigned long long prio(int i) const {
-    int s = lv[i].z;
-    unsigned long long key = (3ULL << 62) | (unsigned long long)(i - sd[s].l0);
-    return splitmix64(sd[s].seed ^ key);
-  }
-};
 
 __device__ __forceinline__ bool movable(const Pool& P, int v) { return v >= 0 && (P.vflag[v] & VF_MOVABLE); }
 
-struct GridSync {
-  cg::grid_group g;
-  __device__ void operator()() { g.sync(); }
-};
-struct BlockSync {
-  __device__ void operator()() { __syncthreads(); }
-};
-
-// The greedy colouring is computed without rounds.  Each (constraint,
-// movable vertex) incidence gets its rank among that vertex's constraints by
-// descending priority.  A constraint is ready once every one of its vertices
-// has coloured exactly `rank` constraints (all its higher-priority
-// neighbours there); it then takes the smallest colour not used at its
-// vertices, publishes the colour bit, fences, and advances the vertices'
-// counters.  Threads poll their constraints without blocking, so the highest
-// priority uncoloured constraint is always ready and the colouring always
-// progresses; the polls are bounded and report CCH_E_TIMEOUT past the bound.
-
 template <class Acc>
-__global__ void k_ci_count(Pool P, Acc acc, const int* n_ptr, int fixed_n, int cap, int* col, ColourBufs B) {
-  int n = n_ptr ? *n_ptr : fixed_n;
-  if (n > cap) n = cap;
+__global__ void k_inc_count(Pool P, Acc acc, OrderBufs B) {
+  int n = min(P.cnt->n_cons, P.cons_cap);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    col[c] = -1;
     int4 v = acc.verts(c);
     int vv[4] = {v.x, v.y, v.z, v.w};
     for (int k = 0; k < 4; k++)
-      if (movable(P, vv[k])) {
-        atomicAdd(&B.vstart[vv[k]], 1);
-        B.vdone[vv[k]] = 0;
-        for (int w = 0; w < MASK_WORDS; w++) P.vmask[MASK_WORDS * vv[k] + w] = 0ull;
-      }
+      if (movable(P, vv[k])) atomicAdd(&B.vstart[vv[k]], 1);
   }
 }
 
 template <class Acc>
-__global__ void k_ci_scatter(Pool P, Acc acc, const int* n_ptr, int fixed_n, int cap, ColourBufs B) {
-  int n = n_ptr ? *n_ptr : fixed_n;
-  if (n > cap) n = cap;
+__global__ void k_inc_scatter(Pool P, Acc acc, OrderBufs B) {
+  int n = min(P.cnt->n_cons, P.cons_cap);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
     int4 v = acc.verts(c);
     unsigned long long p = acc.prio(c);
@@ -349,9 +315,12 @@ __global__ void k_ci_scatter(Pool P, Acc acc, const int* n_ptr, int fixed_n, int
   }
 }
 
+// rank of each incidence at its vertex by descending priority (priorities
+// are a bijection of the unique pair keys: no ties); the vertex with the most
+// contacts is recorded for the statistics
 template <class Acc>
-__global__ void k_ci_rank(Pool P, Acc acc, ColourBufs B, int nv) {
-  int total = B.vstart[nv];
+__global__ void k_inc_rank(Pool P, Acc acc, OrderBufs B) {
+  int total = B.vstart[P.nv];
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
     int id = B.iid[s];
     int4 v = acc.verts(id >> 2);
@@ -362,54 +331,7 @@ __global__ void k_ci_rank(Pool P, Acc acc, ColourBufs B, int nv) {
     int r = 0;
     for (int t = a; t < b; t++) r += B.iprio[t] > p;
     B.rank[id] = r;
-  }
-}
-
-template <class Acc>
-__global__ void k_ci_poll(Pool P, Acc acc, const int* n_ptr, int fixed_n, int cap, int* col, ColourBufs B,
-                          int max_polls) {
-  int n = n_ptr ? *n_ptr : fixed_n;
-  if (n > cap) n = cap;
-  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  int polls = 0;
-  for (;;) {
-    bool pending = false;
-    for (int c = tid; c < n; c += nth) {
-      if (col[c] >= 0) continue;
-      int4 v = acc.verts(c);
-      int vv[4] = {v.x, v.y, v.z, v.w};
-      bool ready = true;
-      for (int k = 0; k < 4 && ready; k++)
-        if (movable(P, vv[k]) && __ldcg(&B.vdone[vv[k]]) != B.rank[4 * c + k]) ready = false;
-      if (!ready) {
-        pending = true;
-        continue;
-      }
-      __threadfence();  // the neighbours' colour bits were published before their counters
-      int cc = -1;
-      for (int w = 0; w < MASK_WORDS && cc < 0; w++) {
-        unsigned long long m = 0;
-        for (int k = 0; k < 4; k++)
-          if (movable(P, vv[k])) m |= __ldcg(&P.vmask[MASK_WORDS * vv[k] + w]);
-        if (~m) cc = 64 * w + __ffsll((long long)~m) - 1;
-      }
-      if (cc < 0) {
-        atomicOr(&P.cnt->overflow, OV_COLOURS);
-        cc = MAX_COLOURS - 1;
-      }
-      col[c] = cc;
-      for (int k = 0; k < 4; k++)
-        if (movable(P, vv[k])) atomicOr(&P.vmask[MASK_WORDS * vv[k] + (cc >> 6)], 1ull << (cc & 63));
-      __threadfence();
-      for (int k = 0; k < 4; k++)
-        if (movable(P, vv[k])) atomicAdd(&B.vdone[vv[k]], 1);
-    }
-    if (!pending) break;
-    if (++polls > max_polls) {
-      atomicOr(&P.cnt->err, 16);  // bounded wait ran out
-      break;
-    }
-    __nanosleep(64);
+    if (r == 0) atomicMax(&P.cnt->vcontacts, b - a);
   }
 }
 
@@ -436,52 +358,10 @@ __global__ void k_scan_ints(int* a, int m) {
   }
 }
 
-// counting sort of the constraints by colour: histogram, scan, scatter
-__global__ void k_colour_hist(Pool P, const int* n_ptr, int fixed_n, int cap, const int* col) {
-  int n = n_ptr ? *n_ptr : fixed_n;
-  if (n > cap) n = cap;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int c = col[i];
-    if (c < 0) c = MAX_COLOURS - 1;
-    atomicAdd(&P.cnt->colour_hist[c], 1);
-  }
-}
-__global__ void k_colour_scan(Pool P, int* cstart, int* ncol_out) {
-  __shared__ int h[MAX_COLOURS];
-  __shared__ int last;
-  Counters* C = P.cnt;
-  if (threadIdx.x == 0) last = 0;
-  __syncthreads();
-  for (int c = threadIdx.x; c < MAX_COLOURS; c += blockDim.x) {
-    h[c] = C->colour_hist[c];
-    if (h[c]) atomicMax(&last, c + 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int c = 0; c < MAX_COLOURS; c++) {
-      cstart[c] = run;
-      C->colour_cursor[c] = run;
-      run += h[c];
-    }
-    cstart[MAX_COLOURS] = run;
-    *ncol_out = last;
-  }
-}
-__global__ void k_colour_scatter(Pool P, const int* n_ptr, int fixed_n, int cap, const int* col, int* order) {
-  int n = n_ptr ? *n_ptr : fixed_n;
-  if (n > cap) n = cap;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int c = col[i];
-    if (c < 0) c = MAX_COLOURS - 1;
-    order[atomicAdd(&P.cnt->colour_cursor[c], 1)] = i;
-  }
-}
-
 // ---------------------------------------------------------------------------
-// Backward step: projected Gauss-Seidel over the colour classes (Eq. LCP),
-// contacts first then edge-length constraints (R10).  Inside a colour no two
-// constraints share a movable vertex, so each class is one parallel pass.
+// Backward step: projected Gauss-Seidel (Eq. LCP), one constraint at a time.
+// y is read and written through L2 (ld.cg / st.cg): a constraint applied on
+// one SM is seen by the next constraint at the same vertex on another.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ dv3 ldy(const Pool& P, int v) {
   const double* p = (const double*)(P.y + v);
@@ -494,7 +374,8 @@ __device__ __forceinline__ void sty(Pool& P, int v, dv3 a) {
   __stcg(p + 2, a.z);
 }
 
-__device__ __forceinline__ void pgs_contact(Pool& P, int ci, double* lam) {
+// lam: multipliers when gs_sweeps > 1 (zero at the first sweep)
+__device__ __forceinline__ void pgs_contact(Pool& P, int ci, double* lam, bool first) {
   const Contact& c = P.cons[ci];
   if (!(c.den > 0.0)) return;
   int vid[4] = {c.v.x, c.v.y, c.v.z, c.v.w};
@@ -506,7 +387,7 @@ __device__ __forceinline__ void pgs_contact(Pool& P, int ci, double* lam) {
     dv3 g = {c.g[3 * k], c.g[3 * k + 1], c.g[3 * k + 2]};
     w = w + vdot(g, vsub(yv[k], mk(P.x[vid[k]])));
   }
-  double l0 = lam ? lam[ci] : 0.0;
+  double l0 = lam && !first ? lam[ci] : 0.0;
   double tl = l0 - w / c.den;
   double ln = tl > 0.0 ? tl : 0.0;
   double dl = ln - l0;
@@ -521,7 +402,7 @@ __device__ __forceinline__ void pgs_contact(Pool& P, int ci, double* lam) {
 
 // mixed precision: the same updates in FP32 on the float copy of y
 __device__ __forceinline__ float4 ldyf(const Pool& P, int v) { return __ldcg(P.yf + v); }
-__device__ __forceinline__ void pgs_contact_f(Pool& P, int ci, double* lam) {
+__device__ __forceinline__ void pgs_contact_f(Pool& P, int ci, double* lam, bool first) {
   const ContactF& c = ((const ContactF*)P.cons)[ci];
   if (!(c.den > 0.f)) return;
   int vid[4] = {c.v.x, c.v.y, c.v.z, c.v.w};
@@ -533,7 +414,7 @@ __device__ __forceinline__ void pgs_contact_f(Pool& P, int ci, double* lam) {
     float4 xv = P.xf[vid[k]];
     w = w + (c.g[3 * k] * (yv[k].x - xv.x) + c.g[3 * k + 1] * (yv[k].y - xv.y) + c.g[3 * k + 2] * (yv[k].z - xv.z));
   }
-  float l0 = lam ? (float)lam[ci] : 0.f;
+  float l0 = lam && !first ? (float)lam[ci] : 0.f;
   float tl = l0 - w / c.den;
   float ln = tl > 0.f ? tl : 0.f;
   float dl = ln - l0;
@@ -545,15 +426,13 @@ __device__ __forceinline__ void pgs_contact_f(Pool& P, int ci, double* lam) {
     __stcg(P.yf + vid[k], o);
   }
 }
-__device__ __forceinline__ void pgs_edge_f(Pool& P, int e, double* lam) {
+__device__ __forceinline__ void pgs_edge_f(Pool& P, int e, double* lam, bool first) {
   int4 l = P.lv[e];
-  const SceneState& S = P.ss[l.z];
-  if (!S.active || S.done) return;
   float4 gd = P.lgf[e];
   if (!(gd.w > 0.f)) return;
   float4 yi = ldyf(P, l.x), yj = ldyf(P, l.y);
   float w = (float)P.sd[l.z].sigma - (gd.x * (yi.x - yj.x) + gd.y * (yi.y - yj.y) + gd.z * (yi.z - yj.z));
-  float l0 = lam ? (float)lam[e] : 0.f;
+  float l0 = lam && !first ? (float)lam[e] : 0.f;
   float tl = l0 - w / gd.w;
   float ln = tl > 0.f ? tl : 0.f;
   float dl = ln - l0;
@@ -564,16 +443,14 @@ __device__ __forceinline__ void pgs_edge_f(Pool& P, int e, double* lam) {
   __stcg(P.yf + l.y, make_float4(yj.x + sj * gd.x, yj.y + sj * gd.y, yj.z + sj * gd.z, 0.f));
 }
 
-__device__ __forceinline__ void pgs_edge(Pool& P, int e, double* lam) {
+__device__ __forceinline__ void pgs_edge(Pool& P, int e, double* lam, bool first) {
   int4 l = P.lv[e];
-  const SceneState& S = P.ss[l.z];
-  if (!S.active || S.done) return;
   P4 gd = P.lg[e];
   if (!(gd.w > 0.0)) return;
   dv3 g = {gd.x, gd.y, gd.z};
   dv3 yi = ldy(P, l.x), yj = ldy(P, l.y);
   double w = P.sd[l.z].sigma - vdot(g, vsub(yi, yj));
-  double l0 = lam ? lam[e] : 0.0;
+  double l0 = lam && !first ? lam[e] : 0.0;
   double tl = l0 - w / gd.w;
   double ln = tl > 0.0 ? tl : 0.0;
   double dl = ln - l0;
@@ -584,76 +461,209 @@ __device__ __forceinline__ void pgs_edge(Pool& P, int e, double* lam) {
   sty(P, l.y, vadd(yj, vscl(sj, g)));
 }
 
-// Contact colours in ascending order.  Colour classes shrink with the colour
-// index (greedy colouring); once a class has at most PGS_TAIL constraints the
-// remaining classes run in one block with block barriers.
-constexpr int PGS_TAIL = 1024;
+// ---------------------------------------------------------------------------
+// One Gauss-Seidel sweep as a dataflow over vertex counters.  The paper
+// sweeps the colour classes of a randomized colouring with a barrier between
+// classes; here no barrier is needed.  A constraint is applied once the
+// counter of every one of its movable vertices (constraints applied there so
+// far) equals its rank at that vertex; it then increments those counters.
+// Constraints that share no movable vertex commute, so the result is exactly
+// the sequential sweep in the order above.  Sweep s of gs_sweeps starts at
+// counter s * (constraints at the vertex), so counters need no reset between
+// sweeps.
+//
+// All blocks are resident (cooperative launch).  Each thread takes up to 32
+// constraints (i = tid + k * nth), sorts them into the sweep order and
+// applies them one after the other, waiting before each only for its own
+// vertex counters.  The earliest pending constraint of the whole sweep is at
+// the head of its thread's list and is ready, so the sweep always progresses.
+// With more constraints than 32 per thread, every thread polls all of its
+// pending constraints each round instead.  Waits are bounded and set
+// ERR_POLL past the bound.  The chain length of each applied constraint (one
+// more than the chain ending at its predecessors) gives the sweep's critical
+// path for the statistics.
+// ---------------------------------------------------------------------------
+struct SweepCtx {
+  int nc;          // contacts (items [0, nc)); edge-length constraints follow
+  int sweep;
+  double* lam;     // contact multipliers (gs_sweeps > 1), else null
+  double* elam;    // edge multipliers
+};
 
-__global__ void k_pgs_contacts(Pool P, int sweep) {
-  int n = P.cnt->n_cons;
-  if (n > P.cons_cap) n = P.cons_cap;
-  int ncol = P.cnt->ncol;
-  const int* cs = P.cnt->colour_hist;  // contact colour starts after the colouring
-  double* lam = P.sd[0].gs_sweeps > 1 ? P.lam : nullptr;
-  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  if (lam && sweep == 0)
-    for (int i = tid; i < n; i += nth) lam[i] = 0.0;
-  int k = 0;
-  if (n > SMALL_WORK) {
-    cg::grid_group grid = cg::this_grid();
-    if (lam && sweep == 0) grid.sync();
-    for (; k < ncol && cs[k + 1] - cs[k] > PGS_TAIL; k++) {
-      for (int i = cs[k] + tid; i < cs[k + 1]; i += nth) {
-        if (P.mixed) pgs_contact_f(P, P.corder[i], lam);
-        else pgs_contact(P, P.corder[i], lam);
-      }
-      grid.sync();
-    }
-  } else if (lam && sweep == 0) {
-    cg::this_grid().sync();
+__device__ __forceinline__ int contacts_at(const OrderBufs& B, int v) {
+  return __ldg(&B.vstart[v + 1]) - __ldg(&B.vstart[v]);
+}
+// counter value at which a constraint of rank r among the contacts (edge:
+// among the edges) of v may be applied in sweep s
+__device__ __forceinline__ int target_at(const Pool& P, const OrderBufs& B, int v, int s, int r, bool edge) {
+  int nct = contacts_at(B, v);
+  return s * (nct + __ldg(&P.edeg[v])) + (edge ? nct : 0) + r;
+}
+
+// the vertices an item waits on and the counter values it waits for
+struct ItemWait {
+  int v[4];
+  int t[4];  // -1: no wait (vertex absent or not movable)
+};
+__device__ __forceinline__ void item_wait(const Pool& P, const OrderBufs& B, const SweepCtx& X, int i, ItemWait& w) {
+  if (i < X.nc) {
+    int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
+    w.v[0] = v.x; w.v[1] = v.y; w.v[2] = v.z; w.v[3] = v.w;
+    for (int k = 0; k < 4; k++)
+      w.t[k] = movable(P, w.v[k]) ? target_at(P, B, w.v[k], X.sweep, __ldg(&B.rank[4 * i + k]), false) : -1;
+  } else {
+    int e = i - X.nc;
+    int4 l = P.lv[e];
+    int2 r = __ldg(&P.erank[e]);
+    w.v[0] = l.x; w.v[1] = l.y; w.v[2] = w.v[3] = -1;
+    w.t[0] = movable(P, l.x) ? target_at(P, B, l.x, X.sweep, r.x, true) : -1;
+    w.t[1] = movable(P, l.y) ? target_at(P, B, l.y, X.sweep, r.y, true) : -1;
+    w.t[2] = w.t[3] = -1;
   }
-  if (blockIdx.x != 0) return;
-  for (; k < ncol; k++) {
-    for (int i = cs[k] + threadIdx.x; i < cs[k + 1]; i += blockDim.x) {
-      if (P.mixed) pgs_contact_f(P, P.corder[i], lam);
-      else pgs_contact(P, P.corder[i], lam);
-    }
-    __syncthreads();
+}
+// Counters are read with acquire and incremented with release semantics
+// (GPU scope): a constraint that sees its predecessor's increment also sees
+// the predecessor's writes of y.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// brings the item's read-only data (constraint record, x) into L1 while it waits
+__device__ __forceinline__ void item_prefetch(const Pool& P, const SweepCtx& X, int i, const ItemWait& w) {
+  if (i < X.nc) {
+    const char* c = P.mixed ? (const char*)(((const ContactF*)P.cons) + i) : (const char*)(P.cons + i);
+    prefetch_l1(c);
+    prefetch_l1(c + 64);
+    if (!P.mixed) prefetch_l1(c + 128);
+    for (int k = 0; k < 4; k++)
+      if (w.v[k] >= 0) prefetch_l1(P.x + w.v[k]);
+  } else {
+    int e = i - X.nc;
+    if (P.mixed) prefetch_l1(P.lgf + e);
+    else prefetch_l1(P.lg + e);
   }
 }
 
-// Edge-length constraints, colour by colour (colouring fixed at creation).
-__global__ void k_pgs_edges(Pool P, int sweep) {
-  double* lam = P.sd[0].gs_sweeps > 1 ? P.lam + P.cons_cap : nullptr;
-  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  if (P.nl <= SMALL_WORK) {
-    if (blockIdx.x != 0) return;
-    if (lam && sweep == 0) {
-      for (int i = threadIdx.x; i < P.nl; i += blockDim.x) lam[i] = 0.0;
-      __syncthreads();
-    }
-    for (int k = 0; k < P.nlcol; k++) {
-      for (int i = P.lcstart[k] + threadIdx.x; i < P.lcstart[k + 1]; i += blockDim.x) {
-        if (P.mixed) pgs_edge_f(P, P.lorder[i], lam);
-        else pgs_edge(P, P.lorder[i], lam);
-      }
-      __syncthreads();
-    }
-    return;
-  }
-  cg::grid_group grid = cg::this_grid();
-  if (lam && sweep == 0) {
-    for (int i = tid; i < P.nl; i += nth) lam[i] = 0.0;
-    grid.sync();
-  }
-  for (int k = 0; k < P.nlcol; k++) {
-    for (int i = P.lcstart[k] + tid; i < P.lcstart[k + 1]; i += nth) {
-      if (P.mixed) pgs_edge_f(P, P.lorder[i], lam);
-      else pgs_edge(P, P.lorder[i], lam);
-    }
-    grid.sync();
-  }
+__device__ __forceinline__ bool item_ready(const OrderBufs& B, const ItemWait& w) {
+  bool ok = true;
+  for (int k = 0; k < 4; k++)
+    if (w.t[k] >= 0) ok &= ld_acquire(&B.vdone[w.v[k]]) == w.t[k];
+  return ok;
 }
+__device__ __forceinline__ void item_apply(Pool& P, const OrderBufs& B, const SweepCtx& X, int i, const ItemWait& w,
+                                           int& maxlvl) {
+  int lvl = 0;
+  for (int k = 0; k < 4; k++)
+    if (w.t[k] >= 0) lvl = max(lvl, __ldcg(&P.vlevel[w.v[k]]));
+  lvl++;
+  bool first = X.sweep == 0;
+  if (i < X.nc) {
+    if (P.mixed) pgs_contact_f(P, i, X.lam, first);
+    else pgs_contact(P, i, X.lam, first);
+  } else {
+    if (P.mixed) pgs_edge_f(P, i - X.nc, X.elam, first);
+    else pgs_edge(P, i - X.nc, X.elam, first);
+  }
+  for (int k = 0; k < 4; k++)
+    if (w.t[k] >= 0) __stcg(&P.vlevel[w.v[k]], lvl);
+  for (int k = 0; k < 4; k++)
+    if (w.t[k] >= 0) red_release_add(&B.vdone[w.v[k]], 1);
+  maxlvl = max(maxlvl, lvl);
+}
+
+// edge-length constraints of scenes that are not running take no part
+__device__ __forceinline__ bool item_live(const Pool& P, const SweepCtx& X, int i) {
+  if (i < X.nc) return true;
+  const SceneState& S = P.ss[P.lv[i - X.nc].z];
+  return S.active && !S.done;
+}
+// sweep-order key: contacts (class 0) before edges (class 1), then
+// descending priority; compared as (class, ~prio) ascending
+__device__ __forceinline__ unsigned long long item_prio(const Pool& P, const SweepCtx& X, int i) {
+  if (i < X.nc) return P.mixed ? ((const ContactF*)P.cons)[i].prio : P.cons[i].prio;
+  int e = i - X.nc;
+  const SceneDesc& d = P.sd[P.lv[e].z];
+  return splitmix64(d.seed ^ ((3ULL << 62) | (unsigned long long)(e - d.l0)));
+}
+
+__global__ void __launch_bounds__(256, 3) k_gs_sweep(Pool P, OrderBufs B, int sweep, int max_polls) {
+  SweepCtx X;
+  X.nc = min(P.cnt->n_cons, P.cons_cap);
+  X.sweep = sweep;
+  X.lam = P.sd[0].gs_sweeps > 1 ? P.lam : nullptr;
+  X.elam = X.lam ? P.lam + P.cons_cap : nullptr;
+  int n = X.nc + P.nl;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  int maxlvl = 0;
+  long long polls = 0;
+  if (n <= 32 * nth) {
+    // this thread's items in sweep order (insertion sort, at most 32)
+    int items[32];
+    unsigned long long keys[32];
+    int m = 0;
+    for (int i = tid; i < n; i += nth) {
+      if (!item_live(P, X, i)) continue;
+      unsigned long long key = ~item_prio(P, X, i);
+      bool edge = i >= X.nc;
+      int j = m++;
+      while (j > 0 && ((items[j - 1] >= X.nc) > edge || ((items[j - 1] >= X.nc) == edge && keys[j - 1] > key))) {
+        items[j] = items[j - 1];
+        keys[j] = keys[j - 1];
+        j--;
+      }
+      items[j] = i;
+      keys[j] = key;
+    }
+    for (int j = 0; j < m; j++) {
+      ItemWait w;
+      item_wait(P, B, X, items[j], w);
+      item_prefetch(P, X, items[j], w);
+      while (!item_ready(B, w)) {
+        if (++polls > max_polls) {
+          atomicOr(&P.cnt->err, ERR_POLL);
+          j = m;
+          break;
+        }
+        __nanosleep(20);
+      }
+      if (j < m) item_apply(P, B, X, items[j], w, maxlvl);
+    }
+  } else {
+    // more items than that: poll every pending item each round
+    for (;;) {
+      bool pending = false, progressed = false;
+      for (int i = tid; i < n; i += nth) {
+        if (P.fdone[i] || !item_live(P, X, i)) continue;
+        ItemWait w;
+        item_wait(P, B, X, i, w);
+        if (item_ready(B, w)) {
+          item_apply(P, B, X, i, w, maxlvl);
+          P.fdone[i] = 1;
+          progressed = true;
+        } else {
+          pending = true;
+        }
+      }
+      if (!pending) break;
+      if (!progressed) {
+        if (++polls > max_polls) {
+          atomicOr(&P.cnt->err, ERR_POLL);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+  }
+  unsigned mx = __reduce_max_sync(0xffffffffu, (unsigned)maxlvl);
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&P.cnt->depth, (int)mx);
+}
+
 
 // ---------------------------------------------------------------------------
 // Backward step, projected Jacobi variant (Sec. 4.3.2, R12).  Every
@@ -676,7 +686,7 @@ __device__ __forceinline__ bool scene_running(const Pool& P, int s) {
 }
 
 // incidences (contact, movable vertex) of every contact that can move y
-__global__ void k_jac_count(Pool P, ColourBufs B) {
+__global__ void k_jac_count(Pool P, OrderBufs B) {
   int n = min(P.cnt->n_cons, P.cons_cap);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
     int4 v;
@@ -695,7 +705,7 @@ __global__ void k_jac_count(Pool P, ColourBufs B) {
       if (movable(P, vv[k])) atomicAdd(&B.vstart[vv[k]], 1);
   }
 }
-__global__ void k_jac_scatter(Pool P, ColourBufs B) {
+__global__ void k_jac_scatter(Pool P, OrderBufs B) {
   int n = min(P.cnt->n_cons, P.cons_cap);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
     int4 v;
@@ -723,7 +733,7 @@ __global__ void k_jac_scatter(Pool P, ColourBufs B) {
 }
 // place each incidence at its key rank inside its vertex's segment
 // (B.rank becomes the key-sorted incidence list; pair keys are unique)
-__global__ void k_jac_rank(Pool P, ColourBufs B) {
+__global__ void k_jac_rank(Pool P, OrderBufs B) {
   int total = B.vstart[P.nv];
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < total; s += gridDim.x * blockDim.x) {
     int id = B.iid[s];
@@ -740,7 +750,7 @@ __global__ void k_jac_rank(Pool P, ColourBufs B) {
 
 // constraints at each movable vertex: its contacts (the scattered count in
 // vfill) plus its edge-length constraints with a positive denominator
-__global__ void k_jac_nv(Pool P, ColourBufs B) {
+__global__ void k_jac_nv(Pool P, OrderBufs B) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
     int m = 0;
     if (P.vflag[v] & VF_MOVABLE) {
@@ -753,13 +763,13 @@ __global__ void k_jac_nv(Pool P, ColourBufs B) {
     B.vdone[v] = m;
   }
 }
-__device__ __forceinline__ int nmax_at(const Pool& P, const ColourBufs& B, int v, int m) {
+__device__ __forceinline__ int nmax_at(const Pool& P, const OrderBufs& B, int v, int m) {
   return (v >= 0 && (P.vflag[v] & VF_MOVABLE) && B.vdone[v] > m) ? B.vdone[v] : m;
 }
 __device__ __forceinline__ double relax(double omega, int m) { return omega / (double)(m > 0 ? m : 1); }
 
 // s = omega_c dl of every contact and edge-length constraint from the same y
-__global__ void k_jac_dl(Pool P, ColourBufs B, int sweep) {
+__global__ void k_jac_dl(Pool P, OrderBufs B, int sweep) {
   int n = min(P.cnt->n_cons, P.cons_cap);
   double* lam = P.sd[0].gs_sweeps > 1 ? P.lam : nullptr;
   int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
@@ -843,7 +853,7 @@ __global__ void k_jac_dl(Pool P, ColourBufs B, int sweep) {
 }
 
 // per-vertex segmented sum in canonical order, then y += omega * sum
-__global__ void k_jac_apply(Pool P, ColourBufs B) {
+__global__ void k_jac_apply(Pool P, OrderBufs B) {
   const double* edl = P.jdl + P.cons_cap;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
     int s = P.vscene[v];
@@ -1041,8 +1051,8 @@ __global__ void k_control(Pool P, int cur) {
     S.final_r = rmax;
     S.move_bits = 0;
     S.rmax_bits = 0;
-    if (C->ncol > S.max_colours) S.max_colours = C->ncol;
-    if (C->jp_rounds > S.max_rounds) S.max_rounds = C->jp_rounds;
+    if (C->vcontacts > S.max_vcontacts) S.max_vcontacts = C->vcontacts;
+    if (C->depth > S.max_depth) S.max_depth = C->depth;
     if (rmax < d.eps) {
       S.done = 1;
       S.converged = 1;
@@ -1068,7 +1078,8 @@ __global__ void k_control(Pool P, int cur) {
     C->n_pairs[cur] = 0;
     C->n_active = 0;
     C->n_cons = 0;
-    C->ncol = 0;
+    C->vcontacts = 0;
+    C->depth = 0;
   }
 }
 
@@ -1098,40 +1109,9 @@ int coop_grid(int threads) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int a = 0, b = 0, c = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ci_poll<ContactAcc>, threads, 0);
-  int a2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, k_ci_poll<ContactFAcc>, threads, 0);
-  if (a2 < a) a = a2;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ci_poll<EdgeAcc>, threads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pgs_contacts, threads, 0);
-  per = a < b ? a : b;
-  per = per < c ? per : c;
-  if (per > 2) per = 2;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gs_sweep, threads, 0);
   if (per < 1) per = 1;
   return sms * per;
-}
-
-// Greedy colouring in descending priority of n constraints (count on the
-// device when n_ptr is set), then the counting sort by colour.
-template <class Acc>
-cudaError_t colour_greedy(Runtime& R, Acc acc, const int* n_ptr, int fixed_n, int cap, int* col, int* order,
-                          int* cstart, int* ncol_out, const ColourBufs& B, cudaStream_t st) {
-  Pool& P = R.pool;
-  cudaMemsetAsync(B.vstart, 0, sizeof(int) * ((size_t)P.nv + 1), st);
-  cudaMemsetAsync(B.vfill, 0, sizeof(int) * (size_t)P.nv, st);
-  k_ci_count<<<grid_for(cap, 256), 256, 0, st>>>(P, acc, n_ptr, fixed_n, cap, col, B);
-  k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
-  k_ci_scatter<<<grid_for(cap, 256), 256, 0, st>>>(P, acc, n_ptr, fixed_n, cap, B);
-  k_ci_rank<<<grid_for(4LL * cap, 256), 256, 0, st>>>(P, acc, B, P.nv);
-  cudaError_t e = coop_launch(k_ci_poll<Acc>, R.coop_blocks, 256, st, P, acc, n_ptr, fixed_n, cap, col, B, 1 << 22);
-  if (e != cudaSuccess) return e;
-  cudaMemsetAsync(P.cnt->colour_hist, 0, sizeof(int) * (MAX_COLOURS + 2), st);
-  k_colour_hist<<<grid_for(cap, 256), 256, 0, st>>>(P, n_ptr, fixed_n, cap, col);
-  k_colour_scan<<<1, 512, 0, st>>>(P, cstart, ncol_out);
-  k_colour_scatter<<<grid_for(cap, 256), 256, 0, st>>>(P, n_ptr, fixed_n, cap, col, order);
-  R.launches += 8;
-  return cudaGetLastError();
 }
 
 __global__ void k_clear_start(Pool P) {
@@ -1182,42 +1162,49 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   prof_mark(R, PG_ASSEMBLE, 0, st);
   k_assemble<<<grid_for(P.act_cap, 128), 128, 0, st>>>(P, nxt);
   prof_mark(R, PG_ASSEMBLE, 1, st);
-  prof_mark(R, PG_COLOUR, 0, st);
-  cudaError_t e;
+  prof_mark(R, PG_ORDER, 0, st);
+  cudaError_t e = cudaSuccess;
+  const OrderBufs& B = R.obuf;
+  cudaMemsetAsync(B.vstart, 0, sizeof(int) * ((size_t)P.nv + 1), st);
+  cudaMemsetAsync(B.vfill, 0, sizeof(int) * (size_t)P.nv, st);
   if (R.solver == 1) {  // projected Jacobi
-    const ColourBufs& B = R.cbuf;
-    cudaMemsetAsync(B.vstart, 0, sizeof(int) * ((size_t)P.nv + 1), st);
-    cudaMemsetAsync(B.vfill, 0, sizeof(int) * (size_t)P.nv, st);
     k_jac_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, B);
     k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
     k_jac_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, B);
     k_jac_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, B);
     k_jac_nv<<<grid_for(P.nv, 256), 256, 0, st>>>(P, B);
-    prof_mark(R, PG_COLOUR, 1, st);
-    prof_mark(R, PG_PGS, 0, st);
+    prof_mark(R, PG_ORDER, 1, st);
+    prof_mark(R, PG_SWEEP, 0, st);
     for (int sw = 0; sw < R.sweeps; sw++) {
       k_jac_dl<<<grid_for((long long)P.cons_cap + P.nl, 256), 256, 0, st>>>(P, B, sw);
       k_jac_apply<<<grid_for(P.nv, 256), 256, 0, st>>>(P, B);
     }
-    prof_mark(R, PG_PGS, 1, st);
+    prof_mark(R, PG_SWEEP, 1, st);
     R.launches += 5 + 2 * R.sweeps;
-    e = cudaGetLastError();
-  } else {
-  if (P.mixed)
-    e = colour_greedy(R, ContactFAcc{(const ContactF*)P.cons}, &P.cnt->n_cons, 0, P.cons_cap, P.ccol, P.corder,
-                      P.cnt->colour_hist, &P.cnt->ncol, R.cbuf, st);
-  else
-    e = colour_greedy(R, ContactAcc{P.cons}, &P.cnt->n_cons, 0, P.cons_cap, P.ccol, P.corder, P.cnt->colour_hist,
-                      &P.cnt->ncol, R.cbuf, st);
-  prof_mark(R, PG_COLOUR, 1, st);
-  if (e != cudaSuccess) return e;
-  prof_mark(R, PG_PGS, 0, st);
-  for (int sw = 0; sw < R.sweeps && e == cudaSuccess; sw++) {
-    e = coop_launch(k_pgs_contacts, R.coop_blocks, 256, st, P, sw);
-    if (e == cudaSuccess) e = coop_launch(k_pgs_edges, R.coop_blocks, 256, st, P, sw);
-    R.launches += 2;
-  }
-  prof_mark(R, PG_PGS, 1, st);
+  } else {  // projected Gauss-Seidel
+    cudaMemsetAsync(B.vdone, 0, sizeof(int) * (size_t)P.nv, st);
+    cudaMemsetAsync(P.vlevel, 0, sizeof(int) * (size_t)P.nv, st);
+    if (P.mixed) {
+      ContactFAcc acc{(const ContactF*)P.cons};
+      k_inc_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
+      k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
+      k_inc_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
+      k_inc_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
+    } else {
+      ContactAcc acc{P.cons};
+      k_inc_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
+      k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
+      k_inc_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
+      k_inc_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
+    }
+    prof_mark(R, PG_ORDER, 1, st);
+    prof_mark(R, PG_SWEEP, 0, st);
+    for (int sw = 0; sw < R.sweeps && e == cudaSuccess; sw++) {
+      cudaMemsetAsync(P.fdone, 0, (size_t)P.cons_cap + P.nl, st);
+      e = coop_launch(k_gs_sweep, R.coop_blocks, 256, st, P, B, sw, 1 << 22);
+    }
+    prof_mark(R, PG_SWEEP, 1, st);
+    R.launches += 4 + R.sweeps;
   }
   if (e != cudaSuccess) return e;
   prof_mark(R, PG_FORWARD, 0, st);
@@ -1235,13 +1222,6 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t colour_edges(Runtime& R, cudaStream_t st, const ColourBufs& B) {
-  Pool& P = R.pool;
-  if (P.nl == 0) return cudaSuccess;
-  EdgeAcc ea{P.lv, P.sd};
-  cudaMemsetAsync(P.cnt, 0, sizeof(Counters), st);
-  return colour_greedy(R, ea, nullptr, P.nl, P.nl, P.lcol, P.lorder, P.lcstart, &P.cnt->pad, B, st);
-}
 
 __global__ void k_reset_accept(Pool P) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;

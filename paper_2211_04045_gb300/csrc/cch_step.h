@@ -8,7 +8,6 @@ void step_init(Runtime& R, cudaStream_t st, int mode);
 void output_scene(Runtime& R, int s, cudaStream_t st);
 void set_any_search(Runtime& R, cudaStream_t st);
 cudaError_t iteration(Runtime& R, int cur, cudaStream_t st);
-cudaError_t colour_edges(Runtime& R, cudaStream_t st, const ColourBufs& B);
 void output(Runtime& R, cudaStream_t st);
 void reset_accept(Runtime& R, cudaStream_t st);
 }  // namespace cch

@@ -436,11 +436,28 @@ class TorchDynamics:
             self.ok = ws > 0
             self.wi, self.wj = wi, wj
             self.ws = torch.where(self.ok, ws, torch.ones_like(ws))
-            n = scene.n_verts
-            deg = torch.zeros(n, device=device, dtype=torch.float64)
-            deg.index_add_(0, self.i[self.ok], torch.ones_like(ws[self.ok]))
-            deg.index_add_(0, self.j[self.ok], torch.ones_like(ws[self.ok]))
-            self.deg = torch.clamp(deg, min=1.0)[:, None]
+            n, m = scene.n_verts, len(le)
+            im = scene.inv_mass
+            ok = (im[le[:, 0]] + im[le[:, 1]]) > 0
+            deg = np.maximum(np.bincount(le[ok, 0], minlength=n) + np.bincount(le[ok, 1], minlength=n), 1)
+            self.deg = f(deg.astype(np.float64))[:, None]
+            # per-vertex incidence table (edge row, weight), padded with a
+            # zero row: the per-vertex sums then run in a fixed order and the
+            # prediction is bitwise reproducible (no atomic accumulation)
+            ends = np.concatenate([le[:, 0], le[:, 1]])
+            rows = np.concatenate([np.arange(m), np.arange(m)])
+            wts = np.concatenate([-im[le[:, 0]], im[le[:, 1]]])
+            order = np.argsort(ends, kind="stable")
+            ends, rows, wts = ends[order], rows[order], wts[order]
+            cnt = np.bincount(ends, minlength=n)
+            width = max(1, int(cnt.max()) if len(cnt) else 1)
+            start = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+            slot = np.arange(len(ends)) - start[ends]
+            idx = np.full((n, width), m, np.int64)
+            w = np.zeros((n, width))
+            idx[ends, slot] = rows
+            w[ends, slot] = wts
+            self.inc_idx, self.inc_w = f(idx), f(w)[:, :, None]
             self.rest = f(scene.rest_len)
 
     def predict(self, x, v):
@@ -454,9 +471,8 @@ class TorchDynamics:
                 L = torch.linalg.norm(d, dim=1)
                 L = torch.where(L > 0, L, torch.ones_like(L))
                 c = torch.where(self.ok, (L - self.rest) / L / self.ws, torch.zeros_like(L))[:, None] * d
-                dx = torch.zeros_like(xt)
-                dx.index_add_(0, self.i, -self.wi[:, None] * c)
-                dx.index_add_(0, self.j, self.wj[:, None] * c)
+                c = torch.cat([c, torch.zeros_like(c[:1])])
+                dx = (self.inc_w * c[self.inc_idx]).sum(dim=1)
                 xt = xt + dx / self.deg
         return xt
 
