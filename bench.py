@@ -281,6 +281,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-configuration autotuner")
+    ap.add_argument("--tune-iters", type=int, default=48, help="iterations of the autotuner's probe step")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests batched at once")
@@ -359,6 +361,10 @@ def main():
         log(f"warm-up step {s}: {st['iterations']} iterations, {time.perf_counter() - t0:.2f} s")
     torch.cuda.synchronize(dev)
     timed_inputs = (x.clone(), xt.clone())
+    tune = None
+    if not args.no_tune:
+        tune = gpu.autotune(x, xt, probe_iters=args.tune_iters)
+        log(f"autotune: {tune}")
 
     # ---- timed region: K further steps of the chain ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -496,7 +502,8 @@ def main():
                "sweep_depth": int(max(s["gs_depth"] for s in stats)),
                "max_vertex_contacts": int(max(s["max_vertex_contacts"] for s in stats)),
                "deterministic_replay": bool(deterministic and e2e_same),
-               "roofline": roof, "kernel_groups": groups, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "autotune": tune, "roofline": roof, "kernel_groups": groups, "cpu_baseline": cpu, "e2e": e2e,
+               "clocks": clk,
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)
     gpu.close()

@@ -160,6 +160,30 @@ cch_status cch_handle_step_host(cch_scene* s, const double* x_t, const double* x
 cch_status cch_batch_handle_step(cch_scene* s, const double* const* x_t, const double* const* x_tilde,
                                  double* const* x_next, cch_step_stats* stats);
 
+/* ---- autotuning (the benchmark spec pattern 2) -----------------------------------
+ * Times candidate launch configurations on a probe: one step from x_t and
+ * x_tilde (device pointers of the single scene), capped at probe_iters
+ * iterations (1..4096), run twice per candidate.  Coordinate descent over:
+ * iterations per graph launch group G in {4, 8, 16, 32, 64}; threads per block
+ * of the BVH queries in {64, 128, 256}; BVH refit at later searches against a
+ * rebuild at every search.  The fastest configuration is kept for the scene's
+ * later steps.  Results never depend on the configuration: each probe's output
+ * is compared bitwise with the first (consistent = 1).  Allocates one scratch
+ * output of n_verts x 3 doubles for the duration of the call. */
+typedef struct {
+  int32_t iters_per_launch;  /* chosen G                                      */
+  int32_t query_block;       /* chosen threads per block of the BVH queries   */
+  int32_t bvh_refit_only;    /* chosen: 1 refit, 0 rebuild at every search    */
+  int32_t trials;            /* configurations timed                          */
+  int32_t consistent;        /* 1: every probe gave the same x_next bitwise    */
+  int32_t reserved_;
+  double best_ms;            /* probe time with the chosen configuration      */
+  double default_ms;         /* probe time with the configuration at entry    */
+} cch_tune_result;
+
+cch_status cch_autotune(cch_scene* s, const double* x_t, const double* x_tilde, int32_t probe_iters,
+                        cch_tune_result* out);
+
 cch_status cch_destroy(cch_scene* s);
 
 /* ---- inspection (tests) ------------------------------------------------ */

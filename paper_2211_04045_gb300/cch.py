@@ -60,6 +60,15 @@ class StepStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("iters_per_launch", C.c_int32), ("query_block", C.c_int32), ("bvh_refit_only", C.c_int32),
+                ("trials", C.c_int32), ("consistent", C.c_int32), ("reserved_", C.c_int32),
+                ("best_ms", C.c_double), ("default_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_"}
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -95,10 +104,12 @@ def lib():
             L.cch_query_pairs_noalloc.argtypes = [p, p, p, d, i32, p, p, i64, C.POINTER(i64)]
             L.cch_set_profiling.argtypes = [p, i32]
             L.cch_get_profile.argtypes = [p, p, p, i32]
+            L.cch_autotune.argtypes = [p, p, p, i32, C.POINTER(TuneResult)]
             for f in ("cch_params_default", "cch_create_scene", "cch_create_batch", "cch_handle_step",
                       "cch_handle_step_host", "cch_batch_handle_step", "cch_destroy", "cch_query_pairs",
                       "cch_server_create", "cch_server_add_scene", "cch_server_submit", "cch_server_wait",
-                      "cch_server_destroy", "cch_set_profiling", "cch_get_profile", "cch_query_pairs_noalloc"):
+                      "cch_server_destroy", "cch_set_profiling", "cch_get_profile", "cch_query_pairs_noalloc",
+                      "cch_autotune"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -254,6 +265,15 @@ class Scene:
         m = min(cnt.value, cap)
         o = np.argsort(keys[:m], kind="stable")
         return keys[:m][o], dist[:m][o]
+
+    def autotune(self, x_t, x_tilde, probe_iters: int = 64):
+        """Times launch configurations on a probe step from (x_t, x_tilde) and
+        keeps the fastest for later steps; returns the choice and timings."""
+        n = self.topos[0].n
+        r = TuneResult()
+        _check(lib().cch_autotune(self.h, C.c_void_p(_dev_ptr(x_t, n)), C.c_void_p(_dev_ptr(x_tilde, n)),
+                                  int(probe_iters), C.byref(r)), "cch_autotune")
+        return r.as_dict()
 
     PROFILE_GROUPS = ("refit", "query_vt", "query_ee", "query_vv", "refresh", "assemble", "order", "sweep",
                       "forward", "control", "setup", "output", "finalize")

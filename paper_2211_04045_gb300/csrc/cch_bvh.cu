@@ -78,7 +78,11 @@ __device__ __forceinline__ int nprim(const Pool& P, int c) { return c == 0 ? P.n
 // ---------------------------------------------------------------------------
 // build
 // ---------------------------------------------------------------------------
-__global__ void k_scene_bounds_reset(Pool P) {
+// gated: run only in iterations that search (BVH rebuilt at every search)
+__device__ __forceinline__ bool gate_off(const Pool& P, int gated) { return gated && !P.cnt->any_search; }
+
+__global__ void k_scene_bounds_reset(Pool P, int gated) {
+  if (gate_off(P, gated)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < P.nscene) {
     unsigned int* b = (unsigned int*)(P.sbox + 2 * i);
@@ -87,7 +91,8 @@ __global__ void k_scene_bounds_reset(Pool P) {
   }
 }
 // bounds of the collision vertices of every scene (ordered-int float atomics)
-__global__ void k_scene_bounds(Pool P) {
+__global__ void k_scene_bounds(Pool P, int gated) {
+  if (gate_off(P, gated)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nvc; i += gridDim.x * blockDim.x) {
     int v = P.vc[i];
     int s = P.vscene[v];
@@ -103,7 +108,8 @@ __global__ void k_scene_bounds(Pool P) {
   }
 }
 
-__global__ void k_morton(Pool P, int c) {
+__global__ void k_morton(Pool P, int c, int gated) {
+  if (gate_off(P, gated)) return;
   BVH& B = bvh_of(P, c);
   int n = nprim(P, c);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -133,7 +139,9 @@ __global__ void k_morton(Pool P, int c) {
 // scatters it.
 constexpr int RS_THREADS = 256, RS_ITEMS = 8, RS_TILE = RS_THREADS * RS_ITEMS;
 
-__global__ void k_radix_hist(const unsigned long long* keys, int n, int shift, unsigned int* hist, int ntiles) {
+__global__ void k_radix_hist(const unsigned long long* keys, int n, int shift, unsigned int* hist, int ntiles,
+                             const int* gate) {
+  if (gate && !*gate) return;
   __shared__ unsigned int h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -147,7 +155,8 @@ __global__ void k_radix_hist(const unsigned long long* keys, int n, int shift, u
 }
 
 // exclusive scan of m entries in one block of 1024 threads
-__global__ void k_scan_1block(unsigned int* a, int m) {
+__global__ void k_scan_1block(unsigned int* a, int m, const int* gate) {
+  if (gate && !*gate) return;
   __shared__ unsigned int part[1024];
   int per = (m + 1023) / 1024;
   int lo = threadIdx.x * per, hi = min(lo + per, m);
@@ -170,7 +179,8 @@ __global__ void k_scan_1block(unsigned int* a, int m) {
 }
 
 __global__ void k_radix_scatter(const unsigned long long* kin, const int* vin, unsigned long long* kout, int* vout,
-                                int n, int shift, const unsigned int* hist, int ntiles) {
+                                int n, int shift, const unsigned int* hist, int ntiles, const int* gate) {
+  if (gate && !*gate) return;
   __shared__ unsigned int wc[8][256];    // per-warp digit counts, then prefixes
   __shared__ unsigned int gb[256];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -228,7 +238,8 @@ __device__ __forceinline__ int delta_k(const unsigned long long* k, int n, int i
 }
 
 // Karras 2012: internal node i covers a contiguous range of sorted leaves
-__global__ void k_karras(Pool P, int c) {
+__global__ void k_karras(Pool P, int c, int gated) {
+  if (gate_off(P, gated)) return;
   BVH& B = bvh_of(P, c);
   int n = B.n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += gridDim.x * blockDim.x) {
@@ -267,7 +278,8 @@ __global__ void k_karras(Pool P, int c) {
 __device__ __forceinline__ int scene_of_pos(const BVH& B, int pos) { return (int)(B.keys[pos] >> 30); }
 
 // the root of each scene's subtree: the highest node whose leaves all belong to one scene
-__global__ void k_scene_roots(Pool P, int c) {
+__global__ void k_scene_roots(Pool P, int c, int gated) {
+  if (gate_off(P, gated)) return;
   BVH& B = bvh_of(P, c);
   int n = B.n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n - 1; i += gridDim.x * blockDim.x) {
@@ -395,7 +407,7 @@ __device__ __forceinline__ void add_candidates(Pool& P, int s, long long n) {
 }
 
 // vertex-triangle pairs: every collision vertex against its scene's triangles
-__global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, double Dq) {
+__global__ void __launch_bounds__(256) k_query_vt(Pool P, int nxt, int mode, double Dq) {
   if (mode == 0 && !P.cnt->any_search) return;
   for (int qi = blockIdx.x * blockDim.x + threadIdx.x; qi < P.nvc; qi += gridDim.x * blockDim.x) {
     int a = P.vc[qi];
@@ -407,7 +419,7 @@ __global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, dou
     double ra = P.rho[a];
     dv3 alo = {xa.x - ra, xa.y - ra, xa.z - ra}, ahi = {xa.x + ra, xa.y + ra, xa.z + ra};
     float Df = __double2float_ru(D);
-    float raf = __double2float_rd(ra);
+    float raf = __double2float_ru(ra);  // rounded up: the bound stays below the distance
     fv3 fa = fk(P.xf[a]);
     bool sa = is_static(P, a);
     long long ncand = 0;
@@ -435,7 +447,7 @@ __global__ void __launch_bounds__(128) k_query_vt(Pool P, int nxt, int mode, dou
 }
 
 // edge-edge pairs: each edge (at sorted leaf position i) against the later leaves of its scene
-__global__ void __launch_bounds__(128) k_query_ee(Pool P, int nxt, int mode, double Dq) {
+__global__ void __launch_bounds__(256) k_query_ee(Pool P, int nxt, int mode, double Dq) {
   if (mode == 0 && !P.cnt->any_search) return;
   const BVH& B = P.be;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n; i += gridDim.x * blockDim.x) {
@@ -468,9 +480,14 @@ __global__ void __launch_bounds__(128) k_query_ee(Pool P, int nxt, int mode, dou
       }
       ncand++;
       fv3 fb0 = fk(P.xf[eb.x]), fb1 = fk(P.xf[eb.y]);
-      float lower = __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
+      // the bound is evaluated in key order (lower edge id first), whichever
+      // edge is the query, so that it does not depend on the tree: in mixed
+      // precision it is the pair's distance
+      bool qlo = lo_e == e1;
+      float lower = qlo ? __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1))
+                        : __fsub_rd(f_ss(fb0, fb1, fa0, fa1), ftol(fb0, fb1, fa0, fa1));
       if (lower >= Df) return;
-      int4 A = lo_e == e1 ? ea : eb, Bv = lo_e == e1 ? eb : ea;
+      int4 A = qlo ? ea : eb, Bv = qlo ? eb : ea;
       push_survivor(P, K_EE, key, make_int4(A.x, A.y, Bv.x, Bv.y), lower);
     });
     if (mode == 0) add_candidates(P, s, ncand);
@@ -478,7 +495,7 @@ __global__ void __launch_bounds__(128) k_query_ee(Pool P, int nxt, int mode, dou
 }
 
 // vertex-vertex pairs: each point against every collision vertex of its scene
-__global__ void __launch_bounds__(128) k_query_vv(Pool P, int nxt, int mode, double Dq) {
+__global__ void __launch_bounds__(256) k_query_vv(Pool P, int nxt, int mode, double Dq) {
   if (mode == 0 && !P.cnt->any_search) return;
   for (int qi = blockIdx.x * blockDim.x + threadIdx.x; qi < P.nq; qi += gridDim.x * blockDim.x) {
     int a = P.pts[qi];
@@ -663,12 +680,30 @@ static int grid_for(long long n, int threads) {
   return (int)g;
 }
 
-void bvh_build(Runtime& R, int c, cudaStream_t st) {
+__global__ void k_copy_sorted(unsigned long long* kd, int* id, const unsigned long long* ks, const int* is, int n,
+                              const int* gate) {
+  if (gate && !*gate) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    kd[i] = ks[i];
+    id[i] = is[i];
+  }
+}
+__global__ void k_sroot_reset(Pool P, int c, int gated) {
+  if (gate_off(P, gated)) return;
+  BVH& B = bvh_of(P, c);
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.nscene; s += gridDim.x * blockDim.x) B.sroot[s] = -1;
+}
+
+// Rebuild of one BVH: Morton codes, radix sort, Karras hierarchy, scene
+// roots.  gated = 1 inside the iteration graph: every kernel returns at once
+// unless the iteration searches.
+void bvh_build(Runtime& R, int c, cudaStream_t st, int gated) {
   Pool& P = R.pool;
   BVH& B = c == 0 ? P.bt : (c == 1 ? P.be : P.bv);
   int n = B.n;
   if (n == 0) return;
-  k_morton<<<grid_for(n, 256), 256, 0, st>>>(P, c);
+  const int* gate = gated ? &P.cnt->any_search : nullptr;
+  k_morton<<<grid_for(n, 256), 256, 0, st>>>(P, c, gated);
   R.launches++;
   int bits = 30 + R.scene_bits;
   int ntiles = (n + RS_TILE - 1) / RS_TILE;
@@ -677,30 +712,30 @@ void bvh_build(Runtime& R, int c, cudaStream_t st) {
   int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; p++) {
     int shift = 8 * p;
-    k_radix_hist<<<ntiles, 256, 0, st>>>(k0, n, shift, B.hist, ntiles);
-    k_scan_1block<<<1, 1024, 0, st>>>(B.hist, 256 * ntiles);
-    k_radix_scatter<<<ntiles, 256, 0, st>>>(k0, v0, k1, v1, n, shift, B.hist, ntiles);
+    k_radix_hist<<<ntiles, 256, 0, st>>>(k0, n, shift, B.hist, ntiles, gate);
+    k_scan_1block<<<1, 1024, 0, st>>>(B.hist, 256 * ntiles, gate);
+    k_radix_scatter<<<ntiles, 256, 0, st>>>(k0, v0, k1, v1, n, shift, B.hist, ntiles, gate);
     R.launches += 3;
     std::swap(k0, k1);
     std::swap(v0, v1);
   }
   if (k0 != B.keys) {
-    cudaMemcpyAsync(B.keys, k0, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(B.ids, v0, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+    k_copy_sorted<<<grid_for(n, 256), 256, 0, st>>>(B.keys, B.ids, k0, v0, n, gate);
+    R.launches++;
   }
-  cudaMemsetAsync(B.sroot, 0xff, sizeof(int) * P.nscene, st);
-  if (n > 1) k_karras<<<grid_for(n - 1, 256), 256, 0, st>>>(P, c);
-  else k_karras<<<1, 32, 0, st>>>(P, c);
-  k_scene_roots<<<grid_for(2 * n - 1, 256), 256, 0, st>>>(P, c);
-  R.launches += 2;
+  k_sroot_reset<<<1, 128, 0, st>>>(P, c, gated);
+  if (n > 1) k_karras<<<grid_for(n - 1, 256), 256, 0, st>>>(P, c, gated);
+  else k_karras<<<1, 32, 0, st>>>(P, c, gated);
+  k_scene_roots<<<grid_for(2 * n - 1, 256), 256, 0, st>>>(P, c, gated);
+  R.launches += 3;
 }
 
-void bvh_build_all(Runtime& R, cudaStream_t st) {
+void bvh_build_all(Runtime& R, cudaStream_t st, int gated) {
   Pool& P = R.pool;
-  k_scene_bounds_reset<<<(P.nscene + 127) / 128, 128, 0, st>>>(P);
-  k_scene_bounds<<<grid_for(P.nvc, 256), 256, 0, st>>>(P);
+  k_scene_bounds_reset<<<(P.nscene + 127) / 128, 128, 0, st>>>(P, gated);
+  k_scene_bounds<<<grid_for(P.nvc, 256), 256, 0, st>>>(P, gated);
   R.launches += 2;
-  for (int c = 0; c < 3; c++) bvh_build(R, c, st);
+  for (int c = 0; c < 3; c++) bvh_build(R, c, st, gated);
 }
 
 __global__ void k_refit_guard_reset(Pool P, int c, int force) {
@@ -763,16 +798,17 @@ void bvh_refit_all(Runtime& R, cudaStream_t st, int force) {
 
 void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t st) {
   Pool& P = R.pool;
+  int bs = R.query_block;
   if (c == 0 && P.nvc && P.nt) {
-    k_query_vt<<<grid_for(P.nvc, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+    k_query_vt<<<grid_for(P.nvc, bs), bs, 0, st>>>(P, nxt, mode, Dq);
     R.launches++;
   }
   if (c == 1 && P.ne > 1) {
-    k_query_ee<<<grid_for(P.ne, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+    k_query_ee<<<grid_for(P.ne, bs), bs, 0, st>>>(P, nxt, mode, Dq);
     R.launches++;
   }
   if (c == 2 && P.nq && P.nvc) {
-    k_query_vv<<<grid_for(P.nq, 128), 128, 0, st>>>(P, nxt, mode, Dq);
+    k_query_vv<<<grid_for(P.nq, bs), bs, 0, st>>>(P, nxt, mode, Dq);
     R.launches++;
   }
 }

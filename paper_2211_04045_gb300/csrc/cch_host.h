@@ -42,7 +42,9 @@ struct Runtime {
   int coop_blocks = 0;               // grid of the cooperative sweep kernel
   int sweeps = 1, solver = 0, ccd = 0, accept = 0, validate = 0;
   int max_iters = 0;                 // max over scenes
-  int iters_per_check = 16;
+  int iters_per_check = 16;          // G: iterations per graph launch group (autotuned)
+  int query_block = 128;             // threads per block of the BVH queries (autotuned)
+  int refit_only = 1;                // 0: rebuild the BVH at every search (autotuned)
   int use_graphs = 1;
   cudaGraphExec_t graph = nullptr;   // two captured iterations
   int graph_pair_cap = -1;
@@ -145,7 +147,7 @@ __device__ __forceinline__ bool is_static(const Pool& P, int v) { return (P.vfla
 
 
 // launchers (cch_bvh.cu)
-void bvh_build_all(Runtime& R, cudaStream_t st);
+void bvh_build_all(Runtime& R, cudaStream_t st, int gated = 0);
 void bvh_refit_all(Runtime& R, cudaStream_t st, int force);
 void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st);
 void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t st);

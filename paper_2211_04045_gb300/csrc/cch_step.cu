@@ -1146,6 +1146,7 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   Pool& P = R.pool;
   int nxt = 1 - cur;
   prof_mark(R, PG_REFIT, 0, st);
+  if (!R.refit_only) bvh_build_all(R, st, 1);
   bvh_refit_all(R, st, 0);
   prof_mark(R, PG_REFIT, 1, st);
   for (int c = 0; c < 3; c++) {

@@ -1,6 +1,7 @@
 """Serving (the benchmark spec pattern 5): resident scenes, requests arriving while
 others run, continuous batching at launch boundaries.  Each result must equal
-the result of the same request run alone (bitwise, FP64)."""
+the result of the same request run alone, bitwise, in FP64 and in mixed
+precision, with either backward step (every path is deterministic)."""
 import time
 
 import numpy as np
@@ -16,13 +17,14 @@ def T(a, dev):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
 
 
-def test_served_results_equal_single_results(cuda):
+@pytest.mark.parametrize("precision,solver", [(0, 0), (1, 0), (0, 1)])
+def test_served_results_equal_single_results(cuda, precision, solver):
     import torch
     mk = [lambda: scenes.cloth_over_sphere(n=10, side=0.5, sphere_subdiv=1, sphere_r=0.15, noise=0.3, seed=1),
           lambda: scenes.two_cloths(n=24, side=0.25, sep=0.004, omega=6.0, noise=0.3, seed=2),
           lambda: scenes.tet_bodies(n_bodies=8, n=4, side=0.08, box=0.32, seed=3)]
     scs = [f() for f in mk]
-    kw = dict(max_iters=150, iters_per_launch=4)
+    kw = dict(max_iters=150, iters_per_launch=4, precision=precision, solver=solver)
     # requests: two successive steps of each scene, plus repeats
     reqs = []
     for k, sc in enumerate(scs):
