@@ -499,7 +499,7 @@ def main():
                "contact_pairs_per_sec": world * pairs / (total_ms / 1000.0),
                "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                "iterations_per_step": float(np.mean(iters)), "converged_steps": int(sum(s["converged"] for s in stats)),
-               "sweep_depth": int(max(s["gs_depth"] for s in stats)),
+               "sweep_depth": int(pst["gs_depth"]),
                "max_vertex_contacts": int(max(s["max_vertex_contacts"] for s in stats)),
                "deterministic_replay": bool(deterministic and e2e_same),
                "autotune": tune, "roofline": roof, "kernel_groups": groups, "cpu_baseline": cpu, "e2e": e2e,

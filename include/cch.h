@@ -123,7 +123,8 @@ typedef struct {
   int32_t gs_depth;          /* longest chain of constraints in one
                                 Gauss-Seidel backward step, each applied after
                                 the previous one at a shared vertex: the
-                                sweep's critical path                         */
+                                sweep's critical path (recorded while
+                                profiling is on, else 1)                      */
   int32_t reserved_;
 } cch_step_stats;
 

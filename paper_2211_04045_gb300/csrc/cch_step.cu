@@ -374,21 +374,27 @@ __device__ __forceinline__ void sty(Pool& P, int v, dv3 a) {
   __stcg(p + 2, a.z);
 }
 
-// lam: multipliers when gs_sweeps > 1 (zero at the first sweep)
-__device__ __forceinline__ void pgs_contact(Pool& P, int ci, double* lam, bool first) {
+// One projected Gauss-Seidel update of a contact (FP64) or edge-length
+// constraint.  The vertex ids come from the caller, so that every load the
+// update needs (y, x, the constraint record) is issued at once; the
+// arithmetic is the same sequence as the oracle's.  lam: multipliers when
+// gs_sweeps > 1 (zero at the first sweep).
+__device__ __forceinline__ void pgs_contact(Pool& P, int ci, const int* vid, double* lam, bool first) {
   const Contact& c = P.cons[ci];
-  if (!(c.den > 0.0)) return;
-  int vid[4] = {c.v.x, c.v.y, c.v.z, c.v.w};
   int nv = vid[2] < 0 ? 2 : 4;
-  double w = c.c0;
-  dv3 yv[4];
+  dv3 yv[4], xv[4];
   for (int k = 0; k < nv; k++) {
     yv[k] = ldy(P, vid[k]);
+    xv[k] = mk(P.x[vid[k]]);
+  }
+  double den = c.den, w = c.c0;
+  if (!(den > 0.0)) return;
+  for (int k = 0; k < nv; k++) {
     dv3 g = {c.g[3 * k], c.g[3 * k + 1], c.g[3 * k + 2]};
-    w = w + vdot(g, vsub(yv[k], mk(P.x[vid[k]])));
+    w = w + vdot(g, vsub(yv[k], xv[k]));
   }
   double l0 = lam && !first ? lam[ci] : 0.0;
-  double tl = l0 - w / c.den;
+  double tl = l0 - w / den;
   double ln = tl > 0.0 ? tl : 0.0;
   double dl = ln - l0;
   if (lam) lam[ci] = ln;
@@ -402,20 +408,21 @@ __device__ __forceinline__ void pgs_contact(Pool& P, int ci, double* lam, bool f
 
 // mixed precision: the same updates in FP32 on the float copy of y
 __device__ __forceinline__ float4 ldyf(const Pool& P, int v) { return __ldcg(P.yf + v); }
-__device__ __forceinline__ void pgs_contact_f(Pool& P, int ci, double* lam, bool first) {
+__device__ __forceinline__ void pgs_contact_f(Pool& P, int ci, const int* vid, double* lam, bool first) {
   const ContactF& c = ((const ContactF*)P.cons)[ci];
-  if (!(c.den > 0.f)) return;
-  int vid[4] = {c.v.x, c.v.y, c.v.z, c.v.w};
   int nv = vid[2] < 0 ? 2 : 4;
-  float w = c.c0;
-  float4 yv[4];
+  float4 yv[4], xv[4];
   for (int k = 0; k < nv; k++) {
     yv[k] = ldyf(P, vid[k]);
-    float4 xv = P.xf[vid[k]];
-    w = w + (c.g[3 * k] * (yv[k].x - xv.x) + c.g[3 * k + 1] * (yv[k].y - xv.y) + c.g[3 * k + 2] * (yv[k].z - xv.z));
+    xv[k] = P.xf[vid[k]];
   }
+  float den = c.den, w = c.c0;
+  if (!(den > 0.f)) return;
+  for (int k = 0; k < nv; k++)
+    w = w + (c.g[3 * k] * (yv[k].x - xv[k].x) + c.g[3 * k + 1] * (yv[k].y - xv[k].y) +
+             c.g[3 * k + 2] * (yv[k].z - xv[k].z));
   float l0 = lam && !first ? (float)lam[ci] : 0.f;
-  float tl = l0 - w / c.den;
+  float tl = l0 - w / den;
   float ln = tl > 0.f ? tl : 0.f;
   float dl = ln - l0;
   if (lam) lam[ci] = ln;
@@ -426,39 +433,39 @@ __device__ __forceinline__ void pgs_contact_f(Pool& P, int ci, double* lam, bool
     __stcg(P.yf + vid[k], o);
   }
 }
-__device__ __forceinline__ void pgs_edge_f(Pool& P, int e, double* lam, bool first) {
-  int4 l = P.lv[e];
+__device__ __forceinline__ void pgs_edge_f(Pool& P, int e, int i, int j, double* lam, bool first) {
   float4 gd = P.lgf[e];
+  float4 yi = ldyf(P, i), yj = ldyf(P, j);
+  float sigma = (float)P.sd[P.vscene[i]].sigma;
   if (!(gd.w > 0.f)) return;
-  float4 yi = ldyf(P, l.x), yj = ldyf(P, l.y);
-  float w = (float)P.sd[l.z].sigma - (gd.x * (yi.x - yj.x) + gd.y * (yi.y - yj.y) + gd.z * (yi.z - yj.z));
+  float w = sigma - (gd.x * (yi.x - yj.x) + gd.y * (yi.y - yj.y) + gd.z * (yi.z - yj.z));
   float l0 = lam && !first ? (float)lam[e] : 0.f;
   float tl = l0 - w / gd.w;
   float ln = tl > 0.f ? tl : 0.f;
   float dl = ln - l0;
   if (lam) lam[e] = ln;
   if (dl == 0.f) return;
-  float si = (float)P.im[l.x] * dl, sj = (float)P.im[l.y] * dl;
-  __stcg(P.yf + l.x, make_float4(yi.x - si * gd.x, yi.y - si * gd.y, yi.z - si * gd.z, 0.f));
-  __stcg(P.yf + l.y, make_float4(yj.x + sj * gd.x, yj.y + sj * gd.y, yj.z + sj * gd.z, 0.f));
+  float si = (float)P.im[i] * dl, sj = (float)P.im[j] * dl;
+  __stcg(P.yf + i, make_float4(yi.x - si * gd.x, yi.y - si * gd.y, yi.z - si * gd.z, 0.f));
+  __stcg(P.yf + j, make_float4(yj.x + sj * gd.x, yj.y + sj * gd.y, yj.z + sj * gd.z, 0.f));
 }
 
-__device__ __forceinline__ void pgs_edge(Pool& P, int e, double* lam, bool first) {
-  int4 l = P.lv[e];
+__device__ __forceinline__ void pgs_edge(Pool& P, int e, int i, int j, double* lam, bool first) {
   P4 gd = P.lg[e];
+  dv3 yi = ldy(P, i), yj = ldy(P, j);
+  double sigma = P.sd[P.vscene[i]].sigma;
   if (!(gd.w > 0.0)) return;
   dv3 g = {gd.x, gd.y, gd.z};
-  dv3 yi = ldy(P, l.x), yj = ldy(P, l.y);
-  double w = P.sd[l.z].sigma - vdot(g, vsub(yi, yj));
+  double w = sigma - vdot(g, vsub(yi, yj));
   double l0 = lam && !first ? lam[e] : 0.0;
   double tl = l0 - w / gd.w;
   double ln = tl > 0.0 ? tl : 0.0;
   double dl = ln - l0;
   if (lam) lam[e] = ln;
   if (dl == 0.0) return;
-  double si = P.im[l.x] * dl, sj = P.im[l.y] * dl;
-  sty(P, l.x, vsub(yi, vscl(si, g)));
-  sty(P, l.y, vadd(yj, vscl(sj, g)));
+  double si = P.im[i] * dl, sj = P.im[j] * dl;
+  sty(P, i, vsub(yi, vscl(si, g)));
+  sty(P, j, vadd(yj, vscl(sj, g)));
 }
 
 // ---------------------------------------------------------------------------
@@ -488,6 +495,7 @@ struct SweepCtx {
   int sweep;
   double* lam;     // contact multipliers (gs_sweeps > 1), else null
   double* elam;    // edge multipliers
+  int levels;      // record chain lengths (statistics; costs a few percent)
 };
 
 __device__ __forceinline__ int contacts_at(const OrderBufs& B, int v) {
@@ -521,59 +529,49 @@ __device__ __forceinline__ void item_wait(const Pool& P, const OrderBufs& B, con
     w.t[2] = w.t[3] = -1;
   }
 }
-// Counters are read with acquire and incremented with release semantics
-// (GPU scope): a constraint that sees its predecessor's increment also sees
-// the predecessor's writes of y.
-__device__ __forceinline__ int ld_acquire(const int* p) {
+// Synchronisation at GPU scope: counters are polled with relaxed loads; once
+// an item's counters are all right, one acquire fence makes its
+// predecessors' writes of y visible; after the item's own writes, one
+// release fence precedes relaxed increments of its counters.  (A release on
+// each increment costs one fence per vertex.)
+__device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void red_release_add(int* p, int v) {
-  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_relaxed_add(int* p, int v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-// brings the item's read-only data (constraint record, x) into L1 while it waits
-__device__ __forceinline__ void item_prefetch(const Pool& P, const SweepCtx& X, int i, const ItemWait& w) {
-  if (i < X.nc) {
-    const char* c = P.mixed ? (const char*)(((const ContactF*)P.cons) + i) : (const char*)(P.cons + i);
-    prefetch_l1(c);
-    prefetch_l1(c + 64);
-    if (!P.mixed) prefetch_l1(c + 128);
-    for (int k = 0; k < 4; k++)
-      if (w.v[k] >= 0) prefetch_l1(P.x + w.v[k]);
-  } else {
-    int e = i - X.nc;
-    if (P.mixed) prefetch_l1(P.lgf + e);
-    else prefetch_l1(P.lg + e);
-  }
-}
-
-__device__ __forceinline__ bool item_ready(const OrderBufs& B, const ItemWait& w) {
-  bool ok = true;
+// constraints still to be applied at the item's vertices before it (0: ready)
+__device__ __forceinline__ int item_gap(const OrderBufs& B, const ItemWait& w) {
+  int gap = 0;
   for (int k = 0; k < 4; k++)
-    if (w.t[k] >= 0) ok &= ld_acquire(&B.vdone[w.v[k]]) == w.t[k];
-  return ok;
+    if (w.t[k] >= 0) gap = max(gap, w.t[k] - ld_relaxed(&B.vdone[w.v[k]]));
+  return gap;
 }
 __device__ __forceinline__ void item_apply(Pool& P, const OrderBufs& B, const SweepCtx& X, int i, const ItemWait& w,
                                            int& maxlvl) {
-  int lvl = 0;
-  for (int k = 0; k < 4; k++)
-    if (w.t[k] >= 0) lvl = max(lvl, __ldcg(&P.vlevel[w.v[k]]));
-  lvl++;
+  fence_acq_rel();
+  int lvl = 1;
+  if (X.levels)
+    for (int k = 0; k < 4; k++)
+      if (w.t[k] >= 0) lvl = max(lvl, __ldcg(&P.vlevel[w.v[k]]) + 1);
   bool first = X.sweep == 0;
   if (i < X.nc) {
-    if (P.mixed) pgs_contact_f(P, i, X.lam, first);
-    else pgs_contact(P, i, X.lam, first);
+    if (P.mixed) pgs_contact_f(P, i, w.v, X.lam, first);
+    else pgs_contact(P, i, w.v, X.lam, first);
   } else {
-    if (P.mixed) pgs_edge_f(P, i - X.nc, X.elam, first);
-    else pgs_edge(P, i - X.nc, X.elam, first);
+    if (P.mixed) pgs_edge_f(P, i - X.nc, w.v[0], w.v[1], X.elam, first);
+    else pgs_edge(P, i - X.nc, w.v[0], w.v[1], X.elam, first);
   }
+  if (X.levels)
+    for (int k = 0; k < 4; k++)
+      if (w.t[k] >= 0) __stcg(&P.vlevel[w.v[k]], lvl);
+  fence_acq_rel();
   for (int k = 0; k < 4; k++)
-    if (w.t[k] >= 0) __stcg(&P.vlevel[w.v[k]], lvl);
-  for (int k = 0; k < 4; k++)
-    if (w.t[k] >= 0) red_release_add(&B.vdone[w.v[k]], 1);
+    if (w.t[k] >= 0) red_relaxed_add(&B.vdone[w.v[k]], 1);
   maxlvl = max(maxlvl, lvl);
 }
 
@@ -592,8 +590,9 @@ __device__ __forceinline__ unsigned long long item_prio(const Pool& P, const Swe
   return splitmix64(d.seed ^ ((3ULL << 62) | (unsigned long long)(e - d.l0)));
 }
 
-__global__ void __launch_bounds__(256, 3) k_gs_sweep(Pool P, OrderBufs B, int sweep, int max_polls) {
+__global__ void __launch_bounds__(256, 2) k_gs_sweep(Pool P, OrderBufs B, int sweep, int max_polls, int levels) {
   SweepCtx X;
+  X.levels = levels;
   X.nc = min(P.cnt->n_cons, P.cons_cap);
   X.sweep = sweep;
   X.lam = P.sd[0].gs_sweeps > 1 ? P.lam : nullptr;
@@ -620,19 +619,32 @@ __global__ void __launch_bounds__(256, 3) k_gs_sweep(Pool P, OrderBufs B, int sw
       items[j] = i;
       keys[j] = key;
     }
-    for (int j = 0; j < m; j++) {
-      ItemWait w;
-      item_wait(P, B, X, items[j], w);
-      item_prefetch(P, X, items[j], w);
-      while (!item_ready(B, w)) {
-        if (++polls > max_polls) {
-          atomicOr(&P.cnt->err, ERR_POLL);
-          j = m;
-          break;
+    // The lanes of a warp advance together: each round every lane checks
+    // its head item; the lanes whose head is ready apply it, and the warp
+    // sleeps only when none is (a lane spinning alone would take issue
+    // slots from a lane of its warp that could apply).  The sleep grows with
+    // the smallest number of constraints still ahead of a head item.
+    int j = 0;
+    ItemWait w;
+    bool has = m > 0;
+    if (has) item_wait(P, B, X, items[0], w);
+    while (__any_sync(0xffffffffu, has)) {
+      int gap = has ? item_gap(B, w) : 1 << 30;
+      bool ready = has && gap == 0;
+      if (__any_sync(0xffffffffu, ready)) {
+        if (ready) {
+          item_apply(P, B, X, items[j], w, maxlvl);
+          has = ++j < m;
+          if (has) item_wait(P, B, X, items[j], w);
         }
-        __nanosleep(20);
+        continue;
       }
-      if (j < m) item_apply(P, B, X, items[j], w, maxlvl);
+      if (++polls > max_polls) {  // the same count in every lane
+        if ((threadIdx.x & 31) == 0) atomicOr(&P.cnt->err, ERR_POLL);
+        break;
+      }
+      int g = __reduce_min_sync(0xffffffffu, gap);
+      __nanosleep(min(32 + 128 * (g - 1), 4096));
     }
   } else {
     // more items than that: poll every pending item each round
@@ -642,7 +654,7 @@ __global__ void __launch_bounds__(256, 3) k_gs_sweep(Pool P, OrderBufs B, int sw
         if (P.fdone[i] || !item_live(P, X, i)) continue;
         ItemWait w;
         item_wait(P, B, X, i, w);
-        if (item_ready(B, w)) {
+        if (item_gap(B, w) == 0) {
           item_apply(P, B, X, i, w, maxlvl);
           P.fdone[i] = 1;
           progressed = true;
@@ -1184,7 +1196,7 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     R.launches += 5 + 2 * R.sweeps;
   } else {  // projected Gauss-Seidel
     cudaMemsetAsync(B.vdone, 0, sizeof(int) * (size_t)P.nv, st);
-    cudaMemsetAsync(P.vlevel, 0, sizeof(int) * (size_t)P.nv, st);
+    if (R.profiling) cudaMemsetAsync(P.vlevel, 0, sizeof(int) * (size_t)P.nv, st);
     if (P.mixed) {
       ContactFAcc acc{(const ContactF*)P.cons};
       k_inc_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
@@ -1202,7 +1214,7 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     prof_mark(R, PG_SWEEP, 0, st);
     for (int sw = 0; sw < R.sweeps && e == cudaSuccess; sw++) {
       cudaMemsetAsync(P.fdone, 0, (size_t)P.cons_cap + P.nl, st);
-      e = coop_launch(k_gs_sweep, R.coop_blocks, 256, st, P, B, sw, 1 << 22);
+      e = coop_launch(k_gs_sweep, R.coop_blocks, 256, st, P, B, sw, 1 << 22, R.profiling);
     }
     prof_mark(R, PG_SWEEP, 1, st);
     R.launches += 4 + R.sweeps;
