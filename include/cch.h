@@ -167,7 +167,9 @@ cch_status cch_batch_handle_step(cch_scene* s, const double* const* x_t, const d
  * iterations (1..4096), run twice per candidate.  Coordinate descent over:
  * iterations per graph launch group G in {4, 8, 16, 32, 64}; threads per block
  * of the BVH queries in {64, 128, 256}; BVH refit at later searches against a
- * rebuild at every search.  The fastest configuration is kept for the scene's
+ * rebuild at every search; warp-packet traversal (the 32 lanes of a warp
+ * descend together, each keeping its own tests) against one traversal per
+ * thread.  The fastest configuration is kept for the scene's
  * later steps.  Results never depend on the configuration: each probe's output
  * is compared bitwise with the first (consistent = 1).  Allocates one scratch
  * output of n_verts x 3 doubles for the duration of the call. */
@@ -177,7 +179,7 @@ typedef struct {
   int32_t bvh_refit_only;    /* chosen: 1 refit, 0 rebuild at every search    */
   int32_t trials;            /* configurations timed                          */
   int32_t consistent;        /* 1: every probe gave the same x_next bitwise    */
-  int32_t reserved_;
+  int32_t packet_traversal;  /* chosen: 1 warp-packet, 0 thread-per-query      */
   double best_ms;            /* probe time with the chosen configuration      */
   double default_ms;         /* probe time with the configuration at entry    */
 } cch_tune_result;

@@ -62,11 +62,11 @@ class StepStats(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("iters_per_launch", C.c_int32), ("query_block", C.c_int32), ("bvh_refit_only", C.c_int32),
-                ("trials", C.c_int32), ("consistent", C.c_int32), ("reserved_", C.c_int32),
+                ("trials", C.c_int32), ("consistent", C.c_int32), ("packet_traversal", C.c_int32),
                 ("best_ms", C.c_double), ("default_ms", C.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def lib_path() -> str:

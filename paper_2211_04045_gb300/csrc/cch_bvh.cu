@@ -406,6 +406,182 @@ __device__ __forceinline__ void add_candidates(Pool& P, int s, long long n) {
   if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].candidates, (unsigned long long)t);
 }
 
+// ---------------------------------------------------------------------------
+// Packet traversal for the step's searches.  The 32 lanes of a warp take 32
+// consecutive queries in Morton order (close in space) and descend the tree
+// together: a node is entered when the box of any lane is near it, and every
+// lane keeps its own tests, so each lane reaches exactly the leaves that its
+// own traversal would.  The node loads are shared and the box tests run on
+// all lanes at once (a thread-per-query traversal kept ~5 of 32 lanes busy).
+// The stack lives in shared memory, one per warp; lanes of different scenes
+// descend in turn, each from its scene's root.
+// ---------------------------------------------------------------------------
+constexpr int PACKET_STACK = 64;
+
+template <class LeafFn>
+__device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, float3 qlo, float3 qhi, float Df,
+                                              int min_pos, int* stack, Counters* cnt, LeafFn leaf) {
+  const unsigned FULL = 0xffffffffu;
+  int lane = threadIdx.x & 31;
+  if (root < 0) return;
+  if (root & LEAF) {
+    int l = root & ~LEAF;
+    if (act && l > min_pos) {
+      float4 lo = B.leafbox[2 * l], hi = B.leafbox[2 * l + 1];
+      if (fbox_near(lo, hi, qlo, qhi, Df)) leaf(l);
+    }
+    return;
+  }
+  __syncwarp();
+  if (lane == 0) stack[0] = root;
+  int sp = 1;  // identical in every lane
+  int budget = B.n + 2;
+  __syncwarp();
+  while (sp > 0) {
+    if (--budget < 0) {
+      if (lane == 0) atomicOr(&cnt->err, 4);
+      return;
+    }
+    int node = stack[--sp];
+    __syncwarp();
+    bool ok = act && B.range_hi[node] > min_pos;
+    float4 a = B.box[3 * node], b = B.box[3 * node + 1], d = B.box[3 * node + 2];
+    float4 llo = make_float4(a.x, a.y, a.z, 0.f), lhi = make_float4(a.w, b.x, b.y, 0.f);
+    float4 rlo = make_float4(b.z, b.w, d.x, 0.f), rhi = make_float4(d.y, d.z, d.w, 0.f);
+    int L = B.left[node], R = B.right[node];
+    bool hr = ok && fbox_near(rlo, rhi, qlo, qhi, Df) && (!(R & LEAF) || (R & ~LEAF) > min_pos);
+    bool hl = ok && fbox_near(llo, lhi, qlo, qhi, Df) && (!(L & LEAF) || (L & ~LEAF) > min_pos);
+    unsigned mr = __ballot_sync(FULL, hr), ml = __ballot_sync(FULL, hl);
+    if (mr) {
+      if (R & LEAF) {
+        if (hr) leaf(R & ~LEAF);
+      } else if (sp < PACKET_STACK) {
+        if (lane == 0) stack[sp] = R;
+        sp++;
+      } else if (lane == 0) {
+        atomicOr(&cnt->err, 2);
+      }
+    }
+    if (ml) {
+      if (L & LEAF) {
+        if (hl) leaf(L & ~LEAF);
+      } else if (sp < PACKET_STACK) {
+        if (lane == 0) stack[sp] = L;
+        sp++;
+      } else if (lane == 0) {
+        atomicOr(&cnt->err, 2);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// vertex-triangle pairs of the step's searches, queries in the Morton order
+// of the collision vertices
+__global__ void __launch_bounds__(256) k_pquery_vt(Pool P) {
+  __shared__ int stacks[8][PACKET_STACK];
+  if (!P.cnt->any_search) return;
+  const unsigned FULL = 0xffffffffu;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  int nq = P.bv.n;
+  for (int base = gw * 32; base < nq; base += nw * 32) {
+    int i = base + lane;
+    int a = -1, s = -1;
+    bool pend = false;
+    if (i < nq) {
+      a = P.vc[P.bv.ids[i]];
+      s = P.vscene[a];
+      pend = searching(P, s);
+    }
+    double ra = a >= 0 ? P.rho[a] : 0.0;
+    dv3 xa = a >= 0 ? mk(P.x[a]) : dv3{0.0, 0.0, 0.0};
+    dv3 alo = {xa.x - ra, xa.y - ra, xa.z - ra}, ahi = {xa.x + ra, xa.y + ra, xa.z + ra};
+    float3 qlo = f3rd(alo), qhi = f3ru(ahi);
+    float Df = s >= 0 ? __double2float_ru(P.sd[s].d_max) : 0.f;
+    float raf = __double2float_ru(ra);  // rounded up: the bound stays below the distance
+    fv3 fa = a >= 0 ? fk(P.xf[a]) : fv3{0.f, 0.f, 0.f};
+    bool sa = a >= 0 && is_static(P, a);
+    long long ncand = 0;
+    while (__any_sync(FULL, pend)) {
+      int leader = __ffs(__ballot_sync(FULL, pend)) - 1;
+      int sc = __shfl_sync(FULL, s, leader);
+      bool mine = pend && s == sc;
+      const SceneDesc& S = P.sd[sc];
+      traverse_warp(P.bt, P.bt.sroot[sc], mine, qlo, qhi, Df, -1, stacks[warp], P.cnt, [&](int pos) {
+        int t = P.bt.ids[pos];
+        int4 tv = P.tv[t];
+        if (a == tv.x || a == tv.y || a == tv.z) return;
+        if (sa && is_static(P, tv.x) && is_static(P, tv.y) && is_static(P, tv.z)) return;
+        ncand++;
+        fv3 f1 = fk(P.xf[tv.x]), f2 = fk(P.xf[tv.y]), f3 = fk(P.xf[tv.z]);
+        float lower = __fsub_rd(__fsub_rd(f_pt(fa, f1, f2, f3), raf), ftol(fa, f1, f2, f3));
+        if (lower >= Df) return;
+        push_survivor(P, K_VT, mkkey(K_VT, a - S.v0, t - S.t0), make_int4(a, tv.x, tv.y, tv.z), lower);
+      });
+      if (mine) pend = false;
+    }
+    if (s >= 0 && ncand) add_candidates(P, s, ncand);
+  }
+}
+
+// edge-edge pairs of the step's searches: each edge (at sorted leaf position
+// i) against the later leaves of its scene
+__global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
+  __shared__ int stacks[8][PACKET_STACK];
+  if (!P.cnt->any_search) return;
+  const unsigned FULL = 0xffffffffu;
+  const BVH& B = P.be;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int base = gw * 32; base < B.n; base += nw * 32) {
+    int i = base + lane;
+    int e1 = -1, s = -1;
+    int4 ea = make_int4(-1, -1, -1, -1);
+    bool pend = false;
+    if (i < B.n) {
+      e1 = B.ids[i];
+      ea = P.ev[e1];
+      s = ea.z;
+      pend = searching(P, s);
+    }
+    dv3 alo = {0.0, 0.0, 0.0}, ahi = {0.0, 0.0, 0.0};
+    if (e1 >= 0) {
+      int sc;
+      prim_box(P, 1, e1, alo, ahi, sc);
+    }
+    float3 qlo = f3rd(alo), qhi = f3ru(ahi);
+    float Df = s >= 0 ? __double2float_ru(P.sd[s].d_max) : 0.f;
+    bool sa = e1 >= 0 && is_static(P, ea.x) && is_static(P, ea.y);
+    fv3 fa0 = e1 >= 0 ? fk(P.xf[ea.x]) : fv3{0.f, 0.f, 0.f}, fa1 = e1 >= 0 ? fk(P.xf[ea.y]) : fv3{0.f, 0.f, 0.f};
+    long long ncand = 0;
+    while (__any_sync(FULL, pend)) {
+      int leader = __ffs(__ballot_sync(FULL, pend)) - 1;
+      int sc = __shfl_sync(FULL, s, leader);
+      bool mine = pend && s == sc;
+      const SceneDesc& S = P.sd[sc];
+      traverse_warp(B, B.sroot[sc], mine, qlo, qhi, Df, i, stacks[warp], P.cnt, [&](int pos) {
+        int e2 = B.ids[pos];
+        int4 eb = P.ev[e2];
+        if (ea.x == eb.x || ea.x == eb.y || ea.y == eb.x || ea.y == eb.y) return;
+        if (sa && is_static(P, eb.x) && is_static(P, eb.y)) return;
+        ncand++;
+        fv3 fb0 = fk(P.xf[eb.x]), fb1 = fk(P.xf[eb.y]);
+        // the bound in key order (lower edge id first), whichever edge is the query
+        bool qlow = e1 < e2;
+        float lower = qlow ? __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1))
+                           : __fsub_rd(f_ss(fb0, fb1, fa0, fa1), ftol(fb0, fb1, fa0, fa1));
+        if (lower >= Df) return;
+        int4 A = qlow ? ea : eb, Bv = qlow ? eb : ea;
+        push_survivor(P, K_EE, mkkey(K_EE, min(e1, e2) - S.e0, max(e1, e2) - S.e0), make_int4(A.x, A.y, Bv.x, Bv.y),
+                      lower);
+      });
+      if (mine) pend = false;
+    }
+    if (s >= 0 && ncand) add_candidates(P, s, ncand);
+  }
+}
+
 // vertex-triangle pairs: every collision vertex against its scene's triangles
 __global__ void __launch_bounds__(256) k_query_vt(Pool P, int nxt, int mode, double Dq) {
   if (mode == 0 && !P.cnt->any_search) return;
@@ -799,6 +975,18 @@ void bvh_refit_all(Runtime& R, cudaStream_t st, int force) {
 void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t st) {
   Pool& P = R.pool;
   int bs = R.query_block;
+  if (mode == 0 && R.packet) {
+    if (c == 0 && P.nvc && P.nt) {
+      k_pquery_vt<<<grid_for(P.nvc, bs), bs, 0, st>>>(P);
+      R.launches++;
+      return;
+    }
+    if (c == 1 && P.ne > 1) {
+      k_pquery_ee<<<grid_for(P.ne, bs), bs, 0, st>>>(P);
+      R.launches++;
+      return;
+    }
+  }
   if (c == 0 && P.nvc && P.nt) {
     k_query_vt<<<grid_for(P.nvc, bs), bs, 0, st>>>(P, nxt, mode, Dq);
     R.launches++;

@@ -669,23 +669,24 @@ cch_status cch_handle_step_host(cch_scene* S, const double* x_t, const double* x
 // Autotuner of the launch configuration (the benchmark spec pattern 2).  Candidate
 // values are timed on a probe (one step from the caller's inputs, capped at
 // probe_iters iterations) by coordinate descent: iterations per graph launch
-// group, then the block size of the BVH queries, then BVH refit against
-// rebuild.  The configuration does not change results; every probe's output
+// group, the block size of the BVH queries, BVH refit against rebuild, and
+// warp-packet against thread-per-query traversal.  The configuration does not change results; every probe's output
 // is compared bitwise with the first and the outcome reported.
 namespace {
 struct TuneCfg {
-  int g, block, refit;
+  int g, block, refit, packet;
 };
 cch_status time_probe(cch_scene* S, const TuneCfg& c, double* ms, std::vector<double>& out, double* dout,
                       size_t n3) {
   Runtime& R = S->R;
-  if (R.iters_per_check != c.g || R.query_block != c.block || R.refit_only != c.refit) {
+  if (R.iters_per_check != c.g || R.query_block != c.block || R.refit_only != c.refit || R.packet != c.packet) {
     if (R.graph) cudaGraphExecDestroy(R.graph);
     R.graph = nullptr;
   }
   R.iters_per_check = c.g;
   R.query_block = c.block;
   R.refit_only = c.refit;
+  R.packet = c.packet;
   double best = 1e300;
   for (int rep = 0; rep < 2; rep++) {
     cch_step_stats st;
@@ -717,22 +718,23 @@ cch_status cch_autotune(cch_scene* S, const double* x_t, const double* x_tilde, 
   int saved_max = R.max_iters;
   cudaError_t e = cudaMemcpy(R.pool.sd, capped.data(), sizeof(SceneDesc) * capped.size(), cudaMemcpyHostToDevice);
   R.max_iters = probe_iters;
-  TuneCfg best{R.iters_per_check, R.query_block, R.refit_only};
+  TuneCfg best{R.iters_per_check, R.query_block, R.refit_only, R.packet};
   double best_ms = 0.0, default_ms = 0.0;
   int trials = 0, consistent = 1;
   std::vector<double> ref, got;
   cch_status r = e == cudaSuccess ? time_probe(S, best, &best_ms, ref, dout, n3) : cuda_fail(e);
   default_ms = best_ms;
   trials++;
-  static const int gs[] = {4, 8, 16, 32, 64}, blocks[] = {64, 128, 256}, refits[] = {1, 0};
-  for (int stage = 0; stage < 3 && r == CCH_OK; stage++) {
+  static const int gs[] = {4, 8, 16, 32, 64}, blocks[] = {64, 128, 256}, binary[] = {1, 0};
+  for (int stage = 0; stage < 4 && r == CCH_OK; stage++) {
     int nc = stage == 0 ? 5 : (stage == 1 ? 3 : 2);
     for (int k = 0; k < nc && r == CCH_OK; k++) {
       TuneCfg c = best;
       if (stage == 0) c.g = gs[k];
       if (stage == 1) c.block = blocks[k];
-      if (stage == 2) c.refit = refits[k];
-      if (c.g == best.g && c.block == best.block && c.refit == best.refit) continue;
+      if (stage == 2) c.refit = binary[k];
+      if (stage == 3) c.packet = binary[k];
+      if (c.g == best.g && c.block == best.block && c.refit == best.refit && c.packet == best.packet) continue;
       double ms = 0.0;
       r = time_probe(S, c, &ms, got, dout, n3);
       trials++;
@@ -752,6 +754,7 @@ cch_status cch_autotune(cch_scene* S, const double* x_t, const double* x_tilde, 
   R.iters_per_check = best.g;
   R.query_block = best.block;
   R.refit_only = best.refit;
+  R.packet = best.packet;
   cudaFree(dout);
   if (r != CCH_OK) return r;
   out->iters_per_launch = best.g;
@@ -759,7 +762,7 @@ cch_status cch_autotune(cch_scene* S, const double* x_t, const double* x_tilde, 
   out->bvh_refit_only = best.refit;
   out->trials = trials;
   out->consistent = consistent;
-  out->reserved_ = 0;
+  out->packet_traversal = best.packet;
   out->best_ms = best_ms;
   out->default_ms = default_ms;
   return CCH_OK;

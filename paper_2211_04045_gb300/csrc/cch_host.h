@@ -45,6 +45,7 @@ struct Runtime {
   int iters_per_check = 16;          // G: iterations per graph launch group (autotuned)
   int query_block = 128;             // threads per block of the BVH queries (autotuned)
   int refit_only = 1;                // 0: rebuild the BVH at every search (autotuned)
+  int packet = 1;                    // warp-packet BVH traversal for the searches (autotuned)
   int use_graphs = 1;
   cudaGraphExec_t graph = nullptr;   // two captured iterations
   int graph_pair_cap = -1;
