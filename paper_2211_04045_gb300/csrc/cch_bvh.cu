@@ -18,13 +18,6 @@ namespace cch {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned int fl_ord(float f) {
-  unsigned int u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float ord_fl(unsigned int u) {
-  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
 __device__ __forceinline__ unsigned int expand10(unsigned int v) {
   v = (v * 0x00010001u) & 0xFF0000FFu;
   v = (v * 0x00000101u) & 0x0F00F00Fu;
@@ -713,52 +706,104 @@ __global__ void __launch_bounds__(256) k_query_vv(Pool P, int nxt, int mode, dou
 // R3 (implied by dist < D up to rounding; evaluated so that P equals the
 // oracle's set), for every FP32-filter survivor.  The three kinds occupy
 // separate regions, so a warp almost always runs one kind's arithmetic.
+// exact FP64 distance of a pair (R5) and the exact candidate box test (R3)
+__device__ __forceinline__ double exact_dist(const Pool& P, int kind, int4 v) {
+  dv3 a = mk(P.x[v.x]), b = mk(P.x[v.y]);
+  if (kind == K_VV) return (vnorm(vsub(a, b)) - P.rho[v.x]) - P.rho[v.y];
+  dv3 c = mk(P.x[v.z]), e = mk(P.x[v.w]);
+  if (kind == K_VT) return d_pt(a, b, c, e) - P.rho[v.x];
+  double ps, pt;
+  return d_ss(a, b, c, e, &ps, &pt);
+}
+__device__ __forceinline__ bool exact_box(const Pool& P, int kind, int4 v, double D) {
+  dv3 a = mk(P.x[v.x]), b = mk(P.x[v.y]);
+  dv3 alo, ahi, blo, bhi;
+  if (kind == K_VV) {
+    double ra = P.rho[v.x], rb = P.rho[v.y];
+    alo = {a.x - ra, a.y - ra, a.z - ra}; ahi = {a.x + ra, a.y + ra, a.z + ra};
+    blo = {b.x - rb, b.y - rb, b.z - rb}; bhi = {b.x + rb, b.y + rb, b.z + rb};
+  } else {
+    dv3 c = mk(P.x[v.z]), e = mk(P.x[v.w]);
+    if (kind == K_VT) {
+      double ra = P.rho[v.x];
+      alo = {a.x - ra, a.y - ra, a.z - ra}; ahi = {a.x + ra, a.y + ra, a.z + ra};
+      blo = {fmin(fmin(b.x, c.x), e.x), fmin(fmin(b.y, c.y), e.y), fmin(fmin(b.z, c.z), e.z)};
+      bhi = {fmax(fmax(b.x, c.x), e.x), fmax(fmax(b.y, c.y), e.y), fmax(fmax(b.z, c.z), e.z)};
+    } else {
+      alo = {fmin(a.x, b.x), fmin(a.y, b.y), fmin(a.z, b.z)}; ahi = {fmax(a.x, b.x), fmax(a.y, b.y), fmax(a.z, b.z)};
+      blo = {fmin(c.x, e.x), fmin(c.y, e.y), fmin(c.z, e.z)}; bhi = {fmax(c.x, e.x), fmax(c.y, e.y), fmax(c.z, e.z)};
+    }
+  }
+  return box_near(alo, ahi, blo, bhi, D);
+}
+
+__device__ __forceinline__ void survivor_at(const Pool& P, int i, int& kind, size_t& o) {
+  int n0 = min(P.cnt->n_fcand[0], P.pair_cap), n1 = min(P.cnt->n_fcand[1], P.pair_cap);
+  kind = i < n0 ? K_VT : (i < n0 + n1 ? K_EE : K_VV);
+  int j = kind == K_VT ? i : (kind == K_EE ? i - n0 : i - n0 - n1);
+  o = (size_t)kind * P.pair_cap + j;
+}
+__device__ __forceinline__ int survivors(const Pool& P) {
+  return min(P.cnt->n_fcand[0], P.pair_cap) + min(P.cnt->n_fcand[1], P.pair_cap) +
+         min(P.cnt->n_fcand[2], P.pair_cap);
+}
+
+// Step searches in FP64, pass A: FP32 bounds and the exact box test of every
+// survivor, smallest upper bound of the certain pairs per vertex.
+__global__ void k_final_bounds(Pool P) {
+  if (!P.cnt->any_search) return;
+  int total = survivors(P);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int kind;
+    size_t o;
+    survivor_at(P, i, kind, o);
+    int4 v = P.fv[o];
+    double D = P.sd[P.vscene[v.x]].d_max;
+    float2 b = pair_bounds32(P, P.fkey[o], v);
+    // a distance below D bounds every axis gap of the boxes, so the exact box
+    // test passes whenever the upper bound is below D by more than the
+    // rounding of the box corners; it runs only for the other pairs
+    if ((double)b.y < D * (1.0 - 1e-12)) note_upper(P, v, b.y);
+    else if (!exact_box(P, kind, v, D)) b = make_float2(INFINITY, INFINITY);
+    else if ((double)b.y < D) note_upper(P, v, b.y);
+    P.fbs[o] = b;
+  }
+}
+
+// The exact stage of a search: P = survivors with an FP64 distance below D
+// that pass the exact box test.  mode 0 (the step, FP64): pass B, exact
+// distances only where they decide something; mixed precision: the FP32
+// lower bound is the distance; modes 1, 2 (inspection): everything exact.
 __global__ void k_finalize(Pool P, int nxt, int mode, double Dq) {
   if (mode == 0 && !P.cnt->any_search) return;
-  int n0 = min(P.cnt->n_fcand[0], P.pair_cap), n1 = min(P.cnt->n_fcand[1], P.pair_cap);
-  int n2 = min(P.cnt->n_fcand[2], P.pair_cap);
-  int total = n0 + n1 + n2;
+  int total = survivors(P);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    int kind = i < n0 ? K_VT : (i < n0 + n1 ? K_EE : K_VV);
-    int j = kind == K_VT ? i : (kind == K_EE ? i - n0 : i - n0 - n1);
-    size_t o = (size_t)kind * P.pair_cap + j;
+    int kind;
+    size_t o;
+    survivor_at(P, i, kind, o);
     unsigned long long key = P.fkey[o];
     int4 v = P.fv[o];
     int s = P.vscene[v.x];
     double D = mode == 0 ? P.sd[s].d_max : Dq;
-    if (P.mixed && mode == 0) {
+    if (mode == 0 && P.mixed) {
       // mixed precision: the FP32 lower bound is the pair's distance
       double d = (double)P.fd[o];
       if (d < D) emit_pair(P, nxt, s, key, v, d);
       continue;
     }
-    dv3 a = mk(P.x[v.x]), b = mk(P.x[v.y]);
-    double d;
-    dv3 alo, ahi, blo, bhi;
-    if (kind == K_VV) {
-      double ra = P.rho[v.x], rb = P.rho[v.y];
-      d = (vnorm(vsub(a, b)) - ra) - rb;
-      if (!(d < D)) continue;
-      alo = {a.x - ra, a.y - ra, a.z - ra}; ahi = {a.x + ra, a.y + ra, a.z + ra};
-      blo = {b.x - rb, b.y - rb, b.z - rb}; bhi = {b.x + rb, b.y + rb, b.z + rb};
-    } else {
-      dv3 c = mk(P.x[v.z]), e = mk(P.x[v.w]);
-      if (kind == K_VT) {
-        double ra = P.rho[v.x];
-        d = d_pt(a, b, c, e) - ra;
-        if (!(d < D)) continue;
-        alo = {a.x - ra, a.y - ra, a.z - ra}; ahi = {a.x + ra, a.y + ra, a.z + ra};
-        blo = {fmin(fmin(b.x, c.x), e.x), fmin(fmin(b.y, c.y), e.y), fmin(fmin(b.z, c.z), e.z)};
-        bhi = {fmax(fmax(b.x, c.x), e.x), fmax(fmax(b.y, c.y), e.y), fmax(fmax(b.z, c.z), e.z)};
+    if (mode == 0) {
+      float2 b = P.fbs[o];
+      if (!(b.x < INFINITY)) continue;  // failed the exact box test
+      if (needs_exact(P, v, b, D, P.sd[s].delta)) {
+        double d = exact_dist(P, kind, v);
+        if (d < D) emit_pair(P, nxt, s, key, v, d);
       } else {
-        double ps, pt;
-        d = d_ss(a, b, c, e, &ps, &pt);
-        if (!(d < D)) continue;
-        alo = {fmin(a.x, b.x), fmin(a.y, b.y), fmin(a.z, b.z)}; ahi = {fmax(a.x, b.x), fmax(a.y, b.y), fmax(a.z, b.z)};
-        blo = {fmin(c.x, e.x), fmin(c.y, e.y), fmin(c.z, e.z)}; bhi = {fmax(c.x, e.x), fmax(c.y, e.y), fmax(c.z, e.z)};
+        emit_pair(P, nxt, s, key, v, (double)b.x);  // certainly in P; its distance decides nothing
       }
+      continue;
     }
-    if (!box_near(alo, ahi, blo, bhi, D)) continue;
+    double d = exact_dist(P, kind, v);
+    if (!(d < D) || !exact_box(P, kind, v, D)) continue;
     if (mode == 2) emit_query(P, key, d);
     else emit_pair(P, nxt, s, key, v, d);
   }
@@ -1003,6 +1048,10 @@ void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t s
 
 void finalize_search(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) {
   Pool& P = R.pool;
+  if (mode == 0 && !P.mixed) {
+    k_final_bounds<<<grid_for(3LL * P.pair_cap, 256), 256, 0, st>>>(P);
+    R.launches++;
+  }
   k_finalize<<<grid_for(3LL * P.pair_cap, 256), 256, 0, st>>>(P, nxt, mode, Dq);
   R.launches++;
 }

@@ -151,7 +151,13 @@ cudaError_t alloc_pairs(Runtime& R) {
   if ((e = dalloc_in(L, &P.fkey, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.fv, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
   P.fd = nullptr;
+  P.fbs = nullptr;
+  P.fbr = nullptr;
   if (P.mixed && (e = dalloc_in(L, &P.fd, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
+  if (!P.mixed) {
+    if ((e = dalloc_in(L, &P.fbs, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
+    if ((e = dalloc_in(L, &P.fbr, (size_t)P.pair_cap)) != cudaSuccess) return e;
+  }
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.fdone, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.iprio, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
@@ -305,6 +311,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(dalloc(R, &P.cnt, 1));
   CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
   CK(dalloc(R, &P.vlevel, nv));
+  CK(dalloc(R, &P.vmin, nv));
   P.vlstart = nullptr;
   P.vllist = nullptr;
   if (R.solver == CCH_SOLVER_JACOBI) {

@@ -164,6 +164,9 @@ struct Pool {
   unsigned long long* fkey;  // FP32-filter survivors: 3 regions of pair_cap (VT, EE, VV)
   int4* fv;
   float* fd;               // mixed precision: the survivor's FP32 distance lower bound
+  float2* fbs;             // FP64 mode: survivors' FP32 bounds (3 regions of pair_cap); +inf = dropped
+  float2* fbr;             // FP64 mode: refreshed pairs' FP32 bounds (pair_cap)
+  unsigned int* vmin;      // per vertex: smallest upper bound of a certain pair (fl_ord image)
   Contact* cons;
   unsigned char* fdone;    // Gauss-Seidel sweep: applied flags (cons_cap + nl)
   int* vlevel;             // per vertex: chain length of its last applied constraint
@@ -394,6 +397,14 @@ __device__ __forceinline__ float ftol(fv3 a, fv3 b, fv3 c, fv3 d) {
   return FILTER_TOL * (X + M) + 1e-30f;
 }
 
+// monotone unsigned image of a float (a < b <=> fl_ord(a) < fl_ord(b))
+__device__ __forceinline__ unsigned int fl_ord(float f) {
+  unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_fl(unsigned int u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
 // The exact candidate test (R3): on every axis fl(lo_b - hi_a) <= D and
 // fl(lo_a - hi_b) <= D.
 __device__ __forceinline__ bool box_near(dv3 alo, dv3 ahi, dv3 blo, dv3 bhi, double D) {

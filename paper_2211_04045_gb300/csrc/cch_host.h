@@ -102,6 +102,62 @@ __device__ __forceinline__ int claim(int* ctr, int cap) {
   return idx < cap ? idx : -1;
 }
 
+// FP32 bounds (lower, upper) of a pair's FP64 distance from the float copy of
+// the positions: d32 -/+ FILTER_TOL * (|x|max + extent), rounded outward.
+// VT: point-triangle minus the point's radius; EE: segment-segment; VV:
+// centre distance minus both radii.  The lower bound is the one the search's
+// FP32 filter uses.
+__device__ __forceinline__ float2 pair_bounds32(const Pool& P, unsigned long long key, int4 v) {
+  int kind = (int)(key >> 62);
+  fv3 a = fk(P.xf[v.x]), b = fk(P.xf[v.y]);
+  if (kind == K_VV) {
+    fv3 d = fsub(a, b);
+    float dd = sqrtf(fdot(d, d)), t = ftol(a, b, b, b);
+    double r = P.rho[v.x] + P.rho[v.y];
+    return make_float2(__fsub_rd(__fsub_rd(dd, __double2float_ru(r)), t),
+                       __fadd_ru(__fsub_ru(dd, __double2float_rd(r)), t));
+  }
+  fv3 c = fk(P.xf[v.z]), d = fk(P.xf[v.w]);
+  float t = ftol(a, b, c, d);
+  if (kind == K_VT) {
+    float dd = f_pt(a, b, c, d);
+    double r = P.rho[v.x];
+    return make_float2(__fsub_rd(__fsub_rd(dd, __double2float_ru(r)), t),
+                       __fadd_ru(__fsub_ru(dd, __double2float_rd(r)), t));
+  }
+  float dd = f_ss(a, b, c, d);
+  return make_float2(__fsub_rd(dd, t), __fadd_ru(dd, t));
+}
+
+// Exact FP64 distances are needed only where they decide something: a pair
+// whose upper bound is below D is certainly in P, and its exact distance is
+// needed only if it may be a contact (lower < delta) or the closest pair at
+// one of its vertices (lower <= the smallest upper bound among the certain
+// pairs there).  Pass A records those smallest upper bounds per vertex.
+__device__ __forceinline__ void min_at(unsigned int* p, unsigned int u) {
+  if (u < __ldcg(p)) atomicMin(p, u);  // most pairs at a vertex are not its closest: skip their atomics
+}
+__device__ __forceinline__ void note_upper(Pool& P, int4 v, float up) {
+  unsigned int u = fl_ord(up);
+  min_at(&P.vmin[v.x], u);
+  min_at(&P.vmin[v.y], u);
+  if (v.z >= 0) min_at(&P.vmin[v.z], u);
+  if (v.w >= 0) min_at(&P.vmin[v.w], u);
+}
+__device__ __forceinline__ bool needs_exact(const Pool& P, int4 v, float2 b, double D, double delta) {
+  if (!((double)b.y < D) || (double)b.x < delta) return true;
+  unsigned int lo = fl_ord(b.x);
+  if (lo <= P.vmin[v.x] || lo <= P.vmin[v.y]) return true;
+  if (v.z >= 0 && lo <= P.vmin[v.z]) return true;
+  return v.w >= 0 && lo <= P.vmin[v.w];
+}
+
+// per-vertex minimum of the bits of non-negative doubles; a pair that is not
+// the closest at the vertex so far skips the atomic
+__device__ __forceinline__ void dmin_at(unsigned long long* p, unsigned long long b) {
+  if (b < __ldcg(p)) atomicMin(p, b);
+}
+
 // Record one pair of P found at iteration l (search or refresh).
 // mode 0: normal; 1: inspection of candidates; 2: inspection of P.
 __device__ __forceinline__ void emit_pair(Pool& P, int nxt, int s, unsigned long long key, int4 v, double d) {
@@ -116,10 +172,10 @@ __device__ __forceinline__ void emit_pair(Pool& P, int nxt, int s, unsigned long
   B.v[idx] = v;
   B.d[idx] = d;
   unsigned long long db = dbits(d > 0.0 ? d : 0.0);
-  atomicMin(&P.Dv[v.x], db);
-  atomicMin(&P.Dv[v.y], db);
-  if (v.z >= 0) atomicMin(&P.Dv[v.z], db);
-  if (v.w >= 0) atomicMin(&P.Dv[v.w], db);
+  dmin_at(&P.Dv[v.x], db);
+  dmin_at(&P.Dv[v.y], db);
+  if (v.z >= 0) dmin_at(&P.Dv[v.z], db);
+  if (v.w >= 0) dmin_at(&P.Dv[v.w], db);
   {
     cg::coalesced_group g = cg::coalesced_threads();
     auto part = cg::labeled_partition(g, s);

@@ -104,18 +104,23 @@ __device__ __forceinline__ double pair_dist(const Pool& P, unsigned long long ke
   return (vnorm(vsub(mk(P.x[v.x]), mk(P.x[v.y]))) - P.rho[v.x]) - P.rho[v.y];
 }
 
-// FP32 lower bound of a pair's distance (see FILTER_TOL)
-__device__ __forceinline__ float pair_lower32(const Pool& P, unsigned long long key, int4 v) {
-  int kind = (int)(key >> 62);
-  fv3 a = fk(P.xf[v.x]), b = fk(P.xf[v.y]);
-  if (kind == K_VV) {
-    fv3 d = fsub(a, b);
-    float r = __double2float_ru(P.rho[v.x] + P.rho[v.y]);
-    return __fsub_rd(__fsub_rd(sqrtf(fdot(d, d)), r), ftol(a, b, b, b));
+// Distance refresh, FP64 mode: pass A records every reused pair's FP32 bounds
+// and the smallest upper bound of the certain pairs per vertex; pass B keeps
+// the pairs below D^(l), with exact distances only where they decide
+// something (see needs_exact).  Mixed precision: one pass, the FP32 lower
+// bound is the distance.
+__global__ void k_refresh_bounds(Pool P, int cur) {
+  if (!P.cnt->any_refresh) return;
+  int n = min(P.cnt->n_pairs[cur], P.pair_cap);
+  const PairBuf B = P.pb[cur];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int4 v = B.v[i];
+    const SceneState& S = P.ss[P.vscene[v.x]];
+    if (!S.active || S.done || S.do_search) continue;
+    float2 b = pair_bounds32(P, B.key[i], v);
+    P.fbr[i] = b;
+    if (b.x < __double2float_ru(S.D) && (double)b.y < S.D) note_upper(P, v, b.y);
   }
-  fv3 c = fk(P.xf[v.z]), d = fk(P.xf[v.w]);
-  float dd = kind == K_VT ? __fsub_rd(f_pt(a, b, c, d), __double2float_ru(P.rho[v.x])) : f_ss(a, b, c, d);
-  return __fsub_rd(dd, ftol(a, b, c, d));
 }
 
 __global__ void k_refresh(Pool P, int cur, int nxt) {
@@ -129,15 +134,21 @@ __global__ void k_refresh(Pool P, int cur, int nxt) {
     const SceneState& S = P.ss[s];
     if (!S.active || S.done || S.do_search) continue;
     unsigned long long key = B.key[i];
-    float lower = pair_lower32(P, key, v);
-    if (lower >= __double2float_ru(S.D)) continue;
     if (P.mixed) {
       // mixed precision: the FP32 lower bound is the pair's distance
+      float lower = pair_bounds32(P, key, v).x;
+      if (lower >= __double2float_ru(S.D)) continue;
       if ((double)lower < S.D) emit_pair(P, nxt, s, key, v, (double)lower);
       continue;
     }
-    double d = pair_dist(P, key, v);
-    if (d < S.D) emit_pair(P, nxt, s, key, v, d);
+    float2 b = P.fbr[i];
+    if (b.x >= __double2float_ru(S.D)) continue;
+    if (needs_exact(P, v, b, S.D, P.sd[s].delta)) {
+      double d = pair_dist(P, key, v);
+      if (d < S.D) emit_pair(P, nxt, s, key, v, d);
+    } else {
+      emit_pair(P, nxt, s, key, v, (double)b.x);  // certainly in P; its distance decides nothing
+    }
   }
 }
 
@@ -1167,9 +1178,14 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     prof_mark(R, PG_VT + c, 1, st);
   }
   prof_mark(R, PG_FINAL, 0, st);
+  if (!P.mixed) cudaMemsetAsync(P.vmin, 0xff, sizeof(unsigned int) * (size_t)P.nv, st);
   finalize_search(R, nxt, 0, 0.0, st);
   prof_mark(R, PG_FINAL, 1, st);
   prof_mark(R, PG_REFRESH, 0, st);
+  if (!P.mixed) {
+    k_refresh_bounds<<<grid_for(P.pair_cap, 256), 256, 0, st>>>(P, cur);
+    R.launches++;
+  }
   k_refresh<<<grid_for(P.pair_cap, 256), 256, 0, st>>>(P, cur, nxt);
   prof_mark(R, PG_REFRESH, 1, st);
   prof_mark(R, PG_ASSEMBLE, 0, st);
