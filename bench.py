@@ -192,7 +192,8 @@ def run_serving(args):
     for g in plain:
         g.close()
     # served: requests arrive on the Poisson clock while others run
-    prm = cch.params_for(scs[0], precision=1 if args.precision == "mixed" else 0, iters_per_launch=8)
+    prm = cch.params_for(scs[0], precision=1 if args.precision == "mixed" else 0, iters_per_launch=8,
+                         solver=1 if args.solver == "jacobi" else 0)
     sv = cch.Server(80 << 30, prm, max_active=args.max_active)
     ids = [sv.add_scene(sc) for sc in scs]
     # one warm request per scene (pool build, graph capture)
@@ -221,7 +222,8 @@ def run_serving(args):
     out = {"metric": METRIC, "value": N / served_s, "unit": "steps/s", "n_gpus": 1, "steps": N, "warmup": len(scs),
            "ms_per_step": 1000.0 * served_s / N, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-           "config": {"workload": f"serving_mix_{args.precision}", "requests": N, "rate_per_s": args.rate,
+           "config": {"workload": f"serving_mix_{args.precision}" + ("_jacobi" if args.solver == "jacobi" else ""),
+                      "requests": N, "rate_per_s": args.rate,
                       "scene_tris": tris, "max_active": args.max_active, "budget_bytes": 80 << 30},
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
            "plain_fp64": {"value": N / plain_s, "unit": "steps/s", "p50_ms": float(np.percentile(plain_ms, 50)),
