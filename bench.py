@@ -121,6 +121,34 @@ def dist_env():
     return rank, world, local
 
 
+def _ranks(dev):
+    import torch
+    d = torch.distributed
+    return d if (d.is_available() and d.is_initialized() and d.get_world_size() > 1) else None
+
+
+def slowest(x: float, dev) -> float:
+    """The job's time is its slowest rank's: max over ranks (x itself on one rank)."""
+    import torch
+    d = _ranks(dev)
+    if d is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    d.all_reduce(t, op=d.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_total(x: float, dev) -> float:
+    """Units processed by the whole job: sum over ranks."""
+    import torch
+    d = _ranks(dev)
+    if d is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    d.all_reduce(t, op=d.ReduceOp.SUM)
+    return float(t.item())
+
+
 def min_iterations(x_t, x_tilde, d_max, gamma):
     """Fewest iterations a step can take: every vertex moves at most
     0.5 gamma D^max per iteration (Eq. forward2 with D_i <= D^max)."""
@@ -396,17 +424,14 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     log(f"timed {K} steps in {total_ms / 1000:.2f} s: " + ", ".join(f"{m:.0f} ms" for m in step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = slowest(total_ms, dev)
     # replaying the first timed step must give the same result (determinism)
     first_out = None
 
     iters = np.array([s["iterations"] for s in stats])
-    pairs = float(np.sum([s["pairs_evaluated"] for s in stats]))
-    launches = int(np.sum([s["kernel_launches"] for s in stats]))
-    steps_per_s = world * K / (total_ms / 1000.0)
+    pairs = job_total(float(np.sum([s["pairs_evaluated"] for s in stats])), dev)
+    launches = int(job_total(float(np.sum([s["kernel_launches"] for s in stats])), dev))
+    steps_per_s = job_total(float(K), dev) / (total_ms / 1000.0)
 
     # ---- per-kernel timing (events on the launching stream, no graphs) ----
     gpu.set_profiling(True)
@@ -474,12 +499,8 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_same = bool(np.array_equal(hout, prof_out.cpu().numpy()))
     log(f"end to end: {e2e_s:.2f} s")
-    e2e = {"value": world * e2e_n / e2e_s if world == 1 else None, "unit": "steps/s",
+    e2e = {"value": job_total(float(e2e_n), dev) / slowest(e2e_s, dev), "unit": "steps/s",
            "h2d_bytes_per_step": 2 * n * 24, "d2h_bytes_per_step": n * 24}
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e["value"] = world * e2e_n / float(t.item())
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
     cpu = None
@@ -498,7 +519,7 @@ def main():
                "config": {"workload": f"{wname}_{args.precision}" + ("_jacobi" if args.solver == "jacobi" else ""), "verts": n, "tris": T, "edges": E,
                           "len_edges": len(sc.len_edges), "dt": sc.dt, "l2": "flushed between steps (256 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single"},
-               "contact_pairs_per_sec": world * pairs / (total_ms / 1000.0),
+               "contact_pairs_per_sec": pairs / (total_ms / 1000.0),
                "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                "iterations_per_step": float(np.mean(iters)), "converged_steps": int(sum(s["converged"] for s in stats)),
                "sweep_depth": int(pst["gs_depth"]),
