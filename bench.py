@@ -310,6 +310,7 @@ def main():
                     help="backward step: projected Gauss-Seidel (the paper's) or projected Jacobi (omega 0.5)")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
+    ap.add_argument("--gap", action="store_true", help="gap contact constraints instead of the volume-based ones")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-configuration autotuner")
     ap.add_argument("--tune-iters", type=int, default=48, help="iterations of the autotuner's probe step")
@@ -338,7 +339,7 @@ def main():
     from paper_2211_04045_gb300 import cch, scenes
     sc, wname = workload(args.config)
     prm = cch.params_for(sc, precision=1 if args.precision == "mixed" else 0,
-                         solver=1 if args.solver == "jacobi" else 0)
+                         solver=1 if args.solver == "jacobi" else 0, constraint_form=1 if args.gap else 0)
     if args.ncu_case:
         x0, xt0, v0 = scenes.initial(sc)
         x, xt, v = (torch.tensor(a, device=dev) for a in (x0, xt0, v0))
@@ -516,7 +517,8 @@ def main():
         out = {"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-               "config": {"workload": f"{wname}_{args.precision}" + ("_jacobi" if args.solver == "jacobi" else ""), "verts": n, "tris": T, "edges": E,
+               "config": {"workload": f"{wname}_{args.precision}" + ("_jacobi" if args.solver == "jacobi" else "")
+                          + ("_gap" if args.gap else ""), "verts": n, "tris": T, "edges": E,
                           "len_edges": len(sc.len_edges), "dt": sc.dt, "l2": "flushed between steps (256 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single"},
                "contact_pairs_per_sec": pairs / (total_ms / 1000.0),

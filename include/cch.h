@@ -56,6 +56,11 @@ typedef enum { CCH_PREC_FP64 = 0, CCH_PREC_MIXED = 1 } cch_precision;
  * the projected Jacobi variant (Sec. 4.3.2) with per-constraint
  * under-relaxation jacobi_omega / (most constraints at one of its vertices). */
 typedef enum { CCH_SOLVER_GAUSS_SEIDEL = 0, CCH_SOLVER_JACOBI = 1 } cch_solver;
+/* Contact constraints: the volume-based constraints of Sec. 4.1 (default), or
+ * the gap constraints c = d/delta - 1 the paper compares them with (gradient:
+ * the closest-point weights times the unit separation direction, over delta).
+ * Vertex-vertex pairs use the distance form in both. */
+typedef enum { CCH_FORM_VOLUME = 0, CCH_FORM_GAP = 1 } cch_constraint_form;
 
 /* Parameters of Algorithm 1.  cch_params_default() fills Table 2's values
  * (L = 2048, eps = 1e-4, D^min = 2 mm, D^max = 4 mm, delta = 1 mm,
@@ -80,7 +85,7 @@ typedef struct {
   int32_t iters_per_launch; /* iterations captured per CUDA-graph launch (G)   */
   int32_t bvh_refit_only;   /* 1: rebuild the BVH at the first search of a step
                                and only refit it at later searches             */
-  int32_t reserved_;
+  int32_t constraint_form;  /* cch_constraint_form                             */
   uint64_t seed;         /* priorities of the randomized sweep order (Sec. 4.3) */
 } cch_params;
 

@@ -47,7 +47,7 @@ class Params(C.Structure):
     _fields_ = [("d_min", C.c_double), ("d_max", C.c_double), ("delta", C.c_double), ("sigma", C.c_double),
                 ("gamma", C.c_double), ("eps", C.c_double), ("jacobi_omega", C.c_double),
                 ("max_iters", C.c_int32), ("gs_sweeps", C.c_int32), ("solver", C.c_int32),
-                ("ccd_check", C.c_int32), ("search_mode", C.c_int32), ("pad_", C.c_int32), ("seed", C.c_uint64)]
+                ("ccd_check", C.c_int32), ("search_mode", C.c_int32), ("constraint_form", C.c_int32), ("seed", C.c_uint64)]
 
 
 class Stats(C.Structure):
@@ -91,7 +91,7 @@ def lib():
             L.orc_proximity.restype = i64
             L.orc_proximity.argtypes = [C.POINTER(Topology), p, p, d, i32, p, p, i64]
             L.orc_contact_constraint.restype = C.c_int
-            L.orc_contact_constraint.argtypes = [C.c_int, p, p, d, p, p]
+            L.orc_contact_constraint.argtypes = [C.c_int, p, p, d, C.c_int, p, p]
             L.orc_backward_once.restype = C.c_int
             L.orc_backward_once.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, p, p, p]
             L.orc_ccd.restype = C.c_int
@@ -244,12 +244,12 @@ def splitmix64(x: int) -> int:
     return int(lib().orc_splitmix64(C.c_uint64(x & 0xFFFFFFFFFFFFFFFF)))
 
 
-def contact_constraint(kind, pos, rho, delta):
+def contact_constraint(kind, pos, rho, delta, form=0):
     pos = _f64(pos).reshape(-1)
     rho = _f64(rho).reshape(-1)
     c0 = C.c_double()
     g = np.zeros(12)
-    ok = lib().orc_contact_constraint(kind, _ptr(pos), _ptr(rho), delta, C.addressof(c0), _ptr(g))
+    ok = lib().orc_contact_constraint(kind, _ptr(pos), _ptr(rho), delta, int(form), C.addressof(c0), _ptr(g))
     nv = 2 if kind == VV else 4
     return bool(ok), c0.value, g.reshape(4, 3)[:nv]
 

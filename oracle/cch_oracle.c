@@ -60,7 +60,7 @@ void orc_params_default(orc_params* p) {
   p->d_min = 2e-3; p->d_max = 4e-3; p->delta = 1e-3; p->sigma = 1.1; p->gamma = 0.9;
   p->eps = 1e-4; p->jacobi_omega = 0.5;
   p->max_iters = 2048; p->gs_sweeps = 1; p->solver = 0; p->ccd_check = 0; p->search_mode = 2;
-  p->pad_ = 0; p->seed = 0x2211040450ULL;
+  p->constraint_form = 0; p->seed = 0x2211040450ULL;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -84,6 +84,28 @@ static double ps_dist(v3 p, v3 a, v3 b, double* t_out) {
 /* Closest distance from p to triangle (a,b,c).  The closest point is either
  * the projection onto the plane (when it falls inside, barycentric weights
  * of Sec. 4.1 all >= 0) or lies on one of the three edges. */
+/* The same distance with the closest point's barycentric weights on (a, b, c)
+ * and whether it lies inside the triangle (the plane projection). */
+static double pt_closest(v3 p, v3 a, v3 b, v3 c, double wt[3], int* inside) {
+  v3 e1 = sub3(b, a), e2 = sub3(c, a), w = sub3(p, a);
+  v3 n = cross3(e1, e2);
+  double nn = dot3(n, n);
+  if (nn > 0.0) {
+    double u = dot3(cross3(w, e2), n) / nn, v = dot3(cross3(e1, w), n) / nn;
+    if (u >= 0.0 && v >= 0.0 && u + v <= 1.0) {
+      wt[0] = (1.0 - u) - v; wt[1] = u; wt[2] = v;
+      *inside = 1;
+      return fabs(dot3(w, n)) / sqrt(nn);
+    }
+  }
+  *inside = 0;
+  double t1, t2, t3;
+  double d = ps_dist(p, a, b, &t1), d2 = ps_dist(p, b, c, &t2), d3 = ps_dist(p, c, a, &t3);
+  wt[0] = 1.0 - t1; wt[1] = t1; wt[2] = 0.0;
+  if (d2 < d) { d = d2; wt[0] = 0.0; wt[1] = 1.0 - t2; wt[2] = t2; }
+  if (d3 < d) { d = d3; wt[0] = t3; wt[1] = 0.0; wt[2] = 1.0 - t3; }
+  return d;
+}
 static double pt_dist(v3 p, v3 a, v3 b, v3 c) {
   v3 e1 = sub3(b, a), e2 = sub3(c, a), w = sub3(p, a);
   v3 n = cross3(e1, e2);
@@ -625,16 +647,42 @@ static int volume_constraint(const v3 p[4], const double sgn[4], v3 n, double h,
   return 1;
 }
 
+/* Gap constraint (reading G1; the comparison constraints of Sec. 4.1's gap
+ * figure): c = d/delta - 1, d the pair distance, with gradient w_v n / delta
+ * at each vertex, w_v its signed closest-point weight (+ on the first
+ * primitive, - on the second) and n the unit direction from the second
+ * primitive's closest point to the first's. */
+static void gap_constraint(double d, double delta, v3 n, const double w[4], double* c0, v3 g[4]) {
+  *c0 = d / delta - 1.0;
+  for (int k = 0; k < 4; k++) g[k] = scl3(w[k] / delta, n);
+}
+
 /* VT (R6): n is the unit triangle normal flipped to the vertex's side; the
  * vertex moves along +n and the triangle along -n.  d is the pair distance
  * (point radius already subtracted). */
-static int vt_constraint(const v3 p[4], double d, double delta, double* c0, v3 g[4]) {
+static int vt_constraint(const v3 p[4], double d, double delta, int form, double* c0, v3 g[4]) {
   v3 nrm = cross3(sub3(p[2], p[1]), sub3(p[3], p[1]));
   double nn = dot3(nrm, nrm);
   if (!(nn > 0.0)) return 0;
   v3 nh = div3(nrm, sqrt(nn));
   double side = dot3(nh, sub3(p[0], p[1])) < 0.0 ? -1.0 : 1.0;
   v3 n = scl3(side, nh);
+  if (form == 1) {
+    /* gap (G1): the closest point q of the triangle; n = (p - q)/|p - q|,
+     * the flipped normal when the projection is inside or p lies on it */
+    double wt[3];
+    int inside;
+    pt_closest(p[0], p[1], p[2], p[3], wt, &inside);
+    if (!inside) {
+      v3 q = add3(add3(scl3(wt[0], p[1]), scl3(wt[1], p[2])), scl3(wt[2], p[3]));
+      v3 dv = sub3(p[0], q);
+      double L = norm3(dv);
+      if (L > 0.0) n = div3(dv, L);
+    }
+    double w[4] = {1.0, -wt[0], -wt[1], -wt[2]};
+    gap_constraint(d, delta, n, w, c0, g);
+    return 1;
+  }
   static const double sg[4] = {1.0, -1.0, -1.0, -1.0};
   return volume_constraint(p, sg, n, 0.5 * (delta - d), c0, g);
 }
@@ -642,7 +690,8 @@ static int vt_constraint(const v3 p[4], double d, double delta, double* c0, v3 g
 /* EE (R7): n points from the closest point of cd to that of ab; ab moves
  * along +n and cd along -n.  Near-parallel edges (sin < 1e-6) use the gap
  * form c = d/delta - 1 with the closest-point weights. */
-static int ee_constraint(const v3 p[4], double d, double s, double t, double delta, double* c0, v3 g[4]) {
+static int ee_constraint(const v3 p[4], double d, double s, double t, double delta, int form, double* c0,
+                         v3 g[4]) {
   v3 e1 = sub3(p[1], p[0]), e2 = sub3(p[3], p[2]);
   v3 nx = cross3(e1, e2);
   double nn = dot3(nx, nx);
@@ -653,12 +702,9 @@ static int ee_constraint(const v3 p[4], double d, double s, double t, double del
   if (L > 0.0) n = div3(dv, L);
   else if (nn > 0.0) n = div3(nx, sqrt(nn));
   else return 0;
-  if (nn < 1e-12 * (dot3(e1, e1) * dot3(e2, e2))) {
-    *c0 = d / delta - 1.0;
-    g[0] = scl3((1.0 - s) / delta, n);
-    g[1] = scl3(s / delta, n);
-    g[2] = scl3(-((1.0 - t) / delta), n);
-    g[3] = scl3(-(t / delta), n);
+  if (form == 1 || nn < 1e-12 * (dot3(e1, e1) * dot3(e2, e2))) {
+    double w[4] = {1.0 - s, s, -(1.0 - t), -t};
+    gap_constraint(d, delta, n, w, c0, g);
     return 1;
   }
   static const double sg[4] = {1.0, 1.0, -1.0, -1.0};
@@ -679,17 +725,18 @@ static int vv_constraint(const v3 p[2], double ra, double rb, double delta, doub
   return 1;
 }
 
-int orc_contact_constraint(int kind, const double* p, const double* rho, double delta, double* c0, double* g) {
+int orc_contact_constraint(int kind, const double* p, const double* rho, double delta, int form, double* c0,
+                           double* g) {
   v3 P[4], G[4];
   int ok;
   if (kind == ORC_VT) {
     for (int i = 0; i < 4; i++) P[i] = ld3(p, i);
     double d = pt_dist(P[0], P[1], P[2], P[3]) - rho[0];
-    ok = vt_constraint(P, d, delta, c0, G);
+    ok = vt_constraint(P, d, delta, form, c0, G);
   } else if (kind == ORC_EE) {
     for (int i = 0; i < 4; i++) P[i] = ld3(p, i);
     double s, t, d = ss_dist(P[0], P[1], P[2], P[3], &s, &t);
-    ok = ee_constraint(P, d, s, t, delta, c0, G);
+    ok = ee_constraint(P, d, s, t, delta, form, c0, G);
   } else {
     P[0] = ld3(p, 0); P[1] = ld3(p, 1);
     ok = vv_constraint(P, rho[0], rho[1], delta, c0, G);
@@ -884,11 +931,11 @@ static int64_t build_contacts(const orc_topology* t, const orc_params* prm, cons
     v3 p[4];
     for (int k = 0; k < c->nv; k++) p[k] = ld3(x, c->v[k]);
     int ok;
-    if (kind == ORC_VT) ok = vt_constraint(p, P->d[i], prm->delta, &c->c0, c->g);
+    if (kind == ORC_VT) ok = vt_constraint(p, P->d[i], prm->delta, prm->constraint_form, &c->c0, c->g);
     else if (kind == ORC_EE) {
       double s, tt, d = ss_dist(p[0], p[1], p[2], p[3], &s, &tt);
       (void)d;
-      ok = ee_constraint(p, P->d[i], s, tt, prm->delta, &c->c0, c->g);
+      ok = ee_constraint(p, P->d[i], s, tt, prm->delta, prm->constraint_form, &c->c0, c->g);
     } else ok = vv_constraint(p, rho_of(t, c->v[0]), rho_of(t, c->v[1]), prm->delta, &c->c0, c->g);
     if (!ok) { (*degenerate)++; continue; }
     c->den = 0.0;

@@ -48,7 +48,8 @@ typedef struct {
   int32_t solver;        /* 0 = projected Gauss-Seidel, 1 = projected Jacobi */
   int32_t ccd_check;     /* 1 = run the segment CCD safety check each iter   */
   int32_t search_mode;   /* 0 = all pairs, 1 = sorted-axis window, 2 = auto  */
-  int32_t pad_;
+  int32_t constraint_form; /* 0 = volume (Sec. 4.1), 1 = gap (the comparison */
+                           /*     constraints of Sec. 4.1's gap figure)      */
   uint64_t seed;         /* sweep priorities (R11)                            */
 } orc_params;
 
@@ -102,10 +103,10 @@ int64_t orc_proximity(const orc_topology* t, const double* x, const double* x_ti
 
 /* ---- one constraint (Sec. 4.1, 4.2) ---- */
 /* kind VT/EE/VV with vertex positions p[4][3] (VV uses 2), radii rho[2]
- * (VT: rho[0] of the vertex; VV: both).  Returns 1 if assembled, 0 if
- * skipped as degenerate; c0 and g[4][3] receive the constraint value and
- * gradient at x. */
-int orc_contact_constraint(int kind, const double* p, const double* rho, double delta,
+ * (VT: rho[0] of the vertex; VV: both), form 0 (volume) or 1 (gap).
+ * Returns 1 if assembled, 0 if skipped as degenerate; c0 and g[4][3] receive
+ * the constraint value and gradient at x. */
+int orc_contact_constraint(int kind, const double* p, const double* rho, double delta, int form,
                            double* c0, double* g);
 
 /* ---- one backward step (Sec. 4), used by single-constraint pins ---- */

@@ -127,6 +127,7 @@ cch_status validate_params(const cch_params* p) {
   if (p->max_iters < 0 || p->gs_sweeps < 1 || p->gs_sweeps > 64) return CCH_E_INVALID_ARG;
   if (p->precision != CCH_PREC_FP64 && p->precision != CCH_PREC_MIXED) return CCH_E_INVALID_ARG;
   if (p->solver != CCH_SOLVER_GAUSS_SEIDEL && p->solver != CCH_SOLVER_JACOBI) return CCH_E_INVALID_ARG;
+  if (p->constraint_form != CCH_FORM_VOLUME && p->constraint_form != CCH_FORM_GAP) return CCH_E_INVALID_ARG;
   if (p->iters_per_launch < 0 || p->iters_per_launch > 4096) return CCH_E_INVALID_ARG;
   return CCH_OK;
 }
@@ -229,6 +230,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
     d.c0 = (int)vc.size();
     d.d_min = prm->d_min; d.d_max = prm->d_max; d.delta = prm->delta; d.sigma = prm->sigma;
     d.hgamma = 0.5 * prm->gamma; d.eps = prm->eps; d.omega = prm->jacobi_omega;
+    d.form = prm->constraint_form;
     d.max_iters = prm->max_iters; d.gs_sweeps = prm->gs_sweeps; d.solver = prm->solver; d.ccd = prm->ccd_check;
     d.seed = prm->seed;
     d.rho_max = 0.0;
@@ -583,6 +585,7 @@ cch_status cch_params_default(cch_params* p) {
   p->validate_input = 0;
   p->iters_per_launch = 16;
   p->bvh_refit_only = 1;
+  p->constraint_form = CCH_FORM_VOLUME;
   p->seed = 0x2211040450ULL;
   return CCH_OK;
 }

@@ -32,6 +32,7 @@ struct SceneDesc {
   int q0, nq;      // point range
   int c0, nc;      // collision-vertex range (index into the vc list)
   double d_min, d_max, delta, sigma, hgamma, eps, omega;
+  int form;                       // contact constraint: 0 volume, 1 gap
   double rho_max;  // largest point radius of the scene
   int max_iters, gs_sweeps, solver, ccd;
   uint64_t seed;
@@ -294,20 +295,59 @@ __device__ __forceinline__ bool volume_cons(const dv3 p[4], const double sg[4], 
 }
 
 // vertex p0 against triangle (p1,p2,p3): unit normal flipped to the vertex
-__device__ __forceinline__ bool vt_cons(const dv3 p[4], double d, double delta, double* c0, dv3 g[4]) {
+// closest point of triangle (a, b, c) to p: barycentric weights, and whether
+// it is the plane projection (the same branches as d_pt)
+__device__ __forceinline__ bool pt_weights(dv3 p, dv3 a, dv3 b, dv3 c, double wt[3]) {
+  dv3 e1 = vsub(b, a), e2 = vsub(c, a), w = vsub(p, a);
+  dv3 n = vcross(e1, e2);
+  double nn = vdot(n, n);
+  if (nn > 0.0) {
+    double u = vdot(vcross(w, e2), n) / nn, v = vdot(vcross(e1, w), n) / nn;
+    if (u >= 0.0 && v >= 0.0 && u + v <= 1.0) {
+      wt[0] = (1.0 - u) - v; wt[1] = u; wt[2] = v;
+      return true;
+    }
+  }
+  double t1, t2, t3;
+  double d = d_ps(p, a, b, &t1), d2 = d_ps(p, b, c, &t2), d3 = d_ps(p, c, a, &t3);
+  wt[0] = 1.0 - t1; wt[1] = t1; wt[2] = 0.0;
+  if (d2 < d) { d = d2; wt[0] = 0.0; wt[1] = 1.0 - t2; wt[2] = t2; }
+  if (d3 < d) { wt[0] = t3; wt[1] = 0.0; wt[2] = 1.0 - t3; }
+  return false;
+}
+// gap constraint (reading G1): c = d/delta - 1, gradient w_v n / delta
+__device__ __forceinline__ void gap_cons(double d, double delta, dv3 n, const double w[4], double* c0, dv3 g[4]) {
+  *c0 = d / delta - 1.0;
+  for (int k = 0; k < 4; k++) g[k] = vscl(w[k] / delta, n);
+}
+
+// form: 0 volume (Sec. 4.1), 1 gap
+__device__ __forceinline__ bool vt_cons(const dv3 p[4], double d, double delta, int form, double* c0, dv3 g[4]) {
   dv3 nrm = vcross(vsub(p[2], p[1]), vsub(p[3], p[1]));
   double nn = vdot(nrm, nrm);
   if (!(nn > 0.0)) return false;
   dv3 nh = vdiv(nrm, sqrt(nn));
   double side = vdot(nh, vsub(p[0], p[1])) < 0.0 ? -1.0 : 1.0;
   dv3 n = vscl(side, nh);
+  if (form == 1) {
+    double wt[3];
+    if (!pt_weights(p[0], p[1], p[2], p[3], wt)) {
+      dv3 q = vadd(vadd(vscl(wt[0], p[1]), vscl(wt[1], p[2])), vscl(wt[2], p[3]));
+      dv3 dv = vsub(p[0], q);
+      double L = vnorm(dv);
+      if (L > 0.0) n = vdiv(dv, L);
+    }
+    const double w[4] = {1.0, -wt[0], -wt[1], -wt[2]};
+    gap_cons(d, delta, n, w, c0, g);
+    return true;
+  }
   const double sg[4] = {1.0, -1.0, -1.0, -1.0};
   return volume_cons(p, sg, n, 0.5 * (delta - d), c0, g);
 }
 
 // edge (p0,p1) against edge (p2,p3); near-parallel edges use the gap form
-__device__ __forceinline__ bool ee_cons(const dv3 p[4], double d, double s, double t, double delta, double* c0,
-                                        dv3 g[4]) {
+__device__ __forceinline__ bool ee_cons(const dv3 p[4], double d, double s, double t, double delta, int form,
+                                        double* c0, dv3 g[4]) {
   dv3 e1 = vsub(p[1], p[0]), e2 = vsub(p[3], p[2]);
   dv3 nx = vcross(e1, e2);
   double nn = vdot(nx, nx);
@@ -318,12 +358,9 @@ __device__ __forceinline__ bool ee_cons(const dv3 p[4], double d, double s, doub
   if (L > 0.0) n = vdiv(dv, L);
   else if (nn > 0.0) n = vdiv(nx, sqrt(nn));
   else return false;
-  if (nn < 1e-12 * (vdot(e1, e1) * vdot(e2, e2))) {
-    *c0 = d / delta - 1.0;
-    g[0] = vscl((1.0 - s) / delta, n);
-    g[1] = vscl(s / delta, n);
-    g[2] = vscl(-((1.0 - t) / delta), n);
-    g[3] = vscl(-(t / delta), n);
+  if (form == 1 || nn < 1e-12 * (vdot(e1, e1) * vdot(e2, e2))) {
+    const double w[4] = {1.0 - s, s, -(1.0 - t), -t};
+    gap_cons(d, delta, n, w, c0, g);
     return true;
   }
   const double sg[4] = {1.0, 1.0, -1.0, -1.0};
@@ -612,16 +649,44 @@ __device__ __forceinline__ bool volume_cons_f(const fv3 p[4], const float sg[4],
   g[0] = fscl3(-1.f, fadd3(fadd3(g[1], g[2]), g[3]));
   return true;
 }
-__device__ __forceinline__ bool vt_cons_f(const fv3 p[4], float d, float delta, float* c0, fv3 g[4]) {
+__device__ __forceinline__ void gap_cons_f(float d, float delta, fv3 n, const float w[4], float* c0, fv3 g[4]) {
+  *c0 = d / delta - 1.f;
+  for (int k = 0; k < 4; k++) g[k] = fscl3(w[k] / delta, n);
+}
+__device__ __forceinline__ bool vt_cons_f(const fv3 p[4], float d, float delta, int form, float* c0, fv3 g[4]) {
   fv3 nrm = fcross(fsub(p[2], p[1]), fsub(p[3], p[1]));
   float nn = fdot(nrm, nrm);
   if (!(nn > 0.f)) return false;
   fv3 nh = fdiv3(nrm, sqrtf(nn));
   float side = fdot(nh, fsub(p[0], p[1])) < 0.f ? -1.f : 1.f;
+  fv3 n = fscl3(side, nh);
+  if (form == 1) {
+    // closest point of the triangle, as in the FP64 form
+    fv3 e1 = fsub(p[2], p[1]), e2 = fsub(p[3], p[1]), w = fsub(p[0], p[1]);
+    float u = fdot(fcross(w, e2), nrm) / nn, v = fdot(fcross(e1, w), nrm) / nn;
+    float wt[3];
+    if (u >= 0.f && v >= 0.f && u + v <= 1.f) {
+      wt[0] = (1.f - u) - v; wt[1] = u; wt[2] = v;
+    } else {
+      float t1, t2, t3;
+      float da = f_ps_t(p[0], p[1], p[2], &t1), db = f_ps_t(p[0], p[2], p[3], &t2), dc = f_ps_t(p[0], p[3], p[1], &t3);
+      wt[0] = 1.f - t1; wt[1] = t1; wt[2] = 0.f;
+      if (db < da) { da = db; wt[0] = 0.f; wt[1] = 1.f - t2; wt[2] = t2; }
+      if (dc < da) { wt[0] = t3; wt[1] = 0.f; wt[2] = 1.f - t3; }
+      fv3 q = fadd3(fadd3(fscl3(wt[0], p[1]), fscl3(wt[1], p[2])), fscl3(wt[2], p[3]));
+      fv3 dv = fsub(p[0], q);
+      float L = sqrtf(fdot(dv, dv));
+      if (L > 0.f) n = fdiv3(dv, L);
+    }
+    const float gw[4] = {1.f, -wt[0], -wt[1], -wt[2]};
+    gap_cons_f(d, delta, n, gw, c0, g);
+    return true;
+  }
   const float sg[4] = {1.f, -1.f, -1.f, -1.f};
-  return volume_cons_f(p, sg, fscl3(side, nh), 0.5f * (delta - d), c0, g);
+  return volume_cons_f(p, sg, n, 0.5f * (delta - d), c0, g);
 }
-__device__ __forceinline__ bool ee_cons_f(const fv3 p[4], float d, float s, float t, float delta, float* c0, fv3 g[4]) {
+__device__ __forceinline__ bool ee_cons_f(const fv3 p[4], float d, float s, float t, float delta, int form, float* c0,
+                                          fv3 g[4]) {
   fv3 e1 = fsub(p[1], p[0]), e2 = fsub(p[3], p[2]);
   fv3 nx = fcross(e1, e2);
   float nn = fdot(nx, nx);
@@ -631,12 +696,9 @@ __device__ __forceinline__ bool ee_cons_f(const fv3 p[4], float d, float s, floa
   if (L > 0.f) n = fdiv3(dv, L);
   else if (nn > 0.f) n = fdiv3(nx, sqrtf(nn));
   else return false;
-  if (nn < 1e-12f * (fdot(e1, e1) * fdot(e2, e2))) {
-    *c0 = d / delta - 1.f;
-    g[0] = fscl3((1.f - s) / delta, n);
-    g[1] = fscl3(s / delta, n);
-    g[2] = fscl3(-((1.f - t) / delta), n);
-    g[3] = fscl3(-(t / delta), n);
+  if (form == 1 || nn < 1e-12f * (fdot(e1, e1) * fdot(e2, e2))) {
+    const float w[4] = {1.f - s, s, -(1.f - t), -t};
+    gap_cons_f(d, delta, n, w, c0, g);
     return true;
   }
   const float sg[4] = {1.f, 1.f, -1.f, -1.f};

@@ -172,11 +172,11 @@ __device__ __forceinline__ void assemble_f(Pool& P, int s, const SceneDesc& S, i
     q[2] = fk(P.xf[v.z]);
     q[3] = fk(P.xf[v.w]);
     nv = 4;
-    if (kind == K_VT) ok = vt_cons_f(q, d, delta, &c0, g);
+    if (kind == K_VT) ok = vt_cons_f(q, d, delta, S.form, &c0, g);
     else {
       float ps, pt;
       f_ss_st(q[0], q[1], q[2], q[3], &ps, &pt);
-      ok = ee_cons_f(q, d, ps, pt, delta, &c0, g);
+      ok = ee_cons_f(q, d, ps, pt, delta, S.form, &c0, g);
     }
   }
   if (!ok) {
@@ -238,11 +238,11 @@ __global__ void k_assemble(Pool P, int nxt) {
       q[2] = mk(P.x[v.z]);
       q[3] = mk(P.x[v.w]);
       nv = 4;
-      if (kind == K_VT) ok = vt_cons(q, d, S.delta, &c0, g);
+      if (kind == K_VT) ok = vt_cons(q, d, S.delta, S.form, &c0, g);
       else {
         double ps, pt;
         d_ss(q[0], q[1], q[2], q[3], &ps, &pt);
-        ok = ee_cons(q, d, ps, pt, S.delta, &c0, g);
+        ok = ee_cons(q, d, ps, pt, S.delta, S.form, &c0, g);
       }
     }
     if (!ok) {

@@ -60,7 +60,8 @@ def test_invalid_topology_rejected(bad):
 
 
 @pytest.mark.parametrize("field,value", [("d_min", 0.0), ("d_max", 1e-3), ("delta", 3e-3), ("gamma", 1.0),
-                                         ("gs_sweeps", 0), ("precision", 7), ("solver", 3), ("max_iters", -1)])
+                                         ("gs_sweeps", 0), ("precision", 7), ("solver", 3), ("max_iters", -1),
+                                         ("constraint_form", 2)])
 def test_invalid_params_rejected(field, value):
     p = cch.params()
     setattr(p, field, value)
