@@ -411,18 +411,62 @@ __device__ __forceinline__ void add_candidates(Pool& P, int s, long long n) {
 // ---------------------------------------------------------------------------
 constexpr int PACKET_STACK = 64;
 
-template <class LeafFn>
+// Leaf work runs from a per-warp queue: a lane that reaches a leaf first runs
+// the cheap checks (pre), and the pairs that pass are queued; whenever 32 are
+// queued, the whole warp evaluates them at once (work), each lane fetching
+// its entry's query data from the lane that queued it.  The distance bounds
+// thus run with all lanes busy instead of on the few lanes at a leaf.
+constexpr int PACKET_QUEUE = 96;  // a node adds at most 64 entries to at most 31 pending
+
+template <class PreFn, class WorkFn>
 __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, float3 qlo, float3 qhi, float Df,
-                                              int min_pos, int* stack, Counters* cnt, LeafFn leaf) {
+                                              int min_pos, int* stack, int* qlane, int* qleaf, Counters* cnt,
+                                              PreFn pre, WorkFn work) {
   const unsigned FULL = 0xffffffffu;
   int lane = threadIdx.x & 31;
   if (root < 0) return;
+  int qn = 0;  // identical in every lane
+  auto enqueue = [&](bool hit, int l) {
+    bool want = hit && pre(l);
+    unsigned m = __ballot_sync(FULL, want);
+    if (!m) return;
+    if (want) {
+      int at = qn + __popc(m & ((1u << lane) - 1u));
+      qlane[at] = lane;
+      qleaf[at] = l;
+    }
+    qn += __popc(m);
+    __syncwarp();
+  };
+  auto drain = [&](bool all) {
+    int base = 0;
+    for (; base + 32 <= qn || (all && base < qn); base += 32) {
+      int e = base + lane;
+      bool valid = e < qn;
+      work(valid, valid ? qlane[e] : 0, valid ? qleaf[e] : 0);
+    }
+    __syncwarp();
+    int rest = qn - base;  // fewer than 32 left (none when all)
+    if (rest > 0) {
+      int a = lane < rest ? qlane[base + lane] : 0, b = lane < rest ? qleaf[base + lane] : 0;
+      __syncwarp();
+      if (lane < rest) {
+        qlane[lane] = a;
+        qleaf[lane] = b;
+      }
+    }
+    qn = rest > 0 ? rest : 0;
+    __syncwarp();
+  };
   if (root & LEAF) {
     int l = root & ~LEAF;
+    bool hit = false;
     if (act && l > min_pos) {
       float4 lo = B.leafbox[2 * l], hi = B.leafbox[2 * l + 1];
-      if (fbox_near(lo, hi, qlo, qhi, Df)) leaf(l);
+      hit = fbox_near(lo, hi, qlo, qhi, Df);
     }
+    enqueue(hit, l);
+    drain(true);
     return;
   }
   __syncwarp();
@@ -433,7 +477,7 @@ __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, 
   while (sp > 0) {
     if (--budget < 0) {
       if (lane == 0) atomicOr(&cnt->err, 4);
-      return;
+      break;
     }
     int node = stack[--sp];
     __syncwarp();
@@ -447,7 +491,7 @@ __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, 
     unsigned mr = __ballot_sync(FULL, hr), ml = __ballot_sync(FULL, hl);
     if (mr) {
       if (R & LEAF) {
-        if (hr) leaf(R & ~LEAF);
+        enqueue(hr, R & ~LEAF);
       } else if (sp < PACKET_STACK) {
         if (lane == 0) stack[sp] = R;
         sp++;
@@ -457,7 +501,7 @@ __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, 
     }
     if (ml) {
       if (L & LEAF) {
-        if (hl) leaf(L & ~LEAF);
+        enqueue(hl, L & ~LEAF);
       } else if (sp < PACKET_STACK) {
         if (lane == 0) stack[sp] = L;
         sp++;
@@ -465,14 +509,17 @@ __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, 
         atomicOr(&cnt->err, 2);
       }
     }
+    if (qn >= 32) drain(false);
     __syncwarp();
   }
+  drain(true);
 }
 
 // vertex-triangle pairs of the step's searches, queries in the Morton order
 // of the collision vertices
 __global__ void __launch_bounds__(256) k_pquery_vt(Pool P) {
   __shared__ int stacks[8][PACKET_STACK];
+  __shared__ int qlanes[8][PACKET_QUEUE], qleaves[8][PACKET_QUEUE];
   if (!P.cnt->any_search) return;
   const unsigned FULL = 0xffffffffu;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -501,17 +548,28 @@ __global__ void __launch_bounds__(256) k_pquery_vt(Pool P) {
       int sc = __shfl_sync(FULL, s, leader);
       bool mine = pend && s == sc;
       const SceneDesc& S = P.sd[sc];
-      traverse_warp(P.bt, P.bt.sroot[sc], mine, qlo, qhi, Df, -1, stacks[warp], P.cnt, [&](int pos) {
-        int t = P.bt.ids[pos];
-        int4 tv = P.tv[t];
-        if (a == tv.x || a == tv.y || a == tv.z) return;
-        if (sa && is_static(P, tv.x) && is_static(P, tv.y) && is_static(P, tv.z)) return;
-        ncand++;
-        fv3 f1 = fk(P.xf[tv.x]), f2 = fk(P.xf[tv.y]), f3 = fk(P.xf[tv.z]);
-        float lower = __fsub_rd(__fsub_rd(f_pt(fa, f1, f2, f3), raf), ftol(fa, f1, f2, f3));
-        if (lower >= Df) return;
-        push_survivor(P, K_VT, mkkey(K_VT, a - S.v0, t - S.t0), make_int4(a, tv.x, tv.y, tv.z), lower);
-      });
+      traverse_warp(P.bt, P.bt.sroot[sc], mine, qlo, qhi, Df, -1, stacks[warp], qlanes[warp], qleaves[warp], P.cnt,
+        [&](int pos) {
+          int4 tv = P.tv[P.bt.ids[pos]];
+          if (a == tv.x || a == tv.y || a == tv.z) return false;
+          if (sa && is_static(P, tv.x) && is_static(P, tv.y) && is_static(P, tv.z)) return false;
+          ncand++;
+          return true;
+        },
+        [&](bool valid, int src, int pos) {
+          // the queuing lane's query: the vertex, its float position and radius bound, D
+          int qa = __shfl_sync(FULL, a, src);
+          float ax = __shfl_sync(FULL, fa.x, src), ay = __shfl_sync(FULL, fa.y, src), az = __shfl_sync(FULL, fa.z, src);
+          float qr = __shfl_sync(FULL, raf, src), qD = __shfl_sync(FULL, Df, src);
+          if (!valid) return;
+          int t = P.bt.ids[pos];
+          int4 tv = P.tv[t];
+          fv3 qf = {ax, ay, az};
+          fv3 f1 = fk(P.xf[tv.x]), f2 = fk(P.xf[tv.y]), f3 = fk(P.xf[tv.z]);
+          float lower = __fsub_rd(__fsub_rd(f_pt(qf, f1, f2, f3), qr), ftol(qf, f1, f2, f3));
+          if (lower >= qD) return;
+          push_survivor(P, K_VT, mkkey(K_VT, qa - S.v0, t - S.t0), make_int4(qa, tv.x, tv.y, tv.z), lower);
+        });
       if (mine) pend = false;
     }
     if (s >= 0 && ncand) add_candidates(P, s, ncand);
@@ -522,6 +580,7 @@ __global__ void __launch_bounds__(256) k_pquery_vt(Pool P) {
 // i) against the later leaves of its scene
 __global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
   __shared__ int stacks[8][PACKET_STACK];
+  __shared__ int qlanes[8][PACKET_QUEUE], qleaves[8][PACKET_QUEUE];
   if (!P.cnt->any_search) return;
   const unsigned FULL = 0xffffffffu;
   const BVH& B = P.be;
@@ -546,29 +605,37 @@ __global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
     float3 qlo = f3rd(alo), qhi = f3ru(ahi);
     float Df = s >= 0 ? __double2float_ru(P.sd[s].d_max) : 0.f;
     bool sa = e1 >= 0 && is_static(P, ea.x) && is_static(P, ea.y);
-    fv3 fa0 = e1 >= 0 ? fk(P.xf[ea.x]) : fv3{0.f, 0.f, 0.f}, fa1 = e1 >= 0 ? fk(P.xf[ea.y]) : fv3{0.f, 0.f, 0.f};
     long long ncand = 0;
     while (__any_sync(FULL, pend)) {
       int leader = __ffs(__ballot_sync(FULL, pend)) - 1;
       int sc = __shfl_sync(FULL, s, leader);
       bool mine = pend && s == sc;
       const SceneDesc& S = P.sd[sc];
-      traverse_warp(B, B.sroot[sc], mine, qlo, qhi, Df, i, stacks[warp], P.cnt, [&](int pos) {
-        int e2 = B.ids[pos];
-        int4 eb = P.ev[e2];
-        if (ea.x == eb.x || ea.x == eb.y || ea.y == eb.x || ea.y == eb.y) return;
-        if (sa && is_static(P, eb.x) && is_static(P, eb.y)) return;
-        ncand++;
-        fv3 fb0 = fk(P.xf[eb.x]), fb1 = fk(P.xf[eb.y]);
-        // the bound in key order (lower edge id first), whichever edge is the query
-        bool qlow = e1 < e2;
-        float lower = qlow ? __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1))
-                           : __fsub_rd(f_ss(fb0, fb1, fa0, fa1), ftol(fb0, fb1, fa0, fa1));
-        if (lower >= Df) return;
-        int4 A = qlow ? ea : eb, Bv = qlow ? eb : ea;
-        push_survivor(P, K_EE, mkkey(K_EE, min(e1, e2) - S.e0, max(e1, e2) - S.e0), make_int4(A.x, A.y, Bv.x, Bv.y),
-                      lower);
-      });
+      traverse_warp(B, B.sroot[sc], mine, qlo, qhi, Df, i, stacks[warp], qlanes[warp], qleaves[warp], P.cnt,
+        [&](int pos) {
+          int4 eb = P.ev[B.ids[pos]];
+          if (ea.x == eb.x || ea.x == eb.y || ea.y == eb.x || ea.y == eb.y) return false;
+          if (sa && is_static(P, eb.x) && is_static(P, eb.y)) return false;
+          ncand++;
+          return true;
+        },
+        [&](bool valid, int src, int pos) {
+          // the queuing lane's query edge and D
+          int q1 = __shfl_sync(FULL, e1, src);
+          int qx = __shfl_sync(FULL, ea.x, src), qy = __shfl_sync(FULL, ea.y, src);
+          float qD = __shfl_sync(FULL, Df, src);
+          if (!valid) return;
+          int e2 = B.ids[pos];
+          int4 eb = P.ev[e2];
+          // the bound in key order (lower edge id first), whichever edge is the query
+          bool qlow = q1 < e2;
+          int4 A = qlow ? make_int4(qx, qy, 0, 0) : eb, Bv = qlow ? eb : make_int4(qx, qy, 0, 0);
+          fv3 fa0 = fk(P.xf[A.x]), fa1 = fk(P.xf[A.y]), fb0 = fk(P.xf[Bv.x]), fb1 = fk(P.xf[Bv.y]);
+          float lower = __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
+          if (lower >= qD) return;
+          push_survivor(P, K_EE, mkkey(K_EE, min(q1, e2) - S.e0, max(q1, e2) - S.e0),
+                        make_int4(A.x, A.y, Bv.x, Bv.y), lower);
+        });
       if (mine) pend = false;
     }
     if (s >= 0 && ncand) add_candidates(P, s, ncand);
