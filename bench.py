@@ -57,10 +57,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def csrc_hash() -> str:
+def csrc_hash(files=None) -> str:
+    """Hash of the CUDA sources (all of them, or the named files that define a
+    kernel): a recorded ncu traffic figure is used only while it matches."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2211_04045_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files or os.listdir(d)):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -483,7 +485,7 @@ def main():
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tj = json.load(f)
         ent = tj.get(wname, {}).get(dominant)
-        if ent and ent.get("csrc") == csrc_hash():
+        if ent and ent.get("csrc") == csrc_hash(ent.get("files")):
             roof["traffic"] = ent["bytes_per_launch"]
     except Exception:
         pass
