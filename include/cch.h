@@ -44,7 +44,8 @@ typedef enum {
   CCH_E_CUDA = 4,              /* a CUDA runtime call failed                   */
   CCH_E_CAPACITY = 5,          /* an internal bound was exceeded (buffers past
                                   2^30 pairs, BVH traversal or sweep bounds)   */
-  CCH_E_TIMEOUT = 6,           /* a bounded device loop ran out                */
+  CCH_E_TIMEOUT = 6,           /* a bounded device wait ran out (the sweep's
+                                  vertex counters); the context stays usable   */
   CCH_E_INPUT_NOT_FEASIBLE = 7,/* validate_input: x_t already intersects       */
   CCH_E_CANCELLED = 8,         /* a server request was cancelled               */
   CCH_E_STATE = 9              /* call not valid in the object's current state */

@@ -283,7 +283,7 @@ __global__ void k_scene_roots(Pool P, int c, int gated) {
       // leftmost leaf: descend left
       int cur = i, steps = 0;
       while (!(cur & LEAF) && ++steps < 256) cur = B.left[cur];
-      if (!(cur & LEAF)) { atomicOr(&P.cnt->err, 8); continue; }
+      if (!(cur & LEAF)) { atomicOr(&P.cnt->err, ERR_TREE); continue; }
       lo = cur & ~LEAF;
       hi = B.range_hi[i];
       par = B.parent[i];
@@ -300,7 +300,7 @@ __global__ void k_scene_roots(Pool P, int c, int gated) {
       int plo;
       int cur = par, steps = 0;
       while (!(cur & LEAF) && ++steps < 256) cur = B.left[cur];
-      if (!(cur & LEAF)) { atomicOr(&P.cnt->err, 8); continue; }
+      if (!(cur & LEAF)) { atomicOr(&P.cnt->err, ERR_TREE); continue; }
       plo = cur & ~LEAF;
       int phi = B.range_hi[par];
       top = scene_of_pos(B, plo) != s || scene_of_pos(B, phi) != s;
@@ -346,7 +346,7 @@ __device__ __forceinline__ void traverse(const BVH& B, int root, float3 qlo, flo
   int budget = B.n + 2;
   while (sp > 0) {
     if (--budget < 0) {
-      atomicOr(&cnt->err, 4);
+      atomicOr(&cnt->err, ERR_BUDGET);
       return;
     }
     int node = stack[--sp];
@@ -359,12 +359,12 @@ __device__ __forceinline__ void traverse(const BVH& B, int root, float3 qlo, flo
     if (hr) {
       if (R & LEAF) { if ((R & ~LEAF) > min_pos) leaf(R & ~LEAF); }
       else if (sp < 64) stack[sp++] = R;
-      else atomicOr(&cnt->err, 2);
+      else atomicOr(&cnt->err, ERR_STACK);
     }
     if (hl) {
       if (L & LEAF) { if ((L & ~LEAF) > min_pos) leaf(L & ~LEAF); }
       else if (sp < 64) stack[sp++] = L;
-      else atomicOr(&cnt->err, 2);
+      else atomicOr(&cnt->err, ERR_STACK);
     }
   }
 }
@@ -476,7 +476,7 @@ __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, 
   __syncwarp();
   while (sp > 0) {
     if (--budget < 0) {
-      if (lane == 0) atomicOr(&cnt->err, 4);
+      if (lane == 0) atomicOr(&cnt->err, ERR_BUDGET);
       break;
     }
     int node = stack[--sp];
@@ -496,7 +496,7 @@ __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, 
         if (lane == 0) stack[sp] = R;
         sp++;
       } else if (lane == 0) {
-        atomicOr(&cnt->err, 2);
+        atomicOr(&cnt->err, ERR_STACK);
       }
     }
     if (ml) {
@@ -506,7 +506,7 @@ __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, 
         if (lane == 0) stack[sp] = L;
         sp++;
       } else if (lane == 0) {
-        atomicOr(&cnt->err, 2);
+        atomicOr(&cnt->err, ERR_STACK);
       }
     }
     if (qn >= 32) drain(false);
@@ -1052,7 +1052,7 @@ __global__ void k_refit_guard(Pool P, int c, int force) {
     int climb = 0;
     while (node >= 0) {
       if (++climb > 256) {  // deeper than any Karras tree over 64-bit keys
-        atomicOr(&P.cnt->err, 8);
+        atomicOr(&P.cnt->err, ERR_TREE);
         break;
       }
       __threadfence();

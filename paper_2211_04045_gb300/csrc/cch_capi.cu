@@ -132,6 +132,11 @@ cch_status validate_params(const cch_params* p) {
   return CCH_OK;
 }
 
+// Status of a device error word: a bounded wait that ran out (the sweep's
+// counters) is a timeout; a tree bound (stack, visit budget, climb) is a
+// capacity error.
+cch_status device_status(int err) { return (err & ERR_POLL) ? CCH_E_TIMEOUT : CCH_E_CAPACITY; }
+
 // Pair-buffer capacities; grown on overflow.
 void set_caps(Runtime& R, int pair_cap) {
   R.pool.pair_cap = pair_cap;
@@ -523,7 +528,7 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
         fprintf(stderr, "cch: iteration %d err=%d overflow=%d n_cons=%d pairs=%d/%d\n", iters,
                 R.h_cnt->err, R.h_cnt->overflow, R.h_cnt->n_cons,
                 R.h_cnt->n_pairs[0], R.h_cnt->n_pairs[1]);
-      if (R.h_cnt->err) return CCH_E_CAPACITY;
+      if (R.h_cnt->err) return device_status(R.h_cnt->err);
       if (R.h_cnt->overflow & (OV_PAIRS | OV_CONTACTS)) {
         overflow = true;
         break;
@@ -805,7 +810,7 @@ cch_status cch_query_pairs(cch_scene* S, const double* x, const double* x_ref, d
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (R.h_cnt->err) return CCH_E_CAPACITY;
+    if (R.h_cnt->err) return device_status(R.h_cnt->err);
     if (R.h_cnt->overflow & OV_PAIRS) {
       // the FP32-filter survivors outgrew the pair-sized buffers
       cch_status g = grow_pairs(R);
@@ -892,7 +897,7 @@ cch_status cch_query_pairs_noalloc(cch_scene* S, const double* x, const double* 
   Pool used = R.pool;
   R.pool = saved;
   if (e != cudaSuccess) return cuda_fail(e);
-  if (R.h_cnt->err) return CCH_E_CAPACITY;
+  if (R.h_cnt->err) return device_status(R.h_cnt->err);
   int64_t n = R.h_cnt->n_query;
   if (n < 0) n = (int64_t)1 << 31;  // the counter passed 2^31
   *count = n;
@@ -1113,7 +1118,7 @@ void server_loop(cch_server* sv) {
         if (sv->running[s] >= 0) {
           Request& r = sv->reqs[(uint64_t)sv->running[s]];
           r.state = 2;
-          r.status = e != cudaSuccess ? cuda_fail(e) : CCH_E_CAPACITY;
+          r.status = e != cudaSuccess ? cuda_fail(e) : device_status(R.h_cnt->err);
           r.t_done = now;
           sv->running[s] = -1;
         }
