@@ -167,7 +167,7 @@ cch_status cch_handle_step_host(cch_scene* s, const double* x_t, const double* x
 cch_status cch_batch_handle_step(cch_scene* s, const double* const* x_t, const double* const* x_tilde,
                                  double* const* x_next, cch_step_stats* stats);
 
-/* ---- autotuning (the benchmark spec pattern 2) -----------------------------------
+/* ---- autotuning of the launch configuration ------------------------------
  * Times candidate launch configurations on a probe: one step from x_t and
  * x_tilde (device pointers of the single scene), capped at probe_iters
  * iterations (1..4096), run twice per candidate.  Coordinate descent over:

@@ -681,7 +681,7 @@ cch_status cch_handle_step_host(cch_scene* S, const double* x_t, const double* x
   return r;
 }
 
-// Autotuner of the launch configuration (the benchmark spec pattern 2).  Candidate
+// Autotuner of the launch configuration.  Candidate
 // values are timed on a probe (one step from the caller's inputs, capped at
 // probe_iters iterations) by coordinate descent: iterations per graph launch
 // group, the block size of the BVH queries, BVH refit against rebuild, and

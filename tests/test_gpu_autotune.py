@@ -1,4 +1,4 @@
-"""Autotuner of the launch configuration (the benchmark spec pattern 2): it picks
+"""Autotuner of the launch configuration: it picks
 from the stated candidate sets, every probe gives the same result, and steps
 after tuning equal steps before it bitwise (the configuration never changes
 results)."""

@@ -1,5 +1,5 @@
-"""Segment CCD safety check (Sec. 5.1 scheme, row a11) and the acceptance test
-of x^{t+1} (row a12) on the GPU, against the oracle."""
+"""Segment CCD safety check (the CCD of Sec. 5.1's comparison scheme, used as
+a check) and the acceptance test of x^{t+1} on the GPU, against the oracle."""
 import numpy as np
 import pytest
 

@@ -1,4 +1,4 @@
-"""Serving (the benchmark spec pattern 5): resident scenes, requests arriving while
+"""Serving: resident scenes, requests arriving while
 others run, continuous batching at launch boundaries.  Each result must equal
 the result of the same request run alone, bitwise, in FP64 and in mixed
 precision, with either backward step (every path is deterministic)."""
