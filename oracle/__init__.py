@@ -47,7 +47,8 @@ class Params(C.Structure):
     _fields_ = [("d_min", C.c_double), ("d_max", C.c_double), ("delta", C.c_double), ("sigma", C.c_double),
                 ("gamma", C.c_double), ("eps", C.c_double), ("jacobi_omega", C.c_double),
                 ("max_iters", C.c_int32), ("gs_sweeps", C.c_int32), ("solver", C.c_int32),
-                ("ccd_check", C.c_int32), ("search_mode", C.c_int32), ("constraint_form", C.c_int32), ("seed", C.c_uint64)]
+                ("ccd_check", C.c_int32), ("search_mode", C.c_int32), ("constraint_form", C.c_int32),
+                ("step_rule", C.c_int32), ("ccd_rounds", C.c_int32), ("seed", C.c_uint64)]
 
 
 class Stats(C.Structure):

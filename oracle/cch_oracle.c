@@ -60,7 +60,7 @@ void orc_params_default(orc_params* p) {
   p->d_min = 2e-3; p->d_max = 4e-3; p->delta = 1e-3; p->sigma = 1.1; p->gamma = 0.9;
   p->eps = 1e-4; p->jacobi_omega = 0.5;
   p->max_iters = 2048; p->gs_sweeps = 1; p->solver = 0; p->ccd_check = 0; p->search_mode = 2;
-  p->constraint_form = 0; p->seed = 0x2211040450ULL;
+  p->constraint_form = 0; p->step_rule = 0; p->ccd_rounds = 8; p->seed = 0x2211040450ULL;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1000,8 +1000,8 @@ int orc_backward_once(const orc_topology* t, const orc_params* prm, const double
 }
 
 /* ------------------------------------------------------------------------ */
-/* CCD of a linearly moving pair (Sec. 5.1's comparison scheme; here only a  */
-/* safety check of each forward segment).                                    */
+/* CCD of a linearly moving pair (Sec. 5.1's comparison scheme: the step    */
+/* rule of its CCD-based variant, or a safety check of each segment).       */
 /* ------------------------------------------------------------------------ */
 static double cubic_at(const double c[4], double t) { return ((c[3] * t + c[2]) * t + c[1]) * t + c[0]; }
 
@@ -1238,13 +1238,19 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
     backward(t, prm, cc, nc, ce, ne, x, y);
     free(cc);
 
-    /* forward step, Eq. forward2 (R2) */
+    /* forward step, Eq. forward2 (R2).  The CCD-based rule (Sec. 5.1's
+     * comparison scheme) caps every vertex by the global bound D^(l) instead
+     * of its own D_i and lets the CCD below decide the step: a pair outside P
+     * is at least D^(l) apart and its two sides close at most 0.9 D^(l) */
+    const int ccd_rule = prm->step_rule == 1;
+    double Dcap = D;
+    if (!(Dcap >= ORC_D_FLOOR)) Dcap = 0.0;
     for (int64_t v = 0; v < n; v++) {
       v3 xv = ld3(x, v), yv = ld3(y, v);
       v3 dx = sub3(yv, xv);
       double nd = norm3(dx), a = 1.0;
       if (nd > 0.0) {
-        double q = (hg * Di[v]) / nd;
+        double q = (hg * (ccd_rule ? Dcap : Di[v])) / nd;
         a = q < 1.0 ? q : 1.0;
       } else if (nd != 0.0) {
         a = 0.0; /* R2c: y not finite, the vertex does not move */
@@ -1252,29 +1258,38 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
       alpha[v] = a;
       st3(xn, v, step_to(xv, yv, a));
     }
-    /* optional CCD safety check on each pair's segment; a hit scales the
-     * step of the pair's vertices by half the time of impact */
-    if (prm->ccd_check) {
-      for (int64_t v = 0; v < n; v++) clampf[v] = 1.0;
-      int hit_any = 0;
-      for (int64_t i = 0; i < P.n; i++) {
-        int32_t v4[4];
-        int nv = pair_verts(t, P.k[i], v4);
-        double a0[12], a1[12], rr[2] = {rho_of(t, v4[0]), nv == 2 ? rho_of(t, v4[1]) : 0.0}, toi;
-        for (int k = 0; k < nv; k++) { st3(a0, k, ld3(x, v4[k])); st3(a1, k, ld3(xn, v4[k])); }
-        if (orc_ccd(key_kind(P.k[i]), a0, a1, rr, &toi)) {
-          hit_any = 1;
-          S.ccd_clamps++;
-          for (int k = 0; k < nv; k++)
-            if (0.5 * toi < clampf[v4[k]]) clampf[v4[k]] = 0.5 * toi;
+    /* CCD of each pair's segment x^(l) -> x^(l+1) (the safety check, or the
+     * step rule): a hit at time t_hit scales the step of the pair's vertices by
+     * t_hit / 2 (the smallest factor over their pairs) and the segments are tested
+     * again, for at most ccd_rounds rounds; a hit after the last round keeps
+     * every vertex of the scene where it is for this iteration */
+    if (prm->ccd_check || ccd_rule) {
+      for (int32_t round = 0;; round++) {
+        for (int64_t v = 0; v < n; v++) clampf[v] = 1.0;
+        int hit_any = 0;
+        for (int64_t i = 0; i < P.n; i++) {
+          int32_t v4[4];
+          int nv = pair_verts(t, P.k[i], v4);
+          double a0[12], a1[12], rr[2] = {rho_of(t, v4[0]), nv == 2 ? rho_of(t, v4[1]) : 0.0}, toi;
+          for (int k = 0; k < nv; k++) { st3(a0, k, ld3(x, v4[k])); st3(a1, k, ld3(xn, v4[k])); }
+          if (orc_ccd(key_kind(P.k[i]), a0, a1, rr, &toi)) {
+            hit_any = 1;
+            S.ccd_clamps++;
+            for (int k = 0; k < nv; k++)
+              if (0.5 * toi < clampf[v4[k]]) clampf[v4[k]] = 0.5 * toi;
+          }
         }
-      }
-      if (hit_any)
+        if (!hit_any) break;
+        if (round >= prm->ccd_rounds) {
+          for (int64_t v = 0; v < n; v++) { alpha[v] = 0.0; st3(xn, v, ld3(x, v)); }
+          break;
+        }
         for (int64_t v = 0; v < n; v++)
           if (clampf[v] < 1.0) {
             alpha[v] = clampf[v] * alpha[v];
             st3(xn, v, step_to(ld3(x, v), ld3(y, v), alpha[v]));
           }
+      }
     }
     double mmax = 0.0, rmax = 0.0;
     for (int64_t v = 0; v < n; v++) {

@@ -50,6 +50,10 @@ typedef struct {
   int32_t search_mode;   /* 0 = all pairs, 1 = sorted-axis window, 2 = auto  */
   int32_t constraint_form; /* 0 = volume (Sec. 4.1), 1 = gap (the comparison */
                            /*     constraints of Sec. 4.1's gap figure)      */
+  int32_t step_rule;     /* 0 = distance bound of Eq. forward2; 1 = CCD-based
+                            step size (the comparison scheme of Sec. 5.1)     */
+  int32_t ccd_rounds;    /* CCD clamp rounds before the scene's step is
+                            frozen for the iteration (CCD check and rule)     */
   uint64_t seed;         /* sweep priorities (R11)                            */
 } orc_params;
 

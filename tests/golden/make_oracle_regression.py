@@ -25,7 +25,7 @@ CASES = {
     "hair_sand": lambda: scenes.hair_sand(n_strands=36, segs=8, n_points=120, grain_r=0.002, bowl_r=0.12,
                                           bowl_subdiv=2, seg_len=0.01, seed=4),
 }
-VARIANTS = {"gs": {}, "jacobi": {"solver": 1}, "gap": {"constraint_form": 1}}
+VARIANTS = {"gs": {}, "jacobi": {"solver": 1}, "gap": {"constraint_form": 1}, "ccd_rule": {"step_rule": 1}}
 
 
 def record(name, variant):
@@ -44,6 +44,6 @@ def lines():
 
 if __name__ == "__main__":
     with open(os.path.join(HERE, "oracle_regression.txt"), "w") as f:
-        f.write("# written by make_oracle_regression.py; one line per scene and backward-step variant\n")
+        f.write("# written by make_oracle_regression.py; one line per scene and variant (backward step or step rule)\n")
         for line in lines():
             f.write(line + "\n")
