@@ -158,18 +158,18 @@ def min_iterations(x_t, x_tilde, d_max, gamma):
     return max(1, math.ceil(far / (0.5 * gamma * d_max)))
 
 
-def oracle_sample(sc, x_t, x_tilde, budget_s: float, solver: int = 0):
+def oracle_sample(sc, x_t, x_tilde, budget_s: float, solver: int = 0, step_rule: int = 0):
     """Times the oracle, as it stands, on the first iterations of one step.
     Returns (seconds per iteration, iterations timed, pairs evaluated)."""
     import oracle
     osc = oracle.OracleScene(sc)
-    prm = oracle.params_for(sc, max_iters=0, solver=solver)
+    prm = oracle.params_for(sc, max_iters=0, solver=solver, step_rule=step_rule)
     t0 = time.perf_counter()
     _, st, _ = oracle.handle_step(osc, prm, x_t, x_tilde)
     t1 = time.perf_counter() - t0
     m = int(max(1, min(64, budget_s / max(t1, 1e-6))))
     if m > 1:
-        prm = oracle.params_for(sc, max_iters=m - 1, solver=solver)
+        prm = oracle.params_for(sc, max_iters=m - 1, solver=solver, step_rule=step_rule)
         t0 = time.perf_counter()
         _, st, _ = oracle.handle_step(osc, prm, x_t, x_tilde)
         t1 = time.perf_counter() - t0
@@ -313,6 +313,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--gap", action="store_true", help="gap contact constraints instead of the volume-based ones")
+    ap.add_argument("--step-rule", default="distance", choices=["distance", "ccd"],
+                    help="forward step size: the distance bound (Eq. forward2) or the CCD-based scheme of Sec. 5.1")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-configuration autotuner")
     ap.add_argument("--tune-iters", type=int, default=48, help="iterations of the autotuner's probe step")
@@ -341,7 +343,8 @@ def main():
     from paper_2211_04045_gb300 import cch, scenes
     sc, wname = workload(args.config)
     prm = cch.params_for(sc, precision=1 if args.precision == "mixed" else 0,
-                         solver=1 if args.solver == "jacobi" else 0, constraint_form=1 if args.gap else 0)
+                         solver=1 if args.solver == "jacobi" else 0, constraint_form=1 if args.gap else 0,
+                         step_rule=1 if args.step_rule == "ccd" else 0)
     if args.ncu_case:
         x0, xt0, v0 = scenes.initial(sc)
         x, xt, v = (torch.tensor(a, device=dev) for a in (x0, xt0, v0))
@@ -508,7 +511,8 @@ def main():
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        spi, its, pe = oracle_sample(sc, x0, xt0, args.cpu_budget, 1 if args.solver == "jacobi" else 0)
+        spi, its, pe = oracle_sample(sc, x0, xt0, args.cpu_budget, 1 if args.solver == "jacobi" else 0,
+                                     1 if args.step_rule == "ccd" else 0)
         mean_it = float(np.mean(iters))
         cpu = {"value": 1.0 / (spi * mean_it), "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": f"first {its} iterations of the chain's first step ({spi * its:.1f} s), seconds per "
@@ -520,7 +524,7 @@ def main():
                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
                "config": {"workload": f"{wname}_{args.precision}" + ("_jacobi" if args.solver == "jacobi" else "")
-                          + ("_gap" if args.gap else ""), "verts": n, "tris": T, "edges": E,
+                          + ("_gap" if args.gap else "") + ("_ccdstep" if args.step_rule == "ccd" else ""), "verts": n, "tris": T, "edges": E,
                           "len_edges": len(sc.len_edges), "dt": sc.dt, "l2": "flushed between steps (256 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single"},
                "contact_pairs_per_sec": pairs / (total_ms / 1000.0),
@@ -528,6 +532,7 @@ def main():
                "iterations_per_step": float(np.mean(iters)), "converged_steps": int(sum(s["converged"] for s in stats)),
                "sweep_depth": int(pst["gs_depth"]),
                "max_vertex_contacts": int(max(s["max_vertex_contacts"] for s in stats)),
+               "ccd_hits": int(sum(s["ccd_clamps"] for s in stats)),
                "deterministic_replay": bool(deterministic and e2e_same),
                "autotune": tune, "roofline": roof, "kernel_groups": groups, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": clk,

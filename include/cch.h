@@ -63,6 +63,15 @@ typedef enum { CCH_SOLVER_GAUSS_SEIDEL = 0, CCH_SOLVER_JACOBI = 1 } cch_solver;
  * Vertex-vertex pairs use the distance form in both. */
 typedef enum { CCH_FORM_VOLUME = 0, CCH_FORM_GAP = 1 } cch_constraint_form;
 
+/* Step size of the forward step.  CCH_STEP_DISTANCE: Eq. forward2,
+ * alpha_i = min(0.5 gamma D_i / |y_i - x_i|, 1), safe by construction (Sec.
+ * 5).  CCH_STEP_CCD: the CCD-based scheme Sec. 5.1 compares it with: every
+ * vertex is capped by the global bound 0.5 gamma D^(l) (a pair outside P is at
+ * least D^(l) apart, so only pairs of P can meet), and the CCD of each pair's
+ * segment decides the rest: a hit at time t scales the step of the pair's
+ * vertices by t/2, and the segments are tested again (ccd_rounds). */
+typedef enum { CCH_STEP_DISTANCE = 0, CCH_STEP_CCD = 1 } cch_step_rule;
+
 /* Parameters of Algorithm 1.  cch_params_default() fills Table 2's values
  * (L = 2048, eps = 1e-4, D^min = 2 mm, D^max = 4 mm, delta = 1 mm,
  * sigma = 1.1, gamma = 0.9). */
@@ -80,13 +89,18 @@ typedef struct {
   int32_t solver;        /* cch_solver                                         */
   int32_t ccd_check;     /* 1: CCD of every pair's segment each iteration, with
                             the time-of-impact clamp (Sec. 5.1 scheme as a
-                            safety net)                                        */
+                            safety net; always on under CCH_STEP_CCD)          */
   int32_t accept_check;  /* 1: exact-filtered intersection test of x^{t+1}     */
   int32_t validate_input;/* 1: the same test on x^t before the loop            */
   int32_t iters_per_launch; /* iterations captured per CUDA-graph launch (G)   */
   int32_t bvh_refit_only;   /* 1: rebuild the BVH at the first search of a step
                                and only refit it at later searches             */
   int32_t constraint_form;  /* cch_constraint_form                             */
+  int32_t step_rule;        /* cch_step_rule                                   */
+  int32_t ccd_rounds;       /* CCD clamp rounds per iteration, 0..64 (default
+                               8); a hit that remains after the last round
+                               keeps every vertex of the scene in place for the
+                               iteration                                       */
   uint64_t seed;         /* priorities of the randomized sweep order (Sec. 4.3) */
 } cch_params;
 
@@ -109,7 +123,8 @@ typedef struct {
   int32_t iterations;        /* Algorithm 1 iterations executed               */
   int32_t searches;          /* proximity searches                            */
   int32_t converged;         /* ||r||_inf < eps reached                       */
-  int32_t ccd_clamps;        /* CCD hits that clamped a step (expected 0)     */
+  int32_t ccd_clamps;        /* CCD hits, summed over the rounds of every
+                                iteration (0 expected under CCH_STEP_DISTANCE) */
   int64_t pairs_evaluated;   /* sum over iterations of |P|                    */
   int64_t max_pairs;         /* max over iterations of |P|                    */
   int64_t active_contacts;   /* sum over iterations of contacts (dist<delta)  */

@@ -38,7 +38,8 @@ class Params(C.Structure):
                 ("max_iters", C.c_int32), ("gs_sweeps", C.c_int32), ("precision", C.c_int32),
                 ("solver", C.c_int32), ("ccd_check", C.c_int32), ("accept_check", C.c_int32),
                 ("validate_input", C.c_int32), ("iters_per_launch", C.c_int32), ("bvh_refit_only", C.c_int32),
-                ("constraint_form", C.c_int32), ("seed", C.c_uint64)]
+                ("constraint_form", C.c_int32), ("step_rule", C.c_int32), ("ccd_rounds", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class Topology(C.Structure):

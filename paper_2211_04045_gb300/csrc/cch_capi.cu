@@ -128,6 +128,8 @@ cch_status validate_params(const cch_params* p) {
   if (p->precision != CCH_PREC_FP64 && p->precision != CCH_PREC_MIXED) return CCH_E_INVALID_ARG;
   if (p->solver != CCH_SOLVER_GAUSS_SEIDEL && p->solver != CCH_SOLVER_JACOBI) return CCH_E_INVALID_ARG;
   if (p->constraint_form != CCH_FORM_VOLUME && p->constraint_form != CCH_FORM_GAP) return CCH_E_INVALID_ARG;
+  if (p->step_rule != CCH_STEP_DISTANCE && p->step_rule != CCH_STEP_CCD) return CCH_E_INVALID_ARG;
+  if (p->ccd_rounds < 0 || p->ccd_rounds > 64) return CCH_E_INVALID_ARG;
   if (p->iters_per_launch < 0 || p->iters_per_launch > 4096) return CCH_E_INVALID_ARG;
   return CCH_OK;
 }
@@ -237,6 +239,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
     d.hgamma = 0.5 * prm->gamma; d.eps = prm->eps; d.omega = prm->jacobi_omega;
     d.form = prm->constraint_form;
     d.max_iters = prm->max_iters; d.gs_sweeps = prm->gs_sweeps; d.solver = prm->solver; d.ccd = prm->ccd_check;
+    d.step_rule = prm->step_rule;
     d.seed = prm->seed;
     d.rho_max = 0.0;
     if (t.point_radius)
@@ -272,7 +275,8 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   while ((1 << R.scene_bits) < n_scenes) R.scene_bits++;
   R.sweeps = prm->gs_sweeps;
   R.solver = prm->solver;
-  R.ccd = prm->ccd_check;
+  R.ccd = prm->ccd_check || prm->step_rule == CCH_STEP_CCD;
+  R.ccd_rounds = prm->ccd_rounds;
   R.accept = prm->accept_check;
   R.validate = prm->validate_input;
   R.iters_per_check = prm->iters_per_launch > 0 ? prm->iters_per_launch : 16;
@@ -295,7 +299,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   P.xp = nullptr;
   P.alpha = nullptr;
   P.clampb = nullptr;
-  if (prm->ccd_check) {
+  if (R.ccd) {
     CK(dalloc(R, &P.xp, nv));
     CK(dalloc(R, &P.alpha, nv));
     CK(dalloc(R, &P.clampb, nv));
@@ -591,6 +595,8 @@ cch_status cch_params_default(cch_params* p) {
   p->iters_per_launch = 16;
   p->bvh_refit_only = 1;
   p->constraint_form = CCH_FORM_VOLUME;
+  p->step_rule = CCH_STEP_DISTANCE;
+  p->ccd_rounds = 8;
   p->seed = 0x2211040450ULL;
   return CCH_OK;
 }

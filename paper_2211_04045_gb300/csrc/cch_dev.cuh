@@ -35,6 +35,7 @@ struct SceneDesc {
   int form;                       // contact constraint: 0 volume, 1 gap
   double rho_max;  // largest point radius of the scene
   int max_iters, gs_sweeps, solver, ccd;
+  int step_rule;                  // 0 distance bound (Eq. forward2), 1 CCD-based
   uint64_t seed;
 };
 
@@ -59,6 +60,8 @@ struct SceneState {
   double final_r;
   long long isect, uncertain;
   int bad_input;                  // x_t or x~ held a non-finite coordinate
+  int ccd_live;                   // the CCD rounds of this iteration go on
+  int ccd_hits[2];                // hits of the current CCD round (by parity)
   int pad_;
 };
 

@@ -41,6 +41,7 @@ struct Runtime {
   int scene_bits = 0;                // bits of the scene index in Morton keys
   int coop_blocks = 0;               // grid of the cooperative sweep kernel
   int sweeps = 1, solver = 0, ccd = 0, accept = 0, validate = 0;
+  int ccd_rounds = 8;  // CCD clamp rounds per iteration
   int max_iters = 0;                 // max over scenes
   int iters_per_check = 16;          // G: iterations per graph launch group (autotuned)
   int query_block = 128;             // threads per block of the BVH queries (autotuned)

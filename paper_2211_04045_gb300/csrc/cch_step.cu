@@ -957,7 +957,9 @@ __global__ void k_forward(Pool P) {
     int s = P.vscene[v];
     const SceneState& S = P.ss[s];
     if (!S.active || S.done) continue;
-    double Di = bitsd(P.Dv[v]);
+    // CCD-based rule: the global bound D^(l) caps every vertex, the CCD
+    // rounds decide the rest
+    double Di = P.sd[s].step_rule ? S.D : bitsd(P.Dv[v]);
     if (S.D < Di) Di = S.D;
     if (!(Di >= D_FLOOR)) Di = 0.0;
     P.Dv[v] = 0x7ff0000000000000ULL;
@@ -993,18 +995,30 @@ __global__ void k_forward(Pool P) {
 }
 
 // ---------------------------------------------------------------------------
-// Segment safety check (CCD mode): every pair of P is tested over its segment
-// x^(l) -> x^(l+1); a contact at time t* scales the step of the pair's
-// vertices by t*/2 (minimum over the pairs).
+// CCD of every pair's segment x^(l) -> x^(l+1) (the safety check, or the
+// CCD-based step rule of Sec. 5.1): a hit at time t scales the step of the
+// pair's vertices by t/2 (the smallest factor over their pairs), and the
+// segments are tested again.  Round k runs k_ccd_pairs then k_ccd_apply; a
+// scene whose round finds no hit leaves the rounds; a hit in the test after
+// the last round keeps every vertex of the scene in place (k_ccd_fix).
 // ---------------------------------------------------------------------------
-__global__ void k_ccd_pairs(Pool P, int nxt) {
+__global__ void k_ccd_begin(Pool P) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < P.nscene) {
+    P.ss[s].ccd_live = 1;
+    P.ss[s].ccd_hits[0] = 0;
+    P.ss[s].ccd_hits[1] = 0;
+  }
+}
+
+__global__ void k_ccd_pairs(Pool P, int nxt, int round) {
   int n = min(P.cnt->n_pairs[nxt], P.pair_cap);
   const PairBuf B = P.pb[nxt];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int4 v = B.v[i];
     int s = P.vscene[v.x];
     const SceneState& S = P.ss[s];
-    if (!S.active || S.done) continue;
+    if (!S.active || S.done || !S.ccd_live) continue;
     int kind = (int)(B.key[i] >> 62);
     int vid[4] = {v.x, v.y, v.z, v.w};
     int nv = kind == K_VV ? 2 : 4;
@@ -1018,31 +1032,60 @@ __global__ void k_ccd_pairs(Pool P, int nxt) {
       unsigned long long cb = dbits(0.5 * toi);
       for (int k = 0; k < nv; k++) atomicMin(&P.clampb[vid[k]], cb);
       atomicAdd(&P.ss[s].ccd_clamps, 1);
+      atomicAdd(&P.ss[s].ccd_hits[round & 1], 1);
     }
   }
 }
 
-__global__ void k_ccd_fix(Pool P) {
+__device__ __forceinline__ dv3 y_of(const Pool& P, int v) {
+  if (P.yf) {
+    float4 f = P.yf[v];
+    return {(double)f.x, (double)f.y, (double)f.z};
+  }
+  return mk(P.y[v]);
+}
+
+// Round `round` (< ccd_rounds) found hits: scale the clamped steps.  The
+// counter of the next round is cleared here (nothing reads it in this launch).
+__global__ void k_ccd_apply(Pool P, int round) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
+    int s = P.vscene[v];
+    SceneState& S = P.ss[s];
+    if (!S.active || S.done) continue;
+    if (v == P.sd[s].v0) S.ccd_hits[(round + 1) & 1] = 0;
+    if (S.ccd_hits[round & 1] == 0) {
+      if (v == P.sd[s].v0) S.ccd_live = 0;
+      continue;
+    }
+    double c = bitsd(P.clampb[v]);
+    if (c < 1.0) {
+      double a = c * P.alpha[v];
+      P.alpha[v] = a;
+      dv3 xn = step_to(mk(P.xp[v]), y_of(P, v), a);
+      P.x[v] = {xn.x, xn.y, xn.z, 0.0};
+      P.xf[v] = make_float4((float)xn.x, (float)xn.y, (float)xn.z, 0.f);
+      P.clampb[v] = dbits(1.0);
+    }
+  }
+}
+
+// After the last round: a remaining hit keeps the scene in place; then r and
+// the reductions of the forward step.
+__global__ void k_ccd_fix(Pool P, int round) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < P.nv; v += gridDim.x * blockDim.x) {
     int s = P.vscene[v];
     const SceneState& S = P.ss[s];
     if (!S.active || S.done) continue;
     double a = P.alpha[v];
-    double c = bitsd(P.clampb[v]);
     dv3 xv = mk(P.xp[v]);
     dv3 xn = mk(P.x[v]);
-    if (c < 1.0) {
-      a = c * a;
-      dv3 yv;
-      if (P.yf) {
-        float4 f = P.yf[v];
-        yv = {(double)f.x, (double)f.y, (double)f.z};
-      } else yv = mk(P.y[v]);
-      xn = step_to(xv, yv, a);
+    if (S.ccd_live && S.ccd_hits[round & 1] > 0) {
+      a = 0.0;
+      xn = xv;
       P.x[v] = {xn.x, xn.y, xn.z, 0.0};
       P.xf[v] = make_float4((float)xn.x, (float)xn.y, (float)xn.z, 0.f);
-      P.clampb[v] = dbits(1.0);
     }
+    P.clampb[v] = dbits(1.0);
     double r = P.r[v] * (1.0 - a);
     P.r[v] = r;
     double mv = vnorm(vsub(xn, xv));
@@ -1239,9 +1282,14 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   prof_mark(R, PG_FORWARD, 0, st);
   k_forward<<<grid_for(P.nv, 256), 256, 0, st>>>(P);
   if (P.alpha) {
-    k_ccd_pairs<<<grid_for(P.pair_cap, 128), 128, 0, st>>>(P, nxt);
-    k_ccd_fix<<<grid_for(P.nv, 256), 256, 0, st>>>(P);
-    R.launches += 2;
+    k_ccd_begin<<<(P.nscene + 127) / 128, 128, 0, st>>>(P);
+    for (int k = 0; k < R.ccd_rounds; k++) {
+      k_ccd_pairs<<<grid_for(P.pair_cap, 128), 128, 0, st>>>(P, nxt, k);
+      k_ccd_apply<<<grid_for(P.nv, 256), 256, 0, st>>>(P, k);
+    }
+    k_ccd_pairs<<<grid_for(P.pair_cap, 128), 128, 0, st>>>(P, nxt, R.ccd_rounds);
+    k_ccd_fix<<<grid_for(P.nv, 256), 256, 0, st>>>(P, R.ccd_rounds);
+    R.launches += 3 + 2 * R.ccd_rounds;
   }
   prof_mark(R, PG_FORWARD, 1, st);
   prof_mark(R, PG_CONTROL, 0, st);

@@ -33,6 +33,10 @@ def test_defaults_are_table_2():
     p = cch.params()
     assert (p.d_min, p.d_max, p.delta, p.sigma, p.gamma, p.eps) == (2e-3, 4e-3, 1e-3, 1.1, 0.9, 1e-4)
     assert p.max_iters == 2048 and p.gs_sweeps == 1
+    # the step rule and CCD rounds agree with the oracle's defaults
+    import oracle
+    o = oracle.params()
+    assert (p.step_rule, p.ccd_rounds, p.ccd_check) == (o.step_rule, o.ccd_rounds, o.ccd_check) == (0, 8, 0)
 
 
 def topo(**kw):
@@ -61,7 +65,8 @@ def test_invalid_topology_rejected(bad):
 
 @pytest.mark.parametrize("field,value", [("d_min", 0.0), ("d_max", 1e-3), ("delta", 3e-3), ("gamma", 1.0),
                                          ("gs_sweeps", 0), ("precision", 7), ("solver", 3), ("max_iters", -1),
-                                         ("constraint_form", 2)])
+                                         ("constraint_form", 2), ("step_rule", 2), ("ccd_rounds", -1),
+                                         ("ccd_rounds", 65)])
 def test_invalid_params_rejected(field, value):
     p = cch.params()
     setattr(p, field, value)
