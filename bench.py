@@ -45,6 +45,8 @@ def workload(name: str):
         return scenes.tet_bodies(), "tets64x8"
     if name == "knot":
         return scenes.tube_knot(), "knot2x64x561"
+    if name == "normal_flow":
+        return scenes.normal_flow_torus(), "normal_flow_torus512x96"
     raise SystemExit(f"unknown config {name}")
 
 

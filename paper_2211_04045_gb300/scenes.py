@@ -9,6 +9,11 @@ synthetic stand-in shaped like the paper's examples: cloth over a sphere, two
 stacked cloth layers, a pile of volumetric bodies, two interleaved tubes that
 tighten like a knot, and hair strands with sand grains in a bowl.
 
+A second workload is the globally injective normal flow of Sec. 7.4: the
+target of each step is the surface pushed along its vertex normals and then
+smoothed by three Jacobi steps of the cotangent Laplacian (Eq. normal flow);
+the collision-handling step keeps the flow free of self-intersections.
+
 The stand-in dynamics (not part of the method, which receives ``x~`` as
 input) is explicit inertia ``x~ = x^t + dt v`` with scripted kinematic
 vertices, followed by a few Jacobi sweeps that pull mesh edges toward their
@@ -42,6 +47,7 @@ class Scene:
     relax_sweeps: int = 4
     steps: int = 30
     params: dict = dataclasses.field(default_factory=dict)
+    flow: Optional[dict] = None             # normal-flow target instead of the dynamics (beta, alpha, sign, iters)
 
     @property
     def n_verts(self) -> int:
@@ -354,9 +360,100 @@ def hair_sand(n_strands: int = 10000, segs: int = 32, n_points: int = 100000, gr
 # --------------------------------------------------------------------------
 # stand-in dynamics that produces x~ for each step
 # --------------------------------------------------------------------------
+# --------------------------------------------------------------------------
+# globally injective normal flow (Sec. 7.4, Eq. normal flow)
+# --------------------------------------------------------------------------
+def torus_mesh(n_major: int, n_minor: int, R: float, r: float):
+    """Closed torus around the z axis: n_major rings of n_minor vertices;
+    triangles wound so that (b - a) x (c - a) points outward."""
+    u = 2 * math.pi * np.arange(n_major) / n_major
+    w = 2 * math.pi * np.arange(n_minor) / n_minor
+    U, W = np.meshgrid(u, w, indexing="ij")
+    A = R + r * np.cos(W)
+    x = np.stack([A * np.cos(U), A * np.sin(U), r * np.sin(W)], -1).reshape(-1, 3)
+    i, j = np.meshgrid(np.arange(n_major), np.arange(n_minor), indexing="ij")
+    v00 = i * n_minor + j
+    v10 = ((i + 1) % n_major) * n_minor + j
+    v11 = ((i + 1) % n_major) * n_minor + (j + 1) % n_minor
+    v01 = i * n_minor + (j + 1) % n_minor
+    tris = np.concatenate([np.stack([v00, v10, v11], -1).reshape(-1, 3),
+                           np.stack([v00, v11, v01], -1).reshape(-1, 3)]).astype(np.int32)
+    return x, tris
+
+
+def vertex_normals(x: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    """Unit vertex normals: the area-weighted sum of the incident faces'
+    normals (each face adds (b - a) x (c - a), twice its area times its unit
+    normal)."""
+    a, b, c = x[tris[:, 0]], x[tris[:, 1]], x[tris[:, 2]]
+    fn = np.cross(b - a, c - a)
+    n = np.zeros_like(x)
+    for k in range(3):
+        np.add.at(n, tris[:, k], fn)
+    L = np.linalg.norm(n, axis=1)
+    return n / np.where(L > 0, L, 1.0)[:, None]
+
+
+def cotan_laplacian(y: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    """Cotangent discretisation of the Laplace-Beltrami operator applied to
+    the coordinates y: (Lap y)(v) = 1/(2 A_v) sum_u (cot a_vu + cot b_vu)
+    (y_u - y_v), with A_v the mixed Voronoi area of Meyer et al. (2003): a
+    corner of a non-obtuse triangle takes its Voronoi part, (|e1|^2 cot +
+    |e2|^2 cot)/8 over its two edges and their opposite angles; in an obtuse
+    triangle the obtuse corner takes half the area and the others a quarter."""
+    p = [y[tris[:, k]] for k in range(3)]
+    n = np.zeros_like(y)
+    A = np.zeros(len(y))
+    area2 = np.linalg.norm(np.cross(p[1] - p[0], p[2] - p[0]), axis=1)
+    safe2 = np.where(area2 > 0, area2, 1.0)
+    dots = [np.einsum("ij,ij->i", p[(k + 1) % 3] - p[k], p[(k + 2) % 3] - p[k]) for k in range(3)]
+    cot = [d / safe2 for d in dots]
+    obtuse = (dots[0] < 0) | (dots[1] < 0) | (dots[2] < 0)
+    for k in range(3):
+        q, s_ = p[(k + 1) % 3], p[(k + 2) % 3]
+        # the edge (q, s) opposite corner k carries cot/2 to both its ends
+        np.add.at(n, tris[:, (k + 1) % 3], 0.5 * cot[k][:, None] * (s_ - q))
+        np.add.at(n, tris[:, (k + 2) % 3], 0.5 * cot[k][:, None] * (q - s_))
+        e_q = np.einsum("ij,ij->i", q - p[k], q - p[k])    # edge k-(k+1), opposite corner k+2
+        e_s = np.einsum("ij,ij->i", s_ - p[k], s_ - p[k])  # edge k-(k+2), opposite corner k+1
+        vor = (e_q * cot[(k + 2) % 3] + e_s * cot[(k + 1) % 3]) / 8.0
+        np.add.at(A, tris[:, k], np.where(~obtuse, vor, np.where(dots[k] < 0, area2 / 4.0, area2 / 8.0)))
+    return n / np.where(A > 0, A, 1.0)[:, None]
+
+
+def normal_flow_target(x: np.ndarray, tris: np.ndarray, beta: float, alpha: float, sign: float = 1.0,
+                       iters: int = 3) -> np.ndarray:
+    """Eq. normal flow: y_0 = x + sign beta n(x), then `iters` Jacobi steps
+    y_{i+1} = y_i + alpha Lap(y_i), the operator taken on the surface y_i."""
+    y = x + (sign * beta) * vertex_normals(x, tris)
+    for _ in range(iters):
+        y = y + alpha * cotan_laplacian(y, tris)
+    return y
+
+
+def normal_flow_torus(n_major: int = 512, n_minor: int = 96, R: float = 0.1, r: float = 0.008,
+                      beta: float = 2e-3, alpha_frac: float = 0.1, sign: float = -1.0, steps: int = 8) -> Scene:
+    """A closed torus under the normal flow of Sec. 7.4 (the paper's meshes
+    are not available).  sign = -1 shrinks the tube until its opposite sides
+    meet; sign = +1 with R - r small closes the hole.  alpha is alpha_frac
+    times the squared mean edge length (the explicit Jacobi step is stable
+    well below 1/4 of it)."""
+    x, tris = torus_mesh(n_major, n_minor, R, r)
+    edges = unique_edges(tris)
+    h = float(np.mean(np.linalg.norm(x[edges[:, 0]] - x[edges[:, 1]], axis=1)))
+    flow = dict(beta=beta, alpha=alpha_frac * h * h, sign=sign, iters=3)
+    n = len(x)
+    return Scene(f"normal_flow_torus{n_major}x{n_minor}{'+' if sign > 0 else '-'}", np.ones(n), tris, edges,
+                 edges.copy(), np.zeros(0, np.int32), x, np.zeros_like(x), 1.0, np.zeros(3), relax_sweeps=0,
+                 steps=steps, params=dict(max_iters=2048), flow=flow)
+
+
 def predict(scene: Scene, x: np.ndarray, v: np.ndarray) -> np.ndarray:
     """x~ = x + dt v, kinematic vertices on their script, then Jacobi
-    sweeps toward rest edge lengths (inverse-mass weighted)."""
+    sweeps toward rest edge lengths (inverse-mass weighted).  A normal-flow
+    scene ignores v: its target is Eq. normal flow at x."""
+    if scene.flow is not None:
+        return normal_flow_target(x, scene.tris, **scene.flow)
     xt = x + scene.dt * v
     im = scene.inv_mass
     fixed = im == 0.0
@@ -408,6 +505,7 @@ def by_name(name: str, **kw) -> Scene:
         "tets": tet_bodies,
         "knot": tube_knot,
         "hair_sand": hair_sand,
+        "normal_flow": normal_flow_torus,
     }
     return table[name](**kw)
 
@@ -422,6 +520,24 @@ class TorchDynamics:
         self.torch = torch
         self.sc = scene
         f = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=device)  # noqa: E731
+        if scene.flow is not None:
+            # per-vertex table of (triangle, corner) slots, padded with a
+            # zero slot: the per-vertex sums of the normal flow run in a
+            # fixed order, without atomics
+            t = scene.tris.astype(np.int64)
+            n, T = scene.n_verts, len(t)
+            ends = t.reshape(-1)
+            slots = np.arange(3 * T)
+            order = np.argsort(ends, kind="stable")
+            ends, slots = ends[order], slots[order]
+            cnt = np.bincount(ends, minlength=n)
+            width = max(1, int(cnt.max()))
+            start = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+            col = np.arange(len(ends)) - start[ends]
+            idx = np.full((n, width), 3 * T, np.int64)
+            idx[ends, col] = slots
+            self.f_tris = f(t)
+            self.f_slot = f(idx)
         self.im = f(scene.inv_mass)
         self.fixed = self.im == 0.0
         self.kin_v = f(scene.kin_v if scene.kin_v is not None else np.zeros_like(scene.x0))
@@ -460,9 +576,48 @@ class TorchDynamics:
             self.inc_idx, self.inc_w = f(idx), f(w)[:, :, None]
             self.rest = f(scene.rest_len)
 
+    def _gather(self, per_corner):
+        # per_corner: (T, 3, ...) values of each triangle corner -> per-vertex sums
+        flat = per_corner.reshape(-1, *per_corner.shape[2:])
+        flat = self.torch.cat([flat, self.torch.zeros_like(flat[:1])])
+        return flat[self.f_slot].sum(dim=1)
+
+    def _flow(self, x):
+        torch = self.torch
+        fl = self.sc.flow
+        t = self.f_tris
+        p = [x[t[:, k]] for k in range(3)]
+        fn = torch.linalg.cross(p[1] - p[0], p[2] - p[0])
+        nv = self._gather(torch.stack([fn, fn, fn], 1))
+        L = torch.linalg.norm(nv, dim=1, keepdim=True)
+        y = x + (fl["sign"] * fl["beta"]) * (nv / torch.where(L > 0, L, torch.ones_like(L)))
+        for _ in range(fl["iters"]):
+            p = [y[t[:, k]] for k in range(3)]
+            area2 = torch.linalg.norm(torch.linalg.cross(p[1] - p[0], p[2] - p[0]), dim=1)
+            safe2 = torch.where(area2 > 0, area2, torch.ones_like(area2))
+            dots = [((p[(k + 1) % 3] - p[k]) * (p[(k + 2) % 3] - p[k])).sum(1) for k in range(3)]
+            cot = [d / safe2 for d in dots]
+            obtuse = (dots[0] < 0) | (dots[1] < 0) | (dots[2] < 0)
+            lap = [torch.zeros_like(p[0]) for _ in range(3)]
+            area = []
+            for k in range(3):
+                q, s_ = p[(k + 1) % 3], p[(k + 2) % 3]
+                lap[(k + 1) % 3] = lap[(k + 1) % 3] + 0.5 * cot[k][:, None] * (s_ - q)
+                lap[(k + 2) % 3] = lap[(k + 2) % 3] + 0.5 * cot[k][:, None] * (q - s_)
+                e_q = ((q - p[k]) ** 2).sum(1)
+                e_s = ((s_ - p[k]) ** 2).sum(1)
+                vor = (e_q * cot[(k + 2) % 3] + e_s * cot[(k + 1) % 3]) / 8.0
+                area.append(torch.where(~obtuse, vor, torch.where(dots[k] < 0, area2 / 4.0, area2 / 8.0)))
+            Lv = self._gather(torch.stack(lap, 1))
+            Av = self._gather(torch.stack(area, 1))
+            y = y + fl["alpha"] * (Lv / torch.where(Av > 0, Av, torch.ones_like(Av))[:, None])
+        return y
+
     def predict(self, x, v):
         torch = self.torch
         sc = self.sc
+        if sc.flow is not None:
+            return self._flow(x)
         xt = x + sc.dt * v
         xt = torch.where(self.fixed[:, None], x + sc.dt * self.kin_v, xt)
         if self.relax:
