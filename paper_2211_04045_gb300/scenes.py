@@ -9,6 +9,11 @@ synthetic stand-in shaped like the paper's examples: cloth over a sphere, two
 stacked cloth layers, a pile of volumetric bodies, two interleaved tubes that
 tighten like a knot, and hair strands with sand grains in a bowl.
 
+Frictional contact follows the paper's velocity filter (Sec. 6.3): a
+pre-pass that turns each vertex-triangle contact's estimated penetration of
+the frictionless target into a normal correction and a Coulomb-bounded
+tangential one, before the collision-handling step.
+
 A second workload is the globally injective normal flow of Sec. 7.4: the
 target of each step is the surface pushed along its vertex normals and then
 smoothed by three Jacobi steps of the cotangent Laplacian (Eq. normal flow);
@@ -48,6 +53,8 @@ class Scene:
     steps: int = 30
     params: dict = dataclasses.field(default_factory=dict)
     flow: Optional[dict] = None             # normal-flow target instead of the dynamics (beta, alpha, sign, iters)
+    kin_rot: Optional[tuple] = None         # (angular velocity (3,), centre (3,)): kinematic vertices rotate
+    friction: Optional[dict] = None         # velocity filter on the target (mu, reach, sep)
 
     @property
     def n_verts(self) -> int:
@@ -448,6 +455,145 @@ def normal_flow_torus(n_major: int = 512, n_minor: int = 96, R: float = 0.1, r: 
                  steps=steps, params=dict(max_iters=2048), flow=flow)
 
 
+# --------------------------------------------------------------------------
+# friction by velocity filtering (Sec. 6.3, after Bridson et al. 2002)
+# --------------------------------------------------------------------------
+def rotate(p: np.ndarray, rotvec: np.ndarray, centre) -> np.ndarray:
+    """Rodrigues rotation of the rows of p by the rotation vector rotvec
+    about an axis through centre."""
+    c = np.asarray(centre, dtype=np.float64)
+    th = float(np.linalg.norm(rotvec))
+    if th == 0.0:
+        return p.copy()
+    k = np.asarray(rotvec, dtype=np.float64) / th
+    q = p - c
+    kq = np.cross(k, q)
+    return c + q * math.cos(th) + kq * math.sin(th) + np.outer(q @ k, k) * (1.0 - math.cos(th))
+
+
+def closest_on_triangle(p, a, b, c):
+    """Closest points of the triangles (a, b, c) to the points p (one per
+    row) as barycentric weights, by the Voronoi regions of the triangle:
+    the three corners, the three edges, else the interior (Ericson,
+    Real-Time Collision Detection, Sec. 5.1.5)."""
+    ab, ac = b - a, c - a
+    dot = lambda u, w: np.einsum("ij,ij->i", u, w)  # noqa: E731
+    ap, bp, cp = p - a, p - b, p - c
+    d1, d2 = dot(ab, ap), dot(ac, ap)
+    d3, d4 = dot(ab, bp), dot(ac, bp)
+    d5, d6 = dot(ab, cp), dot(ac, cp)
+    va, vb, vc = d3 * d6 - d5 * d4, d5 * d2 - d1 * d6, d1 * d4 - d3 * d2
+    n = len(p)
+    w = np.zeros((n, 3))
+    done = np.zeros(n, bool)
+
+    def put(mask, w0, w1, w2):
+        m = mask & ~done
+        w[m, 0], w[m, 1], w[m, 2] = w0[m], w1[m], w2[m]
+        done[m] = True
+
+    one, zero = np.ones(n), np.zeros(n)
+    put((d1 <= 0) & (d2 <= 0), one, zero, zero)
+    put((d3 >= 0) & (d4 <= d3), zero, one, zero)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = d1 / (d1 - d3)
+        put((vc <= 0) & (d1 >= 0) & (d3 <= 0), 1 - t, t, zero)
+        put((d6 >= 0) & (d5 <= d6), zero, zero, one)
+        t = d2 / (d2 - d6)
+        put((vb <= 0) & (d2 >= 0) & (d6 <= 0), 1 - t, zero, t)
+        t = (d4 - d3) / ((d4 - d3) + (d5 - d6))
+        put((va <= 0) & (d4 - d3 >= 0) & (d5 - d6 >= 0), zero, 1 - t, t)
+        den = va + vb + vc
+        v_, w_ = vb / den, vc / den
+        put(np.ones(n, bool), 1 - v_ - w_, v_, w_)
+    return w
+
+
+def friction_filter(x: np.ndarray, y: np.ndarray, inv_mass: np.ndarray, tris: np.ndarray, mu: float,
+                    reach: float, sep: float) -> np.ndarray:
+    """Velocity filter of Sec. 6.3 on the frictionless target y.
+
+    Every vertex-triangle pair closer than `reach` at x (any vertex; the triangle not
+    containing the vertex, not all four vertices fixed) is a contact with
+    normal n from the triangle's closest point to the vertex.  Its relative
+    displacement u = (y_p - x_p) - sum_i w_i (y_i - x_i) would leave it at
+    separation d + n.u; the penetration depth pen = sep - (d + n.u) > 0 is
+    the collision impulse (as a displacement along n), and Coulomb's law
+    bounds the friction impulse, which opposes the tangential part u_t, by
+    mu pen.  The pair's relative correction pen n - min(mu pen, |u_t|)
+    u_t/|u_t| is shared by inverse mass (vertex m_p^-1 / W, triangle vertex i
+    -w_i m_i^-1 / W, W = m_p^-1 + sum w_i^2 m_i^-1), which keeps the momentum
+    sum m Delta at zero.  A vertex in several contacts takes the mean of its
+    corrections (a Jacobi pass, independent of the pair order)."""
+    from scipy.spatial import cKDTree
+    tris = np.asarray(tris, np.int64)
+    n = len(x)
+    if len(tris) == 0:
+        return y.copy()
+    a, b, c = x[tris[:, 0]], x[tris[:, 1]], x[tris[:, 2]]
+    cen = (a + b + c) / 3.0
+    rad = np.max(np.stack([np.linalg.norm(q - cen, axis=1) for q in (a, b, c)], 1), axis=1)
+    verts = np.arange(n)
+    lists = cKDTree(cen).query_ball_point(x[verts], reach + float(rad.max()))
+    pv = np.repeat(verts, [len(l) for l in lists])
+    pt = np.fromiter((t for l in lists for t in l), np.int64, count=len(pv))
+    if len(pv) == 0:
+        return y.copy()
+    tv = tris[pt]
+    keep = (tv != pv[:, None]).all(1)
+    keep &= (inv_mass[pv] > 0) | (inv_mass[tv] > 0).any(1)
+    pv, tv = pv[keep], tv[keep]
+    P, A, B, C = x[pv], x[tv[:, 0]], x[tv[:, 1]], x[tv[:, 2]]
+    w = closest_on_triangle(P, A, B, C)
+    q = w[:, :1] * A + w[:, 1:2] * B + w[:, 2:] * C
+    d = np.linalg.norm(P - q, axis=1)
+    near = (d < reach) & (d > 0)
+    pv, tv, w, d, P, q = pv[near], tv[near], w[near], d[near], P[near], q[near]
+    nrm = (P - q) / d[:, None]
+    dy = y - x
+    u = dy[pv] - np.einsum("ij,ijk->ik", w, dy[tv])
+    un = np.einsum("ij,ij->i", u, nrm)
+    pen = sep - (d + un)
+    W = inv_mass[pv] + np.einsum("ij,ij->i", w * w, inv_mass[tv])
+    act = (pen > 0) & (W > 0)
+    pv, tv, w, nrm, u, un, pen, W = pv[act], tv[act], w[act], nrm[act], u[act], un[act], pen[act], W[act]
+    ut = u - un[:, None] * nrm
+    lt = np.linalg.norm(ut, axis=1)
+    f = np.minimum(mu * pen, lt)
+    du = pen[:, None] * nrm - (f / np.where(lt > 0, lt, 1.0))[:, None] * ut
+    corr = np.zeros_like(y)
+    cnt = np.zeros(n)
+    np.add.at(corr, pv, (inv_mass[pv] / W)[:, None] * du)
+    np.add.at(cnt, pv, inv_mass[pv] > 0)
+    for k in range(3):
+        vi = tv[:, k]
+        np.add.at(corr, vi, -(w[:, k] * inv_mass[vi] / W)[:, None] * du)
+        np.add.at(cnt, vi, (inv_mass[vi] > 0) & (w[:, k] != 0))
+    return y + corr / np.maximum(cnt, 1.0)[:, None]
+
+
+def cloth_on_rotating_sphere(n: int = 32, side: float = 1.0, sphere_subdiv: int = 3, sphere_r: float = 0.3,
+                             gap: float = 0.002, omega: float = 2.0, mu: float = 0.5, dt: float = 1.0 / 30,
+                             steps: int = 30) -> Scene:
+    """The rotating-sphere example of Sec. 6.3: a cloth resting on a sphere
+    that spins about the vertical axis; the velocity filter makes the sphere
+    drag the cloth (without it the cloth slides)."""
+    xc, tc = grid_cloth(n, side, sphere_r + gap)
+    xs, ts = icosphere(sphere_subdiv, sphere_r)
+    nc = len(xc)
+    x = np.concatenate([xc, xs], 0)
+    tris = np.concatenate([tc, ts + nc], 0).astype(np.int32)
+    edges = unique_edges(tris)
+    len_edges = unique_edges(tc)
+    m = lumped_tri_mass(xc, tc, nc)
+    inv_mass = np.concatenate([1.0 / m, np.zeros(len(xs))])
+    return Scene(f"cloth{n}_rotating_sphere{sphere_subdiv}", inv_mass, tris, edges, len_edges,
+                 np.zeros(0, np.int32), x, np.zeros_like(x), dt, np.array([0.0, -9.8, 0.0]),
+                 rest_len=_rest(x, len_edges), steps=steps, params=dict(max_iters=2048),
+                 kin_rot=(np.array([0.0, omega, 0.0]), np.zeros(3)),
+                 friction=dict(mu=mu, reach=2e-3, sep=1e-3) if mu > 0 else None)
+
+
 def predict(scene: Scene, x: np.ndarray, v: np.ndarray) -> np.ndarray:
     """x~ = x + dt v, kinematic vertices on their script, then Jacobi
     sweeps toward rest edge lengths (inverse-mass weighted).  A normal-flow
@@ -459,6 +605,9 @@ def predict(scene: Scene, x: np.ndarray, v: np.ndarray) -> np.ndarray:
     fixed = im == 0.0
     if scene.kin_v is not None:
         xt[fixed] = x[fixed] + scene.dt * scene.kin_v[fixed]
+    if scene.kin_rot is not None:
+        w, c = scene.kin_rot
+        xt[fixed] = rotate(x[fixed], np.asarray(w) * scene.dt, c)
     le = scene.len_edges
     if scene.relax_sweeps and len(le) and scene.rest_len is not None:
         n = len(x)
@@ -478,6 +627,8 @@ def predict(scene: Scene, x: np.ndarray, v: np.ndarray) -> np.ndarray:
                 dx[:, k] -= np.bincount(i, weights=wi * corr[:, k], minlength=n)
                 dx[:, k] += np.bincount(j, weights=wj * corr[:, k], minlength=n)
             xt += dx / deg[:, None]
+    if scene.friction is not None:
+        xt = friction_filter(x, xt, im, scene.tris, **scene.friction)
     return xt
 
 
@@ -506,6 +657,7 @@ def by_name(name: str, **kw) -> Scene:
         "knot": tube_knot,
         "hair_sand": hair_sand,
         "normal_flow": normal_flow_torus,
+        "rotating_sphere": cloth_on_rotating_sphere,
     }
     return table[name](**kw)
 
@@ -618,6 +770,8 @@ class TorchDynamics:
         sc = self.sc
         if sc.flow is not None:
             return self._flow(x)
+        if sc.friction is not None or sc.kin_rot is not None:
+            raise NotImplementedError("the friction filter and kinematic rotation run in scenes.predict (numpy)")
         xt = x + sc.dt * v
         xt = torch.where(self.fixed[:, None], x + sc.dt * self.kin_v, xt)
         if self.relax:
