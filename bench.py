@@ -46,7 +46,7 @@ def workload(name: str):
     if name == "knot":
         return scenes.tube_knot(), "knot2x64x561"
     if name == "normal_flow":
-        return scenes.normal_flow_torus(), "normal_flow_torus512x96"
+        return scenes.normal_flow_torus(), "normal_flow_torus384x64"
     raise SystemExit(f"unknown config {name}")
 
 

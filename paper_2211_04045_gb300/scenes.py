@@ -438,7 +438,7 @@ def normal_flow_target(x: np.ndarray, tris: np.ndarray, beta: float, alpha: floa
     return y
 
 
-def normal_flow_torus(n_major: int = 512, n_minor: int = 96, R: float = 0.1, r: float = 0.008,
+def normal_flow_torus(n_major: int = 384, n_minor: int = 64, R: float = 0.1, r: float = 0.012,
                       beta: float = 2e-3, alpha_frac: float = 0.1, sign: float = -1.0, steps: int = 8) -> Scene:
     """A closed torus under the normal flow of Sec. 7.4 (the paper's meshes
     are not available).  sign = -1 shrinks the tube until its opposite sides
