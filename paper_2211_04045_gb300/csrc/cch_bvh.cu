@@ -1,6 +1,6 @@
 // cch_bvh.cu -- proximity search of Sec. 3.1 on sm_103a.
 //
-// The paper's search is a grid spatial hash; this build uses a linear BVH
+// The paper's search is a grid spatial hash; this implementation uses a linear BVH
 // built from a radix sort of Morton codes (Karras 2012), one tree per
 // primitive class (triangles, collision edges, collision vertices) over the
 // whole pool.  The scene index sits above the Morton bits of every key, so
