@@ -87,6 +87,23 @@ def test_ee_parallel_gap_form():
     assert np.isclose(g[2, 2] + g[3, 2], -1.0 / delta)
 
 
+@pytest.mark.parametrize("sin_theta,gap_form", [(1e-7, True), (1e-5, False)])
+def test_ee_near_parallel_threshold(sin_theta, gap_form):
+    # R7: edges with sin(theta) below 1e-6 take the gap form, gradient
+    # (1-s, s, -(1-t), -t) n / delta; above it the volume form, whose gradient
+    # over the tiny reference volume of near-parallel edges is far larger.
+    # Both give c = d/delta - 1 here (the edges lie in parallel planes).
+    delta, d = 1e-3, 0.5e-3
+    p = np.array([[0.0, 0, d], [1e-2, 0, d], [0.2e-2, 0, 0], [0.8e-2, 0.6e-2 * sin_theta, 0]])
+    ok, c0, g = oracle.contact_constraint(oracle.EE, p, [0.0, 0.0], delta)
+    dist, s, t = oracle.segment_segment_dist(*p)
+    assert ok and abs(c0 - (dist / delta - 1.0)) < 1e-12
+    gap_g = np.outer([1.0 - s, s, -(1.0 - t), -t], [0.0, 0.0, 1.0]) / delta
+    assert np.array_equal(g, gap_g) == gap_form
+    if not gap_form:
+        assert np.abs(g).max() > 1e3 / delta
+
+
 @pytest.mark.parametrize("radius", [0.0, 2e-3])
 def test_p7_vertex_vertex_separation(radius):
     delta = 1e-3

@@ -80,3 +80,14 @@ def test_edges_and_points():
     xp = np.array([[0.0, 0, 0], [3e-3, 0, 0], [1e-2, 0, 0]])
     r = np.array([2e-3, 2e-3, 2e-3])
     assert oracle.count_intersections(oracle.OracleScene(mesh(xp, points=[0, 1, 2], radius=r)), xp) == 1
+
+
+def test_boundary_contacts_count():
+    # a zero-radius point exactly on a triangle's edge, and collinear edges
+    # that touch at one end point (distinct vertex indices), are intersections
+    tri = np.array([[0.0, 0, 0], [1.0, 0, 0], [0, 1.0, 0], [0.5, 0.0, 0.0]])
+    assert oracle.count_intersections(oracle.OracleScene(mesh(tri, tris=[[0, 1, 2]], points=[3])), tri) == 1
+    x = np.array([[0.0, 0, 0], [1.0, 0, 0], [1.0, 0, 0], [2.0, 0, 0]])
+    assert oracle.count_intersections(oracle.OracleScene(mesh(x, edges=[[0, 1], [2, 3]])), x) == 1
+    x[2, 0] = np.nextafter(1.0, 2.0)
+    assert oracle.count_intersections(oracle.OracleScene(mesh(x, edges=[[0, 1], [2, 3]])), x) == 0

@@ -100,6 +100,23 @@ def test_boundary_gap_exactly_D():
         assert np.array_equal(numpy_candidates(sc, x, x, D), oracle.candidates(osc, x, D, mode=0))
 
 
+def test_window_keeps_a_gap_that_rounds_to_D():
+    # the computed gap fl(lo_b - hi_a) of these operands rounds to D while the
+    # window end fl(hi_a + D) lies below lo_b: the sorted-axis window must
+    # widen by its slack to keep the pair that the box test (R3) accepts
+    D = 4e-3
+    ah, bl = -0.0025478467492858173, 0.001452153250714183
+    assert bl - ah == D and bl > ah + D
+    x = np.array([[ah, 1e-3, 1e-3], [bl, 0.0, 0.0], [bl + 0.01, 0.0, 2e-3], [bl + 0.005, 2e-3, 0.0]])
+    sc = NS(n_verts=4, inv_mass=np.ones(4), radius=None, tris=np.array([[1, 2, 3]], np.int32),
+            edges=np.zeros((0, 2), np.int32), len_edges=np.zeros((0, 2), np.int32), points=np.array([0], np.int32))
+    osc = oracle.OracleScene(sc)
+    k0 = oracle.candidates(osc, x, D, mode=0)
+    assert (0 << 62) | (0 << 31) | 0 in [int(q) for q in k0]
+    assert np.array_equal(oracle.candidates(osc, x, D, mode=1), k0)
+    assert np.array_equal(numpy_candidates(sc, x, x, D), k0)
+
+
 def test_window_equals_brute_on_scene():
     sc = scenes.two_cloths(n=20, side=0.2, sep=0.003, omega=6.0, noise=0.3, seed=3)
     x0, xt, _ = scenes.initial(sc)

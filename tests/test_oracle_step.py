@@ -76,6 +76,23 @@ def test_p4b_non_finite_target_does_not_move(solver, bad):
     assert st["converged"] == 0 and st["iterations"] == prm.max_iters + 1
 
 
+def test_r2b_vertex_closer_than_the_floor_does_not_move():
+    # R2b: a vertex 5e-11 m above a fixed triangle (below the 1e-10 floor)
+    # keeps its position, although its target slides 1 mm along the plane
+    from types import SimpleNamespace as NS
+    x = np.array([[-0.1, -0.1, 0.0], [0.1, -0.1, 0.0], [0.0, 0.1, 0.0], [0.0, 0.0, 5e-11]])
+    sc = NS(n_verts=4, inv_mass=np.array([0.0, 0.0, 0.0, 1.0]), radius=None, tris=np.array([[0, 1, 2]], np.int32),
+            edges=np.zeros((0, 2), np.int32), len_edges=np.zeros((0, 2), np.int32), points=np.array([3], np.int32))
+    xt = x.copy()
+    xt[3, 0] += 1e-3
+    xn, st, _ = oracle.handle_step(oracle.OracleScene(sc), oracle.params(max_iters=0), x, xt)
+    assert np.array_equal(xn, x) and st["final_r_inf"] == 1.0
+    # at 2e-10 (above the floor) it moves
+    x[3, 2] = xt[3, 2] = 2e-10
+    xn, st, _ = oracle.handle_step(oracle.OracleScene(sc), oracle.params(max_iters=0), x, xt)
+    assert xn[3, 0] > 0.0
+
+
 def colliding_cases():
     return [
         ("cloth_sphere", scenes.cloth_over_sphere(n=8, side=0.4, sphere_subdiv=1, sphere_r=0.12, noise=0.3, seed=5)),
