@@ -56,7 +56,8 @@ class Stats(C.Structure):
                 ("ccd_clamps", C.c_int32), ("pairs_evaluated", C.c_int64), ("max_pairs", C.c_int64),
                 ("active_contacts", C.c_int64), ("candidates", C.c_int64), ("degenerate", C.c_int64),
                 ("max_vertex_contacts", C.c_int32), ("max_vertex_edges", C.c_int32), ("final_r_inf", C.c_double),
-                ("min_pair_dist", C.c_double)]
+                ("min_pair_dist", C.c_double), ("frozen_vertices", C.c_int32), ("contact_colours", C.c_int32),
+                ("contact_vertices", C.c_int64), ("edge_colours", C.c_int32), ("reserved_", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +96,12 @@ def lib():
             L.orc_contact_constraint.argtypes = [C.c_int, p, p, d, C.c_int, p, p]
             L.orc_backward_once.restype = C.c_int
             L.orc_backward_once.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, p, p, p]
+            L.orc_greedy_colouring.restype = i32
+            L.orc_greedy_colouring.argtypes = [i64, p, p, p, i64, p]
+            L.orc_contact_colours.restype = i64
+            L.orc_contact_colours.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, p, p, p, i64]
+            L.orc_edge_colours.restype = i32
+            L.orc_edge_colours.argtypes = [C.POINTER(Topology), C.POINTER(Params), p]
             L.orc_ccd.restype = C.c_int
             L.orc_ccd.argtypes = [C.c_int, p, p, p, p]
             L.orc_count_intersections.restype = i64
@@ -201,6 +208,37 @@ def backward_once(osc: OracleScene, prm: Params, x, y_in, y_target):
     out = np.empty_like(x)
     lib().orc_backward_once(C.byref(osc.topo), C.byref(prm), _ptr(x), _ptr(y_in), _ptr(y_target), _ptr(out))
     return out
+
+
+def greedy_colouring(verts, prio, inv_mass):
+    """Greedy colouring (Sec. 4.3, R11) of constraints with vertex lists
+    verts (m x 4, -1 = absent) and priorities prio.  Returns (colours, count)."""
+    verts = np.ascontiguousarray(verts, dtype=np.int32).reshape(-1, 4)
+    prio = np.ascontiguousarray(prio, dtype=np.uint64).reshape(-1)
+    im = _f64(inv_mass)
+    col = np.zeros(max(len(prio), 1), np.int32)
+    k = lib().orc_greedy_colouring(len(prio), _ptr(verts), _ptr(prio), _ptr(im), len(im), _ptr(col))
+    return col[:len(prio)], int(k)
+
+
+def contact_colours(osc: OracleScene, prm: Params, x, x_tilde=None):
+    """Keys (ascending) and colours of the contact constraints a backward step
+    at x builds from a search at D^max."""
+    x = _f64(x).reshape(-1, 3)
+    xt = x if x_tilde is None else _f64(x_tilde).reshape(-1, 3)
+    L = lib()
+    n = L.orc_contact_colours(C.byref(osc.topo), C.byref(prm), _ptr(x), _ptr(xt), None, None, 0)
+    keys = np.zeros(max(n, 1), np.uint64)
+    col = np.zeros(max(n, 1), np.int32)
+    L.orc_contact_colours(C.byref(osc.topo), C.byref(prm), _ptr(x), _ptr(xt), _ptr(keys), _ptr(col), n)
+    return keys[:n], col[:n]
+
+
+def edge_colours(osc: OracleScene, prm: Params):
+    """Colours of the edge-length constraints, in the topology's edge order."""
+    col = np.zeros(max(len(osc.len_edges), 1), np.int32)
+    k = lib().orc_edge_colours(C.byref(osc.topo), C.byref(prm), _ptr(col))
+    return col[:len(osc.len_edges)], int(k)
 
 
 def count_intersections(osc: OracleScene, x) -> int:

@@ -755,21 +755,78 @@ typedef struct {
   v3 g[4];        /* dc/dx_v ; edges: g[0] = u/L0                              */
   double den;     /* sum_v m_v^-1 |g_v|^2                                       */
   uint64_t key;   /* canonical identity                                          */
-  uint64_t prio;  /* sweep priority (R11)                                        */
+  uint64_t prio;  /* colouring priority (R11)                                    */
+  int32_t colour; /* colour class of the Gauss-Seidel sweep (Sec. 4.3)          */
   double lambda;
 } cons;
 
 /* Order of the projected Gauss-Seidel sweep (Sec. 4.3, reading R11).  The
- * paper sweeps colour classes of a randomized colouring; what the colouring
- * fixes is the order in which constraints sharing a vertex are applied, and
- * that order is random.  Here it is a random priority order: priorities
- * splitmix64(seed ^ key) (a bijection of the unique keys, so no ties) and the
- * sweep visits constraints by descending priority.  A parallel sweep that
- * applies a constraint once every higher-priority constraint at each of its
- * movable vertices has been applied gives exactly this sequential result. */
+ * paper's sweep is multi-colour Gauss-Seidel: the constraints are split into
+ * colour classes in which no two share a vertex, by a randomized colouring,
+ * and the classes are applied one after the other, the constraints of one
+ * class in parallel.  Here the randomness is a priority per constraint,
+ * splitmix64(seed ^ key) (a bijection of the unique keys, so no ties), and
+ * the colouring is the greedy one in descending priority: each constraint
+ * takes the smallest colour not used by a higher-priority constraint that
+ * shares a movable vertex with it (static vertices never change y, so they
+ * create no conflict).  Contacts are coloured among themselves every
+ * iteration, edge-length constraints among themselves.  The sequential sweep
+ * applies the contact classes in ascending colour, then the edge classes;
+ * inside a class the order does not change the result (no shared movable
+ * vertex), and it is taken by descending priority. */
 static int cmp_cons_prio_desc(const void* a, const void* b) {
   uint64_t pa = ((const cons*)a)->prio, pb = ((const cons*)b)->prio;
   return pa > pb ? -1 : pa < pb;
+}
+static int cmp_cons_colour(const void* a, const void* b) {
+  const cons *ca = (const cons*)a, *cb = (const cons*)b;
+  if (ca->colour != cb->colour) return ca->colour < cb->colour ? -1 : 1;
+  return cmp_cons_prio_desc(a, b);
+}
+
+/* colours used so far at one vertex */
+typedef struct { int32_t* c; int32_t n, cap; } ilist;
+static void il_push(ilist* l, int32_t v) {
+  if (l->n == l->cap) {
+    l->cap = l->cap ? 2 * l->cap : 8;
+    l->c = (int32_t*)realloc(l->c, sizeof(int32_t) * (size_t)l->cap);
+  }
+  l->c[l->n++] = v;
+}
+
+/* Greedy colouring of cs[0..n), which the caller has sorted by descending
+ * priority: each constraint takes the smallest colour that no earlier one
+ * sharing a movable vertex with it has.  Returns the number of colours;
+ * *verts receives the number of distinct movable vertices of the set. */
+static int32_t colour_greedy(cons* cs, int64_t n, const uint8_t* movable, int64_t nverts, int64_t* verts) {
+  ilist* used = (ilist*)calloc((size_t)nverts + 1, sizeof(ilist));
+  int32_t ncol = 0;
+  int64_t nv_used = 0;
+  for (int64_t i = 0; i < n; i++) {
+    int32_t mv[4], nm = 0, tot = 0;
+    for (int k = 0; k < cs[i].nv; k++)
+      if (movable[cs[i].v[k]]) mv[nm++] = cs[i].v[k];
+    for (int k = 0; k < nm; k++) tot += used[mv[k]].n;
+    /* colours of the earlier constraints at these vertices (at most tot of
+     * them, so the smallest free colour is at most tot) */
+    uint8_t* taken = (uint8_t*)calloc((size_t)tot + 1, 1);
+    for (int k = 0; k < nm; k++)
+      for (int32_t j = 0; j < used[mv[k]].n; j++)
+        if (used[mv[k]].c[j] <= tot) taken[used[mv[k]].c[j]] = 1;
+    int32_t col = 0;
+    while (taken[col]) col++;
+    free(taken);
+    cs[i].colour = col;
+    if (col + 1 > ncol) ncol = col + 1;
+    for (int k = 0; k < nm; k++) {
+      if (used[mv[k]].n == 0) nv_used++;
+      il_push(&used[mv[k]], col);
+    }
+  }
+  for (int64_t v = 0; v < nverts; v++) free(used[v].c);
+  free(used);
+  if (verts) *verts = nv_used;
+  return ncol;
 }
 
 /* Largest number of constraints at one movable vertex (statistics). */
@@ -888,9 +945,10 @@ static void jacobi_sweep(cons* cc, int64_t nc, cons* ce, int64_t ne, double sigm
 
 /* Edge-length constraints for the step (R9): every listed edge, u and L0
  * from the target y^[k+1]; an edge with L0 = 0 gets a zero denominator and
- * is skipped by the sweep.  Sweep order: descending priority (R11). */
+ * is skipped by the sweep.  Sweep order: ascending colour of the greedy
+ * colouring of the edges (R11). */
 static int64_t build_edges(const orc_topology* t, const orc_params* prm, const double* ytgt, const uint8_t* movable,
-                           cons** out, int32_t* ncol) {
+                           cons** out, int32_t* ncol, int32_t* ncolours) {
   cons* ce = (cons*)calloc((size_t)t->n_len + 1, sizeof(cons));
   int64_t ne = t->n_len;
   for (int64_t e = 0; e < ne; e++) {
@@ -912,13 +970,16 @@ static int64_t build_edges(const orc_topology* t, const orc_params* prm, const d
   }
   *ncol = max_vertex_degree(ce, ne, movable, t->n_verts);
   qsort(ce, (size_t)ne, sizeof(cons), cmp_cons_prio_desc);
+  *ncolours = colour_greedy(ce, ne, movable, t->n_verts, 0);
+  qsort(ce, (size_t)ne, sizeof(cons), cmp_cons_colour);
   *out = ce;
   return ne;
 }
 
 /* Contact constraints from the active pairs of P (dist < delta) at x^(l). */
 static int64_t build_contacts(const orc_topology* t, const orc_params* prm, const pairset* P, const double* x,
-                              const uint8_t* movable, cons** out, int32_t* ncol, int64_t* degenerate) {
+                              const uint8_t* movable, cons** out, int32_t* ncol, int64_t* degenerate,
+                              int32_t* ncolours, int64_t* nverts_used) {
   cons* cc = (cons*)calloc((size_t)P->n + 1, sizeof(cons));
   int64_t nc = 0;
   for (int64_t i = 0; i < P->n; i++) {
@@ -946,13 +1007,16 @@ static int64_t build_contacts(const orc_topology* t, const orc_params* prm, cons
   }
   *ncol = max_vertex_degree(cc, nc, movable, t->n_verts);
   qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_prio_desc);
+  *ncolours = colour_greedy(cc, nc, movable, t->n_verts, nverts_used);
+  qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_colour);
   *out = cc;
   return nc;
 }
 
 /* Backward step (Sec. 4): y^(l+1) from y^(l) by gs_sweeps projected
- * Gauss-Seidel sweeps, contacts then edges (R10), each by descending priority
- * (R11), each backward step starting its multipliers at zero. */
+ * Gauss-Seidel sweeps, contacts then edges (R10), each in ascending colour
+ * (R11; cc and ce arrive in that order), each backward step starting its
+ * multipliers at zero. */
 static void backward(const orc_topology* t, const orc_params* prm, cons* cc, int64_t nc, cons* ce, int64_t ne,
                      const double* x, double* y) {
   for (int64_t i = 0; i < nc; i++) cc[i].lambda = 0.0;
@@ -981,6 +1045,58 @@ static void backward(const orc_topology* t, const orc_params* prm, cons* cc, int
   }
 }
 
+int32_t orc_greedy_colouring(int64_t n, const int32_t* verts, const uint64_t* prio, const double* inv_mass,
+                             int64_t n_verts, int32_t* colour) {
+  cons* cs = (cons*)calloc((size_t)n + 1, sizeof(cons));
+  uint8_t* movable = (uint8_t*)malloc((size_t)n_verts + 1);
+  for (int64_t v = 0; v < n_verts; v++) movable[v] = inv_mass[v] > 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    int nv = 0;
+    for (int k = 0; k < 4; k++)
+      if (verts[4 * i + k] >= 0) cs[i].v[nv++] = verts[4 * i + k];
+    cs[i].nv = nv;
+    cs[i].prio = prio[i];
+    cs[i].key = (uint64_t)i; /* remembers the input position */
+  }
+  qsort(cs, (size_t)n, sizeof(cons), cmp_cons_prio_desc);
+  int32_t ncol = colour_greedy(cs, n, movable, n_verts, 0);
+  for (int64_t i = 0; i < n; i++) colour[cs[i].key] = cs[i].colour;
+  free(cs); free(movable);
+  return ncol;
+}
+
+int64_t orc_contact_colours(const orc_topology* t, const orc_params* prm, const double* x, const double* x_tilde,
+                            uint64_t* keys, int32_t* colour, int64_t cap) {
+  scene s; scene_init(&s, t, x, x_tilde);
+  uint8_t* movable = (uint8_t*)malloc((size_t)t->n_verts + 1);
+  for (int64_t v = 0; v < t->n_verts; v++) movable[v] = t->inv_mass[v] > 0.0;
+  pairset P = {0, 0, 0, 0};
+  proximity_search(&s, x, prm->d_max, prm->search_mode, &P);
+  cons* cc;
+  int32_t ncc, colc;
+  int64_t degen = 0, nvu = 0;
+  int64_t nc = build_contacts(t, prm, &P, x, movable, &cc, &ncc, &degen, &colc, &nvu);
+  qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_key);
+  for (int64_t i = 0; i < nc && i < cap; i++) {
+    keys[i] = cc[i].key;
+    colour[i] = cc[i].colour;
+  }
+  free(cc); free(P.k); free(P.d); free(movable); scene_free(&s);
+  return nc;
+}
+
+int32_t orc_edge_colours(const orc_topology* t, const orc_params* prm, int32_t* colour) {
+  uint8_t* movable = (uint8_t*)malloc((size_t)t->n_verts + 1);
+  for (int64_t v = 0; v < t->n_verts; v++) movable[v] = t->inv_mass[v] > 0.0;
+  double* z = (double*)calloc(3 * (size_t)t->n_verts + 3, sizeof(double));
+  cons* ce;
+  int32_t nce, cole;
+  int64_t ne = build_edges(t, prm, z, movable, &ce, &nce, &cole);
+  for (int64_t i = 0; i < ne; i++) colour[ce[i].key & 0x3fffffffffffffffULL] = ce[i].colour;
+  free(ce); free(z); free(movable);
+  return cole;
+}
+
 int orc_backward_once(const orc_topology* t, const orc_params* prm, const double* x, const double* y_in,
                       const double* y_target, double* y_out) {
   scene s; scene_init(&s, t, x, y_target);
@@ -989,10 +1105,10 @@ int orc_backward_once(const orc_topology* t, const orc_params* prm, const double
   pairset P = {0, 0, 0, 0};
   proximity_search(&s, x, prm->d_max, prm->search_mode, &P);
   cons *cc, *ce;
-  int32_t ncc, nce;
-  int64_t degen = 0;
-  int64_t nc = build_contacts(t, prm, &P, x, movable, &cc, &ncc, &degen);
-  int64_t ne = build_edges(t, prm, y_target, movable, &ce, &nce);
+  int32_t ncc, nce, colc, cole;
+  int64_t degen = 0, nvu = 0;
+  int64_t nc = build_contacts(t, prm, &P, x, movable, &cc, &ncc, &degen, &colc, &nvu);
+  int64_t ne = build_edges(t, prm, y_target, movable, &ce, &nce, &cole);
   memcpy(y_out, y_in, sizeof(double) * 3 * (size_t)t->n_verts);
   backward(t, prm, cc, nc, ce, ne, x, y_out);
   free(cc); free(ce); free(P.k); free(P.d); free(movable); scene_free(&s);
@@ -1190,7 +1306,7 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
   pairset P = {0, 0, 0, 0};
   cons* ce;
   int32_t nce;
-  int64_t ne = build_edges(t, prm, x_tilde, movable, &ce, &nce);
+  int64_t ne = build_edges(t, prm, x_tilde, movable, &ce, &nce, &S.edge_colours);
   S.max_vertex_edges = nce;
   const double hg = 0.5 * prm->gamma;
   if (tr && tr->x) memcpy(tr->x, x, sizeof(double) * 3 * (size_t)n);
@@ -1231,10 +1347,13 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
 
     /* backward step */
     cons* cc;
-    int32_t ncc;
-    int64_t nc = build_contacts(t, prm, &P, x, movable, &cc, &ncc, &S.degenerate);
+    int32_t ncc, colc;
+    int64_t nvu = 0;
+    int64_t nc = build_contacts(t, prm, &P, x, movable, &cc, &ncc, &S.degenerate, &colc, &nvu);
     S.active_contacts += nc;
+    S.contact_vertices += nvu;
     if (ncc > S.max_vertex_contacts) S.max_vertex_contacts = ncc;
+    if (colc > S.contact_colours) S.contact_colours = colc;
     backward(t, prm, cc, nc, ce, ne, x, y);
     free(cc);
 
@@ -1245,13 +1364,16 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
     const int ccd_rule = prm->step_rule == 1;
     double Dcap = D;
     if (!(Dcap >= ORC_D_FLOOR)) Dcap = 0.0;
+    S.frozen_vertices = 0;
     for (int64_t v = 0; v < n; v++) {
       v3 xv = ld3(x, v), yv = ld3(y, v);
       v3 dx = sub3(yv, xv);
       double nd = norm3(dx), a = 1.0;
+      double bound = ccd_rule ? Dcap : Di[v];
       if (nd > 0.0) {
-        double q = (hg * (ccd_rule ? Dcap : Di[v])) / nd;
+        double q = (hg * bound) / nd;
         a = q < 1.0 ? q : 1.0;
+        if (bound == 0.0) S.frozen_vertices++;
       } else if (nd != 0.0) {
         a = 0.0; /* R2c: y not finite, the vertex does not move */
       }

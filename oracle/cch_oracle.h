@@ -69,6 +69,14 @@ typedef struct {
   int32_t max_vertex_edges;    /* most edge-length constraints at one vertex    */
   double final_r_inf;
   double min_pair_dist;      /* min pair distance seen over the whole step    */
+  int32_t frozen_vertices;   /* vertices held by the D_i floor (1e-10 m) at the
+                                last iteration although y_i differs from x_i  */
+  int32_t contact_colours;   /* most colours of one iteration's contact
+                                colouring (Gauss-Seidel, Sec. 4.3)            */
+  int64_t contact_vertices;  /* sum over iterations of the distinct movable
+                                vertices of the contact constraints           */
+  int32_t edge_colours;      /* colours of the edge-length constraints        */
+  int32_t reserved_;
 } orc_stats;
 
 /* Optional per-iteration record (tests only).  Any pointer may be NULL. */
@@ -118,6 +126,21 @@ int orc_contact_constraint(int kind, const double* p, const double* rho, double 
  * sweeps once, starting from y_in.  y_out receives y^(l+1). */
 int orc_backward_once(const orc_topology* t, const orc_params* prm, const double* x,
                       const double* y_in, const double* y_target, double* y_out);
+
+/* ---- colouring of the Gauss-Seidel sweep (Sec. 4.3) ---- */
+/* Greedy colouring of n constraints with vertex lists verts[4*i..4*i+3] (-1
+ * = absent) and priorities prio[i]: taken by descending priority, each gets
+ * the smallest colour not used by an earlier constraint sharing a movable
+ * vertex with it.  colour[i] receives it; returns the number of colours. */
+int32_t orc_greedy_colouring(int64_t n, const int32_t* verts, const uint64_t* prio, const double* inv_mass,
+                             int64_t n_verts, int32_t* colour);
+/* The contact constraints that a backward step at state x builds from a
+ * search at D^max (keys ascending) and the colour of each; returns the count
+ * (up to cap written). */
+int64_t orc_contact_colours(const orc_topology* t, const orc_params* prm, const double* x, const double* x_tilde,
+                            uint64_t* keys, int32_t* colour, int64_t cap);
+/* Colours of the edge-length constraints (in the topology's edge order). */
+int32_t orc_edge_colours(const orc_topology* t, const orc_params* prm, int32_t* colour);
 
 /* ---- CCD (comparison scheme of Sec. 5.1, used as a safety check) ---- */
 /* Vertices 0..3 move linearly from x0 to x1 (VT: a,i,j,k; EE: a,b,c,d; VV:

@@ -56,9 +56,13 @@ M = [
     ("Jacobi lambda advance", "cc[i].lambda = cc[i].lambda + sc[i];", "cc[i].lambda = cc[i].lambda + 2.0 * sc[i];"),
     ("edges before contacts", "    for (int64_t i = 0; i < nc; i++) pgs_contact(&cc[i], x, y, t->inv_mass);\n    for (int64_t i = 0; i < ne; i++) pgs_edge(&ce[i], prm->sigma, y, t->inv_mass);", "    for (int64_t i = 0; i < ne; i++) pgs_edge(&ce[i], prm->sigma, y, t->inv_mass);\n    for (int64_t i = 0; i < nc; i++) pgs_contact(&cc[i], x, y, t->inv_mass);"),
     ("ascending priority", "return pa > pb ? -1 : pa < pb;", "return pa < pb ? -1 : pa > pb;"),
+    ("colour classes swept in descending colour", "if (ca->colour != cb->colour) return ca->colour < cb->colour ? -1 : 1;", "if (ca->colour != cb->colour) return ca->colour > cb->colour ? -1 : 1;"),
+    ("colouring conflicts through static vertices", "      if (movable[cs[i].v[k]]) mv[nm++] = cs[i].v[k];", "      mv[nm++] = cs[i].v[k];"),
+    ("colouring ignores the last vertex's colours", "    for (int k = 0; k < nm; k++)\n      for (int32_t j = 0;", "    for (int k = 0; k + 1 < nm; k++)\n      for (int32_t j = 0;"),
+    ("colouring without classes (priority order only)", "  qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_colour);", "  qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_prio_desc);"),
     ("contact multipliers kept (equivalent: rebuilt at 0)", "  for (int64_t i = 0; i < nc; i++) cc[i].lambda = 0.0;\n", ""),
-    ("forward step uses gamma not gamma/2", "double q = (hg * (ccd_rule ? Dcap : Di[v])) / nd;", "double q = (2.0 * hg * (ccd_rule ? Dcap : Di[v])) / nd;"),
-    ("CCD rule uses D_i", "double q = (hg * (ccd_rule ? Dcap : Di[v])) / nd;", "double q = (hg * (ccd_rule ? Di[v] : Di[v])) / nd;"),
+    ("forward step uses gamma not gamma/2", "double q = (hg * bound) / nd;", "double q = (2.0 * hg * bound) / nd;"),
+    ("CCD rule uses D_i", "double bound = ccd_rule ? Dcap : Di[v];", "double bound = ccd_rule ? Di[v] : Di[v];"),
     ("r update", "r[v] = r[v] * (1.0 - alpha[v]);", "r[v] = r[v] * alpha[v];"),
     ("D update halves the move", "D = nextafter(D - 2.0 * mmax, -INFINITY);", "D = nextafter(D - mmax, -INFINITY);"),
     ("D_i from the first vertex only", "if (P.d[i] < Di[v4[k]]) Di[v4[k]] = P.d[i];", "if (P.d[i] < Di[v4[0]]) Di[v4[0]] = P.d[i];"),

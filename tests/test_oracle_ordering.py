@@ -2,12 +2,18 @@
 R10 and R11).
 
 The priorities come from SplitMix64, pinned to its published sequence.  The
-sweep applies contacts before edge-length constraints (R10) and, within
-each, constraints by descending priority splitmix64(seed ^ key) (R11).  Two
-closed-form cases fix both rules: a chain of two stretched edges, whose
-result depends on which edge goes first, and a point held by a contact and
-an edge that pull it in opposite directions.
+sweep is multi-colour Gauss-Seidel: contacts before edge-length constraints
+(R10), and within each group the colour classes of the greedy colouring in
+descending priority splitmix64(seed ^ key), in ascending colour (R11).  The
+colouring is checked against networkx's greedy colouring (an independent
+implementation of the same definition) on random constraint sets and on the
+contacts of a real scene.  Closed-form cases fix the order: a chain of two
+stretched edges, whose result depends on which edge goes first; a chain of
+three, where the colour order differs from the priority order whenever the
+priorities fall or rise along the chain; and a point held by a contact and an
+edge that pull it in opposite directions.
 """
+import networkx as nx
 from types import SimpleNamespace as NS
 
 import numpy as np
@@ -75,3 +81,125 @@ def test_contacts_before_edges():
     out = oracle.backward_once(oracle.OracleScene(sc), oracle.params(sigma=1.05, delta=1e-3), x, y, x)
     assert abs(out[1, 2] - 0.775 * mm) <= 1e-15
     assert np.array_equal(out[[0, 2]], y[[0, 2]])
+
+
+def chain3(seed):
+    # vertices 0-1-2-3 on a line 1.5 L0 apart, edges e0 (0,1), e1 (1,2),
+    # e2 (2,3) at rest length L0, sigma = 1.1, unit masses.  An edge applied
+    # at stretch s L0 moves both of its ends by (s - 1.1) L0 / 2 toward each
+    # other.
+    L0, u = 0.01, np.array([0.0, 0.6, 0.8])
+    y0 = np.array([0.0, 1.0, 2.0, 3.0])[:, None] * L0 * u
+    y = np.array([0.0, 1.5, 3.0, 4.5])[:, None] * L0 * u
+    sc = mini([1.0] * 4, len_edges=[[0, 1], [1, 2], [2, 3]])
+    out = oracle.backward_once(oracle.OracleScene(sc), oracle.params(seed=seed), y0, y, y0)
+    assert np.max(np.abs(out - np.outer(out @ u, u))) <= 1e-17  # the chain stays on its line
+    return out @ u / L0, [oracle.splitmix64(seed ^ (EDGE_KIND | e)) for e in range(3)]
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_three_edge_chain_swept_by_colour_classes(seed):
+    out, p = chain3(seed)
+    if p[1] > p[0] and p[1] > p[2]:
+        # e1 takes colour 0, e0 and e2 colour 1: e1 first (0.2 each end), then
+        # e0 and e2 each at stretch 1.7 (0.3 each end)
+        expect = [0.3, 1.4, 3.1, 4.2]
+    else:
+        # e0 and e2 take colour 0 and go first (0.2 each end); e1 then sees
+        # 1.9 L0 and moves its ends by 0.4
+        expect = [0.2, 1.7, 2.8, 4.3]
+    assert np.max(np.abs(out - np.array(expect))) <= 1e-12, (seed, p)
+
+
+def test_seeds_where_colour_order_differs_from_priority_order():
+    # priorities falling or rising along the chain: a pure priority sweep
+    # would apply e1 between e0 and e2 ([0.2, 1.6, 3.05, 4.15] or
+    # [0.35, 1.45, 2.9, 4.3]); the colour classes apply it last
+    monotone = 0
+    for seed in range(16):
+        out, p = chain3(seed)
+        if (p[0] > p[1] > p[2]) or (p[0] < p[1] < p[2]):
+            monotone += 1
+            assert np.max(np.abs(out - np.array([0.2, 1.7, 2.8, 4.3]))) <= 1e-12
+    assert monotone >= 2
+
+
+def nx_greedy(verts, prio, movable):
+    """networkx's greedy colouring of the conflict graph (constraints sharing
+    a movable vertex), taking the constraints by descending priority."""
+    G = nx.Graph()
+    G.add_nodes_from(range(len(prio)))
+    at = {}
+    for i, vs in enumerate(verts):
+        for v in vs:
+            if v >= 0 and movable[v]:
+                at.setdefault(int(v), []).append(i)
+    for lst in at.values():
+        for a in range(len(lst)):
+            for b in range(a + 1, len(lst)):
+                G.add_edge(lst[a], lst[b])
+    order = sorted(range(len(prio)), key=lambda i: -int(prio[i]))
+    col = nx.greedy_color(G, strategy=lambda g, c: iter(order))
+    return np.array([col[i] for i in range(len(prio))]), G
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_greedy_colouring_equals_networkx(seed):
+    rng = np.random.default_rng(seed)
+    nv, m = 40, 120
+    inv_mass = np.where(rng.random(nv) < 0.2, 0.0, 1.0)
+    verts = np.full((m, 4), -1, np.int32)
+    for i in range(m):
+        k = 2 if rng.random() < 0.3 else 4
+        verts[i, :k] = rng.choice(nv, size=k, replace=False)
+    prio = np.array([oracle.splitmix64(int(seed) * 1000 + i) for i in range(m)], dtype=np.uint64)
+    col, ncol = oracle.greedy_colouring(verts, prio, inv_mass)
+    ref, G = nx_greedy(verts, prio, inv_mass > 0)
+    assert np.array_equal(col, ref)
+    assert ncol == col.max() + 1
+    # valid: no two constraints of one colour share a movable vertex, and a
+    # constraint through static vertices only conflicts with nothing
+    for a, b in G.edges:
+        assert col[a] != col[b]
+    assert ncol <= max(d for _, d in G.degree) + 1
+
+
+def test_contact_colouring_of_a_scene_equals_networkx():
+    from paper_2211_04045_gb300 import scenes
+    sc = scenes.two_cloths(n=24, side=0.25, sep=0.004, omega=6.0, noise=0.3, seed=2)
+    x0, xt, _ = scenes.initial(sc)
+    rng = np.random.default_rng(7)
+    x = x0.copy()
+    x[x0[:, 1] > 0.002, 1] -= 0.0033  # the layers 0.7 mm apart, within delta
+    x += rng.normal(0.0, 0.0001, size=x0.shape)
+    osc = oracle.OracleScene(sc)
+    prm = oracle.params_for(sc, seed=99)
+    keys, col = oracle.contact_colours(osc, prm, x, xt)
+    assert len(keys) > 50
+    verts = []
+    for k in keys:
+        kind, a, b = int(k) >> 62, (int(k) >> 31) & 0x7FFFFFFF, int(k) & 0x7FFFFFFF
+        if kind == oracle.VT:
+            verts.append([a, *sc.tris[b]])
+        elif kind == oracle.EE:
+            verts.append([*sc.edges[a], *sc.edges[b]])
+        else:
+            verts.append([a, b, -1, -1])
+    prio = [oracle.splitmix64(99 ^ int(k)) for k in keys]
+    ref, _ = nx_greedy(np.array(verts), prio, sc.inv_mass > 0)
+    assert np.array_equal(col, ref)
+    assert col.max() + 1 >= 2
+
+
+def test_edge_colouring_of_a_cloth_equals_networkx():
+    from paper_2211_04045_gb300 import scenes
+    sc = scenes.two_cloths(n=12, side=0.1, sep=0.004, omega=0.0, noise=0.0)
+    osc = oracle.OracleScene(sc)
+    col, ncol = oracle.edge_colours(osc, oracle.params(seed=5))
+    verts = np.concatenate([sc.len_edges, np.full((len(sc.len_edges), 2), -1)], 1)
+    prio = [oracle.splitmix64(5 ^ (EDGE_KIND | e)) for e in range(len(sc.len_edges))]
+    ref, _ = nx_greedy(verts, prio, sc.inv_mass > 0)
+    assert np.array_equal(col, ref)
+    # a grid vertex has at most six edges, so the greedy needs at least 6
+    # colours and, with random priorities, never more than degree bound 11
+    assert 6 <= ncol <= 11
