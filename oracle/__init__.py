@@ -57,7 +57,8 @@ class Stats(C.Structure):
                 ("active_contacts", C.c_int64), ("candidates", C.c_int64), ("degenerate", C.c_int64),
                 ("max_vertex_contacts", C.c_int32), ("max_vertex_edges", C.c_int32), ("final_r_inf", C.c_double),
                 ("min_pair_dist", C.c_double), ("frozen_vertices", C.c_int32), ("contact_colours", C.c_int32),
-                ("contact_vertices", C.c_int64), ("edge_colours", C.c_int32), ("reserved_", C.c_int32)]
+                ("contact_vertices", C.c_int64), ("edge_colours", C.c_int32), ("reserved_", C.c_int32),
+                ("pair_vertices", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,6 +103,8 @@ def lib():
             L.orc_contact_colours.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, p, p, p, i64]
             L.orc_edge_colours.restype = i32
             L.orc_edge_colours.argtypes = [C.POINTER(Topology), C.POINTER(Params), p]
+            L.orc_ccd_conservative.restype = C.c_int
+            L.orc_ccd_conservative.argtypes = [C.c_int, p, p, p, d]
             L.orc_ccd.restype = C.c_int
             L.orc_ccd.argtypes = [C.c_int, p, p, p, p]
             L.orc_count_intersections.restype = i64
@@ -300,3 +303,12 @@ def ccd(kind, x0, x1, rho=None):
     toi = C.c_double(-1.0)
     hit = lib().orc_ccd(kind, _ptr(x0), _ptr(x1), _ptr(r) if r is not None else None, C.addressof(toi))
     return bool(hit), (toi.value if hit else None)
+
+
+def ccd_conservative(kind, x0, x1, rho=None, tol=0.0):
+    """True when the primitives may come within tol during the linear motion
+    (False: certainly more than tol apart throughout)."""
+    x0 = _f64(x0).reshape(-1)
+    x1 = _f64(x1).reshape(-1)
+    r = None if rho is None else _f64(rho).reshape(-1)
+    return bool(lib().orc_ccd_conservative(kind, _ptr(x0), _ptr(x1), _ptr(r) if r is not None else None, tol))

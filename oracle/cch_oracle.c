@@ -1228,6 +1228,60 @@ int orc_ccd(int kind, const double* x0, const double* x1, const double* rho, dou
   return 0;
 }
 
+/* Conservative CCD, an independent check of orc_ccd: 0 when the two
+ * primitives certainly stay more than tol apart during the whole linear
+ * motion, 1 otherwise (they may come within tol).  Over a time interval of
+ * half-width h around tm, every point of one primitive moves relative to
+ * every point of the other by at most V h, where V is the largest relative
+ * displacement of a vertex of one against a vertex of the other (points of a
+ * primitive are convex combinations of its vertices), so the distance there
+ * is at least d(tm) - V h.  The interval is certified when that bound, less
+ * the rounding error of d(tm) (64 units in the last place of the largest
+ * coordinate), exceeds tol; otherwise it is split in two, down to 2^-44 of
+ * the step and at most 2^20 evaluations in all (past either bound the
+ * answer is 1). */
+static double pair_dist_at(int kind, const v3* p0, const v3* d, const double* rho, double t) {
+  v3 q[4];
+  int nv = kind == ORC_VV ? 2 : 4;
+  for (int i = 0; i < nv; i++) q[i] = add3(p0[i], scl3(t, d[i]));
+  if (kind == ORC_VT) return pt_dist(q[0], q[1], q[2], q[3]) - (rho ? rho[0] : 0.0);
+  if (kind == ORC_EE) return ss_dist(q[0], q[1], q[2], q[3], 0, 0);
+  return (norm3(sub3(q[0], q[1])) - (rho ? rho[0] : 0.0)) - (rho ? rho[1] : 0.0);
+}
+static int certify(int kind, const v3* p0, const v3* d, const double* rho, double V, double err, double tol,
+                   double t0, double t1, int depth, long* budget) {
+  if (--*budget < 0) return 0;
+  double tm = 0.5 * (t0 + t1), h = 0.5 * (t1 - t0);
+  double lower = pair_dist_at(kind, p0, d, rho, tm) - V * h - err;
+  if (lower > tol) return 1;
+  if (depth >= 44) return 0;
+  return certify(kind, p0, d, rho, V, err, tol, t0, tm, depth + 1, budget) &&
+         certify(kind, p0, d, rho, V, err, tol, tm, t1, depth + 1, budget);
+}
+int orc_ccd_conservative(int kind, const double* x0, const double* x1, const double* rho, double tol) {
+  int nv = kind == ORC_VV ? 2 : 4, na = kind == ORC_EE ? 2 : 1;
+  v3 p0[4], d[4];
+  double M = 0.0;
+  for (int i = 0; i < nv; i++) {
+    p0[i] = ld3(x0, i);
+    d[i] = sub3(ld3(x1, i), p0[i]);
+    for (int k = 0; k < 3; k++) {
+      if (fabs(x0[3 * i + k]) > M) M = fabs(x0[3 * i + k]);
+      if (fabs(x1[3 * i + k]) > M) M = fabs(x1[3 * i + k]);
+    }
+  }
+  double V = 0.0;
+  for (int i = 0; i < na; i++)
+    for (int j = na; j < nv; j++) {
+      double r = norm3(sub3(d[i], d[j]));
+      if (r > V) V = r;
+    }
+  V = V * (1.0 + 1e-12);
+  double err = 64.0 * 2.220446049250313e-16 * (M + (rho ? rho[0] + (nv == 2 ? rho[1] : 0.0) : 0.0)) + 1e-300;
+  long budget = 1L << 20; /* interval evaluations; past it the answer is "may touch" */
+  return certify(kind, p0, d, rho, V, err, tol, 0.0, 1.0, 0, &budget) ? 0 : 1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Exact acceptance                                                          */
 /* ------------------------------------------------------------------------ */
@@ -1340,6 +1394,8 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
         if (P.d[i] < Di[v4[k]]) Di[v4[k]] = P.d[i];
       if (P.d[i] < S.min_pair_dist) S.min_pair_dist = P.d[i];
     }
+    /* every pair of P is closer than D^(l), so its vertices have D_i < D^(l) */
+    for (int64_t v = 0; v < n; v++) S.pair_vertices += Di[v] < D;
     /* R2b: below ORC_D_FLOOR the bound D_i/2 is no larger than the rounding
      * of an FP64 position update, so such a vertex does not move */
     for (int64_t v = 0; v < n; v++)

@@ -77,6 +77,8 @@ typedef struct {
                                 vertices of the contact constraints           */
   int32_t edge_colours;      /* colours of the edge-length constraints        */
   int32_t reserved_;
+  int64_t pair_vertices;     /* sum over iterations of the distinct vertices
+                                of the pairs of P                             */
 } orc_stats;
 
 /* Optional per-iteration record (tests only).  Any pointer may be NULL. */
@@ -147,6 +149,12 @@ int32_t orc_edge_colours(const orc_topology* t, const orc_params* prm, int32_t* 
  * a,b with radii rho[0..1]; rho may be NULL).  Returns 1 and the first time
  * of impact in [0,1] if they touch. */
 int orc_ccd(int kind, const double* x0, const double* x1, const double* rho, double* toi);
+
+/* Conservative counterpart used to check orc_ccd: 0 when the primitives
+ * certainly stay more than tol apart over the whole motion (bound: distance
+ * at an interval's midpoint minus the largest relative vertex displacement
+ * over half the interval, with bisection), 1 when that cannot be shown. */
+int orc_ccd_conservative(int kind, const double* x0, const double* x1, const double* rho, double tol);
 
 /* ---- exact acceptance ---- */
 /* Number of intersecting non-adjacent primitive pairs in state x, decided by

@@ -117,3 +117,29 @@ def test_safety_check_finds_nothing_under_the_distance_rule(case):
     a, sa, _ = oracle.handle_step(osc, oracle.params_for(sc, max_iters=120), x, xt)
     b, sb, _ = oracle.handle_step(osc, oracle.params_for(sc, max_iters=120, ccd_check=1), x, xt)
     assert np.array_equal(a, b) and sa == sb and sb["ccd_clamps"] == 0
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_distance_rule_segments_certified_apart(case):
+    # Sec. 5's guarantee checked with the conservative CCD (not the
+    # root-finding one): under the distance rule each vertex moves at most
+    # 0.45 D_i per iteration, so a pair at distance d stays at least 0.1 d
+    # apart along the whole segment x^(l) -> x^(l+1); 0.05 d is certified
+    name, sc = colliding_cases()[case]
+    osc = oracle.OracleScene(sc)
+    prm = oracle.params_for(sc, max_iters=120)
+    x, xt, _ = scenes.initial(sc)
+    xn, st, tr = oracle.handle_step(osc, prm, x, xt, trace_iters=prm.max_iters + 2)
+    checked = 0
+    for l in range(0, st["iterations"], 3):
+        xl, xl1, Dl = tr["x"][l], tr["x"][l + 1], tr["Dl"][l]
+        near, dist = oracle.proximity(osc, xl, 2.0 * Dl, mode=0, x_tilde=xt)
+        for k, d in zip(near.tolist(), dist.tolist()):
+            if d < 1e-10:
+                continue  # held by the D_i floor: its vertices do not move
+            kind, a, b = k >> 62, (k >> 31) & 0x7FFFFFFF, k & 0x7FFFFFFF
+            vs = [a, *sc.tris[b]] if kind == 0 else ([*sc.edges[a], *sc.edges[b]] if kind == 1 else [a, b])
+            rho = None if kind != 2 or sc.radius is None else sc.radius[vs]
+            assert not oracle.ccd_conservative(kind, xl[vs], xl1[vs], rho, tol=0.05 * d), (name, l, k, d)
+            checked += 1
+    assert checked > 100
