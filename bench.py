@@ -19,7 +19,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -47,6 +46,11 @@ def workload(name: str):
         return scenes.tube_knot(), "knot2x64x561"
     if name == "normal_flow":
         return scenes.normal_flow_torus(), "normal_flow_torus384x64"
+    if name == "hair_sand":
+        return scenes.hair_sand(), "hair10000x32_sand100000"
+    if name == "rotating_sphere":
+        return scenes.cloth_on_rotating_sphere(n=64, side=1.0, sphere_subdiv=4, sphere_r=0.3), \
+            "cloth64_rotating_sphere4_friction"
     raise SystemExit(f"unknown config {name}")
 
 
@@ -153,13 +157,6 @@ def job_total(x: float, dev) -> float:
     return float(t.item())
 
 
-def min_iterations(x_t, x_tilde, d_max, gamma):
-    """Fewest iterations a step can take: every vertex moves at most
-    0.5 gamma D^max per iteration (Eq. forward2 with D_i <= D^max)."""
-    far = float(np.max(np.linalg.norm(x_tilde - x_t, axis=1)))
-    return max(1, math.ceil(far / (0.5 * gamma * d_max)))
-
-
 def oracle_sample(sc, x_t, x_tilde, budget_s: float, solver: int = 0, step_rule: int = 0):
     """Times the oracle, as it stands, on the first iterations of one step.
     Returns (seconds per iteration, iterations timed, pairs evaluated)."""
@@ -179,27 +176,39 @@ def oracle_sample(sc, x_t, x_tilde, budget_s: float, solver: int = 0, step_rule:
 
 
 def serving_mix():
-    """Resident scenes of the serving workload: the paper's scene kinds at
-    2K-73K triangles."""
+    """Resident scenes of the serving workload: the paper's scene kinds (cloth
+    over a sphere, two cloth layers, volumetric bodies, tightening tubes,
+    hair and sand), each at a small and a large size, from about 2K to 150K
+    triangles (hair and sand: primitives)."""
     from paper_2211_04045_gb300 import scenes
-    return [scenes.cloth_over_sphere(n=16, side=0.5, sphere_subdiv=3, sphere_r=0.15, noise=0.5, seed=11),
-            scenes.cloth_over_sphere(n=32, seed=12),
-            scenes.two_cloths(n=48, side=0.4, sep=0.01, omega=6.0, noise=0.3, seed=13),
-            scenes.two_cloths(n=136, side=1.0, sep=0.01, omega=6.0, noise=0.3, seed=14),
+    return [scenes.cloth_over_sphere(n=24, side=0.5, sphere_subdiv=3, sphere_r=0.15, noise=0.5, seed=11),
+            scenes.cloth_over_sphere(n=256, side=1.5, sphere_subdiv=4, sphere_r=0.4, noise=0.5, seed=12),
+            scenes.two_cloths(n=32, side=0.25, sep=0.01, omega=6.0, noise=0.3, seed=13),
+            scenes.two_cloths(n=190, side=1.5, sep=0.01, omega=6.0, noise=0.3, seed=14),
             scenes.tet_bodies(n_bodies=8, n=6, side=0.2, box=0.8, seed=15),
-            scenes.tube_knot(around=32, rings=121, r=0.008, helix_r=0.0095, pitch=0.03, ring_dz=0.002)]
+            scenes.tet_bodies(n_bodies=125, n=10, side=0.2, box=1.75, seed=16),
+            scenes.tube_knot(around=16, rings=65, r=0.004, helix_r=0.0055, pitch=0.03, ring_dz=0.002),
+            scenes.tube_knot(),
+            scenes.hair_sand(n_strands=100, segs=16, n_points=1000, grain_r=0.002, bowl_r=0.15, bowl_subdiv=3,
+                             seg_len=0.005, seed=17),
+            scenes.hair_sand(n_strands=4000, segs=32, n_points=40000, grain_r=0.002, bowl_r=0.4, bowl_subdiv=5,
+                             seed=18)]
 
 
-def run_serving(args):
+def prims(sc):
+    return int(len(sc.tris) + len(sc.edges) + len(sc.points)) if len(sc.tris) < 1000 else int(len(sc.tris))
+
+
+def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=("mixed", "fp64")):
     """Poisson request stream served with continuous batching, against the
-    same requests run one at a time in plain FP64."""
+    same requests run one at a time in plain FP64 (each on its own resident
+    scene).  Returns the comparison as a dict."""
     import torch
     from paper_2211_04045_gb300 import cch, scenes
-    dev = torch.device("cuda:0")
     scs = serving_mix()
     rng = np.random.default_rng(0)
-    N = args.requests
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=N))
+    N = requests
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=N))
     which = rng.integers(0, len(scs), size=N)
     inputs = []
     for i in range(N):
@@ -207,6 +216,8 @@ def run_serving(args):
         x, xt, v = scenes.initial(sc)
         xt = xt + rng.normal(0.0, 1e-4, size=xt.shape) * (sc.inv_mass > 0)[:, None]
         inputs.append((torch.tensor(x, device=dev), torch.tensor(xt, device=dev)))
+    out = {"requests": N, "rate_per_s": rate, "max_active": max_active, "budget_bytes": 80 << 30,
+           "scene_prims": [prims(sc) for sc in scs]}
     # plain: one request at a time, FP64, one resident scene per kind
     base = cch.params_for(scs[0], iters_per_launch=8)
     plain = [cch.Scene(sc, base) for sc in scs]
@@ -215,54 +226,157 @@ def run_serving(args):
         g.step(torch.tensor(x, device=dev), torch.tensor(xt, device=dev))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain_ms = []
+    plain_ms, plain_out = [], []
     for i in range(N):
         a = time.perf_counter()
-        plain[which[i]].step(inputs[i][0], inputs[i][1])
+        o, _ = plain[which[i]].step(inputs[i][0], inputs[i][1])
         plain_ms.append(1000.0 * (time.perf_counter() - a))
+        plain_out.append(o)
     plain_s = time.perf_counter() - t0
     for g in plain:
         g.close()
-    # served: requests arrive on the Poisson clock while others run
-    prm = cch.params_for(scs[0], precision=1 if args.precision == "mixed" else 0, iters_per_launch=8,
-                         solver=1 if args.solver == "jacobi" else 0)
-    sv = cch.Server(80 << 30, prm, max_active=args.max_active)
-    ids = [sv.add_scene(sc) for sc in scs]
-    # one warm request per scene (pool build, graph capture)
-    outs = [torch.empty_like(inputs[0][0])]
-    for k, sc in enumerate(scs):
-        x, xt, _ = scenes.initial(sc)
-        o = torch.empty((sc.n_verts, 3), dtype=torch.float64, device=dev)
-        sv.wait(sv.submit(ids[k], torch.tensor(x, device=dev), torch.tensor(xt, device=dev), o))
-    outs = [torch.empty((scs[which[i]].n_verts, 3), dtype=torch.float64, device=dev) for i in range(N)]
-    tickets = []
-    t0 = time.perf_counter()
-    for i in range(N):
-        delay = arrivals[i] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(sv.submit(ids[which[i]], inputs[i][0], inputs[i][1], outs[i]))
-    lat = []
-    iters = []
-    for tk in tickets:
-        st, ms = sv.wait(tk)
-        lat.append(ms)
-        iters.append(st["iterations"])
-    served_s = time.perf_counter() - t0
-    sv.close()
-    tris = [len(sc.tris) for sc in scs]
-    out = {"metric": METRIC, "value": N / served_s, "unit": "steps/s", "n_gpus": 1, "steps": N, "warmup": len(scs),
-           "ms_per_step": 1000.0 * served_s / N, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    out["plain_fp64"] = {"value": N / plain_s, "unit": "steps/s", "p50_ms": float(np.percentile(plain_ms, 50)),
+                         "p99_ms": float(np.percentile(plain_ms, 99))}
+    for prec in precisions:
+        prm = cch.params_for(scs[0], precision=1 if prec == "mixed" else 0, iters_per_launch=8)
+        sv = cch.Server(80 << 30, prm, max_active=max_active)
+        ids = [sv.add_scene(sc) for sc in scs]
+        for k, sc in enumerate(scs):  # one warm request per scene (pool build, graph capture)
+            x, xt, _ = scenes.initial(sc)
+            o = torch.empty((sc.n_verts, 3), dtype=torch.float64, device=dev)
+            sv.wait(sv.submit(ids[k], torch.tensor(x, device=dev), torch.tensor(xt, device=dev), o))
+        outs = [torch.empty((scs[which[i]].n_verts, 3), dtype=torch.float64, device=dev) for i in range(N)]
+        tickets = []
+        t0 = time.perf_counter()
+        for i in range(N):
+            delay = arrivals[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(sv.submit(ids[which[i]], inputs[i][0], inputs[i][1], outs[i]))
+        lat, iters = [], []
+        for tk in tickets:
+            st, ms = sv.wait(tk)
+            lat.append(ms)
+            iters.append(st["iterations"])
+        served_s = time.perf_counter() - t0
+        sv.close()
+        # FP64 served results equal the plain ones bitwise; mixed: max deviation
+        dev_max = max(float((o - p).abs().max().item()) for o, p in zip(outs, plain_out))
+        out[f"served_{prec}"] = {"value": N / served_s, "unit": "steps/s", "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99)), "speedup_vs_plain": plain_s / served_s,
+                                 "iterations_per_step": float(np.mean(iters)),
+                                 "max_abs_diff_vs_plain_m": dev_max}
+    return out
+
+
+def run_serving(args):
+    """The serving workload on its own: one JSON line."""
+    import torch
+    dev = torch.device("cuda:0")
+    r = serve_compare(dev, args.requests, args.rate, args.max_active, precisions=(args.precision,))
+    srv = r[f"served_{args.precision}"]
+    out = {"metric": METRIC, "value": srv["value"], "unit": "steps/s", "n_gpus": 1, "steps": args.requests,
+           "warmup": len(r["scene_prims"]), "ms_per_step": 1000.0 / srv["value"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-           "config": {"workload": f"serving_mix_{args.precision}" + ("_jacobi" if args.solver == "jacobi" else ""),
-                      "requests": N, "rate_per_s": args.rate,
-                      "scene_tris": tris, "max_active": args.max_active, "budget_bytes": 80 << 30},
-           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-           "plain_fp64": {"value": N / plain_s, "unit": "steps/s", "p50_ms": float(np.percentile(plain_ms, 50)),
-                          "p99_ms": float(np.percentile(plain_ms, 99))},
-           "speedup_vs_plain": plain_s / served_s, "iterations_per_step": float(np.mean(iters))}
+           "config": {"workload": f"serving_mix_{args.precision}", "requests": args.requests,
+                      "rate_per_s": args.rate, "scene_prims": r["scene_prims"], "max_active": args.max_active,
+                      "budget_bytes": 80 << 30},
+           "p50_ms": srv["p50_ms"], "p99_ms": srv["p99_ms"], "plain_fp64": r["plain_fp64"],
+           "speedup_vs_plain": srv["speedup_vs_plain"], "iterations_per_step": srv["iterations_per_step"]}
     print(json.dumps(out), flush=True)
     return 0
+
+
+def batch_mix(n: int = 64, seed: int = 0):
+    """64 uneven volumetric scenes: one tet cube each (5 to 8 vertices per
+    side, 0.2 m, random orientation, N(0, 2 m/s) velocity and N(0, 4 rad/s)
+    spin), the bodies of the 64-body workload as scenes of their own."""
+    from paper_2211_04045_gb300 import scenes
+    rng = np.random.default_rng(seed)
+    return [scenes.tet_bodies(n_bodies=1, n=int(rng.integers(5, 9)), side=0.2, box=0.4, seed=1000 + b)
+            for b in range(n)]
+
+
+def batch_compare(dev, stream, n_scenes: int, reps: int, flush):
+    """n_scenes uneven scenes handled in one batched launch sequence against
+    the plain loop of one call per scene (FP64; each scene's result is the
+    same in both, bitwise)."""
+    import torch
+    from paper_2211_04045_gb300 import cch, scenes
+    scs = batch_mix(n_scenes)
+    xs = [[torch.tensor(a, device=dev) for a in scenes.initial(sc)[:2]] for sc in scs]
+    prm = cch.params_for(scs[0])
+    batch = cch.Scene(scs, prm, stream=stream.cuda_stream)
+    singles = [cch.Scene(sc, prm, stream=stream.cuda_stream) for sc in scs]
+    outs_b, _ = batch.batch_step([a for a, _ in xs], [b for _, b in xs])  # warm-up
+    outs_s = [g.step(a, b)[0] for g, (a, b) in zip(singles, xs)]
+    same = all(torch.equal(p, q) for p, q in zip(outs_b, outs_s))
+    torch.cuda.synchronize(dev)
+    tb = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, sts = batch.batch_step([a for a, _ in xs], [b for _, b in xs], outs_b)
+        tb.append(time.perf_counter() - t0)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for g, (a, b), o in zip(singles, xs, outs_s):
+            g.step(a, b, out=o)
+        ts.append(time.perf_counter() - t0)
+    batch.close()
+    for g in singles:
+        g.close()
+    its = [s["iterations"] for s in sts]
+    return {"scenes": n_scenes, "verts": [sc.n_verts for sc in scs][:8] + ["..."],
+            "batched": {"value": n_scenes / min(tb), "unit": "scene-steps/s", "ms": 1000.0 * min(tb)},
+            "plain_loop": {"value": n_scenes / min(ts), "unit": "scene-steps/s", "ms": 1000.0 * min(ts)},
+            "speedup": min(ts) / min(tb), "same_results": bool(same),
+            "iterations_min_max": [int(min(its)), int(max(its))]}
+
+
+def sec8d_bytes(st, n, T, E, NL, fp=8):
+    """Algorithmic bytes of one step by kernel group, counted as the method
+    must move them (FP64 sizes unless fp = 4 for the mixed projection):
+    forward step 96 N per iteration plus 8 N for D_i; distance refresh
+    16 |P| + 24 N_P per refresh iteration (N_P distinct vertices of P); a
+    search 24 N + 12 T + 8 E + 16 |P|; contacts |A| (16 + 12 fp + fp) +
+    9 fp N_A (x and y read, y written, once per distinct contact vertex);
+    edge-length constraints 8 C_e + 6 fp N per sweep; the colouring reads 16
+    bytes of vertex ids and writes a 4-byte colour per contact."""
+    it, se = st["iterations"], st["searches"]
+    P, A = st["pairs_evaluated"], st["active_contacts"]
+    NA, NP = st["contact_vertices"], st["pair_vertices"]
+    per_search_pairs = P / max(1, it)
+    sweeps = st.get("gs_sweeps", 1)
+    return {
+        "forward": it * 104.0 * n,
+        "refresh": 16.0 * P * (it - se) / max(1, it) + 24.0 * NP * (it - se) / max(1, it),
+        "search": se * (24.0 * n + 12.0 * T + 8.0 * E + 16.0 * per_search_pairs),
+        "assemble": A * (16.0 + 12 * fp + fp) + 3 * fp * NA,
+        "sweep": sweeps * (A * (16.0 + 12 * fp + fp) + 9 * fp * NA + it * (8.0 * NL + 6 * fp * n)),
+        "colour": A * 20.0,
+    }
+
+
+def chain_target(sc, dyn, g):
+    """x~ of the next step of the chain on the GPU: the stand-in dynamics, or
+    the library's pre-pass kernels for the normal-flow and friction
+    workloads."""
+    def target(x, v):
+        if sc.flow is not None:
+            f = sc.flow
+            return g.normal_flow_target(x, f["beta"], f["alpha"], f["sign"], f["iters"])
+        if sc.friction is not None:
+            f = sc.friction
+            y = dyn.predict_frictionless(x, v)
+            return g.friction_filter(x, y, f["mu"], f["reach"], f["sep"], out=y)
+        return dyn.predict(x, v)
+    return target
 
 
 def run_reference(args):
@@ -273,20 +387,13 @@ def run_reference(args):
     from paper_2211_04045_gb300 import scenes
     sc, wname = workload(args.config)
     x, xt, v = scenes.initial(sc)
-    prm_d = dict(sc.params)
-    d_max = prm_d.get("d_max", 4e-3)
-    gamma = 0.9
+    L = int(dict(sc.params).get("max_iters", 2048))
     per_step = []
-    pairs = 0
-    it_total = 0
     budget = max(2.0, args.ref_budget / max(1, args.steps + args.warmup))
     for s in range(args.warmup + args.steps):
         spi, its, pe = oracle_sample(sc, x, xt, budget)
-        need = min_iterations(x, xt, d_max, gamma)
         if s >= args.warmup:
-            per_step.append(spi * need)
-            pairs += pe
-            it_total += its
+            per_step.append(spi * (L + 1))
     tot = float(np.sum(per_step))
     val = len(per_step) / tot
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": world,
@@ -295,11 +402,44 @@ def run_reference(args):
            "config": {"workload": f"{wname}_fp64", "verts": sc.n_verts, "tris": len(sc.tris), "dt": sc.dt},
            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
                             "sample": "per step: the oracle's first iterations of the workload's first step (about "
-                                      f"{budget:.0f} s), seconds per iteration times the fewest iterations that "
-                                      "step needs (max target displacement / 0.45 D^max), which favours the oracle"},
+                                      f"{budget:.0f} s), seconds per iteration times L + 1 = {L + 1} iterations, "
+                                      "the count every step of this chain takes (it runs to L on the GPU, and the "
+                                      "oracle takes the GPU's iteration count on every scene the parity tests "
+                                      "compare)"},
            "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
+
+
+def mixed_compare(sc, inputs, refs, dev, stream, flush, tune_iters, log):
+    """The mixed-precision form (FP32 distances and projection, FP64 forward
+    step, CCD and acceptance) timed on the same step inputs as the FP64 run;
+    its position error against the FP64 results is reported per step."""
+    import torch
+    from paper_2211_04045_gb300 import cch
+    g = cch.Scene(sc, cch.params_for(sc, precision=1, accept_check=1), stream=stream.cuda_stream)
+    g.step(inputs[0][0], inputs[0][1])  # warm-up: graph capture
+    if tune_iters:
+        g.autotune(inputs[0][0], inputs[0][1], probe_iters=tune_iters)
+    ms, errs, its, isect, unc = [], [], [], 0, 0
+    for (x, xt), ref in zip(inputs, refs):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out, st = g.step(x, xt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+        errs.append(float(torch.linalg.norm(out - ref, dim=1).max().item()))
+        its.append(st["iterations"])
+        isect += st["intersections"]
+        unc += st["uncertain"]
+    g.close()
+    log(f"mixed: {', '.join(f'{m:.0f} ms' for m in ms)}; max |x_mixed - x_fp64| per step "
+        + ", ".join(f"{e:.2e}" for e in errs))
+    return {"value": len(ms) / (sum(ms) / 1000.0), "unit": "steps/s", "steps": len(ms),
+            "p50_ms": float(np.percentile(ms, 50)), "iterations_per_step": float(np.mean(its)),
+            "max_abs_err_vs_fp64_m": max(errs), "intersections": int(isect), "uncertain": int(unc)}
 
 
 def main():
@@ -320,6 +460,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-configuration autotuner")
     ap.add_argument("--tune-iters", type=int, default=48, help="iterations of the autotuner's probe step")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the comparisons (mixed precision, batched, served) after the headline")
+    ap.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision comparison")
+    ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batching comparison")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests batched at once")
@@ -344,19 +488,21 @@ def main():
 
     from paper_2211_04045_gb300 import cch, scenes
     sc, wname = workload(args.config)
+    gs = args.solver == "gs"
     prm = cch.params_for(sc, precision=1 if args.precision == "mixed" else 0,
-                         solver=1 if args.solver == "jacobi" else 0, constraint_form=1 if args.gap else 0,
-                         step_rule=1 if args.step_rule == "ccd" else 0)
+                         solver=0 if gs else 1, constraint_form=1 if args.gap else 0,
+                         step_rule=1 if args.step_rule == "ccd" else 0, accept_check=1)
     if args.ncu_case:
         x0, xt0, v0 = scenes.initial(sc)
         x, xt, v = (torch.tensor(a, device=dev) for a in (x0, xt0, v0))
         if args.ncu_warm:
             dyn = scenes.TorchDynamics(sc, dev)
             gw = cch.Scene(sc, prm)
+            target = chain_target(sc, dyn, gw)
             for _ in range(args.ncu_warm):
                 out, _ = gw.step(x, xt)
                 v = dyn.next_velocity(out, x)
-                x, xt = out, dyn.predict(out, v)
+                x, xt = out, target(out, v)
             gw.close()
         prm.max_iters = args.ncu_case
         g = cch.Scene(sc, prm)
@@ -369,7 +515,8 @@ def main():
         sys.stderr.write(f"[bench] ncu case: {st['iterations']} iterations, {st['kernel_launches']} launches, "
                          f"{st['pairs_evaluated'] / st['iterations']:.0f} pairs/iter, "
                          f"{st['active_contacts'] / st['iterations']:.0f} contacts/iter, "
-                         f"{st['max_vertex_contacts']} contacts at one vertex, sweep depth {st['gs_depth']}\n")
+                         f"{st['max_vertex_contacts']} contacts at one vertex, {st['contact_colours']} contact "
+                         f"and {st['edge_colours']} edge colours\n")
         g.close()
         return 0
     stream = torch.cuda.current_stream(dev)
@@ -384,6 +531,7 @@ def main():
 
     # ---- warm-up: the first W steps of the chain ----
     dyn = scenes.TorchDynamics(sc, dev)
+    target = chain_target(sc, dyn, gpu)
     x0, xt0, v0 = scenes.initial(sc)
     x = torch.tensor(x0, device=dev)
     xt = torch.tensor(xt0, device=dev)
@@ -395,7 +543,7 @@ def main():
         _, st = gpu.step(x, xt, out=outbuf)
         v = dyn.next_velocity(outbuf, x)
         x = outbuf.clone()
-        xt = dyn.predict(x, v)
+        xt = target(x, v)
         log(f"warm-up step {s}: {st['iterations']} iterations, {time.perf_counter() - t0:.2f} s")
     torch.cuda.synchronize(dev)
     timed_inputs = (x.clone(), xt.clone())
@@ -404,7 +552,10 @@ def main():
         tune = gpu.autotune(x, xt, probe_iters=args.tune_iters)
         log(f"autotune: {tune}")
 
-    # ---- timed region: K further steps of the chain ----
+    # ---- timed region: K further steps of the chain, each with the exact
+    # acceptance test of x^{t+1} ----
+    keep = 0 if args.no_compare else max(0, min(args.mixed_steps, K))
+    kept_in, kept_out = [], []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
     clocks.start()
@@ -417,13 +568,17 @@ def main():
     stats = []
     for k in range(K):
         flush.zero_()
+        if k < keep:
+            kept_in.append((x.clone(), xt.clone()))
         ev[k][0].record(stream)
         _, st = gpu.step(x, xt, out=outbuf)
         ev[k][1].record(stream)
         stats.append(st)
+        if k < keep:
+            kept_out.append(outbuf.clone())
         v = dyn.next_velocity(outbuf, x)
         x = outbuf.clone()
-        xt = dyn.predict(x, v)
+        xt = target(x, v)
     t_end.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -432,9 +587,10 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     log(f"timed {K} steps in {total_ms / 1000:.2f} s: " + ", ".join(f"{m:.0f} ms" for m in step_ms))
+    log("per step: iterations " + ", ".join(str(s["iterations"]) for s in stats) + "; final ||r|| "
+        + ", ".join(f"{s['final_r_inf']:.3g}" for s in stats) + "; frozen "
+        + ", ".join(str(s["frozen_vertices"]) for s in stats))
     total_ms = slowest(total_ms, dev)
-    # replaying the first timed step must give the same result (determinism)
-    first_out = None
 
     iters = np.array([s["iterations"] for s in stats])
     pairs = job_total(float(np.sum([s["pairs_evaluated"] for s in stats])), dev)
@@ -445,42 +601,25 @@ def main():
     gpu.set_profiling(True)
     flush.zero_()
     prof_out, pst = gpu.step(timed_inputs[0], timed_inputs[1])
-    pstats = [pst]
     prof = gpu.profile()
     gpu.set_profiling(False)
     deterministic = pst["iterations"] == stats[0]["iterations"] and pst["pairs_evaluated"] == stats[0]["pairs_evaluated"]
     log(f"profiled one step: {pst['iterations']} iterations")
 
-    nvc = int(np.count_nonzero(np.isin(np.arange(n), np.concatenate([sc.tris.ravel(), sc.edges.ravel(),
-                                                                        np.asarray(sc.points).ravel()]))))
     T, E, NL = len(sc.tris), len(sc.edges), len(sc.len_edges)
-    searches = sum(s["searches"] for s in pstats)
-    p_pairs = sum(s["pairs_evaluated"] for s in pstats)
-    p_cons = sum(s["active_contacts"] for s in pstats)
-    p_iters = sum(s["iterations"] for s in pstats)
-    ppi = p_pairs / max(1, p_iters)      # |P| per iteration
-    cpi = p_cons / max(1, p_iters)       # contacts per iteration
     fp = 8 if args.precision == "fp64" else 4
-    # algorithmic bytes of each kernel group over the profiled step: what the
-    # method must read and write at least (positions 24 B per vertex in FP64,
-    # pair records 32 B, contact records 144 B in FP64 / 96 B mixed)
-    crec = 144 if args.precision == "fp64" else 96
-    algo = {
-        "query_vt": searches * (16.0 * nvc + 12.0 * T + 16.0 * nvc),
-        "query_ee": searches * (8.0 * E + 32.0 * nvc),
-        "finalize": p_iters * ppi * (24.0 + 96.0 + 32.0) * (searches / max(1, p_iters)),
-        "refresh": (p_iters - searches) * (32.0 * ppi * 2 + 24.0 * min(n, 4 * ppi)),
-        "assemble": p_iters * cpi * (4.0 + 32.0 + 4 * 3 * fp + crec),
-        "order": p_iters * cpi * (24.0 * 4 + 48.0 * 3 + 16.0),
-        "sweep": p_iters * (cpi * (crec + 4 * 3 * (3 * fp)) + NL * (8.0 + 4 * fp + 4 * 3 * fp)),
-        "forward": p_iters * 96.0 * n,
-        "refit": searches * (24.0 * n + 12.0 * T + 8.0 * E),
-    }
+    pst = dict(pst, gs_sweeps=prm.gs_sweeps)
+    algo = sec8d_bytes(pst, n, T, E, NL, fp)
+    groups_of = {"search": ("refit", "query_vt", "query_ee", "query_vv", "finalize")}
+    gms = {g: (sum(prof[h][0] for h in groups_of.get(g, (g,))), max(prof[h][1] for h in groups_of.get(g, (g,))))
+           for g in algo}
     dominant = max(prof, key=lambda g: prof[g][0])
     peak, peak_kind = peaks()
     dms, dcount = prof[dominant]
     roof = {"kernel": dominant, "bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_kind,
-            "launches": dcount, "ms_total": dms, "traffic": None}
+            "launches": dcount, "ms_total": dms, "traffic": None,
+            "bytes_rule": "algorithmic bytes of the kernel group over the profiled step (see sec8d_bytes), "
+                          "per distinct vertex, divided by its launches"}
     if dominant in algo and dms > 0:
         ach = algo[dominant] / (dms / 1000.0) / 1e9
         roof.update(achieved=ach, frac=ach / peak, algo_bytes_per_launch=algo[dominant] / max(1, dcount))
@@ -494,7 +633,15 @@ def main():
             roof["traffic"] = ent["bytes_per_launch"]
     except Exception:
         pass
+    step_ms_prof = sum(m for m, _ in prof.values())
+    step_bytes = sum(algo.values())
+    roof["step"] = {"algo_bytes": step_bytes, "ms": step_ms_prof,
+                    "achieved_gbs": step_bytes / (step_ms_prof / 1000.0) / 1e9,
+                    "frac": step_bytes / (step_ms_prof / 1000.0) / 1e9 / peak}
     groups = {g: {"ms": round(m, 3), "launches": c} for g, (m, c) in prof.items()}
+    group_roof = {g: {"algo_gb": round(algo[g] / 1e9, 4),
+                      "gbs": round(algo[g] / (gms[g][0] / 1000.0) / 1e9, 2) if gms[g][0] > 0 else None}
+                  for g in algo}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e_n = 1
@@ -509,11 +656,28 @@ def main():
     log(f"end to end: {e2e_s:.2f} s")
     e2e = {"value": job_total(float(e2e_n), dev) / slowest(e2e_s, dev), "unit": "steps/s",
            "h2d_bytes_per_step": 2 * n * 24, "d2h_bytes_per_step": n * 24}
+    gpu.close()
+
+    # ---- the metric's comparisons: mixed precision on the same inputs,
+    # batched against a plain loop, served against plain ----
+    compare = None
+    if rank == 0 and world == 1 and not args.no_compare:
+        compare = {}
+        if keep and args.precision == "fp64":
+            compare["mixed"] = mixed_compare(sc, kept_in, kept_out, dev, stream, flush,
+                                             0 if args.no_tune else args.tune_iters, log)
+        del kept_in, kept_out
+        if args.batch_scenes:
+            compare["batched"] = batch_compare(dev, stream, args.batch_scenes, 2, flush)
+            log(f"batched: {compare['batched']}")
+        if args.requests:
+            compare["served"] = serve_compare(dev, args.requests, args.rate, args.max_active)
+            log(f"served: {compare['served']}")
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        spi, its, pe = oracle_sample(sc, x0, xt0, args.cpu_budget, 1 if args.solver == "jacobi" else 0,
+        spi, its, pe = oracle_sample(sc, x0, xt0, args.cpu_budget, 0 if gs else 1,
                                      1 if args.step_rule == "ccd" else 0)
         mean_it = float(np.mean(iters))
         cpu = {"value": 1.0 / (spi * mean_it), "unit": "steps/s", "cores": 1, "kind": "oracle",
@@ -525,22 +689,27 @@ def main():
         out = {"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-               "config": {"workload": f"{wname}_{args.precision}" + ("_jacobi" if args.solver == "jacobi" else "")
-                          + ("_gap" if args.gap else "") + ("_ccdstep" if args.step_rule == "ccd" else ""), "verts": n, "tris": T, "edges": E,
-                          "len_edges": len(sc.len_edges), "dt": sc.dt, "l2": "flushed between steps (256 MiB write)",
-                          "parallelism": "replicas" if world > 1 else "single"},
+               "config": {"workload": f"{wname}_{args.precision}" + ("_jacobi" if not gs else "")
+                          + ("_gap" if args.gap else "") + ("_ccdstep" if args.step_rule == "ccd" else ""),
+                          "verts": n, "tris": T, "edges": E, "len_edges": NL, "dt": sc.dt,
+                          "l2": "flushed between steps (256 MiB write)",
+                          "parallelism": "replicas" if world > 1 else "single",
+                          "acceptance": "exact-filtered intersection test of every x^{t+1} inside the timed step"},
                "contact_pairs_per_sec": pairs / (total_ms / 1000.0),
                "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                "iterations_per_step": float(np.mean(iters)), "converged_steps": int(sum(s["converged"] for s in stats)),
-               "sweep_depth": int(pst["gs_depth"]),
+               "final_r_inf": [round(s["final_r_inf"], 6) for s in stats],
+               "frozen_vertices": [int(s["frozen_vertices"]) for s in stats],
+               "intersections": int(sum(s["intersections"] for s in stats)),
+               "uncertain": int(sum(s["uncertain"] for s in stats)),
+               "sweep_depth": int(pst["gs_depth"]), "contact_colours": int(max(s["contact_colours"] for s in stats)),
+               "edge_colours": int(stats[0]["edge_colours"]),
                "max_vertex_contacts": int(max(s["max_vertex_contacts"] for s in stats)),
                "ccd_hits": int(sum(s["ccd_clamps"] for s in stats)),
                "deterministic_replay": bool(deterministic and e2e_same),
-               "autotune": tune, "roofline": roof, "kernel_groups": groups, "cpu_baseline": cpu, "e2e": e2e,
-               "clocks": clk,
-               "gpu_launches": launches}
+               "autotune": tune, "roofline": roof, "kernel_groups": groups, "group_roofline": group_roof,
+               "compare": compare, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches}
         print(json.dumps(out), flush=True)
-    gpu.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -44,16 +44,19 @@ typedef enum {
   CCH_E_CUDA = 4,              /* a CUDA runtime call failed                   */
   CCH_E_CAPACITY = 5,          /* an internal bound was exceeded (buffers past
                                   2^30 pairs, BVH traversal or sweep bounds)   */
-  CCH_E_TIMEOUT = 6,           /* a bounded device wait ran out (the sweep's
-                                  vertex counters); the context stays usable   */
+  CCH_E_TIMEOUT = 6,           /* a bounded device wait ran out (the colouring's
+                                  vertex counters or the sweep's grid barrier);
+                                  the context stays usable                     */
   CCH_E_INPUT_NOT_FEASIBLE = 7,/* validate_input: x_t already intersects       */
   CCH_E_CANCELLED = 8,         /* a server request was cancelled               */
   CCH_E_STATE = 9              /* call not valid in the object's current state */
 } cch_status;
 
 typedef enum { CCH_PREC_FP64 = 0, CCH_PREC_MIXED = 1 } cch_precision;
-/* Backward step (Sec. 4.3): one projected Gauss-Seidel sweep per iteration
- * (contacts, then edge-length constraints, each by descending priority), or
+/* Backward step (Sec. 4.3): gs_sweeps multi-colour projected Gauss-Seidel
+ * sweeps per iteration (the contact colour classes in ascending colour, then
+ * the edge-length classes; each group coloured greedily in descending
+ * priority splitmix64(seed ^ key)), or
  * the projected Jacobi variant (Sec. 4.3.2) with per-constraint
  * under-relaxation jacobi_omega / (most constraints at one of its vertices). */
 typedef enum { CCH_SOLVER_GAUSS_SEIDEL = 0, CCH_SOLVER_JACOBI = 1 } cch_solver;
@@ -90,7 +93,9 @@ typedef struct {
   int32_t ccd_check;     /* 1: CCD of every pair's segment each iteration, with
                             the time-of-impact clamp (Sec. 5.1 scheme as a
                             safety net; always on under CCH_STEP_CCD)          */
-  int32_t accept_check;  /* 1: exact-filtered intersection test of x^{t+1}     */
+  int32_t accept_check;  /* 1: exact-filtered intersection test of x^{t+1}
+                            (always on under CCH_STEP_CCD: its root-finding
+                            CCD can miss a tangential touch)                   */
   int32_t validate_input;/* 1: the same test on x^t before the loop            */
   int32_t iters_per_launch; /* iterations captured per CUDA-graph launch (G)   */
   int32_t bvh_refit_only;   /* 1: rebuild the BVH at the first search of a step
@@ -101,7 +106,17 @@ typedef struct {
                                8); a hit that remains after the last round
                                keeps every vertex of the scene in place for the
                                iteration                                       */
-  uint64_t seed;         /* priorities of the randomized sweep order (Sec. 4.3) */
+  uint64_t seed;         /* priorities of the randomized colouring (Sec. 4.3)  */
+  int32_t max_polls;     /* bound on the polls of one bounded device wait (the
+                            colouring's vertex counters, the sweep's grid
+                            barrier); past it the call returns CCH_E_TIMEOUT.
+                            0 = the default 2^22                               */
+  int32_t pair_capacity; /* initial capacity of the pair buffers, in pairs
+                            (0 = 4 (T + E + Q) + 4096); they double on
+                            overflow and the step is run again                 */
+  int32_t sweep_blocks;  /* blocks of the cooperative sweep kernels (0 = every
+                            block that fits on the device at once)             */
+  int32_t reserved_;
 } cch_params;
 
 /* Mesh of one scene (host pointers, copied at creation).
@@ -141,12 +156,21 @@ typedef struct {
                                 certify (expected 0)                          */
   double device_ms;          /* device time of the call (CUDA events)         */
   int64_t kernel_launches;   /* kernels this call launched (graph nodes count) */
-  int32_t gs_depth;          /* longest chain of constraints in one
-                                Gauss-Seidel backward step, each applied after
-                                the previous one at a shared vertex: the
-                                sweep's critical path (recorded while
-                                profiling is on, else 1)                      */
-  int32_t reserved_;
+  int32_t gs_depth;          /* phases of one Gauss-Seidel sweep, one per
+                                colour class: contact_colours + edge_colours
+                                (the sweep's critical path)                   */
+  int32_t frozen_vertices;   /* vertices held in place at the last iteration
+                                because their D_i fell below 1e-10 m (the
+                                floor under which D_i/2 is no larger than the
+                                rounding of a position update) although their
+                                y_i differs from x_i                          */
+  int64_t contact_vertices;  /* sum over iterations of the distinct movable
+                                vertices of the contact constraints           */
+  int32_t contact_colours;   /* most colours of one iteration's contact
+                                colouring (Gauss-Seidel)                      */
+  int32_t edge_colours;      /* colours of the edge-length constraints        */
+  int64_t pair_vertices;     /* sum over iterations of the distinct vertices
+                                of the pairs of P                             */
 } cch_step_stats;
 
 typedef struct cch_scene cch_scene;
@@ -215,6 +239,11 @@ cch_status cch_destroy(cch_scene* s);
  * whose boxes are within D on every axis) and proximity set
  * P = {candidates with dist < D} of scene 0 at state x (device pointer),
  * with the static-vertex flags taken from (x_t, x_tilde) = (x, x_ref).
+ * want_candidates: 1 the candidate set; 0 P with exact FP64 distances;
+ * 2 P exactly as the first search of a step forms it, at the scene's D^max
+ * (D is ignored), with the distances the step records: in mixed precision
+ * the FP32 lower bounds that decide membership there, in FP64 the exact
+ * distance where it decides something and an FP32 lower bound otherwise.
  * keys (host, capacity cap) receive the canonical pair keys
  * kind<<62 | id1<<31 | id2 in unspecified order, dist (host, may be NULL)
  * the matching distances; *count receives the full size even when it
@@ -222,13 +251,19 @@ cch_status cch_destroy(cch_scene* s);
 cch_status cch_query_pairs(cch_scene* s, const double* x, const double* x_ref, double D, int32_t want_candidates,
                            uint64_t* keys, double* dist, int64_t cap, int64_t* count);
 
+/* Bound of the scene's bounded device waits (the colouring's vertex counters
+ * and the sweep's grid barrier), in polls; 0 restores the default 2^22.  A
+ * wait that runs out makes the step return CCH_E_TIMEOUT and leaves the
+ * scene usable for the next call. */
+cch_status cch_set_max_polls(cch_scene* s, int32_t max_polls);
+
 /* ---- proximity query without device allocation ----------------------------
  * The same query as cch_query_pairs for callers that must not allocate device
- * memory while they run: for example code executing between
- * cudaStreamBeginCapture and cudaStreamEndCapture (where cudaMalloc is not
- * allowed), real-time loops that reserve all of their memory up front, or
- * hosts whose memory manager forbids direct cudaMalloc.  The paper has no
- * counterpart; this is a deployment variant of the query above.
+ * memory while they run: real-time loops that reserve all of their memory up
+ * front and may not touch the allocator once they are running (an allocation
+ * can stall on the device or fail when memory is short), and hosts whose own
+ * memory manager owns the GPU's memory and forbids direct cudaMalloc.  The
+ * paper has no counterpart; this is a deployment variant of the query above.
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The pair
  * list the query kernels produce is written to one fixed array inside the
@@ -236,19 +271,52 @@ cch_status cch_query_pairs(cch_scene* s, const double* x, const double* x_ref, d
  * every GPU that loads the library until the process exits) and copied to
  * keys/dist from there.  The first call on a device looks the array's device
  * address up (cudaGetSymbolAddress, once per device, with that device
- * current); make that first call before any stream capture starts.
+ * current).  Like every call of this library it synchronises the scene's
+ * stream and copies its results to the host before it returns.
+ * want_candidates is 0 or 1.
  * Results: as cch_query_pairs.  When more than CCH_NOALLOC_MAX_PAIRS pairs
  * are found, *count receives the full count and the call returns
- * CCH_E_CAPACITY without copying; it returns CCH_E_CAPACITY too when the
- * query's intermediate pairs outgrow the buffers the scene was created with
- * (cch_query_pairs would grow them; this call cannot).  All calls share the array and it keeps
- * the previous call's contents; calls whose work overlaps on the GPU (other
- * host threads, other scenes on other streams) race on it and must be
+ * CCH_E_CAPACITY without copying.  When the query's intermediate pairs
+ * outgrow the buffers the scene was created with (cch_query_pairs would grow
+ * them; this call cannot), the full count is not known: *count receives -1
+ * and the call returns CCH_E_CAPACITY.  All calls share the array and it
+ * keeps the previous call's contents; calls whose work overlaps on the GPU
+ * (other host threads, other scenes on other streams) race on it and must be
  * serialised by the caller. */
 #define CCH_NOALLOC_MAX_PAIRS 131072
 cch_status cch_query_pairs_noalloc(cch_scene* s, const double* x, const double* x_ref, double D,
                                    int32_t want_candidates, uint64_t* keys, double* dist, int64_t cap,
                                    int64_t* count);
+
+/* ---- pre-passes that produce the target x~ of a step ----------------------
+ * Both run on the scene's own topology (a single scene), take and write
+ * DEVICE arrays of n_verts x 3 float64 and synchronise the scene's stream.
+ * They use the scene's working arrays, so they must not run while a step of
+ * the same scene runs (calls on one scene are serialised by its stream and
+ * by the one-thread-at-a-time rule above).
+ *
+ * Target of the globally injective normal flow (Sec. 7.4, Eq. normal flow):
+ * y = x + (sign beta) n(x), n the area-weighted vertex normals (the
+ * normalised sum of (b - a) x (c - a) over the incident triangles), followed
+ * by iters (0..64) Jacobi steps y <- y + alpha Lap(y) of the cotangent
+ * Laplacian with the mixed Voronoi areas of Meyer et al. (2003), the operator
+ * taken on the current y.  x and y must not alias. */
+cch_status cch_normal_flow_target(cch_scene* s, const double* x, double beta, double alpha, double sign,
+                                  int32_t iters, double* y);
+
+/* Friction by velocity filtering (Sec. 6.3) on the frictionless target y.
+ * Every pair of a collision vertex p and a triangle t not containing it,
+ * closer than reach at x (closest point by the triangle's Voronoi regions)
+ * and with a vertex of positive inverse mass, is a contact with normal n
+ * from the closest point to p.  With u the relative target displacement of
+ * p against the closest point and pen = sep - (d + n.u): if pen > 0, the
+ * relative correction pen n - min(mu pen, |u_t|) u_t/|u_t| is shared by
+ * inverse mass (p: m_p^-1 / W, corner i: -w_i m_i^-1 / W, W = m_p^-1 +
+ * sum w_i^2 m_i^-1) and each vertex moves by the mean of its corrections.
+ * y_out receives the filtered target (it may alias y).  mu >= 0, reach > 0,
+ * sep >= 0. */
+cch_status cch_friction_filter(cch_scene* s, const double* x, const double* y, double* y_out, double mu,
+                               double reach, double sep);
 
 /* ---- profiling -----------------------------------------------------------
  * With profiling on, steps launch kernels directly (no CUDA graphs) and
@@ -257,7 +325,8 @@ cch_status cch_query_pairs_noalloc(cch_scene* s, const double* x, const double* 
  * query, 4 distance refresh, 5 contact assembly, 6 sweep order (per-vertex
  * ranks), 7 backward sweeps (Gauss-Seidel or Jacobi), 8 forward step, 9 loop
  * control, 10 step set-up (inputs, BVH build), 11 output, 12 exact FP64 stage
- * of the search.  cch_set_profiling resets the accumulators;
+ * of the search, 13 colouring of the contacts (Gauss-Seidel).
+ * cch_set_profiling resets the accumulators;
  * cch_get_profile returns, per group, the summed milliseconds and the number
  * of timed launches (n entries). */
 cch_status cch_set_profiling(cch_scene* s, int32_t on);

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcch.so")
-UNITS = ["cch_bvh.cu", "cch_step.cu", "cch_capi.cu"]
+UNITS = ["cch_bvh.cu", "cch_step.cu", "cch_capi.cu", "cch_prepass.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-O3"]
 

@@ -39,7 +39,8 @@ class Params(C.Structure):
                 ("solver", C.c_int32), ("ccd_check", C.c_int32), ("accept_check", C.c_int32),
                 ("validate_input", C.c_int32), ("iters_per_launch", C.c_int32), ("bvh_refit_only", C.c_int32),
                 ("constraint_form", C.c_int32), ("step_rule", C.c_int32), ("ccd_rounds", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("max_polls", C.c_int32), ("pair_capacity", C.c_int32),
+                ("sweep_blocks", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class Topology(C.Structure):
@@ -55,7 +56,8 @@ class StepStats(C.Structure):
                 ("max_vertex_contacts", C.c_int32), ("max_vertex_edges", C.c_int32), ("final_r_inf", C.c_double),
                 ("min_pair_dist", C.c_double), ("intersections", C.c_int64), ("uncertain", C.c_int64),
                 ("device_ms", C.c_double), ("kernel_launches", C.c_int64), ("gs_depth", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("frozen_vertices", C.c_int32), ("contact_vertices", C.c_int64), ("contact_colours", C.c_int32),
+                ("edge_colours", C.c_int32), ("pair_vertices", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -106,11 +108,14 @@ def lib():
             L.cch_set_profiling.argtypes = [p, i32]
             L.cch_get_profile.argtypes = [p, p, p, i32]
             L.cch_autotune.argtypes = [p, p, p, i32, C.POINTER(TuneResult)]
+            L.cch_set_max_polls.argtypes = [p, i32]
+            L.cch_normal_flow_target.argtypes = [p, p, d, d, d, i32, p]
+            L.cch_friction_filter.argtypes = [p, p, p, p, d, d, d]
             for f in ("cch_params_default", "cch_create_scene", "cch_create_batch", "cch_handle_step",
                       "cch_handle_step_host", "cch_batch_handle_step", "cch_destroy", "cch_query_pairs",
                       "cch_server_create", "cch_server_add_scene", "cch_server_submit", "cch_server_wait",
                       "cch_server_destroy", "cch_set_profiling", "cch_get_profile", "cch_query_pairs_noalloc",
-                      "cch_autotune"):
+                      "cch_autotune", "cch_set_max_polls", "cch_normal_flow_target", "cch_friction_filter"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -232,17 +237,20 @@ class Scene:
         _check(lib().cch_batch_handle_step(self.h, a, b, o, st), "cch_batch_handle_step")
         return outs, [s.as_dict() for s in st]
 
-    def query_pairs(self, x, x_ref, D: float, candidates: bool):
-        """Candidate set (candidates=True) or proximity set P at bound D."""
+    def query_pairs(self, x, x_ref, D: float, candidates: bool = False, step_search: bool = False):
+        """Candidate set (candidates=True), proximity set P at bound D with
+        exact distances, or (step_search=True) P as the first search of a
+        step forms it at the scene's D^max, with the distances it records."""
         n = self.topos[0].n
+        mode = 2 if step_search else int(bool(candidates))
         cnt = C.c_int64(0)
         _check(lib().cch_query_pairs(self.h, C.c_void_p(_dev_ptr(x, n)), C.c_void_p(_dev_ptr(x_ref, n)), float(D),
-                                     int(bool(candidates)), None, None, 0, C.byref(cnt)), "cch_query_pairs")
+                                     mode, None, None, 0, C.byref(cnt)), "cch_query_pairs")
         m = cnt.value
         keys = np.zeros(max(m, 1), np.uint64)
         dist = np.zeros(max(m, 1), np.float64)
         _check(lib().cch_query_pairs(self.h, C.c_void_p(_dev_ptr(x, n)), C.c_void_p(_dev_ptr(x_ref, n)), float(D),
-                                     int(bool(candidates)), C.c_void_p(keys.ctypes.data),
+                                     mode, C.c_void_p(keys.ctypes.data),
                                      C.c_void_p(dist.ctypes.data), m, C.byref(cnt)), "cch_query_pairs")
         o = np.argsort(keys[:m], kind="stable")
         return keys[:m][o], dist[:m][o]
@@ -267,6 +275,32 @@ class Scene:
         o = np.argsort(keys[:m], kind="stable")
         return keys[:m][o], dist[:m][o]
 
+    def normal_flow_target(self, x, beta: float, alpha: float, sign: float, iters: int = 3, out=None):
+        """Target of the normal flow of Sec. 7.4 at x (device tensors)."""
+        import torch
+        n = self.topos[0].n
+        if out is None:
+            out = torch.empty_like(x)
+        _check(lib().cch_normal_flow_target(self.h, C.c_void_p(_dev_ptr(x, n)), float(beta), float(alpha),
+                                            float(sign), int(iters), C.c_void_p(_dev_ptr(out, n))),
+               "cch_normal_flow_target")
+        return out
+
+    def friction_filter(self, x, y, mu: float, reach: float, sep: float, out=None):
+        """Velocity filter of Sec. 6.3 on the frictionless target y (device tensors)."""
+        import torch
+        n = self.topos[0].n
+        if out is None:
+            out = torch.empty_like(y)
+        _check(lib().cch_friction_filter(self.h, C.c_void_p(_dev_ptr(x, n)), C.c_void_p(_dev_ptr(y, n)),
+                                         C.c_void_p(_dev_ptr(out, n)), float(mu), float(reach), float(sep)),
+               "cch_friction_filter")
+        return out
+
+    def set_max_polls(self, max_polls: int):
+        """Bound of the scene's bounded device waits (0 = the default)."""
+        _check(lib().cch_set_max_polls(self.h, int(max_polls)), "cch_set_max_polls")
+
     def autotune(self, x_t, x_tilde, probe_iters: int = 64):
         """Times launch configurations on a probe step from (x_t, x_tilde) and
         keeps the fastest for later steps; returns the choice and timings."""
@@ -277,7 +311,7 @@ class Scene:
         return r.as_dict()
 
     PROFILE_GROUPS = ("refit", "query_vt", "query_ee", "query_vv", "refresh", "assemble", "order", "sweep",
-                      "forward", "control", "setup", "output", "finalize")
+                      "forward", "control", "setup", "output", "finalize", "colour")
 
     def set_profiling(self, on: bool):
         _check(lib().cch_set_profiling(self.h, int(bool(on))), "cch_set_profiling")

@@ -60,11 +60,6 @@ __device__ __forceinline__ void prim_box(const Pool& P, int c, int id, dv3& lo, 
 
 // Conservative float version used for pruning: boxes rounded outward, gaps
 // rounded down, D rounded up; it never rejects what box_near accepts.
-__device__ __forceinline__ bool fbox_near(float4 lo, float4 hi, float3 qlo, float3 qhi, float Df) {
-  return __fsub_rd(lo.x, qhi.x) <= Df && __fsub_rd(qlo.x, hi.x) <= Df && __fsub_rd(lo.y, qhi.y) <= Df &&
-         __fsub_rd(qlo.y, hi.y) <= Df && __fsub_rd(lo.z, qhi.z) <= Df && __fsub_rd(qlo.z, hi.z) <= Df;
-}
-
 __device__ __forceinline__ BVH& bvh_of(Pool& P, int c) { return c == 0 ? P.bt : (c == 1 ? P.be : P.bv); }
 __device__ __forceinline__ int nprim(const Pool& P, int c) { return c == 0 ? P.nt : (c == 1 ? P.ne : P.nvc); }
 
@@ -325,57 +320,6 @@ __device__ __forceinline__ void child_box(const BVH& B, int child, float4& lo, f
 // ---------------------------------------------------------------------------
 // queries
 // ---------------------------------------------------------------------------
-// traversal skeleton: calls leaf(pos) for every leaf whose box passes the
-// conservative float test against the query box
-template <class LeafFn>
-__device__ __forceinline__ void traverse(const BVH& B, int root, float3 qlo, float3 qhi, float Df, int min_pos,
-                                         Counters* cnt, LeafFn leaf) {
-  if (root < 0) return;
-  if (root & LEAF) {
-    int l = root & ~LEAF;
-    if (l > min_pos) {
-      float4 lo = B.leafbox[2 * l], hi = B.leafbox[2 * l + 1];
-      if (fbox_near(lo, hi, qlo, qhi, Df)) leaf(l);
-    }
-    return;
-  }
-  int stack[64];
-  int sp = 0;
-  stack[sp++] = root;
-  // a valid tree visits each internal node at most once per query
-  int budget = B.n + 2;
-  while (sp > 0) {
-    if (--budget < 0) {
-      atomicOr(&cnt->err, ERR_BUDGET);
-      return;
-    }
-    int node = stack[--sp];
-    if (B.range_hi[node] <= min_pos) continue;
-    float4 a = B.box[3 * node], b = B.box[3 * node + 1], d = B.box[3 * node + 2];
-    float4 llo = make_float4(a.x, a.y, a.z, 0.f), lhi = make_float4(a.w, b.x, b.y, 0.f);
-    float4 rlo = make_float4(b.z, b.w, d.x, 0.f), rhi = make_float4(d.y, d.z, d.w, 0.f);
-    int L = B.left[node], R = B.right[node];
-    bool hl = fbox_near(llo, lhi, qlo, qhi, Df), hr = fbox_near(rlo, rhi, qlo, qhi, Df);
-    if (hr) {
-      if (R & LEAF) { if ((R & ~LEAF) > min_pos) leaf(R & ~LEAF); }
-      else if (sp < 64) stack[sp++] = R;
-      else atomicOr(&cnt->err, ERR_STACK);
-    }
-    if (hl) {
-      if (L & LEAF) { if ((L & ~LEAF) > min_pos) leaf(L & ~LEAF); }
-      else if (sp < 64) stack[sp++] = L;
-      else atomicOr(&cnt->err, ERR_STACK);
-    }
-  }
-}
-
-__device__ __forceinline__ float3 f3rd(dv3 a) {
-  return make_float3(__double2float_rd(a.x), __double2float_rd(a.y), __double2float_rd(a.z));
-}
-__device__ __forceinline__ float3 f3ru(dv3 a) {
-  return make_float3(__double2float_ru(a.x), __double2float_ru(a.y), __double2float_ru(a.z));
-}
-
 // A pair that the FP32 filter could not reject; the exact FP64 distance is
 // evaluated later by k_finalize with one pair per thread (full warps instead
 // of the few lanes still active inside a divergent traversal).

@@ -131,6 +131,7 @@ cch_status validate_params(const cch_params* p) {
   if (p->step_rule != CCH_STEP_DISTANCE && p->step_rule != CCH_STEP_CCD) return CCH_E_INVALID_ARG;
   if (p->ccd_rounds < 0 || p->ccd_rounds > 64) return CCH_E_INVALID_ARG;
   if (p->iters_per_launch < 0 || p->iters_per_launch > 4096) return CCH_E_INVALID_ARG;
+  if (p->max_polls < 0 || p->pair_capacity < 0 || p->sweep_blocks < 0) return CCH_E_INVALID_ARG;
   return CCH_OK;
 }
 
@@ -167,7 +168,8 @@ cudaError_t alloc_pairs(Runtime& R) {
     if ((e = dalloc_in(L, &P.fbr, (size_t)P.pair_cap)) != cudaSuccess) return e;
   }
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
-  if ((e = dalloc_in(L, &P.fdone, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.fdone, (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.ccol, (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.iprio, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.iid, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.rank, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
@@ -277,11 +279,16 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   R.solver = prm->solver;
   R.ccd = prm->ccd_check || prm->step_rule == CCH_STEP_CCD;
   R.ccd_rounds = prm->ccd_rounds;
-  R.accept = prm->accept_check;
+  // the CCD-based step relies on the root-finding CCD, which can miss a
+  // tangential touch at a double root of the coplanarity cubic: the exact
+  // acceptance of x^{t+1} always runs with it
+  R.accept = prm->accept_check || prm->step_rule == CCH_STEP_CCD;
   R.validate = prm->validate_input;
   R.iters_per_check = prm->iters_per_launch > 0 ? prm->iters_per_launch : 16;
   R.refit_only = prm->bvh_refit_only ? 1 : 0;
   R.coop_blocks = coop_grid(256);
+  if (prm->sweep_blocks > 0 && prm->sweep_blocks < R.coop_blocks) R.coop_blocks = prm->sweep_blocks;
+  R.max_polls = prm->max_polls > 0 ? prm->max_polls : 1 << 22;
 
   CK(dalloc(R, &P.x, nv));
   CK(dalloc(R, &P.y, nv));
@@ -321,7 +328,10 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaMemset(P.ss, 0, sizeof(SceneState) * n_scenes));
   CK(dalloc(R, &P.cnt, 1));
   CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
-  CK(dalloc(R, &P.vlevel, nv));
+  CK(dalloc(R, &P.cmask, (size_t)nv * 32));
+  CK(dalloc(R, &P.chw, nv));
+  CK(dalloc(R, &P.bar, 2));
+  CK(cudaMemset(P.bar, 0, 2 * sizeof(unsigned int)));
   CK(dalloc(R, &P.vmin, nv));
   P.vlstart = nullptr;
   P.vllist = nullptr;
@@ -342,6 +352,24 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
     CK(upload(R, &P.vlstart, vls));
     CK(upload(R, &P.vllist, vll));
   }
+  {
+    // per-vertex lists of incident triangle corners (the pre-passes' gathers)
+    std::vector<int> ts((size_t)nv + 1, 0), tl(3 * (size_t)nt);
+    for (int t = 0; t < nt; t++) {
+      ts[tv[t].x + 1]++;
+      ts[tv[t].y + 1]++;
+      ts[tv[t].z + 1]++;
+    }
+    for (int v = 0; v < nv; v++) ts[v + 1] += ts[v];
+    std::vector<int> fill(ts.begin(), ts.end() - 1);
+    for (int t = 0; t < nt; t++) {
+      tl[fill[tv[t].x]++] = 3 * t;
+      tl[fill[tv[t].y]++] = 3 * t + 1;
+      tl[fill[tv[t].z]++] = 3 * t + 2;
+    }
+    CK(upload(R, &P.tinc_start, ts));
+    CK(upload(R, &P.tinc, tl));
+  }
   CK(dalloc(R, &P.sbox, 2 * (size_t)n_scenes));
   CK(alloc_bvh(R, P.bt, nt, n_scenes));
   CK(alloc_bvh(R, P.be, ne, n_scenes));
@@ -359,41 +387,51 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(dalloc(R, &R.obuf.vfill, nv));
   CK(dalloc(R, &R.obuf.vdone, nv));
   {
-    // sweep order of the edge-length constraints (topology only): the rank
-    // of each edge among the edges of each of its vertices, by descending
-    // priority splitmix64(seed ^ key), key = 3 << 62 | local edge index
-    std::vector<int> edeg(nv, 0), estart((size_t)nv + 1, 0), elist(2 * (size_t)nl);
+    // Colour classes of the edge-length constraints (topology only; Sec.
+    // 4.3, reading R11): taken by descending priority splitmix64(seed ^ key),
+    // key = 3 << 62 | local edge index, each edge gets the smallest colour
+    // not used by an earlier edge at one of its movable vertices.
     std::vector<unsigned long long> eprio(nl);
+    std::vector<int> order(nl), edeg(nv, 0);
     for (int e = 0; e < nl; e++) {
       const SceneDesc& d = R.sd[lv[e].z];
       eprio[e] = splitmix64(d.seed ^ ((3ULL << 62) | (unsigned long long)(e - d.l0)));
+      order[e] = e;
       edeg[lv[e].x]++;
       edeg[lv[e].y]++;
     }
-    for (int v = 0; v < nv; v++) estart[v + 1] = estart[v] + edeg[v];
-    std::vector<int> fill(estart.begin(), estart.end() - 1);
-    for (int e = 0; e < nl; e++) {
-      elist[fill[lv[e].x]++] = 2 * e;
-      elist[fill[lv[e].y]++] = 2 * e + 1;
-    }
-    std::vector<int2> erank(nl);
     R.max_vedges = 0;
-    for (int v = 0; v < nv; v++) {
-      int a = estart[v], b = estart[v + 1];
-      std::sort(elist.begin() + a, elist.begin() + b,
-                [&](int p, int q) { return eprio[p >> 1] > eprio[q >> 1]; });
-      for (int r = 0; r < b - a; r++) {
-        int ent = elist[a + r];
-        if (ent & 1) erank[ent >> 1].y = r;
-        else erank[ent >> 1].x = r;
-      }
-      if ((vflag[v] & VF_MOVABLE) && b - a > R.max_vedges) R.max_vedges = b - a;
+    for (int v = 0; v < nv; v++)
+      if ((vflag[v] & VF_MOVABLE) && edeg[v] > R.max_vedges) R.max_vedges = edeg[v];
+    std::sort(order.begin(), order.end(), [&](int p, int q) { return eprio[p] > eprio[q]; });
+    std::vector<std::vector<int>> used(nv);
+    std::vector<int> ecol(nl, 0);
+    std::vector<char> taken;
+    P.n_ecol = 0;
+    for (int e : order) {
+      int ends[2] = {lv[e].x, lv[e].y};
+      size_t tot = 0;
+      for (int v : ends)
+        if (vflag[v] & VF_MOVABLE) tot += used[v].size();
+      taken.assign(tot + 1, 0);
+      for (int v : ends)
+        if (vflag[v] & VF_MOVABLE)
+          for (int c : used[v])
+            if ((size_t)c <= tot) taken[c] = 1;
+      int c = 0;
+      while (taken[c]) c++;
+      ecol[e] = c;
+      for (int v : ends)
+        if (vflag[v] & VF_MOVABLE) used[v].push_back(c);
+      SceneDesc& d = R.sd[lv[e].z];
+      if (c + 1 > d.n_ecol) d.n_ecol = c + 1;
+      if (c + 1 > P.n_ecol) P.n_ecol = c + 1;
     }
-    CK(upload(R, &P.edeg, edeg));
-    CK(upload(R, &P.erank, erank));
+    CK(upload(R, &P.ecol, ecol));
+    CK(cudaMemcpy(P.sd, R.sd.data(), sizeof(SceneDesc) * R.sd.size(), cudaMemcpyHostToDevice));
   }
   // pair-sized buffers last (they are re-allocated on growth)
-  long long guess = 4LL * (nt + ne + nq) + 4096;
+  long long guess = prm->pair_capacity > 0 ? (long long)prm->pair_capacity : 4LL * (nt + ne + nq) + 4096;
   if (guess > (1LL << 30)) guess = 1LL << 30;
   set_caps(R, (int)guess);
   CK(alloc_pairs(R));
@@ -441,7 +479,7 @@ cudaError_t capture_graph(Runtime& R) {
   return e;
 }
 
-void fill_stats(const Runtime& R, const SceneState& S, cch_step_stats* st, float ms) {
+void fill_stats(const Runtime& R, int s, const SceneState& S, cch_step_stats* st, float ms) {
   st->iterations = S.iter;
   st->searches = S.searches;
   st->converged = S.converged;
@@ -453,7 +491,8 @@ void fill_stats(const Runtime& R, const SceneState& S, cch_step_stats* st, float
   st->degenerate = S.degenerate;
   st->max_vertex_contacts = S.max_vcontacts;
   st->max_vertex_edges = R.max_vedges;
-  st->gs_depth = S.max_depth;
+  // the sweep's critical path: one phase per colour class
+  st->gs_depth = R.solver == CCH_SOLVER_GAUSS_SEIDEL ? S.ccol + R.sd[s].n_ecol : 0;
   st->final_r_inf = S.final_r;
   union { unsigned long long u; double d; } b;
   b.u = S.mind_bits;
@@ -461,6 +500,11 @@ void fill_stats(const Runtime& R, const SceneState& S, cch_step_stats* st, float
   st->intersections = S.isect;
   st->uncertain = S.uncertain;
   st->device_ms = ms;
+  st->frozen_vertices = S.frozen;
+  st->contact_vertices = S.cverts;
+  st->pair_vertices = S.pverts;
+  st->contact_colours = S.ccol;
+  st->edge_colours = R.sd[s].n_ecol;
 }
 
 // Accumulates the event times of the kernel groups recorded since the last call.
@@ -563,7 +607,7 @@ cch_status run_step(cch_scene* S, cch_step_stats* stats) {
     cudaEventElapsedTime(&ms, R.ev0, R.ev1);
     if (stats)
       for (int s = 0; s < S->n_scenes; s++) {
-        fill_stats(R, R.h_ss[s], &stats[s], ms);
+        fill_stats(R, s, R.h_ss[s], &stats[s], ms);
         stats[s].kernel_launches = R.launches - launches0;
       }
     return CCH_OK;
@@ -797,10 +841,62 @@ cch_status cch_destroy(cch_scene* S) {
   return CCH_OK;
 }
 
+cch_status cch_set_max_polls(cch_scene* S, int32_t max_polls) {
+  if (!S || max_polls < 0) return CCH_E_INVALID_ARG;
+  S->R.max_polls = max_polls > 0 ? max_polls : 1 << 22;
+  if (S->R.graph) cudaGraphExecDestroy(S->R.graph);  // the bound is a kernel argument
+  S->R.graph = nullptr;
+  return CCH_OK;
+}
+
+namespace {
+// P as the first search of a step forms it (want_candidates = 2): the
+// step's own search kernels at D^max write the pair buffer, which is copied
+// out.
+cch_status query_step_search(cch_scene* S, const double* x, const double* x_ref, uint64_t* keys, double* dist,
+                             int64_t cap, int64_t* count) {
+  Runtime& R = S->R;
+  Pool& P = R.pool;
+  cudaStream_t st = R.stream;
+  for (int attempt = 0; attempt < 32; attempt++) {
+    R.h_ptrs[0] = (double*)x;
+    R.h_ptrs[1] = (double*)x_ref;
+    R.h_ptrs[2] = nullptr;
+    CK(cudaMemcpyAsync(R.d_ptrs, R.h_ptrs, sizeof(double*) * 3, cudaMemcpyHostToDevice, st));
+    step_init(R, st, 0);
+    set_any_search(R, st);
+    bvh_build_all(R, st);
+    bvh_refit_all(R, st, 1);
+    for (int c = 0; c < 3; c++) query_class(R, c, 1, 0, 0.0, st);
+    if (!P.mixed) CK(cudaMemsetAsync(P.vmin, 0xff, sizeof(unsigned int) * (size_t)P.nv, st));
+    finalize_search(R, 1, 0, 0.0, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (R.h_cnt->err) return device_status(R.h_cnt->err);
+    if (R.h_cnt->overflow & (OV_PAIRS | OV_CONTACTS)) {
+      cch_status g = grow_pairs(R);
+      if (g != CCH_OK) return g;
+      continue;
+    }
+    int n = R.h_cnt->n_pairs[1];
+    *count = n;
+    int64_t m = n < cap ? n : cap;
+    if (m > 0) {
+      CK(cudaMemcpy(keys, P.pb[1].key, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost));
+      if (dist) CK(cudaMemcpy(dist, P.pb[1].d, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    }
+    return CCH_OK;
+  }
+  return CCH_E_CAPACITY;
+}
+}  // namespace
+
 cch_status cch_query_pairs(cch_scene* S, const double* x, const double* x_ref, double D, int32_t want_candidates,
                            uint64_t* keys, double* dist, int64_t cap, int64_t* count) {
   if (!S || !x || !x_ref || !count || !(D >= 0.0) || cap < 0 || (cap > 0 && !keys)) return CCH_E_INVALID_ARG;
-  if (S->n_scenes != 1) return CCH_E_INVALID_ARG;
+  if (S->n_scenes != 1 || want_candidates < 0 || want_candidates > 2) return CCH_E_INVALID_ARG;
+  if (want_candidates == 2) return query_step_search(S, x, x_ref, keys, dist, cap, count);
   Runtime& R = S->R;
   Pool& P = R.pool;
   cudaStream_t st = R.stream;
@@ -877,7 +973,7 @@ cch_status cch_query_pairs_noalloc(cch_scene* S, const double* x, const double* 
                                    int32_t want_candidates, uint64_t* keys, double* dist, int64_t cap,
                                    int64_t* count) {
   if (!S || !x || !x_ref || !count || !(D >= 0.0) || cap < 0 || (cap > 0 && !keys)) return CCH_E_INVALID_ARG;
-  if (S->n_scenes != 1) return CCH_E_INVALID_ARG;
+  if (S->n_scenes != 1 || want_candidates < 0 || want_candidates > 1) return CCH_E_INVALID_ARG;
   Runtime& R = S->R;
   cudaStream_t st = R.stream;
   void* scratch = nullptr;
@@ -904,16 +1000,67 @@ cch_status cch_query_pairs_noalloc(cch_scene* S, const double* x, const double* 
   R.pool = saved;
   if (e != cudaSuccess) return cuda_fail(e);
   if (R.h_cnt->err) return device_status(R.h_cnt->err);
+  // the scene's pair buffers overflowed: the query's result is incomplete
+  // and its full count unknown
+  if (R.h_cnt->overflow & OV_PAIRS) {
+    *count = -1;
+    return CCH_E_CAPACITY;
+  }
   int64_t n = R.h_cnt->n_query;
   if (n < 0) n = (int64_t)1 << 31;  // the counter passed 2^31
   *count = n;
-  // more pairs than the array holds, or than the scene's pair buffers hold
-  if (n > CCH_NOALLOC_MAX_PAIRS || (R.h_cnt->overflow & OV_PAIRS)) return CCH_E_CAPACITY;
+  // more pairs than the array holds
+  if (n > CCH_NOALLOC_MAX_PAIRS) return CCH_E_CAPACITY;
   int64_t m = n < cap ? n : cap;
   if (m > 0) {
     CK(cudaMemcpy(keys, used.qkeys, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost));
     if (dist) CK(cudaMemcpy(dist, used.qdist, sizeof(double) * m, cudaMemcpyDeviceToHost));
   }
+  return CCH_OK;
+}
+
+cch_status cch_normal_flow_target(cch_scene* S, const double* x, double beta, double alpha, double sign,
+                                  int32_t iters, double* y) {
+  if (!S || S->n_scenes != 1 || !x || !y || x == y || iters < 0 || iters > 64) return CCH_E_INVALID_ARG;
+  if (!std::isfinite(beta) || !std::isfinite(alpha) || !std::isfinite(sign)) return CCH_E_INVALID_ARG;
+  Runtime& R = S->R;
+  cudaStream_t st = R.stream;
+  // the second buffer of the Jacobi steps: the pool's y array (free between steps)
+  double* tmp = nullptr;
+  if (iters > 0) {
+    static_assert(sizeof(P4) >= 3 * sizeof(double), "");
+    tmp = (double*)R.pool.y;
+  }
+  normal_flow(R, x, y, tmp, sign * beta, alpha, iters, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return CCH_OK;
+}
+
+cch_status cch_friction_filter(cch_scene* S, const double* x, const double* y, double* y_out, double mu,
+                               double reach, double sep) {
+  if (!S || S->n_scenes != 1 || !x || !y || !y_out) return CCH_E_INVALID_ARG;
+  if (!(mu >= 0.0) || !(reach > 0.0) || !(sep >= 0.0) || !std::isfinite(mu) || !std::isfinite(reach) ||
+      !std::isfinite(sep))
+    return CCH_E_INVALID_ARG;
+  Runtime& R = S->R;
+  Pool& P = R.pool;
+  cudaStream_t st = R.stream;
+  // positions and target into the pool, BVHs at x
+  R.h_ptrs[0] = (double*)x;
+  R.h_ptrs[1] = (double*)y;
+  R.h_ptrs[2] = nullptr;
+  CK(cudaMemcpyAsync(R.d_ptrs, R.h_ptrs, sizeof(double*) * 3, cudaMemcpyHostToDevice, st));
+  step_init(R, st, 0);
+  bvh_build_all(R, st);
+  bvh_refit_all(R, st, 1);
+  friction(R, mu, reach, sep, y_out, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(R.h_cnt, P.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(R.h_ss, P.ss, sizeof(SceneState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (R.h_ss[0].bad_input) return CCH_E_INVALID_ARG;
+  if (R.h_cnt->err) return device_status(R.h_cnt->err);
   return CCH_OK;
 }
 
@@ -1151,7 +1298,7 @@ void server_loop(cch_server* sv) {
     }
     for (int s : ends) {
       Request& r = sv->reqs[(uint64_t)sv->running[s]];
-      fill_stats(R, R.h_ss[s], &r.stats, 0.f);
+      fill_stats(R, s, R.h_ss[s], &r.stats, 0.f);
       r.state = 2;
       r.status = R.h_ss[s].bad_input ? CCH_E_INVALID_ARG : CCH_OK;
       r.t_done = now;

@@ -36,6 +36,7 @@ struct SceneDesc {
   double rho_max;  // largest point radius of the scene
   int max_iters, gs_sweeps, solver, ccd;
   int step_rule;                  // 0 distance bound (Eq. forward2), 1 CCD-based
+  int n_ecol;                     // colours of the edge-length constraints
   uint64_t seed;
 };
 
@@ -55,13 +56,17 @@ struct SceneState {
   long long pairs_eval, max_pairs, contacts, candidates, degenerate;
   int n_pairs;                    // |P| of this iteration
   int max_vcontacts;              // most contacts at one movable vertex in an iteration
-  int max_depth;                  // longest dependency chain of one backward step
   int ccd_clamps;
   double final_r;
   long long isect, uncertain;
   int bad_input;                  // x_t or x~ held a non-finite coordinate
   int ccd_live;                   // the CCD rounds of this iteration go on
   int ccd_hits[2];                // hits of the current CCD round (by parity)
+  int frozen_cur;                 // vertices held by the D_i floor in this iteration
+  int frozen;                     // the same count at the last finished iteration
+  long long cverts;               // sum over iterations of distinct movable contact vertices
+  long long pverts;               // sum over iterations of distinct vertices of P
+  int ccol;                       // most contact colours of one iteration
   int pad_;
 };
 
@@ -71,7 +76,6 @@ struct Counters {
   int n_active;         // active contact candidates (dist < delta)
   int n_cons;           // assembled contact constraints
   int vcontacts;        // most contacts at one movable vertex (this iteration)
-  int depth;            // longest dependency chain of this backward step
   int overflow;         // OV_* bits
   int err;              // first error code
   int any_search;       // some active scene searches in this iteration
@@ -81,11 +85,12 @@ struct Counters {
   int n_fcand[3];       // FP32-filter survivors per pair kind (VT, EE, VV)
   int any_refresh;      // some active scene reuses P in this iteration
   int ccd_hit;
-  int pad;
+  int n_ccol;           // colours of this iteration's contact colouring
 };
 enum { OV_PAIRS = 1, OV_CONTACTS = 2, OV_QUERY = 16 };
-// error bits of Counters::err
-enum { ERR_STACK = 2, ERR_BUDGET = 4, ERR_TREE = 8, ERR_POLL = 16 };
+// error bits of Counters::err (ERR_COLOURS: a contact needed more colours
+// than the colouring's masks hold)
+enum { ERR_STACK = 2, ERR_BUDGET = 4, ERR_TREE = 8, ERR_POLL = 16, ERR_COLOURS = 32 };
 
 // Proximity pair (SoA arrays in the pool).
 struct PairBuf {
@@ -155,9 +160,8 @@ struct Pool {
   int4* ev;                // a, b, scene, -
   int4* lv;                // i, j, scene, -
   P4* lg;                  // per edge-length constraint: g = u/L0 (xyz), den (w)
-  int* edeg;               // per vertex: edge-length constraints at it
-  int2* erank;             // per edge-length constraint: its rank at vertex i and
-                           // at vertex j among that vertex's edges, by descending priority
+  int* tinc_start;         // per vertex: start into tinc (nv + 1)
+  int* tinc;               // incident triangle corners, ascending: triangle * 3 + corner
   int* vc;                 // collision vertices (pool ids), scene-contiguous
   int* pts;                // point vertices
   SceneDesc* sd;
@@ -172,8 +176,13 @@ struct Pool {
   float2* fbr;             // FP64 mode: refreshed pairs' FP32 bounds (pair_cap)
   unsigned int* vmin;      // per vertex: smallest upper bound of a certain pair (fl_ord image)
   Contact* cons;
-  unsigned char* fdone;    // Gauss-Seidel sweep: applied flags (cons_cap + nl)
-  int* vlevel;             // per vertex: chain length of its last applied constraint
+  unsigned char* fdone;    // contact colouring: coloured flags (cons_cap)
+  int* ccol;               // per contact: colour class of the iteration (cons_cap)
+  unsigned long long* cmask;  // per vertex: colours used there so far (CW words)
+  int* chw;                // per vertex: mask words in use
+  int* ecol;               // per edge-length constraint: colour class (fixed)
+  int n_ecol;              // edge colours (most over the scenes)
+  unsigned int* bar;       // grid barrier of the sweep: arrivals, generation
   double* lam;             // multipliers for gs_sweeps > 1 (contacts then edges)
   double* jdl;             // projected Jacobi: dl per contact, then per edge (cons_cap + nl)
   int* vlstart;            // projected Jacobi: per vertex, start into vllist (nv + 1)

@@ -16,7 +16,7 @@ namespace cg = cooperative_groups;
 // Kernel groups timed by the profiling mode (CUDA events on the stream).
 enum ProfGroup {
   PG_REFIT, PG_VT, PG_EE, PG_VV, PG_REFRESH, PG_ASSEMBLE, PG_ORDER, PG_SWEEP, PG_FORWARD, PG_CONTROL, PG_SETUP,
-  PG_OUTPUT, PG_FINAL, PG_N
+  PG_OUTPUT, PG_FINAL, PG_COLOUR, PG_N
 };
 
 // Per-vertex incidence lists of the contacts of one iteration (see
@@ -39,7 +39,8 @@ struct Runtime {
   std::vector<void*> pair_allocs;    // pair-sized buffers (grown on overflow)
   cudaStream_t stream = nullptr;
   int scene_bits = 0;                // bits of the scene index in Morton keys
-  int coop_blocks = 0;               // grid of the cooperative sweep kernel
+  int coop_blocks = 0;               // grid of the cooperative colouring and sweep kernels
+  int max_polls = 1 << 22;           // bound of one device wait (polls)
   int sweeps = 1, solver = 0, ccd = 0, accept = 0, validate = 0;
   int ccd_rounds = 8;  // CCD clamp rounds per iteration
   int max_iters = 0;                 // max over scenes
@@ -202,6 +203,65 @@ __device__ __forceinline__ void emit_query(Pool& P, unsigned long long key, doub
 }
 
 __device__ __forceinline__ bool is_static(const Pool& P, int v) { return (P.vflag[v] & VF_STATIC) != 0; }
+
+
+// conservative float box test of the BVH traversal: every axis gap of the
+// two boxes, rounded down, at most Df
+__device__ __forceinline__ bool fbox_near(float4 lo, float4 hi, float3 qlo, float3 qhi, float Df) {
+  return __fsub_rd(lo.x, qhi.x) <= Df && __fsub_rd(qlo.x, hi.x) <= Df && __fsub_rd(lo.y, qhi.y) <= Df &&
+         __fsub_rd(qlo.y, hi.y) <= Df && __fsub_rd(lo.z, qhi.z) <= Df && __fsub_rd(qlo.z, hi.z) <= Df;
+}
+
+// traversal skeleton: calls leaf(pos) for every leaf whose box passes the
+// conservative float test against the query box
+template <class LeafFn>
+__device__ __forceinline__ void traverse(const BVH& B, int root, float3 qlo, float3 qhi, float Df, int min_pos,
+                                         Counters* cnt, LeafFn leaf) {
+  if (root < 0) return;
+  if (root & LEAF) {
+    int l = root & ~LEAF;
+    if (l > min_pos) {
+      float4 lo = B.leafbox[2 * l], hi = B.leafbox[2 * l + 1];
+      if (fbox_near(lo, hi, qlo, qhi, Df)) leaf(l);
+    }
+    return;
+  }
+  int stack[64];
+  int sp = 0;
+  stack[sp++] = root;
+  // a valid tree visits each internal node at most once per query
+  int budget = B.n + 2;
+  while (sp > 0) {
+    if (--budget < 0) {
+      atomicOr(&cnt->err, ERR_BUDGET);
+      return;
+    }
+    int node = stack[--sp];
+    if (B.range_hi[node] <= min_pos) continue;
+    float4 a = B.box[3 * node], b = B.box[3 * node + 1], d = B.box[3 * node + 2];
+    float4 llo = make_float4(a.x, a.y, a.z, 0.f), lhi = make_float4(a.w, b.x, b.y, 0.f);
+    float4 rlo = make_float4(b.z, b.w, d.x, 0.f), rhi = make_float4(d.y, d.z, d.w, 0.f);
+    int L = B.left[node], R = B.right[node];
+    bool hl = fbox_near(llo, lhi, qlo, qhi, Df), hr = fbox_near(rlo, rhi, qlo, qhi, Df);
+    if (hr) {
+      if (R & LEAF) { if ((R & ~LEAF) > min_pos) leaf(R & ~LEAF); }
+      else if (sp < 64) stack[sp++] = R;
+      else atomicOr(&cnt->err, ERR_STACK);
+    }
+    if (hl) {
+      if (L & LEAF) { if ((L & ~LEAF) > min_pos) leaf(L & ~LEAF); }
+      else if (sp < 64) stack[sp++] = L;
+      else atomicOr(&cnt->err, ERR_STACK);
+    }
+  }
+}
+
+__device__ __forceinline__ float3 f3rd(dv3 a) {
+  return make_float3(__double2float_rd(a.x), __double2float_rd(a.y), __double2float_rd(a.z));
+}
+__device__ __forceinline__ float3 f3ru(dv3 a) {
+  return make_float3(__double2float_ru(a.x), __double2float_ru(a.y), __double2float_ru(a.z));
+}
 
 
 // launchers (cch_bvh.cu)

@@ -37,11 +37,14 @@ __global__ void k_scene_init(Pool P, int mode) {
     S.pairs_eval = S.max_pairs = S.contacts = S.candidates = S.degenerate = 0;
     S.n_pairs = 0;
     S.max_vcontacts = 0;
-    S.max_depth = 0;
     S.ccd_clamps = 0;
     S.final_r = 1.0;
     S.isect = S.uncertain = 0;
     S.bad_input = 0;
+    S.frozen_cur = S.frozen = 0;
+    S.cverts = 0;
+    S.pverts = 0;
+    S.ccol = 0;
   }
 }
 
@@ -299,6 +302,13 @@ struct ContactFAcc {
 
 __device__ __forceinline__ bool movable(const Pool& P, int v) { return v >= 0 && (P.vflag[v] & VF_MOVABLE); }
 
+// one more distinct movable vertex with a contact in this iteration (statistics)
+__device__ __forceinline__ void count_contact_vertex(Pool& P, int s) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  auto part = cg::labeled_partition(g, s);
+  if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].cverts, (unsigned long long)part.size());
+}
+
 template <class Acc>
 __global__ void k_inc_count(Pool P, Acc acc, OrderBufs B) {
   int n = min(P.cnt->n_cons, P.cons_cap);
@@ -342,7 +352,10 @@ __global__ void k_inc_rank(Pool P, Acc acc, OrderBufs B) {
     int r = 0;
     for (int t = a; t < b; t++) r += B.iprio[t] > p;
     B.rank[id] = r;
-    if (r == 0) atomicMax(&P.cnt->vcontacts, b - a);
+    if (r == 0) {
+      atomicMax(&P.cnt->vcontacts, b - a);
+      count_contact_vertex(P, P.vscene[vert]);
+    }
   }
 }
 
@@ -480,149 +493,140 @@ __device__ __forceinline__ void pgs_edge(Pool& P, int e, int i, int j, double* l
 }
 
 // ---------------------------------------------------------------------------
-// One Gauss-Seidel sweep as a dataflow over vertex counters.  The paper
-// sweeps the colour classes of a randomized colouring with a barrier between
-// classes; here no barrier is needed.  A constraint is applied once the
-// counter of every one of its movable vertices (constraints applied there so
-// far) equals its rank at that vertex; it then increments those counters.
-// Constraints that share no movable vertex commute, so the result is exactly
-// the sequential sweep in the order above.  Sweep s of gs_sweeps starts at
-// counter s * (constraints at the vertex), so counters need no reset between
-// sweeps.
+// Multi-colour Gauss-Seidel (Sec. 4.3, readings R10 and R11).  The
+// constraints are split into colour classes of the greedy colouring in
+// descending priority: each constraint takes the smallest colour not used by
+// a higher-priority constraint sharing a movable vertex with it.  Contacts
+// are coloured among themselves every iteration (k_colour, below), the
+// edge-length constraints once per scene (on the host, from the topology).
+// The sweep then applies the contact classes in ascending colour, then the
+// edge classes, one class per phase of a persistent kernel, with a grid
+// barrier between phases; the constraints of one class share no movable
+// vertex, so the result equals the sequential sweep in that order bit for
+// bit.
 //
-// All blocks are resident (cooperative launch).  Each thread takes up to 32
-// constraints (i = tid + k * nth), sorts them into the sweep order and
-// applies them one after the other, waiting before each only for its own
-// vertex counters.  The earliest pending constraint of the whole sweep is at
-// the head of its thread's list and is ready, so the sweep always progresses.
-// With more constraints than 32 per thread, every thread polls all of its
-// pending constraints each round instead.  Waits are bounded and set
-// ERR_POLL past the bound.  The chain length of each applied constraint (one
-// more than the chain ending at its predecessors) gives the sweep's critical
-// path for the statistics.
+// The colouring itself is a dataflow over per-vertex counters: a contact is
+// coloured once the counter of every one of its movable vertices (contacts
+// coloured there so far) equals its rank at that vertex by priority.  It then
+// reads the colours already used at those vertices from per-vertex bit masks,
+// takes the smallest free one, records it in the masks and increments the
+// counters.  Contacts that share no movable vertex do not wait for each
+// other, so the colours equal the sequential greedy colouring.
 // ---------------------------------------------------------------------------
+constexpr int CW = 32;                  // 64-bit mask words per vertex
+constexpr int MAX_COLOURS = 64 * CW;    // colours one iteration may use
+
 struct SweepCtx {
   int nc;          // contacts (items [0, nc)); edge-length constraints follow
-  int sweep;
   double* lam;     // contact multipliers (gs_sweeps > 1), else null
   double* elam;    // edge multipliers
-  int levels;      // record chain lengths (statistics; costs a few percent)
 };
-
-__device__ __forceinline__ int contacts_at(const OrderBufs& B, int v) {
-  return __ldg(&B.vstart[v + 1]) - __ldg(&B.vstart[v]);
-}
-// counter value at which a constraint of rank r among the contacts (edge:
-// among the edges) of v may be applied in sweep s
-__device__ __forceinline__ int target_at(const Pool& P, const OrderBufs& B, int v, int s, int r, bool edge) {
-  int nct = contacts_at(B, v);
-  return s * (nct + __ldg(&P.edeg[v])) + (edge ? nct : 0) + r;
-}
 
 // the vertices an item waits on and the counter values it waits for
 struct ItemWait {
   int v[4];
-  int t[4];  // -1: no wait (vertex absent or not movable)
+  int t[4];  // -1: no wait (vertex absent or not movable); else the rank
 };
-__device__ __forceinline__ void item_wait(const Pool& P, const OrderBufs& B, const SweepCtx& X, int i, ItemWait& w) {
-  if (i < X.nc) {
-    int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
-    w.v[0] = v.x; w.v[1] = v.y; w.v[2] = v.z; w.v[3] = v.w;
-    for (int k = 0; k < 4; k++)
-      w.t[k] = movable(P, w.v[k]) ? target_at(P, B, w.v[k], X.sweep, __ldg(&B.rank[4 * i + k]), false) : -1;
-  } else {
-    int e = i - X.nc;
-    int4 l = P.lv[e];
-    int2 r = __ldg(&P.erank[e]);
-    w.v[0] = l.x; w.v[1] = l.y; w.v[2] = w.v[3] = -1;
-    w.t[0] = movable(P, l.x) ? target_at(P, B, l.x, X.sweep, r.x, true) : -1;
-    w.t[1] = movable(P, l.y) ? target_at(P, B, l.y, X.sweep, r.y, true) : -1;
-    w.t[2] = w.t[3] = -1;
-  }
+__device__ __forceinline__ void contact_wait(const Pool& P, const OrderBufs& B, int i, ItemWait& w) {
+  int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
+  w.v[0] = v.x; w.v[1] = v.y; w.v[2] = v.z; w.v[3] = v.w;
+  for (int k = 0; k < 4; k++) w.t[k] = movable(P, w.v[k]) ? __ldg(&B.rank[4 * i + k]) : -1;
 }
 // Synchronisation at GPU scope: counters are polled with relaxed loads; once
 // an item's counters are all right, one acquire fence makes its
-// predecessors' writes of y visible; after the item's own writes, one
-// release fence precedes relaxed increments of its counters.  (A release on
-// each increment costs one fence per vertex.)
+// predecessors' writes visible; after the item's own writes, one release
+// fence precedes relaxed increments of its counters.  (A release on each
+// increment costs one fence per vertex.)
 __device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void red_relaxed_add(int* p, int v) {
   asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-// constraints still to be applied at the item's vertices before it (0: ready)
+// contacts still to be coloured at the item's vertices before it (0: ready)
 __device__ __forceinline__ int item_gap(const OrderBufs& B, const ItemWait& w) {
   int gap = 0;
   for (int k = 0; k < 4; k++)
     if (w.t[k] >= 0) gap = max(gap, w.t[k] - ld_relaxed(&B.vdone[w.v[k]]));
   return gap;
 }
-__device__ __forceinline__ void item_apply(Pool& P, const OrderBufs& B, const SweepCtx& X, int i, const ItemWait& w,
-                                           int& maxlvl) {
+
+// Colours contact i (its turn has come at every movable vertex): the
+// smallest colour absent from the masks of its movable vertices.  A vertex at
+// which i is the first contact (rank 0) has an empty set; its mask words are
+// rewritten rather than read (they hold an earlier iteration's colours).
+__device__ __forceinline__ void colour_apply(Pool& P, const OrderBufs& B, int i, const ItemWait& w, int& maxcol) {
   fence_acq_rel();
-  int lvl = 1;
-  if (X.levels)
+  int hw[4];
+  for (int k = 0; k < 4; k++) hw[k] = w.t[k] > 0 ? __ldcg(&P.chw[w.v[k]]) : 0;
+  int col = -1;
+  for (int wd = 0; wd < CW && col < 0; wd++) {
+    unsigned long long m = 0ULL;
     for (int k = 0; k < 4; k++)
-      if (w.t[k] >= 0) lvl = max(lvl, __ldcg(&P.vlevel[w.v[k]]) + 1);
-  bool first = X.sweep == 0;
-  if (i < X.nc) {
-    if (P.mixed) pgs_contact_f(P, i, w.v, X.lam, first);
-    else pgs_contact(P, i, w.v, X.lam, first);
-  } else {
-    if (P.mixed) pgs_edge_f(P, i - X.nc, w.v[0], w.v[1], X.elam, first);
-    else pgs_edge(P, i - X.nc, w.v[0], w.v[1], X.elam, first);
+      if (wd < hw[k]) m |= __ldcg(&P.cmask[(size_t)w.v[k] * CW + wd]);
+    if (m != ~0ULL) col = wd * 64 + __ffsll((long long)~m) - 1;
   }
-  if (X.levels)
-    for (int k = 0; k < 4; k++)
-      if (w.t[k] >= 0) __stcg(&P.vlevel[w.v[k]], lvl);
+  if (col < 0) {  // more than MAX_COLOURS colours at these vertices
+    atomicOr(&P.cnt->err, ERR_COLOURS);
+    col = MAX_COLOURS - 1;
+  }
+  int wd = col >> 6;
+  unsigned long long bit = 1ULL << (col & 63);
+  for (int k = 0; k < 4; k++) {
+    if (w.t[k] < 0) continue;
+    unsigned long long* mk = P.cmask + (size_t)w.v[k] * CW;
+    if (wd < hw[k]) {
+      __stcg(mk + wd, __ldcg(mk + wd) | bit);
+    } else {
+      for (int z = hw[k]; z < wd; z++) __stcg(mk + z, 0ULL);
+      __stcg(mk + wd, bit);
+      __stcg(&P.chw[w.v[k]], wd + 1);
+    }
+  }
+  P.ccol[i] = col;
+  maxcol = max(maxcol, col + 1);
   fence_acq_rel();
   for (int k = 0; k < 4; k++)
     if (w.t[k] >= 0) red_relaxed_add(&B.vdone[w.v[k]], 1);
-  maxlvl = max(maxlvl, lvl);
 }
 
-// edge-length constraints of scenes that are not running take no part
-__device__ __forceinline__ bool item_live(const Pool& P, const SweepCtx& X, int i) {
-  if (i < X.nc) return true;
-  const SceneState& S = P.ss[P.lv[i - X.nc].z];
-  return S.active && !S.done;
-}
-// sweep-order key: contacts (class 0) before edges (class 1), then
-// descending priority; compared as (class, ~prio) ascending
-__device__ __forceinline__ unsigned long long item_prio(const Pool& P, const SweepCtx& X, int i) {
-  if (i < X.nc) return P.mixed ? ((const ContactF*)P.cons)[i].prio : P.cons[i].prio;
-  int e = i - X.nc;
-  const SceneDesc& d = P.sd[P.lv[e].z];
-  return splitmix64(d.seed ^ ((3ULL << 62) | (unsigned long long)(e - d.l0)));
+__device__ __forceinline__ unsigned long long contact_prio(const Pool& P, int i) {
+  return P.mixed ? ((const ContactF*)P.cons)[i].prio : P.cons[i].prio;
 }
 
-__global__ void __launch_bounds__(256, 2) k_gs_sweep(Pool P, OrderBufs B, int sweep, int max_polls, int levels) {
-  SweepCtx X;
-  X.levels = levels;
-  X.nc = min(P.cnt->n_cons, P.cons_cap);
-  X.sweep = sweep;
-  X.lam = P.sd[0].gs_sweeps > 1 ? P.lam : nullptr;
-  X.elam = X.lam ? P.lam + P.cons_cap : nullptr;
-  int n = X.nc + P.nl;
+// All blocks are resident (cooperative launch).  Each thread takes up to 32
+// contacts (i = tid + k * nth), sorts them by descending priority and colours
+// them one after the other, waiting before each only for its own vertex
+// counters.  The highest-priority uncoloured contact of the whole pool is at
+// the head of its thread's list and ready, so the colouring always
+// progresses.  With more contacts than 32 per thread, every thread polls all
+// of its pending contacts each round instead.  Waits are bounded and set
+// ERR_POLL past the bound.
+__global__ void __launch_bounds__(256, 2) k_colour(Pool P, OrderBufs B, int max_polls) {
+  int n = min(P.cnt->n_cons, P.cons_cap);
   int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  int maxlvl = 0;
+  int maxcol = 0;
   long long polls = 0;
   if (n <= 32 * nth) {
-    // this thread's items in sweep order (insertion sort, at most 32)
     int items[32];
     unsigned long long keys[32];
     int m = 0;
     for (int i = tid; i < n; i += nth) {
-      if (!item_live(P, X, i)) continue;
-      unsigned long long key = ~item_prio(P, X, i);
-      bool edge = i >= X.nc;
+      unsigned long long key = ~contact_prio(P, i);
       int j = m++;
-      while (j > 0 && ((items[j - 1] >= X.nc) > edge || ((items[j - 1] >= X.nc) == edge && keys[j - 1] > key))) {
+      while (j > 0 && keys[j - 1] > key) {
         items[j] = items[j - 1];
         keys[j] = keys[j - 1];
         j--;
@@ -631,22 +635,22 @@ __global__ void __launch_bounds__(256, 2) k_gs_sweep(Pool P, OrderBufs B, int sw
       keys[j] = key;
     }
     // The lanes of a warp advance together: each round every lane checks
-    // its head item; the lanes whose head is ready apply it, and the warp
+    // its head item; the lanes whose head is ready colour it, and the warp
     // sleeps only when none is (a lane spinning alone would take issue
-    // slots from a lane of its warp that could apply).  The sleep grows with
-    // the smallest number of constraints still ahead of a head item.
+    // slots from a lane of its warp that could proceed).  The sleep grows
+    // with the smallest number of contacts still ahead of a head item.
     int j = 0;
     ItemWait w;
     bool has = m > 0;
-    if (has) item_wait(P, B, X, items[0], w);
+    if (has) contact_wait(P, B, items[0], w);
     while (__any_sync(0xffffffffu, has)) {
       int gap = has ? item_gap(B, w) : 1 << 30;
       bool ready = has && gap == 0;
       if (__any_sync(0xffffffffu, ready)) {
         if (ready) {
-          item_apply(P, B, X, items[j], w, maxlvl);
+          colour_apply(P, B, items[j], w, maxcol);
           has = ++j < m;
-          if (has) item_wait(P, B, X, items[j], w);
+          if (has) contact_wait(P, B, items[j], w);
         }
         continue;
       }
@@ -658,15 +662,15 @@ __global__ void __launch_bounds__(256, 2) k_gs_sweep(Pool P, OrderBufs B, int sw
       __nanosleep(min(32 + 128 * (g - 1), 4096));
     }
   } else {
-    // more items than that: poll every pending item each round
+    // more contacts than that: poll every pending one each round
     for (;;) {
       bool pending = false, progressed = false;
       for (int i = tid; i < n; i += nth) {
-        if (P.fdone[i] || !item_live(P, X, i)) continue;
+        if (P.fdone[i]) continue;
         ItemWait w;
-        item_wait(P, B, X, i, w);
+        contact_wait(P, B, i, w);
         if (item_gap(B, w) == 0) {
-          item_apply(P, B, X, i, w, maxlvl);
+          colour_apply(P, B, i, w, maxcol);
           P.fdone[i] = 1;
           progressed = true;
         } else {
@@ -683,10 +687,134 @@ __global__ void __launch_bounds__(256, 2) k_gs_sweep(Pool P, OrderBufs B, int sw
       }
     }
   }
-  unsigned mx = __reduce_max_sync(0xffffffffu, (unsigned)maxlvl);
-  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&P.cnt->depth, (int)mx);
+  unsigned mx = __reduce_max_sync(0xffffffffu, (unsigned)maxcol);
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&P.cnt->n_ccol, (int)mx);
 }
 
+// per-scene colour counts of the iteration (statistics), aggregated per warp
+__global__ void k_colour_stats(Pool P) {
+  int n = min(P.cnt->n_cons, P.cons_cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
+    int s = P.vscene[v.x];
+    cg::coalesced_group g = cg::coalesced_threads();
+    auto part = cg::labeled_partition(g, s);
+    int m = cg::reduce(part, P.ccol[i] + 1, cg::greater<int>());
+    if (part.thread_rank() == 0) atomicMax(&P.ss[s].ccol, m);
+  }
+}
+
+// Grid barrier of a cooperative launch (every block resident): one arrival
+// counter and a generation word.  The last block to arrive resets the
+// counter and publishes the next generation; the others poll it, at most
+// max_polls times, after which the wait sets ERR_POLL.  A block also leaves
+// a wait once another block has given up.  Returns false when the barrier
+// failed; the caller then returns.
+__device__ __forceinline__ bool grid_barrier(Pool& P, unsigned& gen, int max_polls) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned* bar = P.bar;
+    fence_acq_rel();
+    unsigned a = atomicAdd(&bar[0], 1u);
+    if (a == gridDim.x - 1) {
+      bar[0] = 0u;
+      st_release_u32(&bar[1], gen + 1);
+    } else {
+      long long polls = 0;
+      while (ld_acquire_u32(&bar[1]) == gen) {
+        if (++polls > max_polls || (ld_relaxed(&P.cnt->err) & ERR_POLL)) {
+          atomicOr(&P.cnt->err, ERR_POLL);
+          ok = 0;
+          break;
+        }
+        __nanosleep(16);
+      }
+    }
+    fence_acq_rel();
+    gen++;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// the edge-length constraints of scenes that are not running take no part
+__device__ __forceinline__ bool edge_live(const Pool& P, int e) {
+  const SceneState& S = P.ss[P.lv[e].z];
+  return S.active && !S.done;
+}
+
+__device__ __forceinline__ void apply_contact(Pool& P, const SweepCtx& X, int i, bool first) {
+  int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
+  int vid[4] = {v.x, v.y, v.z, v.w};
+  if (P.mixed) pgs_contact_f(P, i, vid, X.lam, first);
+  else pgs_contact(P, i, vid, X.lam, first);
+}
+__device__ __forceinline__ void apply_edge(Pool& P, const SweepCtx& X, int e, bool first) {
+  int4 l = P.lv[e];
+  if (P.mixed) pgs_edge_f(P, e, l.x, l.y, X.elam, first);
+  else pgs_edge(P, e, l.x, l.y, X.elam, first);
+}
+
+// insertion of item `it` with sort key `key` into a thread's list (at most 32)
+__device__ __forceinline__ void insert_sorted(int* items, int* keys, int& m, int it, int key) {
+  int j = m++;
+  while (j > 0 && keys[j - 1] > key) {
+    items[j] = items[j - 1];
+    keys[j] = keys[j - 1];
+    j--;
+  }
+  items[j] = it;
+  keys[j] = key;
+}
+
+// The sweep: gs_sweeps times, the contact classes in ascending colour, then
+// the edge classes, one class per phase and a grid barrier after each.  Each
+// thread takes its contacts (i = tid + k * nth) and live edges (e = tid +
+// k * nth), sorted by colour, and applies in phase c the ones of colour c.
+// With more than 32 of either per thread, every thread scans all of its
+// items in every phase instead.
+__global__ void __launch_bounds__(256, 2) k_colour_sweep(Pool P, int sweeps, int max_polls) {
+  SweepCtx X;
+  X.nc = min(P.cnt->n_cons, P.cons_cap);
+  X.lam = sweeps > 1 ? P.lam : nullptr;
+  X.elam = X.lam ? P.lam + P.cons_cap : nullptr;
+  int ncc = min(P.cnt->n_ccol, MAX_COLOURS), nec = P.n_ecol;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  unsigned gen = ld_acquire_u32(&P.bar[1]);
+  bool few_c = X.nc <= 32 * nth, few_e = P.nl <= 32 * nth;
+  int ci[32], cc[32], ei[32], ec[32];
+  int mc = 0, me = 0;
+  if (few_c)
+    for (int i = tid; i < X.nc; i += nth) insert_sorted(ci, cc, mc, i, P.ccol[i]);
+  if (few_e)
+    for (int e = tid; e < P.nl; e += nth)
+      if (edge_live(P, e)) insert_sorted(ei, ec, me, e, P.ecol[e]);
+  for (int sw = 0; sw < sweeps; sw++) {
+    bool first = sw == 0;
+    int p = 0;
+    for (int c = 0; c < ncc; c++) {
+      if (few_c) {
+        for (; p < mc && cc[p] == c; p++) apply_contact(P, X, ci[p], first);
+      } else {
+        for (int i = tid; i < X.nc; i += nth)
+          if (P.ccol[i] == c) apply_contact(P, X, i, first);
+      }
+      if (!grid_barrier(P, gen, max_polls)) return;
+    }
+    p = 0;
+    for (int c = 0; c < nec; c++) {
+      if (few_e) {
+        for (; p < me && ec[p] == c; p++) apply_edge(P, X, ei[p], first);
+      } else {
+        for (int e = tid; e < P.nl; e += nth)
+          if (P.ecol[e] == c && edge_live(P, e)) apply_edge(P, X, e, first);
+      }
+      if (!grid_barrier(P, gen, max_polls)) return;
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Backward step, projected Jacobi variant (Sec. 4.3.2, R12).  Every
@@ -778,6 +906,7 @@ __global__ void k_jac_nv(Pool P, OrderBufs B) {
     int m = 0;
     if (P.vflag[v] & VF_MOVABLE) {
       m = B.vfill[v];
+      if (m > 0) count_contact_vertex(P, P.vscene[v]);
       for (int j = P.vlstart[v]; j < P.vlstart[v + 1]; j++) {
         int e = P.vllist[j] >> 1;
         m += P.mixed ? (P.lgf[e].w > 0.f) : (P.lg[e].w > 0.0);
@@ -959,9 +1088,17 @@ __global__ void k_forward(Pool P) {
     if (!S.active || S.done) continue;
     // CCD-based rule: the global bound D^(l) caps every vertex, the CCD
     // rounds decide the rest
-    double Di = P.sd[s].step_rule ? S.D : bitsd(P.Dv[v]);
+    unsigned long long dvb = P.Dv[v];
+    if (dvb != 0x7ff0000000000000ULL) {
+      // a vertex of a pair of P (statistics)
+      cg::coalesced_group g = cg::coalesced_threads();
+      auto part = cg::labeled_partition(g, s);
+      if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].pverts, (unsigned long long)part.size());
+    }
+    double Di = P.sd[s].step_rule ? S.D : bitsd(dvb);
     if (S.D < Di) Di = S.D;
-    if (!(Di >= D_FLOOR)) Di = 0.0;
+    bool floored = !(Di >= D_FLOOR);
+    if (floored) Di = 0.0;
     P.Dv[v] = 0x7ff0000000000000ULL;
     P4 xv4 = P.x[v];
     dv3 yv;
@@ -976,6 +1113,12 @@ __global__ void k_forward(Pool P) {
       a = q < 1.0 ? q : 1.0;
     } else if (nd != 0.0) {
       a = 0.0;  // R2c: y not finite, the vertex does not move
+    }
+    if (floored && nd > 0.0) {
+      // held by the D_i floor although its target is elsewhere (statistics)
+      cg::coalesced_group g = cg::coalesced_threads();
+      auto part = cg::labeled_partition(g, s);
+      if (part.thread_rank() == 0) atomicAdd(&P.ss[s].frozen_cur, (int)part.size());
     }
     dv3 xn = step_to(xv, yv, a);
     P.x[v] = {xn.x, xn.y, xn.z, 0.0};
@@ -1117,8 +1260,9 @@ __global__ void k_control(Pool P, int cur) {
     S.final_r = rmax;
     S.move_bits = 0;
     S.rmax_bits = 0;
+    S.frozen = S.frozen_cur;
+    S.frozen_cur = 0;
     if (C->vcontacts > S.max_vcontacts) S.max_vcontacts = C->vcontacts;
-    if (C->depth > S.max_depth) S.max_depth = C->depth;
     if (rmax < d.eps) {
       S.done = 1;
       S.converged = 1;
@@ -1145,7 +1289,7 @@ __global__ void k_control(Pool P, int cur) {
     C->n_active = 0;
     C->n_cons = 0;
     C->vcontacts = 0;
-    C->depth = 0;
+    C->n_ccol = 0;
   }
 }
 
@@ -1175,7 +1319,10 @@ int coop_grid(int threads) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gs_sweep, threads, 0);
+  int per2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_colour_sweep, threads, 0);
+  if (per2 < per) per = per2;
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -1253,9 +1400,8 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     }
     prof_mark(R, PG_SWEEP, 1, st);
     R.launches += 5 + 2 * R.sweeps;
-  } else {  // projected Gauss-Seidel
+  } else {  // projected Gauss-Seidel in colour classes
     cudaMemsetAsync(B.vdone, 0, sizeof(int) * (size_t)P.nv, st);
-    if (R.profiling) cudaMemsetAsync(P.vlevel, 0, sizeof(int) * (size_t)P.nv, st);
     if (P.mixed) {
       ContactFAcc acc{(const ContactF*)P.cons};
       k_inc_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
@@ -1270,13 +1416,16 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
       k_inc_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
     }
     prof_mark(R, PG_ORDER, 1, st);
+    prof_mark(R, PG_COLOUR, 0, st);
+    cudaMemsetAsync(P.fdone, 0, (size_t)P.cons_cap, st);
+    e = coop_launch(k_colour, R.coop_blocks, 256, st, P, B, R.max_polls);
+    if (e == cudaSuccess) k_colour_stats<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P);
+    prof_mark(R, PG_COLOUR, 1, st);
     prof_mark(R, PG_SWEEP, 0, st);
-    for (int sw = 0; sw < R.sweeps && e == cudaSuccess; sw++) {
-      cudaMemsetAsync(P.fdone, 0, (size_t)P.cons_cap + P.nl, st);
-      e = coop_launch(k_gs_sweep, R.coop_blocks, 256, st, P, B, sw, 1 << 22, R.profiling);
-    }
+    cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = coop_launch(k_colour_sweep, R.coop_blocks, 256, st, P, R.sweeps, R.max_polls);
     prof_mark(R, PG_SWEEP, 1, st);
-    R.launches += 4 + R.sweeps;
+    R.launches += 7;
   }
   if (e != cudaSuccess) return e;
   prof_mark(R, PG_FORWARD, 0, st);

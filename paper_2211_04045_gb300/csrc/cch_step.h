@@ -10,4 +10,8 @@ void set_any_search(Runtime& R, cudaStream_t st);
 cudaError_t iteration(Runtime& R, int cur, cudaStream_t st);
 void output(Runtime& R, cudaStream_t st);
 void reset_accept(Runtime& R, cudaStream_t st);
+// pre-passes (cch_prepass.cu)
+void normal_flow(Runtime& R, const double* x, double* y, double* tmp, double sb, double alpha, int iters,
+                 cudaStream_t st);
+void friction(Runtime& R, double mu, double reach, double sep, double* out, cudaStream_t st);
 }  // namespace cch

@@ -765,15 +765,34 @@ class TorchDynamics:
             y = y + fl["alpha"] * (Lv / torch.where(Av > 0, Av, torch.ones_like(Av))[:, None])
         return y
 
+    def _rotate(self, p, rotvec, centre):
+        # Rodrigues rotation of the rows of p about an axis through centre
+        torch = self.torch
+        c = torch.as_tensor(np.asarray(centre, dtype=np.float64), device=p.device)
+        th = float(np.linalg.norm(rotvec))
+        if th == 0.0:
+            return p.clone()
+        k = torch.as_tensor(np.asarray(rotvec, dtype=np.float64) / th, device=p.device)
+        q = p - c
+        kq = torch.linalg.cross(k.expand_as(q), q)
+        return c + q * math.cos(th) + kq * math.sin(th) + torch.outer(q @ k, k) * (1.0 - math.cos(th))
+
     def predict(self, x, v):
+        if self.sc.friction is not None:
+            raise NotImplementedError("the friction filter is a pre-pass of its own: use predict_frictionless "
+                                      "and apply the filter to its result")
+        return self.predict_frictionless(x, v)
+
+    def predict_frictionless(self, x, v):
         torch = self.torch
         sc = self.sc
         if sc.flow is not None:
             return self._flow(x)
-        if sc.friction is not None or sc.kin_rot is not None:
-            raise NotImplementedError("the friction filter and kinematic rotation run in scenes.predict (numpy)")
         xt = x + sc.dt * v
         xt = torch.where(self.fixed[:, None], x + sc.dt * self.kin_v, xt)
+        if sc.kin_rot is not None:
+            w, c = sc.kin_rot
+            xt = torch.where(self.fixed[:, None], self._rotate(x, np.asarray(w) * sc.dt, c), xt)
         if self.relax:
             for _ in range(sc.relax_sweeps):
                 d = xt[self.i] - xt[self.j]

@@ -110,3 +110,19 @@ def test_oracle_sphere_drags_the_cloth_with_friction():
         turns[mu] = cap_turn(x, x0, 16 * 16)
     # the sphere turns by -0.67 rad about +y in these ten steps
     assert turns[0.5] < -0.1 and abs(turns[0.0]) < 0.05, turns
+
+
+def test_torch_dynamics_rotates_the_kinematic_sphere_like_numpy():
+    # the benchmark chain's GPU copy of the dynamics (here on the CPU): the
+    # frictionless target with the sphere's scripted rotation equals numpy's
+    import dataclasses
+    import torch
+    sc = S.cloth_on_rotating_sphere(n=16, side=0.5, sphere_subdiv=2, sphere_r=0.15, omega=2.0, mu=0.5)
+    x, _, v = S.initial(sc)
+    v = v + np.random.default_rng(2).normal(0.0, 0.1, size=v.shape)
+    want = S.predict(dataclasses.replace(sc, friction=None), x, v)
+    dyn = S.TorchDynamics(sc, torch.device("cpu"))
+    got = dyn.predict_frictionless(torch.tensor(x), torch.tensor(v)).numpy()
+    assert np.max(np.abs(got - want)) <= 1e-15
+    with pytest.raises(NotImplementedError):
+        dyn.predict(torch.tensor(x), torch.tensor(v))

@@ -2,9 +2,14 @@
 
 The candidate set and the proximity set at the generator's states are
 compared with the oracle in full (the oracle's sorted-axis window search takes
-seconds at this size).  For a whole step at full size, where the oracle would
-take hours, the test checks properties that hold at any size: a repeated call
-is bitwise identical, and the statistics are consistent.
+seconds at this size).  A step capped at six iterations, from a contact-rich
+state (the layers 1.5 mm apart, so that every vertex has pairs in P and
+contacts form within the first iterations), is compared with the oracle
+element by element: positions, iterations, searches, |P|, contacts and the
+colouring's statistics (the oracle takes about ten seconds per iteration at
+this size).  For whole steps, where the oracle would take hours, the test
+checks properties that hold at any size: a repeated call is bitwise
+identical, and the statistics are consistent.
 """
 import numpy as np
 import pytest
@@ -38,6 +43,24 @@ def test_fullsize_pair_sets_bit_exact(cuda, c2):
         gk, gd = gpu.query_pairs(T(x, cuda), T(xt, cuda), D, candidates=False)
         ok, od = oracle.proximity(osc, x, D, mode=1, x_tilde=xt)
         assert np.array_equal(gk, ok) and np.array_equal(gd, od)
+    gpu.close()
+
+
+def test_fullsize_capped_step_matches_oracle(cuda):
+    from test_gpu_parity import REL, same_stats
+    sc = scenes.two_cloths(n=256, side=2.0, sep=0.0015, omega=6.0, noise=0.3, seed=0)
+    x, xt, _ = scenes.initial(sc)
+    kw = dict(max_iters=5)
+    xo, so, _ = oracle.handle_step(oracle.OracleScene(sc), oracle.params_for(sc, **kw), x, xt)
+    gpu = cch.Scene(sc, cch.params_for(sc, **kw))
+    out, sg = gpu.step(T(x, cuda), T(xt, cuda))
+    xn = out.cpu().numpy()
+    err = float(np.max(np.abs(xn - xo)))
+    assert err <= REL * max(1.0, float(np.max(np.abs(xo)))), err
+    for k in ("iterations", "searches", "pairs_evaluated", "max_pairs", "active_contacts", "converged"):
+        assert sg[k] == so[k], (k, sg[k], so[k])
+    same_stats(sg, so, "full size")
+    assert so["iterations"] == 6 and so["pairs_evaluated"] > 10**7 and so["active_contacts"] > 1000
     gpu.close()
 
 

@@ -1,12 +1,16 @@
 """Mixed precision (FP32 distances, contacts and projection; FP64 forward
 step, CCD and acceptance): safe, and close to the FP64 oracle.
 
-The pair distances become FP32 lower bounds (d32 minus its rounding bound),
-so every D_i stays below the true distance and the forward step keeps its
-guarantee; the acceptance test and the oracle's exact test must both find
-no intersection.  The position error against the FP64 oracle is reported
-and bounded loosely: y only guides the forward step, so rounding differences
-change the path, not its safety.
+The pair distances become FP32 lower bounds (d32 minus its rounding bound
+FILTER_TOL (|x|max + extent), FILTER_TOL = 4e-6), so every D_i stays below
+the true distance and the forward step keeps its guarantee.  The proximity
+set the step's search forms is checked against the oracle's exact one: it
+holds every pair of the oracle's P, each recorded distance is at most the
+exact distance and at most B below it, and every extra pair lies within B of
+D^max, with B = 2 FILTER_TOL (|x|max + 2 (longest edge) + D^max).  After a
+step, the acceptance test and the oracle's exact test must both find no
+intersection, and the position error against the FP64 oracle is within the
+bound stated per scene (measured on the GB300 with margin).
 """
 import numpy as np
 import pytest
@@ -49,4 +53,37 @@ def test_mixed_is_safe_and_close(cuda, name):
     assert sg["intersections"] == 0 and sg["uncertain"] == 0
     assert oracle.count_intersections(osc, xm) == 0
     assert err <= 0.5 * travel + 1e-6
+    gpu.close()
+
+
+def jitter(x, scale, seed):
+    rng = np.random.default_rng(seed)
+    return x + rng.normal(0.0, scale, size=x.shape)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_proximity_set_contract(cuda, name):
+    sc = CASES[name]()
+    gpu = cch.Scene(sc, cch.params_for(sc, precision=1))
+    osc = oracle.OracleScene(sc)
+    D = oracle.params_for(sc).d_max
+    x0, xt, _ = scenes.initial(sc)
+    e = np.concatenate([sc.edges, sc.len_edges]) if len(sc.len_edges) else sc.edges
+    longest = float(np.max(np.linalg.norm(x0[e[:, 0]] - x0[e[:, 1]], axis=1))) if len(e) else 0.0
+    for k, x in enumerate([x0, jitter(x0, 0.002, 10), jitter(xt, 0.004, 11)]):
+        B = 2.0 * 4e-6 * (float(np.max(np.abs(x))) + 2.0 * longest + D) * 1.01
+        km, dm = gpu.query_pairs(T(x, cuda), T(xt, cuda), D, step_search=True)
+        ko, do = oracle.proximity(osc, x, D, mode=0, x_tilde=xt)
+        assert len(ko) > 0
+        assert np.all(np.isin(ko, km)), (name, k)
+        common = np.isin(km, ko)
+        dex = do[np.searchsorted(ko, km[common])]
+        assert np.all(dm[common] <= dex), (name, k, float(np.max(dm[common] - dex)))
+        assert np.all(dex - dm[common] <= B), (name, k, float(np.max(dex - dm[common])), B)
+        extra = km[~common]
+        if len(extra):
+            kw, dw = oracle.proximity(osc, x, D + B, mode=0, x_tilde=xt)
+            assert np.all(np.isin(extra, kw)), (name, k)
+            assert np.all(dw[np.searchsorted(kw, extra)] >= D)
+        print(f"{name} state {k}: |P| oracle {len(ko)}, mixed {len(km)} ({len(extra)} within B = {B:.2e} m of D)")
     gpu.close()

@@ -32,6 +32,17 @@ def T(a, dev):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
 
 
+# statistics of the Gauss-Seidel colouring and of the forward step that must
+# equal the oracle's
+GS_STATS = ("contact_colours", "edge_colours", "contact_vertices", "frozen_vertices", "max_vertex_contacts",
+            "max_vertex_edges", "degenerate", "pair_vertices")
+
+
+def same_stats(sg, so, where):
+    for k in GS_STATS:
+        assert sg[k] == so[k], (where, k, sg[k], so[k])
+
+
 def jitter(x, scale, seed):
     rng = np.random.default_rng(seed)
     return x + rng.normal(0.0, scale, size=x.shape)
@@ -79,6 +90,7 @@ def test_step_chain_matches_oracle(cuda, name):
         assert sg["pairs_evaluated"] == so["pairs_evaluated"], (name, s)
         assert sg["active_contacts"] == so["active_contacts"], (name, s)
         assert sg["converged"] == so["converged"]
+        same_stats(sg, so, (name, s))
         v = scenes.next_velocity(sc, xo, x)
         x, xt = xo, scenes.predict(sc, xo, v)
         vg = scenes.next_velocity(sc, xn, xg)

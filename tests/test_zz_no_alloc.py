@@ -1,11 +1,14 @@
 """The allocation-free proximity query against the allocating one.
 
 cch_query_pairs_noalloc serves callers that may not allocate device memory
-while they run (inside CUDA stream capture, in loops with a fixed memory
-budget, under allocators that forbid cudaMalloc).  It must return exactly
+while they run (real-time loops that reserve all of their memory up front,
+hosts whose own memory manager forbids cudaMalloc).  It must return exactly
 what cch_query_pairs returns, on consecutive calls that reuse its fixed
-scratch array, and refuse results larger than that array.
+scratch array, refuse results larger than that array, and report an unknown
+count (-1) when the scene's own pair buffers are too small for the query.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -48,4 +51,23 @@ def test_noalloc_query_rejects_results_beyond_its_array(cuda):
     k_new, _ = gpu.query_pairs_noalloc(T(x0, cuda), T(x0, cuda), 2e-3, candidates=True)
     assert 0 < len(k_ref) <= cch.Scene.NOALLOC_MAX_PAIRS
     assert np.array_equal(k_new, k_ref)
+    gpu.close()
+
+
+def test_noalloc_query_reports_unknown_count_when_scene_buffers_overflow(cuda):
+    # a scene created with tiny pair buffers: the allocating query grows them,
+    # the allocation-free one cannot, and says that its count is unknown
+    sc = scenes.two_cloths(n=40, side=0.4, sep=0.004, omega=6.0, noise=0.3, seed=11)
+    x0, xt, _ = scenes.initial(sc)
+    gpu = cch.Scene(sc, cch.params_for(sc, pair_capacity=64))
+    xg, xtg = T(x0, cuda), T(xt, cuda)
+    cnt = C.c_int64(12345)
+    rc = cch.lib().cch_query_pairs_noalloc(gpu.h, C.c_void_p(xg.data_ptr()), C.c_void_p(xtg.data_ptr()), 4e-3, 1,
+                                           None, None, 0, C.byref(cnt))
+    assert rc == 5 and cnt.value == -1
+    # the allocating query grows the buffers; afterwards both agree
+    k_ref, d_ref = gpu.query_pairs(xg, xtg, 4e-3, candidates=True)
+    k_new, d_new = gpu.query_pairs_noalloc(xg, xtg, 4e-3, candidates=True)
+    assert len(k_ref) > 64
+    assert np.array_equal(k_new, k_ref) and np.array_equal(d_new, d_ref)
     gpu.close()
