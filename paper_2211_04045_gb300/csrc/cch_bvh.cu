@@ -337,10 +337,9 @@ __device__ __forceinline__ void push_survivor(Pool& P, int kind, unsigned long l
 
 __device__ __forceinline__ void add_candidates(Pool& P, int s, long long n) {
   if (n == 0) return;
-  cg::coalesced_group g = cg::coalesced_threads();
-  auto part = cg::labeled_partition(g, s);
-  long long t = cg::reduce(part, n, cg::plus<long long>());
-  if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].candidates, (unsigned long long)t);
+  scene_reduce(P, s, n, cg::plus<long long>(), [&](long long t, int) {
+    atomicAdd((unsigned long long*)&P.ss[s].candidates, (unsigned long long)t);
+  });
 }
 
 // ---------------------------------------------------------------------------

@@ -384,6 +384,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaEventCreate(&R.ev0));
   CK(cudaEventCreate(&R.ev1));
   CK(dalloc(R, &R.obuf.vstart, (size_t)nv + 1));
+  CK(dalloc(R, &R.obuf.tsum, ((size_t)nv + 1) / 8192 + 2));
   CK(dalloc(R, &R.obuf.vfill, nv));
   CK(dalloc(R, &R.obuf.vdone, nv));
   {

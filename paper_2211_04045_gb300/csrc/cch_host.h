@@ -28,6 +28,7 @@ struct OrderBufs {
   unsigned long long* iprio; // incidences: priority (Jacobi: key)
   int* iid;                  // incidences: constraint * 4 + slot
   int* rank;                 // constraint * 4 + slot: rank at that vertex
+  int* tsum;                 // tile totals of the multi-block scan of vstart
 };
 
 // Host-side runtime of one pool of scenes (a single scene, a batch, or the
@@ -78,11 +79,38 @@ __device__ __forceinline__ bool searching(const Pool& P, int s) {
   return S.active && !S.done && S.do_search;
 }
 
+// Warp aggregation of a per-scene value: the active lanes of one scene combine
+// their values with op, and one lane per scene calls done(result, lanes).  In
+// a pool of one scene every lane shares the scene, so the whole coalesced
+// group reduces at once (no partition by scene); min, max and sums of
+// integers do not depend on the order, so both forms give the same result.
+template <class T, class Op, class Done>
+__device__ __forceinline__ void scene_reduce(const Pool& P, int s, T v, Op op, Done done) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  if (P.nscene == 1) {
+    T r = cg::reduce(g, v, op);
+    if (g.thread_rank() == 0) done(r, (int)g.size());
+    return;
+  }
+  auto part = cg::labeled_partition(g, s);
+  T r = cg::reduce(part, v, op);
+  if (part.thread_rank() == 0) done(r, (int)part.size());
+}
+// lanes of one scene counted once per warp
+template <class Done>
+__device__ __forceinline__ void scene_count(const Pool& P, int s, Done done) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  if (P.nscene == 1) {
+    if (g.thread_rank() == 0) done((int)g.size());
+    return;
+  }
+  auto part = cg::labeled_partition(g, s);
+  if (part.thread_rank() == 0) done((int)part.size());
+}
+
 // per-scene candidate counts, aggregated over the lanes of one scene
 __device__ __forceinline__ void count_candidate(Pool& P, int s) {
-  cg::coalesced_group g = cg::coalesced_threads();
-  auto part = cg::labeled_partition(g, s);
-  if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].candidates, (unsigned long long)part.size());
+  scene_count(P, s, [&](int n) { atomicAdd((unsigned long long*)&P.ss[s].candidates, (unsigned long long)n); });
 }
 
 __device__ __forceinline__ int append_idx(int* ctr) {
@@ -178,15 +206,10 @@ __device__ __forceinline__ void emit_pair(Pool& P, int nxt, int s, unsigned long
   dmin_at(&P.Dv[v.y], db);
   if (v.z >= 0) dmin_at(&P.Dv[v.z], db);
   if (v.w >= 0) dmin_at(&P.Dv[v.w], db);
-  {
-    cg::coalesced_group g = cg::coalesced_threads();
-    auto part = cg::labeled_partition(g, s);
-    unsigned long long m = cg::reduce(part, db, cg::less<unsigned long long>());
-    if (part.thread_rank() == 0) {
-      atomicMin(&P.ss[s].mind_bits, m);
-      atomicAdd(&P.ss[s].n_pairs, (int)part.size());
-    }
-  }
+  scene_reduce(P, s, db, cg::less<unsigned long long>(), [&](unsigned long long m, int n) {
+    atomicMin(&P.ss[s].mind_bits, m);
+    atomicAdd(&P.ss[s].n_pairs, n);
+  });
   if (d < S.delta) {
     int a = claim(&P.cnt->n_active, P.act_cap);
     if (a >= 0) P.act[a] = idx;

@@ -206,9 +206,7 @@ __device__ __forceinline__ void assemble_f(Pool& P, int s, const SceneDesc& S, i
   c.key = key;
   c.prio = splitmix64(S.seed ^ key);
   ((ContactF*)P.cons)[idx] = c;
-  cg::coalesced_group gg = cg::coalesced_threads();
-  auto part = cg::labeled_partition(gg, s);
-  if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].contacts, (unsigned long long)part.size());
+  scene_count(P, s, [&](int n) { atomicAdd((unsigned long long*)&P.ss[s].contacts, (unsigned long long)n); });
 }
 
 __global__ void k_assemble(Pool P, int nxt) {
@@ -272,11 +270,7 @@ __global__ void k_assemble(Pool P, int nxt) {
     c.key = key;
     c.prio = splitmix64(S.seed ^ key);
     P.cons[idx] = c;
-    {
-      cg::coalesced_group gg = cg::coalesced_threads();
-      auto part = cg::labeled_partition(gg, s);
-      if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].contacts, (unsigned long long)part.size());
-    }
+    scene_count(P, s, [&](int n) { atomicAdd((unsigned long long*)&P.ss[s].contacts, (unsigned long long)n); });
   }
 }
 
@@ -304,9 +298,7 @@ __device__ __forceinline__ bool movable(const Pool& P, int v) { return v >= 0 &&
 
 // one more distinct movable vertex with a contact in this iteration (statistics)
 __device__ __forceinline__ void count_contact_vertex(Pool& P, int s) {
-  cg::coalesced_group g = cg::coalesced_threads();
-  auto part = cg::labeled_partition(g, s);
-  if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].cverts, (unsigned long long)part.size());
+  scene_count(P, s, [&](int n) { atomicAdd((unsigned long long*)&P.ss[s].cverts, (unsigned long long)n); });
 }
 
 template <class Acc>
@@ -359,6 +351,52 @@ __global__ void k_inc_rank(Pool P, Acc acc, OrderBufs B) {
   }
 }
 
+// Exclusive scan of m ints in place, in three launches: every block of 1024
+// threads scans a tile of SCAN_TILE ints (8 per thread) and writes the tile's
+// total, one block scans the totals, and every element adds its tile's
+// offset.
+constexpr int SCAN_TILE = 8192;
+__global__ void __launch_bounds__(1024) k_scan_tiles(int* a, int m, int* tsum) {
+  __shared__ int wtot[32];
+  int base = blockIdx.x * SCAN_TILE + threadIdx.x * 8;
+  int v[8];
+  if (base + 8 <= m) {
+    int4 p = *(const int4*)(a + base), q = *(const int4*)(a + base + 4);
+    v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w; v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+  } else {
+    for (int k = 0; k < 8; k++) v[k] = base + k < m ? a[base + k] : 0;
+  }
+  int sum = 0;
+  for (int k = 0; k < 8; k++) sum += v[k];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wtot[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int t = wtot[lane], ti = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += y;
+    }
+    wtot[lane] = ti - t;
+  }
+  __syncthreads();
+  int run = wtot[w] + inc - sum;
+  for (int k = 0; k < 8; k++) {
+    if (base + k < m) a[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == blockDim.x - 1) tsum[blockIdx.x] = run;
+}
+__global__ void k_scan_add(int* a, int m, const int* tsum) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    if (i >= SCAN_TILE) a[i] += tsum[i / SCAN_TILE];
+}
+
 // exclusive scan of m ints, in place, one block of 1024 threads
 __global__ void k_scan_ints(int* a, int m) {
   __shared__ int part[1024];
@@ -380,6 +418,14 @@ __global__ void k_scan_ints(int* a, int m) {
     a[i] = run;
     run += v;
   }
+}
+
+static void scan_ints(Runtime& R, int* a, int m, cudaStream_t st) {
+  int tiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_tiles<<<tiles, 1024, 0, st>>>(a, m, R.obuf.tsum);
+  k_scan_ints<<<1, 1024, 0, st>>>(R.obuf.tsum, tiles);
+  k_scan_add<<<grid_for(m, 256), 256, 0, st>>>(a, m, R.obuf.tsum);
+  R.launches += 2;  // the third is counted with the caller's kernels
 }
 
 // ---------------------------------------------------------------------------
@@ -697,10 +743,7 @@ __global__ void k_colour_stats(Pool P) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
     int s = P.vscene[v.x];
-    cg::coalesced_group g = cg::coalesced_threads();
-    auto part = cg::labeled_partition(g, s);
-    int m = cg::reduce(part, P.ccol[i] + 1, cg::greater<int>());
-    if (part.thread_rank() == 0) atomicMax(&P.ss[s].ccol, m);
+    scene_reduce(P, s, P.ccol[i] + 1, cg::greater<int>(), [&](int m, int) { atomicMax(&P.ss[s].ccol, m); });
   }
 }
 
@@ -1066,11 +1109,8 @@ __global__ void k_jac_apply(Pool P, OrderBufs B) {
 // ---------------------------------------------------------------------------
 // Forward step, Eq. forward2 (R2): alpha_i = min(0.5 gamma D_i / |y_i - x_i|, 1)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void scene_max(unsigned long long* dst, int s, unsigned long long v) {
-  cg::coalesced_group g = cg::coalesced_threads();
-  auto part = cg::labeled_partition(g, s);
-  unsigned long long m = cg::reduce(part, v, cg::greater<unsigned long long>());
-  if (part.thread_rank() == 0) atomicMax(dst, m);
+__device__ __forceinline__ void scene_max(const Pool& P, unsigned long long* dst, int s, unsigned long long v) {
+  scene_reduce(P, s, v, cg::greater<unsigned long long>(), [&](unsigned long long m, int) { atomicMax(dst, m); });
 }
 
 // x + a (y - x): y itself at a = 1, x itself at a = 0 (a vertex that does
@@ -1091,9 +1131,7 @@ __global__ void k_forward(Pool P) {
     unsigned long long dvb = P.Dv[v];
     if (dvb != 0x7ff0000000000000ULL) {
       // a vertex of a pair of P (statistics)
-      cg::coalesced_group g = cg::coalesced_threads();
-      auto part = cg::labeled_partition(g, s);
-      if (part.thread_rank() == 0) atomicAdd((unsigned long long*)&P.ss[s].pverts, (unsigned long long)part.size());
+      scene_count(P, s, [&](int n) { atomicAdd((unsigned long long*)&P.ss[s].pverts, (unsigned long long)n); });
     }
     double Di = P.sd[s].step_rule ? S.D : bitsd(dvb);
     if (S.D < Di) Di = S.D;
@@ -1116,9 +1154,7 @@ __global__ void k_forward(Pool P) {
     }
     if (floored && nd > 0.0) {
       // held by the D_i floor although its target is elsewhere (statistics)
-      cg::coalesced_group g = cg::coalesced_threads();
-      auto part = cg::labeled_partition(g, s);
-      if (part.thread_rank() == 0) atomicAdd(&P.ss[s].frozen_cur, (int)part.size());
+      scene_count(P, s, [&](int n) { atomicAdd(&P.ss[s].frozen_cur, n); });
     }
     dv3 xn = step_to(xv, yv, a);
     P.x[v] = {xn.x, xn.y, xn.z, 0.0};
@@ -1132,8 +1168,8 @@ __global__ void k_forward(Pool P) {
     double r = P.r[v] * (1.0 - a);
     P.r[v] = r;
     double mv = vnorm(vsub(xn, xv));
-    scene_max(&P.ss[s].move_bits, s, dbits(mv));
-    scene_max(&P.ss[s].rmax_bits, s, dbits(r));
+    scene_max(P, &P.ss[s].move_bits, s, dbits(mv));
+    scene_max(P, &P.ss[s].rmax_bits, s, dbits(r));
   }
 }
 
@@ -1232,8 +1268,8 @@ __global__ void k_ccd_fix(Pool P, int round) {
     double r = P.r[v] * (1.0 - a);
     P.r[v] = r;
     double mv = vnorm(vsub(xn, xv));
-    scene_max(&P.ss[s].move_bits, s, dbits(mv));
-    scene_max(&P.ss[s].rmax_bits, s, dbits(r));
+    scene_max(P, &P.ss[s].move_bits, s, dbits(mv));
+    scene_max(P, &P.ss[s].rmax_bits, s, dbits(r));
   }
 }
 
@@ -1388,7 +1424,7 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
   cudaMemsetAsync(B.vfill, 0, sizeof(int) * (size_t)P.nv, st);
   if (R.solver == 1) {  // projected Jacobi
     k_jac_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, B);
-    k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
+    scan_ints(R, B.vstart, P.nv + 1, st);
     k_jac_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, B);
     k_jac_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, B);
     k_jac_nv<<<grid_for(P.nv, 256), 256, 0, st>>>(P, B);
@@ -1405,13 +1441,13 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     if (P.mixed) {
       ContactFAcc acc{(const ContactF*)P.cons};
       k_inc_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
-      k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
+      scan_ints(R, B.vstart, P.nv + 1, st);
       k_inc_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
       k_inc_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
     } else {
       ContactAcc acc{P.cons};
       k_inc_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
-      k_scan_ints<<<1, 1024, 0, st>>>(B.vstart, P.nv + 1);
+      scan_ints(R, B.vstart, P.nv + 1, st);
       k_inc_scatter<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
       k_inc_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
     }

@@ -78,3 +78,23 @@ def test_fullsize_step_is_deterministic(cuda, c2):
     moved = torch.linalg.norm(a - T(x0, cuda), dim=1).max().item()
     assert moved <= 0.45 * 4e-3 * sa["iterations"] * (1 + 1e-12)
     gpu.close()
+
+
+def test_hair_sand_fullsize_sampled_pairs(cuda):
+    # Full-size hair and sand (10,000 strands x 32 segments, 100,000 grains of
+    # radius 2 mm, a fixed bowl), the movable vertices jittered by 1.5 mm so
+    # that strands and grains come within D^max = 0.8 mm of each other.  The
+    # oracle's whole-scene search takes hours here, so sampled queries are
+    # checked one by one (pair_sampling.check_sampled_pairs): for 400
+    # collision vertices, 400 edges and 400 grains the GPU's pairs in P are
+    # recomputed with the oracle's distance routines.
+    from pair_sampling import check_sampled_pairs, jittered
+    sc = scenes.hair_sand()
+    x0, xt, _ = scenes.initial(sc)
+    x = jittered(sc, x0, 0.0015, 7)
+    D = float(cch.params_for(sc).d_max)
+    gpu = cch.Scene(sc, cch.params_for(sc))
+    gk, gd = gpu.query_pairs(T(x, cuda), T(xt, cuda), D, candidates=False)
+    gpu.close()
+    checked = check_sampled_pairs(sc, x, xt, D, dict(zip(gk.tolist(), gd.tolist())), 400, seed=8)
+    assert checked > 1000

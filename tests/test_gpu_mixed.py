@@ -36,6 +36,14 @@ CASES = {
 }
 
 
+# Position error of one mixed-precision step against the FP64 oracle (metres),
+# stated per scene: five times the error measured on the GB300 (2.1e-6,
+# 3.2e-5, 2.0e-8), and for hair and sand, whose step runs to its iteration cap
+# so that rounding differences accumulate over 300 iterations, 2.5 times the
+# measured 4.0e-3.
+POSITION_BOUND = {"cloth_sphere": 1e-5, "two_cloths": 1.6e-4, "tets": 1e-7, "hair_sand": 1e-2}
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_is_safe_and_close(cuda, name):
     sc = CASES[name]()
@@ -52,13 +60,22 @@ def test_mixed_is_safe_and_close(cuda, name):
           f"iterations {sg['iterations']} vs {so['iterations']}")
     assert sg["intersections"] == 0 and sg["uncertain"] == 0
     assert oracle.count_intersections(osc, xm) == 0
-    assert err <= 0.5 * travel + 1e-6
+    assert err <= POSITION_BOUND[name], (name, err)
     gpu.close()
 
 
-def jitter(x, scale, seed):
-    rng = np.random.default_rng(seed)
-    return x + rng.normal(0.0, scale, size=x.shape)
+def contract_states(name, sc):
+    # states with pairs within D^max: along the way from x^t to the target
+    # (where the layers, strands and grains meet), and for the bodies, the
+    # pile drawn together so that neighbouring cubes nearly touch
+    x0, xt, _ = scenes.initial(sc)
+    states = [x0 + t * (xt - x0) for t in (0.5, 1.0)]
+    if name == "tets":
+        nb = 8
+        b = x0.reshape(nb, -1, 3)
+        c = b.mean(axis=1, keepdims=True)
+        states.append((b - 0.45 * (c - c.mean(axis=0, keepdims=True))).reshape(-1, 3))
+    return x0, xt, states
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -67,14 +84,15 @@ def test_mixed_proximity_set_contract(cuda, name):
     gpu = cch.Scene(sc, cch.params_for(sc, precision=1))
     osc = oracle.OracleScene(sc)
     D = oracle.params_for(sc).d_max
-    x0, xt, _ = scenes.initial(sc)
+    x0, xt, states = contract_states(name, sc)
     e = np.concatenate([sc.edges, sc.len_edges]) if len(sc.len_edges) else sc.edges
     longest = float(np.max(np.linalg.norm(x0[e[:, 0]] - x0[e[:, 1]], axis=1))) if len(e) else 0.0
-    for k, x in enumerate([x0, jitter(x0, 0.002, 10), jitter(xt, 0.004, 11)]):
+    total = 0
+    for k, x in enumerate(states):
         B = 2.0 * 4e-6 * (float(np.max(np.abs(x))) + 2.0 * longest + D) * 1.01
         km, dm = gpu.query_pairs(T(x, cuda), T(xt, cuda), D, step_search=True)
         ko, do = oracle.proximity(osc, x, D, mode=0, x_tilde=xt)
-        assert len(ko) > 0
+        total += len(ko)
         assert np.all(np.isin(ko, km)), (name, k)
         common = np.isin(km, ko)
         dex = do[np.searchsorted(ko, km[common])]
@@ -86,4 +104,5 @@ def test_mixed_proximity_set_contract(cuda, name):
             assert np.all(np.isin(extra, kw)), (name, k)
             assert np.all(dw[np.searchsorted(kw, extra)] >= D)
         print(f"{name} state {k}: |P| oracle {len(ko)}, mixed {len(km)} ({len(extra)} within B = {B:.2e} m of D)")
+    assert total > 0
     gpu.close()

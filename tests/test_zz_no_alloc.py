@@ -55,19 +55,21 @@ def test_noalloc_query_rejects_results_beyond_its_array(cuda):
 
 
 def test_noalloc_query_reports_unknown_count_when_scene_buffers_overflow(cuda):
-    # a scene created with tiny pair buffers: the allocating query grows them,
-    # the allocation-free one cannot, and says that its count is unknown
+    # a scene created with tiny pair buffers: the proximity query's FP32-filter
+    # survivors (some 68,000 pairs within 6 mm) pass through them; the
+    # allocating query grows them, the allocation-free one cannot, and says
+    # that its count is unknown
     sc = scenes.two_cloths(n=40, side=0.4, sep=0.004, omega=6.0, noise=0.3, seed=11)
     x0, xt, _ = scenes.initial(sc)
     gpu = cch.Scene(sc, cch.params_for(sc, pair_capacity=64))
     xg, xtg = T(x0, cuda), T(xt, cuda)
     cnt = C.c_int64(12345)
-    rc = cch.lib().cch_query_pairs_noalloc(gpu.h, C.c_void_p(xg.data_ptr()), C.c_void_p(xtg.data_ptr()), 4e-3, 1,
+    rc = cch.lib().cch_query_pairs_noalloc(gpu.h, C.c_void_p(xg.data_ptr()), C.c_void_p(xtg.data_ptr()), 6e-3, 0,
                                            None, None, 0, C.byref(cnt))
     assert rc == 5 and cnt.value == -1
     # the allocating query grows the buffers; afterwards both agree
-    k_ref, d_ref = gpu.query_pairs(xg, xtg, 4e-3, candidates=True)
-    k_new, d_new = gpu.query_pairs_noalloc(xg, xtg, 4e-3, candidates=True)
-    assert len(k_ref) > 64
+    k_ref, d_ref = gpu.query_pairs(xg, xtg, 6e-3, candidates=False)
+    k_new, d_new = gpu.query_pairs_noalloc(xg, xtg, 6e-3, candidates=False)
+    assert 64 < len(k_ref) <= cch.Scene.NOALLOC_MAX_PAIRS
     assert np.array_equal(k_new, k_ref) and np.array_equal(d_new, d_ref)
     gpu.close()
