@@ -464,7 +464,9 @@ def main():
                     help="skip the comparisons (mixed precision, batched, served) after the headline")
     ap.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision comparison")
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batching comparison")
-    ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
+    ap.add_argument("--requests", type=int, default=None,
+                    help="serving: requests in the stream (default: 16 in the bench line's comparison, 512 with "
+                         "--config serve, the full stream)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests batched at once")
     ap.add_argument("--ncu-warm", type=int, default=0, help="full chain steps before the --ncu-case step")
@@ -472,6 +474,8 @@ def main():
                     help="profiling aid: run one step of the workload capped at this many iterations and exit "
                          "(prints no bench line)")
     args = ap.parse_args()
+    if args.requests is None:
+        args.requests = 512 if args.config == "serve" else 16
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "serve":
@@ -671,7 +675,7 @@ def main():
             compare["batched"] = batch_compare(dev, stream, args.batch_scenes, 2, flush)
             log(f"batched: {compare['batched']}")
         if args.requests:
-            compare["served"] = serve_compare(dev, args.requests, args.rate, args.max_active)
+            compare["served"] = serve_compare(dev, args.requests, args.rate, args.max_active, precisions=("mixed",))
             log(f"served: {compare['served']}")
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----

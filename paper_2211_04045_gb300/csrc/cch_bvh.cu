@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
           bool qlow = q1 < e2;
           int4 A = qlow ? make_int4(qx, qy, 0, 0) : eb, Bv = qlow ? eb : make_int4(qx, qy, 0, 0);
           fv3 fa0 = fk(P.xf[A.x]), fa1 = fk(P.xf[A.y]), fb0 = fk(P.xf[Bv.x]), fb1 = fk(P.xf[Bv.y]);
-          float lower = __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
+          float lower = __fsub_rd(f_ss_lower(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
           if (lower >= qD) return;
           push_survivor(P, K_EE, mkkey(K_EE, min(q1, e2) - S.e0, max(q1, e2) - S.e0),
                         make_int4(A.x, A.y, Bv.x, Bv.y), lower);
@@ -663,8 +663,8 @@ __global__ void __launch_bounds__(256) k_query_ee(Pool P, int nxt, int mode, dou
       // edge is the query, so that it does not depend on the tree: in mixed
       // precision it is the pair's distance
       bool qlo = lo_e == e1;
-      float lower = qlo ? __fsub_rd(f_ss(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1))
-                        : __fsub_rd(f_ss(fb0, fb1, fa0, fa1), ftol(fb0, fb1, fa0, fa1));
+      float lower = qlo ? __fsub_rd(f_ss_lower(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1))
+                        : __fsub_rd(f_ss_lower(fb0, fb1, fa0, fa1), ftol(fb0, fb1, fa0, fa1));
       if (lower >= Df) return;
       int4 A = qlo ? ea : eb, Bv = qlo ? eb : ea;
       push_survivor(P, K_EE, key, make_int4(A.x, A.y, Bv.x, Bv.y), lower);
@@ -805,8 +805,9 @@ __global__ void k_finalize(Pool P, int nxt, int mode, double Dq) {
       float2 b = P.fbs[o];
       if (!(b.x < INFINITY)) continue;  // failed the exact box test
       if (needs_exact(P, v, b, D, P.sd[s].delta)) {
-        double d = exact_dist(P, kind, v);
-        if (d < D) emit_pair(P, nxt, s, key, v, d);
+        // the FP64 distance runs in k_exact_survivors, over a dense list
+        int e = claim(&P.cnt->n_exact[0], 3 * P.pair_cap);
+        if (e >= 0) P.exq[e] = i;
       } else {
         emit_pair(P, nxt, s, key, v, (double)b.x);  // certainly in P; its distance decides nothing
       }
@@ -816,6 +817,23 @@ __global__ void k_finalize(Pool P, int nxt, int mode, double Dq) {
     if (!(d < D) || !exact_box(P, kind, v, D)) continue;
     if (mode == 2) emit_query(P, key, d);
     else emit_pair(P, nxt, s, key, v, d);
+  }
+}
+
+// The exact FP64 distances of the survivors k_finalize left due, one per
+// thread over the dense list (the survivors of one kind stay together), so
+// that no lane of a warp idles through the FP64 arithmetic.
+__global__ void k_exact_survivors(Pool P, int nxt) {
+  if (!P.cnt->any_search) return;
+  int n = min(P.cnt->n_exact[0], 3 * P.pair_cap);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int i = P.exq[j], kind;
+    size_t o;
+    survivor_at(P, i, kind, o);
+    int4 v = P.fv[o];
+    int s = P.vscene[v.x];
+    double d = exact_dist(P, kind, v);
+    if (d < P.sd[s].d_max) emit_pair(P, nxt, s, P.fkey[o], v, d);
   }
 }
 
@@ -1064,6 +1082,10 @@ void finalize_search(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) 
   }
   k_finalize<<<grid_for(3LL * P.pair_cap, 256), 256, 0, st>>>(P, nxt, mode, Dq);
   R.launches++;
+  if (mode == 0 && !P.mixed) {
+    k_exact_survivors<<<grid_for(3LL * P.pair_cap, 256), 256, 0, st>>>(P, nxt);
+    R.launches++;
+  }
 }
 
 void search_queries(Runtime& R, int nxt, int mode, double Dq, cudaStream_t st) {

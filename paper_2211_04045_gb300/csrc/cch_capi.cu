@@ -163,9 +163,13 @@ cudaError_t alloc_pairs(Runtime& R) {
   P.fbs = nullptr;
   P.fbr = nullptr;
   if (P.mixed && (e = dalloc_in(L, &P.fd, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
+  P.exq = nullptr;
+  P.exr = nullptr;
   if (!P.mixed) {
     if ((e = dalloc_in(L, &P.fbs, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
     if ((e = dalloc_in(L, &P.fbr, (size_t)P.pair_cap)) != cudaSuccess) return e;
+    if ((e = dalloc_in(L, &P.exq, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
+    if ((e = dalloc_in(L, &P.exr, (size_t)P.pair_cap)) != cudaSuccess) return e;
   }
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.fdone, (size_t)P.cons_cap)) != cudaSuccess) return e;
@@ -286,8 +290,10 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   R.validate = prm->validate_input;
   R.iters_per_check = prm->iters_per_launch > 0 ? prm->iters_per_launch : 16;
   R.refit_only = prm->bvh_refit_only ? 1 : 0;
-  R.coop_blocks = coop_grid(256);
+  R.coop_blocks = coop_grid(256, 0);
+  R.sweep_blocks = coop_grid(256, 1);
   if (prm->sweep_blocks > 0 && prm->sweep_blocks < R.coop_blocks) R.coop_blocks = prm->sweep_blocks;
+  if (prm->sweep_blocks > 0 && prm->sweep_blocks < R.sweep_blocks) R.sweep_blocks = prm->sweep_blocks;
   R.max_polls = prm->max_polls > 0 ? prm->max_polls : 1 << 22;
 
   CK(dalloc(R, &P.x, nv));
@@ -330,6 +336,9 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
   CK(dalloc(R, &P.cmask, (size_t)nv * 32));
   CK(dalloc(R, &P.chw, nv));
+  CK(dalloc(R, &P.ccount, 2048));
+  CK(cudaMemset(P.ccount, 0, 2048 * sizeof(int)));
+  CK(dalloc(R, &P.tail, 2048));
   CK(dalloc(R, &P.bar, 2));
   CK(cudaMemset(P.bar, 0, 2 * sizeof(unsigned int)));
   CK(dalloc(R, &P.vmin, nv));

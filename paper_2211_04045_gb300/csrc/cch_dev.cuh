@@ -86,6 +86,9 @@ struct Counters {
   int any_refresh;      // some active scene reuses P in this iteration
   int ccd_hit;
   int n_ccol;           // colours of this iteration's contact colouring
+  int n_exact[2];       // pairs whose exact FP64 distance is due: of the
+                        // search's survivors [0], of the refreshed P [1]
+  int n_tail;           // contacts of the sweep's single-block tail
 };
 enum { OV_PAIRS = 1, OV_CONTACTS = 2, OV_QUERY = 16 };
 // error bits of Counters::err (ERR_COLOURS: a contact needed more colours
@@ -174,12 +177,16 @@ struct Pool {
   float* fd;               // mixed precision: the survivor's FP32 distance lower bound
   float2* fbs;             // FP64 mode: survivors' FP32 bounds (3 regions of pair_cap); +inf = dropped
   float2* fbr;             // FP64 mode: refreshed pairs' FP32 bounds (pair_cap)
+  int* exq;                // FP64 mode: survivors due an exact distance (3 pair_cap)
+  int* exr;                // FP64 mode: refreshed pairs due an exact distance (pair_cap)
   unsigned int* vmin;      // per vertex: smallest upper bound of a certain pair (fl_ord image)
   Contact* cons;
   unsigned char* fdone;    // contact colouring: coloured flags (cons_cap)
   int* ccol;               // per contact: colour class of the iteration (cons_cap)
   unsigned long long* cmask;  // per vertex: colours used there so far (CW words)
   int* chw;                // per vertex: mask words in use
+  int* ccount;             // contacts per colour of the iteration (MAX_COLOURS)
+  int* tail;               // contacts of the sweep's single-block tail (TAIL_MAX)
   int* ecol;               // per edge-length constraint: colour class (fixed)
   int n_ecol;              // edge colours (most over the scenes)
   unsigned int* bar;       // grid barrier of the sweep: arrivals, generation
@@ -438,6 +445,66 @@ __device__ __forceinline__ float f_ss(fv3 a, fv3 b, fv3 c, fv3 d) {
     }
   }
   return best;
+}
+// A lower bound of the segment-segment distance that does not rely on the
+// closest-point solution: for nearly parallel segments that solution is
+// ill-conditioned in float (its denominator |d1|^2 |d2|^2 sin^2 of the angle
+// loses its digits), and f_ss can then exceed the true distance by more than
+// the rounding margin.  The interval gap of the projections of both segments
+// onto any direction k is a lower bound of their distance; it is exact for
+// the true separation direction.  The bound is the largest gap over three
+// directions: the difference of f_ss's closest points, d1 x d2 and the part of
+// c - a orthogonal to d1.  Projections are taken relative to a, so their
+// rounding is small against FILTER_TOL (|x|max + extent).
+__device__ __forceinline__ float f_gap(fv3 k, fv3 a, fv3 b, fv3 c, fv3 d) {
+  float kk = fdot(k, k);
+  if (!(kk > 0.f)) return 0.f;
+  float pb = fdot(k, fsub(b, a)), pc = fdot(k, fsub(c, a)), pd = fdot(k, fsub(d, a));
+  float g = fmaxf(fminf(pc, pd) - fmaxf(0.f, pb), fminf(0.f, pb) - fmaxf(pc, pd));
+  return g > 0.f ? g / sqrtf(kk) : 0.f;
+}
+__device__ __forceinline__ fv3 f_seg_pt(fv3 p, fv3 a, fv3 b) {
+  fv3 e = fsub(b, a), w = fsub(p, a);
+  float ee = fdot(e, e), t = 0.f;
+  if (ee > 0.f) t = fminf(fmaxf(fdot(w, e) / ee, 0.f), 1.f);
+  return {a.x + t * e.x, a.y + t * e.y, a.z + t * e.z};
+}
+__device__ __forceinline__ float f_ss_lower(fv3 a, fv3 b, fv3 c, fv3 d) {
+  fv3 d1 = fsub(b, a), d2 = fsub(d, c), r = fsub(a, c);
+  float A = fdot(d1, d1), E = fdot(d2, d2), B = fdot(d1, d2), C = fdot(d1, r), F = fdot(d2, r);
+  // closest points as f_ss finds them: the four endpoint projections and the
+  // interior solution, whichever is nearest
+  fv3 p = a, q = f_seg_pt(a, c, d);
+  fv3 z = fsub(p, q);
+  float bz = fdot(z, z);
+  {
+    fv3 q2 = f_seg_pt(b, c, d), z2 = fsub(b, q2);
+    float b2 = fdot(z2, z2);
+    if (b2 < bz) { bz = b2; z = z2; }
+    fv3 p3 = f_seg_pt(c, a, b), z3 = fsub(p3, c);
+    float b3 = fdot(z3, z3);
+    if (b3 < bz) { bz = b3; z = z3; }
+    fv3 p4 = f_seg_pt(d, a, b), z4 = fsub(p4, d);
+    float b4 = fdot(z4, z4);
+    if (b4 < bz) { bz = b4; z = z4; }
+  }
+  float den = A * E - B * B;
+  if (den > 0.f) {
+    float s = (B * F - C * E) / den, t = (A * F - B * C) / den;
+    if (s >= 0.f && s <= 1.f && t >= 0.f && t <= 1.f) {
+      fv3 zi = {r.x + s * d1.x - t * d2.x, r.y + s * d1.y - t * d2.y, r.z + s * d1.z - t * d2.z};
+      float bi = fdot(zi, zi);
+      if (bi < bz) z = zi;
+    }
+  }
+  float g = f_gap(z, a, b, c, d);
+  g = fmaxf(g, f_gap(fcross(d1, d2), a, b, c, d));
+  if (A > 0.f) {
+    float sc = C / A;
+    fv3 k = {r.x - sc * d1.x, r.y - sc * d1.y, r.z - sc * d1.z};
+    g = fmaxf(g, f_gap(k, a, b, c, d));
+  }
+  return g;
 }
 // error margin of a float distance over these points
 __device__ __forceinline__ float ftol(fv3 a, fv3 b, fv3 c, fv3 d) {

@@ -40,7 +40,8 @@ struct Runtime {
   std::vector<void*> pair_allocs;    // pair-sized buffers (grown on overflow)
   cudaStream_t stream = nullptr;
   int scene_bits = 0;                // bits of the scene index in Morton keys
-  int coop_blocks = 0;               // grid of the cooperative colouring and sweep kernels
+  int coop_blocks = 0;               // grid of the cooperative colouring kernel
+  int sweep_blocks = 0;              // grid of the cooperative sweep kernel
   int max_polls = 1 << 22;           // bound of one device wait (polls)
   int sweeps = 1, solver = 0, ccd = 0, accept = 0, validate = 0;
   int ccd_rounds = 8;  // CCD clamp rounds per iteration
@@ -134,9 +135,10 @@ __device__ __forceinline__ int claim(int* ctr, int cap) {
 
 // FP32 bounds (lower, upper) of a pair's FP64 distance from the float copy of
 // the positions: d32 -/+ FILTER_TOL * (|x|max + extent), rounded outward.
-// VT: point-triangle minus the point's radius; EE: segment-segment; VV:
-// centre distance minus both radii.  The lower bound is the one the search's
-// FP32 filter uses.
+// VT: point-triangle minus the point's radius; EE: segment-segment, whose
+// lower bound is the separating-axis gap of f_ss_lower; VV: centre distance
+// minus both radii.  The lower bound is the one the search's FP32 filter
+// uses.
 __device__ __forceinline__ float2 pair_bounds32(const Pool& P, unsigned long long key, int4 v) {
   int kind = (int)(key >> 62);
   fv3 a = fk(P.xf[v.x]), b = fk(P.xf[v.y]);
@@ -155,8 +157,9 @@ __device__ __forceinline__ float2 pair_bounds32(const Pool& P, unsigned long lon
     return make_float2(__fsub_rd(__fsub_rd(dd, __double2float_ru(r)), t),
                        __fadd_ru(__fsub_ru(dd, __double2float_rd(r)), t));
   }
-  float dd = f_ss(a, b, c, d);
-  return make_float2(__fsub_rd(dd, t), __fadd_ru(dd, t));
+  // upper: a distance between two points of the segments; lower: the
+  // separating-axis bound (see f_ss_lower)
+  return make_float2(__fsub_rd(f_ss_lower(a, b, c, d), t), __fadd_ru(f_ss(a, b, c, d), t));
 }
 
 // Exact FP64 distances are needed only where they decide something: a pair

@@ -147,11 +147,28 @@ __global__ void k_refresh(Pool P, int cur, int nxt) {
     float2 b = P.fbr[i];
     if (b.x >= __double2float_ru(S.D)) continue;
     if (needs_exact(P, v, b, S.D, P.sd[s].delta)) {
-      double d = pair_dist(P, key, v);
-      if (d < S.D) emit_pair(P, nxt, s, key, v, d);
+      // the FP64 distance runs in k_exact_refresh, over a dense list
+      int e = claim(&P.cnt->n_exact[1], P.pair_cap);
+      if (e >= 0) P.exr[e] = i;
     } else {
       emit_pair(P, nxt, s, key, v, (double)b.x);  // certainly in P; its distance decides nothing
     }
+  }
+}
+
+// exact FP64 distances of the refreshed pairs k_refresh left due, one per
+// thread over the dense list
+__global__ void k_exact_refresh(Pool P, int cur, int nxt) {
+  if (!P.cnt->any_refresh) return;
+  int n = min(P.cnt->n_exact[1], P.pair_cap);
+  const PairBuf B = P.pb[cur];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int i = P.exr[j];
+    int4 v = B.v[i];
+    unsigned long long key = B.key[i];
+    int s = P.vscene[v.x];
+    double d = pair_dist(P, key, v);
+    if (d < P.ss[s].D) emit_pair(P, nxt, s, key, v, d);
   }
 }
 
@@ -615,10 +632,31 @@ __device__ __forceinline__ int item_gap(const OrderBufs& B, const ItemWait& w) {
 // rewritten rather than read (they hold an earlier iteration's colours).
 __device__ __forceinline__ void colour_apply(Pool& P, const OrderBufs& B, int i, const ItemWait& w, int& maxcol) {
   fence_acq_rel();
+  // the words in use and the first four mask words (256 colours) of every
+  // movable vertex, all loaded at once; later words only when those are full
   int hw[4];
-  for (int k = 0; k < 4; k++) hw[k] = w.t[k] > 0 ? __ldcg(&P.chw[w.v[k]]) : 0;
+  ulonglong2 w01[4], w23[4];
+  for (int k = 0; k < 4; k++) {
+    hw[k] = 0;
+    w01[k] = w23[k] = make_ulonglong2(0ULL, 0ULL);
+    if (w.t[k] > 0) {
+      const unsigned long long* mk = P.cmask + (size_t)w.v[k] * CW;
+      hw[k] = __ldcg(&P.chw[w.v[k]]);
+      w01[k] = __ldcg((const ulonglong2*)mk);
+      w23[k] = __ldcg((const ulonglong2*)(mk + 2));
+    }
+  }
+  unsigned long long m4[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+  for (int k = 0; k < 4; k++) {
+    if (hw[k] > 0) m4[0] |= w01[k].x;
+    if (hw[k] > 1) m4[1] |= w01[k].y;
+    if (hw[k] > 2) m4[2] |= w23[k].x;
+    if (hw[k] > 3) m4[3] |= w23[k].y;
+  }
   int col = -1;
-  for (int wd = 0; wd < CW && col < 0; wd++) {
+  for (int wd = 0; wd < 4 && col < 0; wd++)
+    if (m4[wd] != ~0ULL) col = wd * 64 + __ffsll((long long)~m4[wd]) - 1;
+  for (int wd = 4; wd < CW && col < 0; wd++) {
     unsigned long long m = 0ULL;
     for (int k = 0; k < 4; k++)
       if (wd < hw[k]) m |= __ldcg(&P.cmask[(size_t)w.v[k] * CW + wd]);
@@ -738,13 +776,24 @@ __global__ void __launch_bounds__(256, 2) k_colour(Pool P, OrderBufs B, int max_
 }
 
 // per-scene colour counts of the iteration (statistics), aggregated per warp
-__global__ void k_colour_stats(Pool P) {
+// and the number of contacts of each colour (a block histogram in shared
+// memory, added to ccount; the sweep sizes its single-block tail from it)
+__global__ void __launch_bounds__(256) k_colour_stats(Pool P) {
+  __shared__ int hist[MAX_COLOURS];
+  for (int c = threadIdx.x; c < MAX_COLOURS; c += blockDim.x) hist[c] = 0;
+  __syncthreads();
   int n = min(P.cnt->n_cons, P.cons_cap);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
     int s = P.vscene[v.x];
-    scene_reduce(P, s, P.ccol[i] + 1, cg::greater<int>(), [&](int m, int) { atomicMax(&P.ss[s].ccol, m); });
+    int c = P.ccol[i];
+    scene_reduce(P, s, c + 1, cg::greater<int>(), [&](int m, int) { atomicMax(&P.ss[s].ccol, m); });
+    if ((unsigned)c < (unsigned)MAX_COLOURS) atomicAdd(&hist[c], 1);
   }
+  __syncthreads();
+  int ncc = min(P.cnt->n_ccol, MAX_COLOURS);
+  for (int c = threadIdx.x; c < ncc; c += blockDim.x)
+    if (hist[c]) atomicAdd(&P.ccount[c], hist[c]);
 }
 
 // Grid barrier of a cooperative launch (every block resident): one arrival
@@ -753,6 +802,9 @@ __global__ void k_colour_stats(Pool P) {
 // max_polls times, after which the wait sets ERR_POLL.  A block also leaves
 // a wait once another block has given up.  Returns false when the barrier
 // failed; the caller then returns.
+// The release fence before the arrival publishes the block's writes (ordered
+// before thread 0 by the block barrier); a waiting block acquires through the
+// load that sees the new generation, the last block through a fence.
 __device__ __forceinline__ bool grid_barrier(Pool& P, unsigned& gen, int max_polls) {
   __shared__ int ok;
   __syncthreads();
@@ -762,6 +814,7 @@ __device__ __forceinline__ bool grid_barrier(Pool& P, unsigned& gen, int max_pol
     fence_acq_rel();
     unsigned a = atomicAdd(&bar[0], 1u);
     if (a == gridDim.x - 1) {
+      fence_acq_rel();
       bar[0] = 0u;
       st_release_u32(&bar[1], gen + 1);
     } else {
@@ -775,7 +828,6 @@ __device__ __forceinline__ bool grid_barrier(Pool& P, unsigned& gen, int max_pol
         __nanosleep(16);
       }
     }
-    fence_acq_rel();
     gen++;
   }
   __syncthreads();
@@ -817,8 +869,12 @@ __device__ __forceinline__ void insert_sorted(int* items, int* keys, int& m, int
 // thread takes its contacts (i = tid + k * nth) and live edges (e = tid +
 // k * nth), sorted by colour, and applies in phase c the ones of colour c.
 // With more than 32 of either per thread, every thread scans all of its
-// items in every phase instead.
-__global__ void __launch_bounds__(256, 2) k_colour_sweep(Pool P, int sweeps, int max_polls) {
+// items in every phase instead.  The last contact classes are small: from
+// the first class after which at most TAIL_MAX contacts remain, block 0
+// alone applies the rest, its threads separated by block barriers only,
+// while the other blocks wait at the next grid barrier.
+constexpr int TAIL_MAX = 2048;
+__global__ void __launch_bounds__(256, 1) k_colour_sweep(Pool P, int sweeps, int max_polls) {
   SweepCtx X;
   X.nc = min(P.cnt->n_cons, P.cons_cap);
   X.lam = sweeps > 1 ? P.lam : nullptr;
@@ -827,22 +883,55 @@ __global__ void __launch_bounds__(256, 2) k_colour_sweep(Pool P, int sweeps, int
   int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   unsigned gen = ld_acquire_u32(&P.bar[1]);
   bool few_c = X.nc <= 32 * nth, few_e = P.nl <= 32 * nth;
+  // first colour of the single-block tail (every block finds the same one)
+  int ctail = ncc;
+  if (few_c && gridDim.x > 1) {
+    int rest = 0;
+    while (ctail > 0 && rest + P.ccount[ctail - 1] <= TAIL_MAX) rest += P.ccount[--ctail];
+  }
   int ci[32], cc[32], ei[32], ec[32];
   int mc = 0, me = 0;
   if (few_c)
-    for (int i = tid; i < X.nc; i += nth) insert_sorted(ci, cc, mc, i, P.ccol[i]);
+    for (int i = tid; i < X.nc; i += nth) {
+      int c = P.ccol[i];
+      if (c < ctail) insert_sorted(ci, cc, mc, i, c);
+      else {
+        int t = atomicAdd(&P.cnt->n_tail, 1);
+        if (t < TAIL_MAX) P.tail[t] = i;
+      }
+    }
   if (few_e)
     for (int e = tid; e < P.nl; e += nth)
       if (edge_live(P, e)) insert_sorted(ei, ec, me, e, P.ecol[e]);
   for (int sw = 0; sw < sweeps; sw++) {
     bool first = sw == 0;
     int p = 0;
-    for (int c = 0; c < ncc; c++) {
+    for (int c = 0; c < ctail; c++) {
       if (few_c) {
         for (; p < mc && cc[p] == c; p++) apply_contact(P, X, ci[p], first);
       } else {
         for (int i = tid; i < X.nc; i += nth)
           if (P.ccol[i] == c) apply_contact(P, X, i, first);
+      }
+      if (!grid_barrier(P, gen, max_polls)) return;
+    }
+    if (ctail < ncc) {
+      // the tail list is complete: every append preceded a grid barrier or
+      // this one
+      if (ctail == 0 && !grid_barrier(P, gen, max_polls)) return;
+      if (blockIdx.x == 0) {
+        int ti[TAIL_MAX / 256], tc[TAIL_MAX / 256];
+        int mt = 0;
+        int nt = min(__ldcg(&P.cnt->n_tail), TAIL_MAX);
+        for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+          int i = __ldcg(&P.tail[j]);
+          insert_sorted(ti, tc, mt, i, P.ccol[i]);
+        }
+        int q = 0;
+        for (int c = ctail; c < ncc; c++) {
+          for (; q < mt && tc[q] == c; q++) apply_contact(P, X, ti[q], first);
+          __syncthreads();
+        }
       }
       if (!grid_barrier(P, gen, max_polls)) return;
     }
@@ -1326,6 +1415,8 @@ __global__ void k_control(Pool P, int cur) {
     C->n_cons = 0;
     C->vcontacts = 0;
     C->n_ccol = 0;
+    C->n_exact[0] = C->n_exact[1] = 0;
+    C->n_tail = 0;
   }
 }
 
@@ -1351,14 +1442,14 @@ static cudaError_t coop_launch(K kern, int blocks, int threads, cudaStream_t st,
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(threads), argv, 0, st);
 }
 
-int coop_grid(int threads) {
+// Resident blocks of the cooperative kernels: the colouring (which = 0) and
+// the sweep (which = 1).
+int coop_grid(int threads, int which) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int per2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour, threads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_colour_sweep, threads, 0);
-  if (per2 < per) per = per2;
+  if (which == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour, threads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_sweep, threads, 0);
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -1413,6 +1504,10 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     R.launches++;
   }
   k_refresh<<<grid_for(P.pair_cap, 256), 256, 0, st>>>(P, cur, nxt);
+  if (!P.mixed) {
+    k_exact_refresh<<<grid_for(P.pair_cap, 256), 256, 0, st>>>(P, cur, nxt);
+    R.launches++;
+  }
   prof_mark(R, PG_REFRESH, 1, st);
   prof_mark(R, PG_ASSEMBLE, 0, st);
   k_assemble<<<grid_for(P.act_cap, 128), 128, 0, st>>>(P, nxt);
@@ -1454,12 +1549,13 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     prof_mark(R, PG_ORDER, 1, st);
     prof_mark(R, PG_COLOUR, 0, st);
     cudaMemsetAsync(P.fdone, 0, (size_t)P.cons_cap, st);
+    cudaMemsetAsync(P.ccount, 0, sizeof(int) * MAX_COLOURS, st);
     e = coop_launch(k_colour, R.coop_blocks, 256, st, P, B, R.max_polls);
     if (e == cudaSuccess) k_colour_stats<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P);
     prof_mark(R, PG_COLOUR, 1, st);
     prof_mark(R, PG_SWEEP, 0, st);
     cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = coop_launch(k_colour_sweep, R.coop_blocks, 256, st, P, R.sweeps, R.max_polls);
+    if (e == cudaSuccess) e = coop_launch(k_colour_sweep, R.sweep_blocks, 256, st, P, R.sweeps, R.max_polls);
     prof_mark(R, PG_SWEEP, 1, st);
     R.launches += 7;
   }

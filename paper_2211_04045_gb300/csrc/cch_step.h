@@ -3,7 +3,7 @@
 #include "cch_host.h"
 
 namespace cch {
-int coop_grid(int threads);
+int coop_grid(int threads, int which);
 void step_init(Runtime& R, cudaStream_t st, int mode);
 void output_scene(Runtime& R, int s, cudaStream_t st);
 void set_any_search(Runtime& R, cudaStream_t st);

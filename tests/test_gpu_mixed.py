@@ -106,3 +106,50 @@ def test_mixed_proximity_set_contract(cuda, name):
         print(f"{name} state {k}: |P| oracle {len(ko)}, mixed {len(km)} ({len(extra)} within B = {B:.2e} m of D)")
     assert total > 0
     gpu.close()
+
+
+def near_parallel_pairs(n_pairs, seed):
+    """n_pairs pairs of 8 mm segments, each pair alone in a 5 cm cell of a
+    lattice reaching 1.5 m from the origin: the second segment at an angle of
+    1e-7 to 1 rad to the first and 1e-10 to 1e-3 m from it (log-uniform),
+    shifted along it.  Nearly parallel segments are where a float
+    closest-point solution is ill-conditioned."""
+    from paper_2211_04045_gb300.scenes import Scene
+    rng = np.random.default_rng(seed)
+    L = 0.008
+    k = int(np.ceil(n_pairs ** (1.0 / 3.0)))
+    pts = []
+    for i in range(n_pairs):
+        ctr = (np.array([i % k, (i // k) % k, i // (k * k)]) - (k - 1) / 2.0) * 0.05 + 0.5
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        v = np.cross(u, rng.normal(size=3))
+        v /= np.linalg.norm(v)
+        w = np.cross(u, v)
+        th, h = 10 ** rng.uniform(-7, 0), 10 ** rng.uniform(-10, -3)
+        u2 = np.cos(th) * u + np.sin(th) * v
+        s0, t0 = rng.uniform(-1, 1, 2) * L
+        pts += [ctr - (L / 2 + s0) * u, ctr + (L / 2 - s0) * u,
+                ctr + h * w - (L / 2 + t0) * u2, ctr + h * w + (L / 2 - t0) * u2]
+    x = np.array(pts)
+    edges = np.arange(len(x), dtype=np.int32).reshape(-1, 2)
+    return Scene("near_parallel_pairs", np.ones(len(x)), np.zeros((0, 3), np.int32), edges,
+                 np.zeros((0, 2), np.int32), np.zeros(0, np.int32), x, np.zeros_like(x), 1.0 / 30, np.zeros(3))
+
+
+def test_mixed_lower_bounds_hold_on_near_parallel_edges(cuda):
+    sc = near_parallel_pairs(3000, seed=5)
+    x = sc.x0
+    gpu = cch.Scene(sc, cch.params_for(sc, precision=1))
+    osc = oracle.OracleScene(sc)
+    D = 4e-3
+    km, dm = gpu.query_pairs(T(x, cuda), T(x, cuda), D, step_search=True)
+    ko, do = oracle.proximity(osc, x, D, mode=0, x_tilde=x)
+    assert len(ko) > 2500
+    assert np.all(np.isin(ko, km))
+    common = np.isin(km, ko)
+    dex = do[np.searchsorted(ko, km[common])]
+    B = 2.0 * 4e-6 * (float(np.max(np.abs(x))) + 2.0 * 0.008 + D) * 1.01
+    assert np.all(dm[common] <= dex), float(np.max(dm[common] - dex))
+    assert np.all(dex - dm[common] <= B)
+    gpu.close()
