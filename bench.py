@@ -212,9 +212,11 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
     which = rng.integers(0, len(scs), size=N)
     inputs = []
     for i in range(N):
+        # a seeded random (x^t, x~) pair: the scene's start and a target that
+        # moves every movable vertex by N(0, 1 mm)
         sc = scs[which[i]]
-        x, xt, v = scenes.initial(sc)
-        xt = xt + rng.normal(0.0, 1e-4, size=xt.shape) * (sc.inv_mass > 0)[:, None]
+        x = sc.x0
+        xt = x + rng.normal(0.0, 1e-3, size=x.shape) * (sc.inv_mass > 0)[:, None]
         inputs.append((torch.tensor(x, device=dev), torch.tensor(xt, device=dev)))
     out = {"requests": N, "rate_per_s": rate, "max_active": max_active, "budget_bytes": 80 << 30,
            "scene_prims": [prims(sc) for sc in scs]}
@@ -411,13 +413,14 @@ def run_reference(args):
     return 0
 
 
-def mixed_compare(sc, inputs, refs, dev, stream, flush, tune_iters, log):
-    """The mixed-precision form (FP32 distances and projection, FP64 forward
-    step, CCD and acceptance) timed on the same step inputs as the FP64 run;
-    its position error against the FP64 results is reported per step."""
+def variant_compare(sc, kw, inputs, refs, dev, stream, flush, tune_iters, log, name):
+    """A variant of the step (mixed precision: FP32 distances and projection,
+    FP64 forward step, CCD and acceptance; or the greedy colouring) timed on
+    the same step inputs as the headline run; its position difference from
+    the headline results is reported per step."""
     import torch
     from paper_2211_04045_gb300 import cch
-    g = cch.Scene(sc, cch.params_for(sc, precision=1, accept_check=1), stream=stream.cuda_stream)
+    g = cch.Scene(sc, cch.params_for(sc, accept_check=1, **kw), stream=stream.cuda_stream)
     g.step(inputs[0][0], inputs[0][1])  # warm-up: graph capture
     if tune_iters:
         g.autotune(inputs[0][0], inputs[0][1], probe_iters=tune_iters)
@@ -435,11 +438,11 @@ def mixed_compare(sc, inputs, refs, dev, stream, flush, tune_iters, log):
         isect += st["intersections"]
         unc += st["uncertain"]
     g.close()
-    log(f"mixed: {', '.join(f'{m:.0f} ms' for m in ms)}; max |x_mixed - x_fp64| per step "
+    log(f"{name}: {', '.join(f'{m:.0f} ms' for m in ms)}; max |x - x_headline| per step "
         + ", ".join(f"{e:.2e}" for e in errs))
     return {"value": len(ms) / (sum(ms) / 1000.0), "unit": "steps/s", "steps": len(ms),
             "p50_ms": float(np.percentile(ms, 50)), "iterations_per_step": float(np.mean(its)),
-            "max_abs_err_vs_fp64_m": max(errs), "intersections": int(isect), "uncertain": int(unc)}
+            "max_abs_diff_vs_headline_m": max(errs), "intersections": int(isect), "uncertain": int(unc)}
 
 
 def main():
@@ -455,6 +458,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--gap", action="store_true", help="gap contact constraints instead of the volume-based ones")
+    ap.add_argument("--colouring", type=int, default=1, choices=[0, 1],
+                    help="randomized colouring of the Gauss-Seidel sweep: 1 level (default), 0 greedy")
     ap.add_argument("--step-rule", default="distance", choices=["distance", "ccd"],
                     help="forward step size: the distance bound (Eq. forward2) or the CCD-based scheme of Sec. 5.1")
     ap.add_argument("--no-cpu", action="store_true")
@@ -464,9 +469,7 @@ def main():
                     help="skip the comparisons (mixed precision, batched, served) after the headline")
     ap.add_argument("--mixed-steps", type=int, default=3, help="timed steps of the mixed-precision comparison")
     ap.add_argument("--batch-scenes", type=int, default=64, help="scenes of the batching comparison")
-    ap.add_argument("--requests", type=int, default=None,
-                    help="serving: requests in the stream (default: 16 in the bench line's comparison, 512 with "
-                         "--config serve, the full stream)")
+    ap.add_argument("--requests", type=int, default=None, help="serving: requests in the stream (512)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests batched at once")
     ap.add_argument("--ncu-warm", type=int, default=0, help="full chain steps before the --ncu-case step")
@@ -475,7 +478,7 @@ def main():
                          "(prints no bench line)")
     args = ap.parse_args()
     if args.requests is None:
-        args.requests = 512 if args.config == "serve" else 16
+        args.requests = 512
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "serve":
@@ -495,7 +498,7 @@ def main():
     gs = args.solver == "gs"
     prm = cch.params_for(sc, precision=1 if args.precision == "mixed" else 0,
                          solver=0 if gs else 1, constraint_form=1 if args.gap else 0,
-                         step_rule=1 if args.step_rule == "ccd" else 0, accept_check=1)
+                         step_rule=1 if args.step_rule == "ccd" else 0, accept_check=1, colouring=args.colouring)
     if args.ncu_case:
         x0, xt0, v0 = scenes.initial(sc)
         x, xt, v = (torch.tensor(a, device=dev) for a in (x0, xt0, v0))
@@ -667,9 +670,13 @@ def main():
     compare = None
     if rank == 0 and world == 1 and not args.no_compare:
         compare = {}
+        tune_it = 0 if args.no_tune else args.tune_iters
         if keep and args.precision == "fp64":
-            compare["mixed"] = mixed_compare(sc, kept_in, kept_out, dev, stream, flush,
-                                             0 if args.no_tune else args.tune_iters, log)
+            compare["mixed"] = variant_compare(sc, dict(precision=1, colouring=args.colouring), kept_in, kept_out,
+                                               dev, stream, flush, tune_it, log, "mixed")
+        if keep and gs and args.colouring == 1:
+            compare["greedy_colouring"] = variant_compare(sc, dict(precision=prm.precision, colouring=0), kept_in,
+                                                          kept_out, dev, stream, flush, tune_it, log, "greedy")
         del kept_in, kept_out
         if args.batch_scenes:
             compare["batched"] = batch_compare(dev, stream, args.batch_scenes, 2, flush)
@@ -694,6 +701,7 @@ def main():
                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
                "config": {"workload": f"{wname}_{args.precision}" + ("_jacobi" if not gs else "")
+                          + ("_greedy" if gs and args.colouring == 0 else "")
                           + ("_gap" if args.gap else "") + ("_ccdstep" if args.step_rule == "ccd" else ""),
                           "verts": n, "tris": T, "edges": E, "len_edges": NL, "dt": sc.dt,
                           "l2": "flushed between steps (256 MiB write)",

@@ -55,11 +55,21 @@ typedef enum {
 typedef enum { CCH_PREC_FP64 = 0, CCH_PREC_MIXED = 1 } cch_precision;
 /* Backward step (Sec. 4.3): gs_sweeps multi-colour projected Gauss-Seidel
  * sweeps per iteration (the contact colour classes in ascending colour, then
- * the edge-length classes; each group coloured greedily in descending
- * priority splitmix64(seed ^ key)), or
+ * the edge-length classes; each group coloured by cch_colouring), or
  * the projected Jacobi variant (Sec. 4.3.2) with per-constraint
  * under-relaxation jacobi_omega / (most constraints at one of its vertices). */
 typedef enum { CCH_SOLVER_GAUSS_SEIDEL = 0, CCH_SOLVER_JACOBI = 1 } cch_solver;
+/* Randomized colouring of the multi-colour Gauss-Seidel sweep (Sec. 4.3), over
+ * the constraints in descending priority splitmix64(seed ^ key), conflicts
+ * through movable vertices only.  CCH_COLOUR_GREEDY: each constraint takes the
+ * smallest colour not used by a higher-priority conflicting constraint (the
+ * Jones-Plassmann colouring; fewest classes, computed by a colouring pass each
+ * iteration, then one class per phase).  CCH_COLOUR_LEVEL (default): one more
+ * than the largest such colour, the round in which its priority first exceeds
+ * that of all its uncoloured conflicting constraints (Luby's rounds); the
+ * classes then follow the priorities, and a dataflow sweep applies them
+ * without a colouring pass. */
+typedef enum { CCH_COLOUR_GREEDY = 0, CCH_COLOUR_LEVEL = 1 } cch_colouring;
 /* Contact constraints: the volume-based constraints of Sec. 4.1 (default), or
  * the gap constraints c = d/delta - 1 the paper compares them with (gradient:
  * the closest-point weights times the unit separation direction, over delta).
@@ -116,7 +126,7 @@ typedef struct {
                             overflow and the step is run again                 */
   int32_t sweep_blocks;  /* blocks of the cooperative sweep kernels (0 = every
                             block that fits on the device at once)             */
-  int32_t reserved_;
+  int32_t colouring;     /* cch_colouring of the Gauss-Seidel sweep            */
 } cch_params;
 
 /* Mesh of one scene (host pointers, copied at creation).
@@ -167,7 +177,7 @@ typedef struct {
   int64_t contact_vertices;  /* sum over iterations of the distinct movable
                                 vertices of the contact constraints           */
   int32_t contact_colours;   /* most colours of one iteration's contact
-                                colouring (Gauss-Seidel)                      */
+                                colouring (Gauss-Seidel, cch_colouring)       */
   int32_t edge_colours;      /* colours of the edge-length constraints        */
   int64_t pair_vertices;     /* sum over iterations of the distinct vertices
                                 of the pairs of P                             */

@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("gamma", C.c_double), ("eps", C.c_double), ("jacobi_omega", C.c_double),
                 ("max_iters", C.c_int32), ("gs_sweeps", C.c_int32), ("solver", C.c_int32),
                 ("ccd_check", C.c_int32), ("search_mode", C.c_int32), ("constraint_form", C.c_int32),
-                ("step_rule", C.c_int32), ("ccd_rounds", C.c_int32), ("seed", C.c_uint64)]
+                ("step_rule", C.c_int32), ("ccd_rounds", C.c_int32), ("colouring", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class Stats(C.Structure):
@@ -97,8 +98,8 @@ def lib():
             L.orc_contact_constraint.argtypes = [C.c_int, p, p, d, C.c_int, p, p]
             L.orc_backward_once.restype = C.c_int
             L.orc_backward_once.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, p, p, p]
-            L.orc_greedy_colouring.restype = i32
-            L.orc_greedy_colouring.argtypes = [i64, p, p, p, i64, p]
+            L.orc_colouring.restype = i32
+            L.orc_colouring.argtypes = [i32, i64, p, p, p, i64, p]
             L.orc_contact_colours.restype = i64
             L.orc_contact_colours.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, p, p, p, i64]
             L.orc_edge_colours.restype = i32
@@ -213,15 +214,20 @@ def backward_once(osc: OracleScene, prm: Params, x, y_in, y_target):
     return out
 
 
-def greedy_colouring(verts, prio, inv_mass):
-    """Greedy colouring (Sec. 4.3, R11) of constraints with vertex lists
-    verts (m x 4, -1 = absent) and priorities prio.  Returns (colours, count)."""
+def colouring(verts, prio, inv_mass, kind=0):
+    """Randomized colouring (Sec. 4.3, R11) of constraints with vertex lists
+    verts (m x 4, -1 = absent) and priorities prio: kind 0 greedy, 1 level.
+    Returns (colours, count)."""
     verts = np.ascontiguousarray(verts, dtype=np.int32).reshape(-1, 4)
     prio = np.ascontiguousarray(prio, dtype=np.uint64).reshape(-1)
     im = _f64(inv_mass)
     col = np.zeros(max(len(prio), 1), np.int32)
-    k = lib().orc_greedy_colouring(len(prio), _ptr(verts), _ptr(prio), _ptr(im), len(im), _ptr(col))
+    k = lib().orc_colouring(int(kind), len(prio), _ptr(verts), _ptr(prio), _ptr(im), len(im), _ptr(col))
     return col[:len(prio)], int(k)
+
+
+def greedy_colouring(verts, prio, inv_mass):
+    return colouring(verts, prio, inv_mass, 0)
 
 
 def contact_colours(osc: OracleScene, prm: Params, x, x_tilde=None):

@@ -60,7 +60,7 @@ void orc_params_default(orc_params* p) {
   p->d_min = 2e-3; p->d_max = 4e-3; p->delta = 1e-3; p->sigma = 1.1; p->gamma = 0.9;
   p->eps = 1e-4; p->jacobi_omega = 0.5;
   p->max_iters = 2048; p->gs_sweeps = 1; p->solver = 0; p->ccd_check = 0; p->search_mode = 2;
-  p->constraint_form = 0; p->step_rule = 0; p->ccd_rounds = 8; p->seed = 0x2211040450ULL;
+  p->constraint_form = 0; p->step_rule = 0; p->ccd_rounds = 8; p->colouring = 1; p->seed = 0x2211040450ULL;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -766,10 +766,14 @@ typedef struct {
  * and the classes are applied one after the other, the constraints of one
  * class in parallel.  Here the randomness is a priority per constraint,
  * splitmix64(seed ^ key) (a bijection of the unique keys, so no ties), and
- * the colouring is the greedy one in descending priority: each constraint
- * takes the smallest colour not used by a higher-priority constraint that
- * shares a movable vertex with it (static vertices never change y, so they
- * create no conflict).  Contacts are coloured among themselves every
+ * the colouring is one of two randomized colourings, both taken over the
+ * constraints in descending priority with conflicts through movable vertices
+ * only (static vertices never change y): the greedy one, each constraint the
+ * smallest colour not used by a higher-priority constraint sharing a movable
+ * vertex with it (the Jones-Plassmann colouring), or the level one, one more
+ * than the largest colour among those (the round in which the constraint's
+ * priority first exceeds that of all its uncoloured conflicting constraints,
+ * as in Luby's rounds).  Contacts are coloured among themselves every
  * iteration, edge-length constraints among themselves.  The sequential sweep
  * applies the contact classes in ascending colour, then the edge classes;
  * inside a class the order does not change the result (no shared movable
@@ -792,6 +796,26 @@ static void il_push(ilist* l, int32_t v) {
     l->c = (int32_t*)realloc(l->c, sizeof(int32_t) * (size_t)l->cap);
   }
   l->c[l->n++] = v;
+}
+
+/* Level colouring of cs[0..n), sorted by descending priority: one more than
+ * the largest colour of an earlier constraint sharing a movable vertex with
+ * it (0 if none), kept per vertex as the largest colour there so far. */
+static int32_t colour_levels(cons* cs, int64_t n, const uint8_t* movable, int64_t nverts) {
+  int32_t* top = (int32_t*)malloc(sizeof(int32_t) * ((size_t)nverts + 1));
+  for (int64_t v = 0; v < nverts; v++) top[v] = -1;
+  int32_t ncol = 0;
+  for (int64_t i = 0; i < n; i++) {
+    int32_t col = 0;
+    for (int k = 0; k < cs[i].nv; k++)
+      if (movable[cs[i].v[k]] && top[cs[i].v[k]] + 1 > col) col = top[cs[i].v[k]] + 1;
+    cs[i].colour = col;
+    if (col + 1 > ncol) ncol = col + 1;
+    for (int k = 0; k < cs[i].nv; k++)
+      if (movable[cs[i].v[k]]) top[cs[i].v[k]] = col;
+  }
+  free(top);
+  return ncol;
 }
 
 /* Greedy colouring of cs[0..n), which the caller has sorted by descending
@@ -970,7 +994,8 @@ static int64_t build_edges(const orc_topology* t, const orc_params* prm, const d
   }
   *ncol = max_vertex_degree(ce, ne, movable, t->n_verts);
   qsort(ce, (size_t)ne, sizeof(cons), cmp_cons_prio_desc);
-  *ncolours = colour_greedy(ce, ne, movable, t->n_verts, 0);
+  *ncolours = prm->colouring == 1 ? colour_levels(ce, ne, movable, t->n_verts)
+                                  : colour_greedy(ce, ne, movable, t->n_verts, 0);
   qsort(ce, (size_t)ne, sizeof(cons), cmp_cons_colour);
   *out = ce;
   return ne;
@@ -1008,6 +1033,7 @@ static int64_t build_contacts(const orc_topology* t, const orc_params* prm, cons
   *ncol = max_vertex_degree(cc, nc, movable, t->n_verts);
   qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_prio_desc);
   *ncolours = colour_greedy(cc, nc, movable, t->n_verts, nverts_used);
+  if (prm->colouring == 1) *ncolours = colour_levels(cc, nc, movable, t->n_verts);
   qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_colour);
   *out = cc;
   return nc;
@@ -1045,8 +1071,8 @@ static void backward(const orc_topology* t, const orc_params* prm, cons* cc, int
   }
 }
 
-int32_t orc_greedy_colouring(int64_t n, const int32_t* verts, const uint64_t* prio, const double* inv_mass,
-                             int64_t n_verts, int32_t* colour) {
+int32_t orc_colouring(int32_t kind, int64_t n, const int32_t* verts, const uint64_t* prio, const double* inv_mass,
+                      int64_t n_verts, int32_t* colour) {
   cons* cs = (cons*)calloc((size_t)n + 1, sizeof(cons));
   uint8_t* movable = (uint8_t*)malloc((size_t)n_verts + 1);
   for (int64_t v = 0; v < n_verts; v++) movable[v] = inv_mass[v] > 0.0;
@@ -1059,7 +1085,7 @@ int32_t orc_greedy_colouring(int64_t n, const int32_t* verts, const uint64_t* pr
     cs[i].key = (uint64_t)i; /* remembers the input position */
   }
   qsort(cs, (size_t)n, sizeof(cons), cmp_cons_prio_desc);
-  int32_t ncol = colour_greedy(cs, n, movable, n_verts, 0);
+  int32_t ncol = kind == 1 ? colour_levels(cs, n, movable, n_verts) : colour_greedy(cs, n, movable, n_verts, 0);
   for (int64_t i = 0; i < n; i++) colour[cs[i].key] = cs[i].colour;
   free(cs); free(movable);
   return ncol;

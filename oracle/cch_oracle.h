@@ -54,7 +54,11 @@ typedef struct {
                             step size (the comparison scheme of Sec. 5.1)     */
   int32_t ccd_rounds;    /* CCD clamp rounds before the scene's step is
                             frozen for the iteration (CCD check and rule)     */
-  uint64_t seed;         /* sweep priorities (R11)                            */
+  int32_t colouring;     /* randomized colouring of the Gauss-Seidel sweep
+                            (R11): 0 greedy (smallest free colour), 1 level
+                            (the round in which the constraint's priority
+                            first exceeds its uncoloured neighbours')         */
+  uint64_t seed;         /* colouring priorities (R11)                        */
 } orc_params;
 
 typedef struct {
@@ -130,12 +134,14 @@ int orc_backward_once(const orc_topology* t, const orc_params* prm, const double
                       const double* y_in, const double* y_target, double* y_out);
 
 /* ---- colouring of the Gauss-Seidel sweep (Sec. 4.3) ---- */
-/* Greedy colouring of n constraints with vertex lists verts[4*i..4*i+3] (-1
- * = absent) and priorities prio[i]: taken by descending priority, each gets
- * the smallest colour not used by an earlier constraint sharing a movable
- * vertex with it.  colour[i] receives it; returns the number of colours. */
-int32_t orc_greedy_colouring(int64_t n, const int32_t* verts, const uint64_t* prio, const double* inv_mass,
-                             int64_t n_verts, int32_t* colour);
+/* Colouring of n constraints with vertex lists verts[4*i..4*i+3] (-1 =
+ * absent) and priorities prio[i], taken by descending priority: kind 0
+ * greedy, each gets the smallest colour not used by an earlier constraint
+ * sharing a movable vertex with it; kind 1 level, one more than the largest
+ * colour among those (0 if none).  colour[i] receives it; returns the number
+ * of colours. */
+int32_t orc_colouring(int32_t kind, int64_t n, const int32_t* verts, const uint64_t* prio, const double* inv_mass,
+                      int64_t n_verts, int32_t* colour);
 /* The contact constraints that a backward step at state x builds from a
  * search at D^max (keys ascending) and the colour of each; returns the count
  * (up to cap written). */

@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("validate_input", C.c_int32), ("iters_per_launch", C.c_int32), ("bvh_refit_only", C.c_int32),
                 ("constraint_form", C.c_int32), ("step_rule", C.c_int32), ("ccd_rounds", C.c_int32),
                 ("seed", C.c_uint64), ("max_polls", C.c_int32), ("pair_capacity", C.c_int32),
-                ("sweep_blocks", C.c_int32), ("reserved_", C.c_int32)]
+                ("sweep_blocks", C.c_int32), ("colouring", C.c_int32)]
 
 
 class Topology(C.Structure):

@@ -132,6 +132,7 @@ cch_status validate_params(const cch_params* p) {
   if (p->ccd_rounds < 0 || p->ccd_rounds > 64) return CCH_E_INVALID_ARG;
   if (p->iters_per_launch < 0 || p->iters_per_launch > 4096) return CCH_E_INVALID_ARG;
   if (p->max_polls < 0 || p->pair_capacity < 0 || p->sweep_blocks < 0) return CCH_E_INVALID_ARG;
+  if (p->colouring != CCH_COLOUR_GREEDY && p->colouring != CCH_COLOUR_LEVEL) return CCH_E_INVALID_ARG;
   return CCH_OK;
 }
 
@@ -156,7 +157,7 @@ cudaError_t alloc_pairs(Runtime& R) {
     if ((e = dalloc_in(L, &P.pb[b].v, P.pair_cap)) != cudaSuccess) return e;
     if ((e = dalloc_in(L, &P.pb[b].d, P.pair_cap)) != cudaSuccess) return e;
   }
-  if ((e = dalloc_in(L, &P.act, P.act_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.act, 3 * (size_t)P.act_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.fkey, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.fv, 3 * (size_t)P.pair_cap)) != cudaSuccess) return e;
   P.fd = nullptr;
@@ -172,7 +173,7 @@ cudaError_t alloc_pairs(Runtime& R) {
     if ((e = dalloc_in(L, &P.exr, (size_t)P.pair_cap)) != cudaSuccess) return e;
   }
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
-  if ((e = dalloc_in(L, &P.fdone, (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.fdone, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.ccol, (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.iprio, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.iid, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
@@ -281,6 +282,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   while ((1 << R.scene_bits) < n_scenes) R.scene_bits++;
   R.sweeps = prm->gs_sweeps;
   R.solver = prm->solver;
+  R.colouring = prm->colouring;
   R.ccd = prm->ccd_check || prm->step_rule == CCH_STEP_CCD;
   R.ccd_rounds = prm->ccd_rounds;
   // the CCD-based step relies on the root-finding CCD, which can miss a
@@ -336,6 +338,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(cudaMemset(P.cnt, 0, sizeof(Counters)));
   CK(dalloc(R, &P.cmask, (size_t)nv * 32));
   CK(dalloc(R, &P.chw, nv));
+  CK(dalloc(R, &P.vlevel, nv));
   CK(dalloc(R, &P.ccount, 2048));
   CK(cudaMemset(P.ccount, 0, 2048 * sizeof(int)));
   CK(dalloc(R, &P.tail, 2048));
@@ -414,31 +417,63 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
     for (int v = 0; v < nv; v++)
       if ((vflag[v] & VF_MOVABLE) && edeg[v] > R.max_vedges) R.max_vedges = edeg[v];
     std::sort(order.begin(), order.end(), [&](int p, int q) { return eprio[p] > eprio[q]; });
+    // greedy: the smallest colour not used at its movable ends so far; level:
+    // one more than the largest colour there so far
     std::vector<std::vector<int>> used(nv);
+    std::vector<int> top(nv, -1);
     std::vector<int> ecol(nl, 0);
     std::vector<char> taken;
     P.n_ecol = 0;
     for (int e : order) {
       int ends[2] = {lv[e].x, lv[e].y};
-      size_t tot = 0;
-      for (int v : ends)
-        if (vflag[v] & VF_MOVABLE) tot += used[v].size();
-      taken.assign(tot + 1, 0);
-      for (int v : ends)
-        if (vflag[v] & VF_MOVABLE)
-          for (int c : used[v])
-            if ((size_t)c <= tot) taken[c] = 1;
       int c = 0;
-      while (taken[c]) c++;
+      if (R.colouring == CCH_COLOUR_LEVEL) {
+        for (int v : ends)
+          if ((vflag[v] & VF_MOVABLE) && top[v] + 1 > c) c = top[v] + 1;
+        for (int v : ends)
+          if (vflag[v] & VF_MOVABLE) top[v] = c;
+      } else {
+        size_t tot = 0;
+        for (int v : ends)
+          if (vflag[v] & VF_MOVABLE) tot += used[v].size();
+        taken.assign(tot + 1, 0);
+        for (int v : ends)
+          if (vflag[v] & VF_MOVABLE)
+            for (int u : used[v])
+              if ((size_t)u <= tot) taken[u] = 1;
+        while (taken[c]) c++;
+        for (int v : ends)
+          if (vflag[v] & VF_MOVABLE) used[v].push_back(c);
+      }
       ecol[e] = c;
-      for (int v : ends)
-        if (vflag[v] & VF_MOVABLE) used[v].push_back(c);
       SceneDesc& d = R.sd[lv[e].z];
       if (c + 1 > d.n_ecol) d.n_ecol = c + 1;
       if (c + 1 > P.n_ecol) P.n_ecol = c + 1;
     }
     CK(upload(R, &P.ecol, ecol));
     CK(cudaMemcpy(P.sd, R.sd.data(), sizeof(SceneDesc) * R.sd.size(), cudaMemcpyHostToDevice));
+    // the level colouring's dataflow sweep waits on each edge's rank among
+    // the edges of each of its vertices, by descending priority
+    std::vector<int> estart((size_t)nv + 1, 0), elist(2 * (size_t)nl);
+    for (int v = 0; v < nv; v++) estart[v + 1] = estart[v] + edeg[v];
+    std::vector<int> fill(estart.begin(), estart.end() - 1);
+    for (int e = 0; e < nl; e++) {
+      elist[fill[lv[e].x]++] = 2 * e;
+      elist[fill[lv[e].y]++] = 2 * e + 1;
+    }
+    std::vector<int2> erank(nl);
+    for (int v = 0; v < nv; v++) {
+      int a = estart[v], b = estart[v + 1];
+      std::sort(elist.begin() + a, elist.begin() + b,
+                [&](int p, int q) { return eprio[p >> 1] > eprio[q >> 1]; });
+      for (int r = 0; r < b - a; r++) {
+        int ent = elist[a + r];
+        if (ent & 1) erank[ent >> 1].y = r;
+        else erank[ent >> 1].x = r;
+      }
+    }
+    CK(upload(R, &P.edeg, edeg));
+    CK(upload(R, &P.erank, erank));
   }
   // pair-sized buffers last (they are re-allocated on growth)
   long long guess = prm->pair_capacity > 0 ? (long long)prm->pair_capacity : 4LL * (nt + ne + nq) + 4096;
@@ -651,6 +686,7 @@ cch_status cch_params_default(cch_params* p) {
   p->constraint_form = CCH_FORM_VOLUME;
   p->step_rule = CCH_STEP_DISTANCE;
   p->ccd_rounds = 8;
+  p->colouring = CCH_COLOUR_LEVEL;
   p->seed = 0x2211040450ULL;
   return CCH_OK;
 }

@@ -73,7 +73,7 @@ struct SceneState {
 // Device-wide counters and flags.
 struct Counters {
   int n_pairs[2];       // pairs in buffer 0 / 1
-  int n_active;         // active contact candidates (dist < delta)
+  int n_active[3];      // active contact candidates (dist < delta) per kind
   int n_cons;           // assembled contact constraints
   int vcontacts;        // most contacts at one movable vertex (this iteration)
   int overflow;         // OV_* bits
@@ -163,6 +163,11 @@ struct Pool {
   int4* ev;                // a, b, scene, -
   int4* lv;                // i, j, scene, -
   P4* lg;                  // per edge-length constraint: g = u/L0 (xyz), den (w)
+  int* edeg;               // per vertex: edge-length constraints at it
+  int2* erank;             // per edge-length constraint: its rank at vertex i and
+                           // at vertex j among that vertex's edges, by descending priority
+  int* vlevel;             // per vertex: colour of its last applied contact
+                           // (level colouring; -1 before the first)
   int* tinc_start;         // per vertex: start into tinc (nv + 1)
   int* tinc;               // incident triangle corners, ascending: triangle * 3 + corner
   int* vc;                 // collision vertices (pool ids), scene-contiguous
@@ -171,7 +176,8 @@ struct Pool {
   SceneState* ss;
   Counters* cnt;
   PairBuf pb[2];
-  int* act;                // active contact list: indices into the next pair buffer
+  int* act;                // active contact lists, one region of act_cap per kind
+                           // (VT, EE, VV): indices into the next pair buffer
   unsigned long long* fkey;  // FP32-filter survivors: 3 regions of pair_cap (VT, EE, VV)
   int4* fv;
   float* fd;               // mixed precision: the survivor's FP32 distance lower bound

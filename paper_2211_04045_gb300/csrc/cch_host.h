@@ -44,6 +44,7 @@ struct Runtime {
   int sweep_blocks = 0;              // grid of the cooperative sweep kernel
   int max_polls = 1 << 22;           // bound of one device wait (polls)
   int sweeps = 1, solver = 0, ccd = 0, accept = 0, validate = 0;
+  int colouring = 1;                 // cch_colouring of the Gauss-Seidel sweep
   int ccd_rounds = 8;  // CCD clamp rounds per iteration
   int max_iters = 0;                 // max over scenes
   int iters_per_check = 16;          // G: iterations per graph launch group (autotuned)
@@ -214,8 +215,12 @@ __device__ __forceinline__ void emit_pair(Pool& P, int nxt, int s, unsigned long
     atomicAdd(&P.ss[s].n_pairs, n);
   });
   if (d < S.delta) {
-    int a = claim(&P.cnt->n_active, P.act_cap);
-    if (a >= 0) P.act[a] = idx;
+    // one list per kind, so that the assembly's warps run one kind's arithmetic
+    int kind = (int)(key >> 62), a;
+    if (kind == K_VT) a = claim(&P.cnt->n_active[0], P.act_cap);
+    else if (kind == K_EE) a = claim(&P.cnt->n_active[1], P.act_cap);
+    else a = claim(&P.cnt->n_active[2], P.act_cap);
+    if (a >= 0) P.act[(size_t)kind * P.act_cap + a] = idx;
     else atomicOr(&P.cnt->overflow, OV_CONTACTS);
   }
 }

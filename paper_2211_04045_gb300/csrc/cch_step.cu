@@ -227,11 +227,11 @@ __device__ __forceinline__ void assemble_f(Pool& P, int s, const SceneDesc& S, i
 }
 
 __global__ void k_assemble(Pool P, int nxt) {
-  int n = P.cnt->n_active;
-  if (n > P.act_cap) n = P.act_cap;
+  int n0 = min(P.cnt->n_active[0], P.act_cap), n1 = min(P.cnt->n_active[1], P.act_cap);
+  int n = n0 + n1 + min(P.cnt->n_active[2], P.act_cap);
   const PairBuf B = P.pb[nxt];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int p = P.act[i];
+    int p = i < n0 ? P.act[i] : (i < n0 + n1 ? P.act[P.act_cap + (i - n0)] : P.act[2 * (size_t)P.act_cap + (i - n0 - n1)]);
     unsigned long long key = B.key[p];
     int4 v = B.v[p];
     double d = B.d[p];
@@ -595,11 +595,16 @@ __device__ __forceinline__ void contact_wait(const Pool& P, const OrderBufs& B, 
   w.v[0] = v.x; w.v[1] = v.y; w.v[2] = v.z; w.v[3] = v.w;
   for (int k = 0; k < 4; k++) w.t[k] = movable(P, w.v[k]) ? __ldg(&B.rank[4 * i + k]) : -1;
 }
-// Synchronisation at GPU scope: counters are polled with relaxed loads; once
-// an item's counters are all right, one acquire fence makes its
-// predecessors' writes visible; after the item's own writes, one release
-// fence precedes relaxed increments of its counters.  (A release on each
-// increment costs one fence per vertex.)
+// Synchronisation at GPU scope: counters are polled with acquire loads, so
+// the loads that find an item ready also make its predecessors' writes
+// visible; after the item's own writes, one release fence precedes relaxed
+// increments of its counters.  (A release on each increment costs one fence
+// per vertex.)
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -622,7 +627,7 @@ __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gp
 __device__ __forceinline__ int item_gap(const OrderBufs& B, const ItemWait& w) {
   int gap = 0;
   for (int k = 0; k < 4; k++)
-    if (w.t[k] >= 0) gap = max(gap, w.t[k] - ld_relaxed(&B.vdone[w.v[k]]));
+    if (w.t[k] >= 0) gap = max(gap, w.t[k] - ld_acquire(&B.vdone[w.v[k]]));
   return gap;
 }
 
@@ -631,7 +636,7 @@ __device__ __forceinline__ int item_gap(const OrderBufs& B, const ItemWait& w) {
 // which i is the first contact (rank 0) has an empty set; its mask words are
 // rewritten rather than read (they hold an earlier iteration's colours).
 __device__ __forceinline__ void colour_apply(Pool& P, const OrderBufs& B, int i, const ItemWait& w, int& maxcol) {
-  fence_acq_rel();
+  // (the acquire loads that found the item ready order the reads below)
   // the words in use and the first four mask words (256 colours) of every
   // movable vertex, all loaded at once; later words only when those are full
   int hw[4];
@@ -944,6 +949,183 @@ __global__ void __launch_bounds__(256, 1) k_colour_sweep(Pool P, int sweeps, int
           if (P.ecol[e] == c && edge_live(P, e)) apply_edge(P, X, e, first);
       }
       if (!grid_barrier(P, gen, max_polls)) return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Multi-colour Gauss-Seidel with the level colouring (R11, colouring = 1):
+// a constraint's colour is one more than the largest colour among the
+// higher-priority constraints sharing a movable vertex with it, the round in
+// which its priority first exceeds that of all its uncoloured conflicting
+// constraints.  Conflicting constraints are then applied in priority order,
+// so sweeping the classes in ascending colour is the sequential sweep in
+// descending priority, and no colouring pass is needed: this kernel applies
+// each constraint once the counter of every one of its movable vertices
+// (constraints applied there so far) equals its rank there by priority, and
+// then increments those counters.  Constraints that share no movable vertex
+// commute, so the result is exactly the sequential sweep.  Sweep s of
+// gs_sweeps starts at counter s * (constraints at the vertex), so counters
+// need no reset between sweeps.  In the first sweep each contact records its
+// colour (its chain length at its vertices) for the statistics.
+//
+// All blocks are resident (cooperative launch).  Each thread takes up to 32
+// constraints (i = tid + k * nth), sorts them into the sweep order and
+// applies them one after the other, waiting before each only for its own
+// vertex counters.  The earliest pending constraint of the whole sweep is at
+// the head of its thread's list and is ready, so the sweep always progresses.
+// With more constraints than 32 per thread, every thread polls all of its
+// pending constraints each round instead.  Waits are bounded and set
+// ERR_POLL past the bound.
+// ---------------------------------------------------------------------------
+struct LevelCtx {
+  int nc;          // contacts (items [0, nc)); edge-length constraints follow
+  int sweep;
+  double* lam;     // contact multipliers (gs_sweeps > 1), else null
+  double* elam;    // edge multipliers
+};
+
+__device__ __forceinline__ int contacts_at(const OrderBufs& B, int v) {
+  return __ldg(&B.vstart[v + 1]) - __ldg(&B.vstart[v]);
+}
+// counter value at which a constraint of rank r among the contacts (edge:
+// among the edges) of v may be applied in sweep s
+__device__ __forceinline__ int target_at(const Pool& P, const OrderBufs& B, int v, int s, int r, bool edge) {
+  int nct = contacts_at(B, v);
+  return s * (nct + __ldg(&P.edeg[v])) + (edge ? nct : 0) + r;
+}
+__device__ __forceinline__ void level_wait(const Pool& P, const OrderBufs& B, const LevelCtx& X, int i, ItemWait& w) {
+  if (i < X.nc) {
+    int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
+    w.v[0] = v.x; w.v[1] = v.y; w.v[2] = v.z; w.v[3] = v.w;
+    for (int k = 0; k < 4; k++)
+      w.t[k] = movable(P, w.v[k]) ? target_at(P, B, w.v[k], X.sweep, __ldg(&B.rank[4 * i + k]), false) : -1;
+  } else {
+    int e = i - X.nc;
+    int4 l = P.lv[e];
+    int2 r = __ldg(&P.erank[e]);
+    w.v[0] = l.x; w.v[1] = l.y; w.v[2] = w.v[3] = -1;
+    w.t[0] = movable(P, l.x) ? target_at(P, B, l.x, X.sweep, r.x, true) : -1;
+    w.t[1] = movable(P, l.y) ? target_at(P, B, l.y, X.sweep, r.y, true) : -1;
+    w.t[2] = w.t[3] = -1;
+  }
+}
+// (the acquire loads of item_gap that found the item ready order its reads)
+__device__ __forceinline__ void level_apply(Pool& P, const OrderBufs& B, const LevelCtx& X, int i,
+                                            const ItemWait& w) {
+  bool first = X.sweep == 0;
+  int lvl = 0;
+  if (first && i < X.nc) {
+    for (int k = 0; k < 4; k++)
+      if (w.t[k] >= 0) lvl = max(lvl, __ldcg(&P.vlevel[w.v[k]]) + 1);
+    P.ccol[i] = lvl;
+  }
+  if (i < X.nc) {
+    if (P.mixed) pgs_contact_f(P, i, w.v, X.lam, first);
+    else pgs_contact(P, i, w.v, X.lam, first);
+  } else {
+    if (P.mixed) pgs_edge_f(P, i - X.nc, w.v[0], w.v[1], X.elam, first);
+    else pgs_edge(P, i - X.nc, w.v[0], w.v[1], X.elam, first);
+  }
+  if (first && i < X.nc)
+    for (int k = 0; k < 4; k++)
+      if (w.t[k] >= 0) __stcg(&P.vlevel[w.v[k]], lvl);
+  fence_acq_rel();
+  for (int k = 0; k < 4; k++)
+    if (w.t[k] >= 0) red_relaxed_add(&B.vdone[w.v[k]], 1);
+}
+
+// edge-length constraints of scenes that are not running take no part
+__device__ __forceinline__ bool level_live(const Pool& P, const LevelCtx& X, int i) {
+  if (i < X.nc) return true;
+  return edge_live(P, i - X.nc);
+}
+// sweep-order key: contacts (class 0) before edges (class 1), then
+// descending priority; compared as (class, ~prio) ascending
+__device__ __forceinline__ unsigned long long level_prio(const Pool& P, const LevelCtx& X, int i) {
+  if (i < X.nc) return contact_prio(P, i);
+  int e = i - X.nc;
+  const SceneDesc& d = P.sd[P.lv[e].z];
+  return splitmix64(d.seed ^ ((3ULL << 62) | (unsigned long long)(e - d.l0)));
+}
+
+__global__ void __launch_bounds__(256, 2) k_level_sweep(Pool P, OrderBufs B, int sweep, int sweeps, int max_polls) {
+  LevelCtx X;
+  X.nc = min(P.cnt->n_cons, P.cons_cap);
+  X.sweep = sweep;
+  X.lam = sweeps > 1 ? P.lam : nullptr;
+  X.elam = X.lam ? P.lam + P.cons_cap : nullptr;
+  int n = X.nc + P.nl;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  long long polls = 0;
+  if (n <= 32 * nth) {
+    // this thread's items in sweep order (insertion sort, at most 32)
+    int items[32];
+    unsigned long long keys[32];
+    int m = 0;
+    for (int i = tid; i < n; i += nth) {
+      if (!level_live(P, X, i)) continue;
+      unsigned long long key = ~level_prio(P, X, i);
+      bool edge = i >= X.nc;
+      int j = m++;
+      while (j > 0 && ((items[j - 1] >= X.nc) > edge || ((items[j - 1] >= X.nc) == edge && keys[j - 1] > key))) {
+        items[j] = items[j - 1];
+        keys[j] = keys[j - 1];
+        j--;
+      }
+      items[j] = i;
+      keys[j] = key;
+    }
+    // The lanes of a warp advance together: each round every lane checks
+    // its head item; the lanes whose head is ready apply it, and the warp
+    // sleeps only when none is.  The sleep grows with the smallest number of
+    // constraints still ahead of a head item.
+    int j = 0;
+    ItemWait w;
+    bool has = m > 0;
+    if (has) level_wait(P, B, X, items[0], w);
+    while (__any_sync(0xffffffffu, has)) {
+      int gap = has ? item_gap(B, w) : 1 << 30;
+      bool ready = has && gap == 0;
+      if (__any_sync(0xffffffffu, ready)) {
+        if (ready) {
+          level_apply(P, B, X, items[j], w);
+          has = ++j < m;
+          if (has) level_wait(P, B, X, items[j], w);
+        }
+        continue;
+      }
+      if (++polls > max_polls) {  // the same count in every lane
+        if ((threadIdx.x & 31) == 0) atomicOr(&P.cnt->err, ERR_POLL);
+        break;
+      }
+      int g = __reduce_min_sync(0xffffffffu, gap);
+      __nanosleep(min(32 + 128 * (g - 1), 4096));
+    }
+  } else {
+    // more items than that: poll every pending item each round
+    for (;;) {
+      bool pending = false, progressed = false;
+      for (int i = tid; i < n; i += nth) {
+        if (P.fdone[i] || !level_live(P, X, i)) continue;
+        ItemWait w;
+        level_wait(P, B, X, i, w);
+        if (item_gap(B, w) == 0) {
+          level_apply(P, B, X, i, w);
+          P.fdone[i] = 1;
+          progressed = true;
+        } else {
+          pending = true;
+        }
+      }
+      if (!pending) break;
+      if (!progressed) {
+        if (++polls > max_polls) {
+          atomicOr(&P.cnt->err, ERR_POLL);
+          break;
+        }
+        __nanosleep(32);
+      }
     }
   }
 }
@@ -1411,7 +1593,7 @@ __global__ void k_control(Pool P, int cur) {
     C->n_fcand[0] = C->n_fcand[1] = C->n_fcand[2] = 0;
     C->all_done = running ? 0 : 1;
     C->n_pairs[cur] = 0;
-    C->n_active = 0;
+    C->n_active[0] = C->n_active[1] = C->n_active[2] = 0;
     C->n_cons = 0;
     C->vcontacts = 0;
     C->n_ccol = 0;
@@ -1442,14 +1624,20 @@ static cudaError_t coop_launch(K kern, int blocks, int threads, cudaStream_t st,
   return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(threads), argv, 0, st);
 }
 
-// Resident blocks of the cooperative kernels: the colouring (which = 0) and
-// the sweep (which = 1).
+// Resident blocks of the cooperative kernels: the colouring and the
+// level-colouring sweep (which = 0), and the colour-class sweep (which = 1).
 int coop_grid(int threads, int which) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (which == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour, threads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_sweep, threads, 0);
+  if (which == 0) {
+    int per2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_level_sweep, threads, 0);
+    if (per2 < per) per = per2;
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_sweep, threads, 0);
+  }
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -1533,6 +1721,7 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
     R.launches += 5 + 2 * R.sweeps;
   } else {  // projected Gauss-Seidel in colour classes
     cudaMemsetAsync(B.vdone, 0, sizeof(int) * (size_t)P.nv, st);
+    if (R.colouring == 1) cudaMemsetAsync(P.vlevel, 0xff, sizeof(int) * (size_t)P.nv, st);
     if (P.mixed) {
       ContactFAcc acc{(const ContactF*)P.cons};
       k_inc_count<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
@@ -1547,17 +1736,32 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
       k_inc_rank<<<grid_for(4LL * P.cons_cap, 256), 256, 0, st>>>(P, acc, B);
     }
     prof_mark(R, PG_ORDER, 1, st);
-    prof_mark(R, PG_COLOUR, 0, st);
-    cudaMemsetAsync(P.fdone, 0, (size_t)P.cons_cap, st);
-    cudaMemsetAsync(P.ccount, 0, sizeof(int) * MAX_COLOURS, st);
-    e = coop_launch(k_colour, R.coop_blocks, 256, st, P, B, R.max_polls);
-    if (e == cudaSuccess) k_colour_stats<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P);
-    prof_mark(R, PG_COLOUR, 1, st);
-    prof_mark(R, PG_SWEEP, 0, st);
-    cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = coop_launch(k_colour_sweep, R.sweep_blocks, 256, st, P, R.sweeps, R.max_polls);
-    prof_mark(R, PG_SWEEP, 1, st);
-    R.launches += 7;
+    if (R.colouring == 1) {
+      // level colouring: the dataflow sweep applies the classes in order
+      prof_mark(R, PG_SWEEP, 0, st);
+      for (int sw = 0; sw < R.sweeps && e == cudaSuccess; sw++) {
+        cudaMemsetAsync(P.fdone, 0, (size_t)P.cons_cap + P.nl, st);
+        e = coop_launch(k_level_sweep, R.coop_blocks, 256, st, P, B, sw, R.sweeps, R.max_polls);
+      }
+      prof_mark(R, PG_SWEEP, 1, st);
+      prof_mark(R, PG_COLOUR, 0, st);
+      cudaMemsetAsync(P.ccount, 0, sizeof(int) * MAX_COLOURS, st);
+      if (e == cudaSuccess) k_colour_stats<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P);
+      prof_mark(R, PG_COLOUR, 1, st);
+      R.launches += 5 + R.sweeps;
+    } else {
+      prof_mark(R, PG_COLOUR, 0, st);
+      cudaMemsetAsync(P.fdone, 0, (size_t)P.cons_cap, st);
+      cudaMemsetAsync(P.ccount, 0, sizeof(int) * MAX_COLOURS, st);
+      e = coop_launch(k_colour, R.coop_blocks, 256, st, P, B, R.max_polls);
+      if (e == cudaSuccess) k_colour_stats<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P);
+      prof_mark(R, PG_COLOUR, 1, st);
+      prof_mark(R, PG_SWEEP, 0, st);
+      cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned int), st);
+      if (e == cudaSuccess) e = coop_launch(k_colour_sweep, R.sweep_blocks, 256, st, P, R.sweeps, R.max_polls);
+      prof_mark(R, PG_SWEEP, 1, st);
+      R.launches += 7;
+    }
   }
   if (e != cudaSuccess) return e;
   prof_mark(R, PG_FORWARD, 0, st);

@@ -25,8 +25,8 @@ CASES = {
     "hair_sand": lambda: scenes.hair_sand(n_strands=36, segs=8, n_points=120, grain_r=0.002, bowl_r=0.12,
                                           bowl_subdiv=2, seg_len=0.01, seed=4),
 }
-VARIANTS = {"gs": {}, "jacobi": {"solver": 1}, "jacobi3": {"solver": 1, "gs_sweeps": 3}, "gap": {"constraint_form": 1},
-            "ccd_rule": {"step_rule": 1}}
+VARIANTS = {"gs": {}, "gs_greedy": {"colouring": 0}, "jacobi": {"solver": 1}, "jacobi3": {"solver": 1, "gs_sweeps": 3},
+            "gap": {"constraint_form": 1}, "ccd_rule": {"step_rule": 1}}
 
 
 def record(name, variant):

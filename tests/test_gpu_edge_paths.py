@@ -1,9 +1,10 @@
 """Paths of the CUDA library that the workload-sized tests do not reach,
 each against the oracle: pair buffers that overflow, grow and replay the
-step; the colouring's and the sweep's branch for more than 32 items per
-thread (forced with a one-block cooperative grid); Gauss-Seidel with several
-sweeps per backward step (Sec. 4.3.1); and a bounded device wait that runs
-out, after which the same scene completes a normal step.
+step; the branch for more than 32 items per thread of the colouring and of
+both sweeps (forced with a one-block cooperative grid); Gauss-Seidel with
+several sweeps per backward step (Sec. 4.3.1); and a bounded device wait that
+runs out, after which the same scene completes a normal step.  Every
+Gauss-Seidel case runs with both colourings (level and greedy).
 """
 import numpy as np
 import pytest
@@ -47,13 +48,14 @@ def test_pair_buffers_grow_and_the_step_replays(cuda):
     ref.close()
 
 
-def test_more_than_32_items_per_thread(cuda):
+@pytest.mark.parametrize("colouring", [1, 0])
+def test_more_than_32_items_per_thread(cuda, colouring):
     # two 48 x 48 layers 0.7 mm apart: 13,442 edge-length constraints and
     # more than 8,192 contacts, against a grid of one block of 256 threads
     # (32 x 256 = 8,192 items per list)
     sc = scenes.two_cloths(n=48, side=0.4, sep=0.0007, omega=6.0, noise=0.3, seed=3)
     assert len(sc.len_edges) > 8192
-    kw = dict(max_iters=24)
+    kw = dict(max_iters=24, colouring=colouring)
     one = cch.Scene(sc, cch.params_for(sc, sweep_blocks=1, **kw))
     full = cch.Scene(sc, cch.params_for(sc, **kw))
     x, xt, _ = scenes.initial(sc)
@@ -67,11 +69,12 @@ def test_more_than_32_items_per_thread(cuda):
     full.close()
 
 
+@pytest.mark.parametrize("colouring", [1, 0])
 @pytest.mark.parametrize("sweeps", [2, 3])
 @pytest.mark.parametrize("name", ["cloth_sphere", "two_cloths", "tets"])
-def test_gauss_seidel_several_sweeps(cuda, name, sweeps):
+def test_gauss_seidel_several_sweeps(cuda, name, sweeps, colouring):
     sc = small_scenes()[name]()
-    kw = dict(max_iters=300, gs_sweeps=sweeps)
+    kw = dict(max_iters=300, gs_sweeps=sweeps, colouring=colouring)
     gpu = cch.Scene(sc, cch.params_for(sc, **kw))
     x, xt, _ = scenes.initial(sc)
     for s in range(2):
@@ -82,11 +85,13 @@ def test_gauss_seidel_several_sweeps(cuda, name, sweeps):
     gpu.close()
 
 
-def test_bounded_wait_runs_out_and_the_scene_recovers(cuda):
+@pytest.mark.parametrize("colouring", [1, 0])
+def test_bounded_wait_runs_out_and_the_scene_recovers(cuda, colouring):
     # layers 0.7 mm apart: the first iteration already has contacts that
-    # share vertices, so the colouring waits on its counters
+    # share vertices, so the sweep (level colouring) or the colouring pass
+    # (greedy) waits on its counters
     sc = scenes.two_cloths(n=24, side=0.25, sep=0.0007, omega=6.0, noise=0.3, seed=5)
-    kw = dict(max_iters=40)
+    kw = dict(max_iters=40, colouring=colouring)
     gpu = cch.Scene(sc, cch.params_for(sc, **kw))
     x, xt, _ = scenes.initial(sc)
     gpu.set_max_polls(1)

@@ -46,11 +46,12 @@ def test_fullsize_pair_sets_bit_exact(cuda, c2):
     gpu.close()
 
 
-def test_fullsize_capped_step_matches_oracle(cuda):
+@pytest.mark.parametrize("colouring", [1, 0])
+def test_fullsize_capped_step_matches_oracle(cuda, colouring):
     from test_gpu_parity import REL, same_stats
     sc = scenes.two_cloths(n=256, side=2.0, sep=0.0015, omega=6.0, noise=0.3, seed=0)
     x, xt, _ = scenes.initial(sc)
-    kw = dict(max_iters=5)
+    kw = dict(max_iters=5, colouring=colouring)
     xo, so, _ = oracle.handle_step(oracle.OracleScene(sc), oracle.params_for(sc, **kw), x, xt)
     gpu = cch.Scene(sc, cch.params_for(sc, **kw))
     out, sg = gpu.step(T(x, cuda), T(xt, cuda))
@@ -85,9 +86,9 @@ def test_hair_sand_fullsize_sampled_pairs(cuda):
     # radius 2 mm, a fixed bowl), the movable vertices jittered by 1.5 mm so
     # that strands and grains come within D^max = 0.8 mm of each other.  The
     # oracle's whole-scene search takes hours here, so sampled queries are
-    # checked one by one (pair_sampling.check_sampled_pairs): for 400
-    # collision vertices, 400 edges and 400 grains the GPU's pairs in P are
-    # recomputed with the oracle's distance routines.
+    # checked one by one (pair_sampling.check_sampled_pairs): for 1,000
+    # collision vertices, 1,000 edges and 1,000 grains the GPU's pairs in P
+    # are recomputed with the oracle's distance routines.
     from pair_sampling import check_sampled_pairs, jittered
     sc = scenes.hair_sand()
     x0, xt, _ = scenes.initial(sc)
@@ -96,5 +97,5 @@ def test_hair_sand_fullsize_sampled_pairs(cuda):
     gpu = cch.Scene(sc, cch.params_for(sc))
     gk, gd = gpu.query_pairs(T(x, cuda), T(xt, cuda), D, candidates=False)
     gpu.close()
-    checked = check_sampled_pairs(sc, x, xt, D, dict(zip(gk.tolist(), gd.tolist())), 400, seed=8)
+    checked = check_sampled_pairs(sc, x, xt, D, dict(zip(gk.tolist(), gd.tolist())), 1000, seed=8)
     assert checked > 1000

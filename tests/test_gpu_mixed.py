@@ -7,7 +7,10 @@ the true distance and the forward step keeps its guarantee.  The proximity
 set the step's search forms is checked against the oracle's exact one: it
 holds every pair of the oracle's P, each recorded distance is at most the
 exact distance and at most B below it, and every extra pair lies within B of
-D^max, with B = 2 FILTER_TOL (|x|max + 2 (longest edge) + D^max).  After a
+D^max, with B = 2 FILTER_TOL (|x|max + 2 (longest edge) + D^max), plus, for
+edge-edge pairs, the slack of the separating-axis lower bound on nearly
+parallel segments, at most 4.6e-5 (|x| + length) over 40,000 float-emulated
+pairs (5e-5 (|x|max + longest edge) here).  After a
 step, the acceptance test and the oracle's exact test must both find no
 intersection, and the position error against the FP64 oracle is within the
 bound stated per scene (measured on the GB300 with margin).
@@ -64,6 +67,14 @@ def test_mixed_is_safe_and_close(cuda, name):
     gpu.close()
 
 
+def slack_bound(x, longest, D):
+    # (vertex-triangle and vertex-vertex, edge-edge) bounds of exact minus
+    # recorded distance: twice the filter's rounding margin, and for edges the
+    # separating-axis bound's slack on nearly parallel segments
+    B = 2.0 * 4e-6 * (float(np.max(np.abs(x))) + 2.0 * longest + D) * 1.01
+    return B, B + 5e-5 * (float(np.max(np.abs(x))) + longest)
+
+
 def contract_states(name, sc):
     # states with pairs within D^max: along the way from x^t to the target
     # (where the layers, strands and grains meet), and for the bodies, the
@@ -89,21 +100,22 @@ def test_mixed_proximity_set_contract(cuda, name):
     longest = float(np.max(np.linalg.norm(x0[e[:, 0]] - x0[e[:, 1]], axis=1))) if len(e) else 0.0
     total = 0
     for k, x in enumerate(states):
-        B = 2.0 * 4e-6 * (float(np.max(np.abs(x))) + 2.0 * longest + D) * 1.01
+        B = slack_bound(x, longest, D)
         km, dm = gpu.query_pairs(T(x, cuda), T(xt, cuda), D, step_search=True)
         ko, do = oracle.proximity(osc, x, D, mode=0, x_tilde=xt)
         total += len(ko)
         assert np.all(np.isin(ko, km)), (name, k)
         common = np.isin(km, ko)
         dex = do[np.searchsorted(ko, km[common])]
+        Bk = np.where((km[common] >> np.uint64(62)) == oracle.EE, B[1], B[0])
         assert np.all(dm[common] <= dex), (name, k, float(np.max(dm[common] - dex)))
-        assert np.all(dex - dm[common] <= B), (name, k, float(np.max(dex - dm[common])), B)
+        assert np.all(dex - dm[common] <= Bk), (name, k, float(np.max(dex - dm[common] - Bk)))
         extra = km[~common]
         if len(extra):
-            kw, dw = oracle.proximity(osc, x, D + B, mode=0, x_tilde=xt)
+            kw, dw = oracle.proximity(osc, x, D + B[1], mode=0, x_tilde=xt)
             assert np.all(np.isin(extra, kw)), (name, k)
             assert np.all(dw[np.searchsorted(kw, extra)] >= D)
-        print(f"{name} state {k}: |P| oracle {len(ko)}, mixed {len(km)} ({len(extra)} within B = {B:.2e} m of D)")
+        print(f"{name} state {k}: |P| oracle {len(ko)}, mixed {len(km)} ({len(extra)} within {B[1]:.2e} m of D)")
     assert total > 0
     gpu.close()
 
@@ -149,7 +161,7 @@ def test_mixed_lower_bounds_hold_on_near_parallel_edges(cuda):
     assert np.all(np.isin(ko, km))
     common = np.isin(km, ko)
     dex = do[np.searchsorted(ko, km[common])]
-    B = 2.0 * 4e-6 * (float(np.max(np.abs(x))) + 2.0 * 0.008 + D) * 1.01
+    B = slack_bound(x, 0.008, D)[1]
     assert np.all(dm[common] <= dex), float(np.max(dm[common] - dex))
-    assert np.all(dex - dm[common] <= B)
+    assert np.all(dex - dm[common] <= B), float(np.max(dex - dm[common]))
     gpu.close()

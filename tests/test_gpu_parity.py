@@ -68,11 +68,12 @@ def test_candidate_and_proximity_sets_bit_exact(cuda, name):
     gpu.close()
 
 
+@pytest.mark.parametrize("colouring", [1, 0])
 @pytest.mark.parametrize("name", list(small_scenes()))
-def test_step_chain_matches_oracle(cuda, name):
+def test_step_chain_matches_oracle(cuda, name, colouring):
     sc = small_scenes()[name]()
     steps = 3
-    prm_kw = dict(max_iters=300)
+    prm_kw = dict(max_iters=300, colouring=colouring)
     gpu = cch.Scene(sc, cch.params_for(sc, **prm_kw))
     osc = oracle.OracleScene(sc)
     oprm = oracle.params_for(sc, **prm_kw)

@@ -3,15 +3,19 @@ R10 and R11).
 
 The priorities come from SplitMix64, pinned to its published sequence.  The
 sweep is multi-colour Gauss-Seidel: contacts before edge-length constraints
-(R10), and within each group the colour classes of the greedy colouring in
-descending priority splitmix64(seed ^ key), in ascending colour (R11).  The
-colouring is checked against networkx's greedy colouring (an independent
-implementation of the same definition) on random constraint sets and on the
-contacts of a real scene.  Closed-form cases fix the order: a chain of two
-stretched edges, whose result depends on which edge goes first; a chain of
-three, where the colour order differs from the priority order whenever the
-priorities fall or rise along the chain; and a point held by a contact and an
-edge that pull it in opposite directions.
+(R10), and within each group the colour classes, in ascending colour, of a
+randomized colouring in descending priority splitmix64(seed ^ key) (R11):
+the greedy colouring (smallest free colour) or the level colouring (one more
+than the largest colour among the higher-priority conflicting constraints).
+The greedy colouring is checked against networkx's greedy colouring, the
+level colouring against the longest chains of networkx's priority DAG (both
+independent implementations of the definitions), on random constraint sets
+and on the contacts of a real scene.  Closed-form cases fix the order: a
+chain of two stretched edges, whose result depends on which edge goes first;
+a chain of three, where the greedy classes differ from the priority order
+whenever the priorities fall or rise along the chain, while the level classes
+keep it; and a point held by a contact and an edge that pull it in opposite
+directions.
 """
 import networkx as nx
 from types import SimpleNamespace as NS
@@ -83,7 +87,7 @@ def test_contacts_before_edges():
     assert np.array_equal(out[[0, 2]], y[[0, 2]])
 
 
-def chain3(seed):
+def chain3(seed, colouring=0):
     # vertices 0-1-2-3 on a line 1.5 L0 apart, edges e0 (0,1), e1 (1,2),
     # e2 (2,3) at rest length L0, sigma = 1.1, unit masses.  An edge applied
     # at stretch s L0 moves both of its ends by (s - 1.1) L0 / 2 toward each
@@ -92,9 +96,22 @@ def chain3(seed):
     y0 = np.array([0.0, 1.0, 2.0, 3.0])[:, None] * L0 * u
     y = np.array([0.0, 1.5, 3.0, 4.5])[:, None] * L0 * u
     sc = mini([1.0] * 4, len_edges=[[0, 1], [1, 2], [2, 3]])
-    out = oracle.backward_once(oracle.OracleScene(sc), oracle.params(seed=seed), y0, y, y0)
+    out = oracle.backward_once(oracle.OracleScene(sc), oracle.params(seed=seed, colouring=colouring), y0, y, y0)
     assert np.max(np.abs(out - np.outer(out @ u, u))) <= 1e-17  # the chain stays on its line
     return out @ u / L0, [oracle.splitmix64(seed ^ (EDGE_KIND | e)) for e in range(3)]
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_three_edge_chain_level_classes_keep_priority_order(seed):
+    # level classes: along the chain the colours follow the priorities, so
+    # the sweep is the plain priority order
+    out, p = chain3(seed, colouring=1)
+    order = sorted(range(3), key=lambda e: -p[e])
+    expect = {(0, 1, 2): [0.2, 1.6, 3.05, 4.15], (2, 1, 0): [0.35, 1.45, 2.9, 4.3]}.get(tuple(order))
+    if expect is None:
+        # the middle edge first ([0.3, 1.4, 3.1, 4.2]) or last ([0.2, 1.7, 2.8, 4.3])
+        expect = [0.3, 1.4, 3.1, 4.2] if order[0] == 1 else [0.2, 1.7, 2.8, 4.3]
+    assert np.max(np.abs(out - np.array(expect))) <= 1e-12, (seed, p)
 
 
 @pytest.mark.parametrize("seed", range(16))
@@ -122,6 +139,19 @@ def test_seeds_where_colour_order_differs_from_priority_order():
             monotone += 1
             assert np.max(np.abs(out - np.array([0.2, 1.7, 2.8, 4.3]))) <= 1e-12
     assert monotone >= 2
+
+
+def nx_levels(verts, prio, movable):
+    """Longest chain of higher-priority conflicting constraints before each
+    one, over networkx's DAG of the conflicts directed by priority."""
+    _, G = nx_greedy(verts, prio, movable)
+    D = nx.DiGraph()
+    D.add_nodes_from(G.nodes)
+    D.add_edges_from((a, b) if int(prio[a]) > int(prio[b]) else (b, a) for a, b in G.edges)
+    lev = {}
+    for c in nx.topological_sort(D):
+        lev[c] = max((lev[q] + 1 for q in D.predecessors(c)), default=0)
+    return np.array([lev[i] for i in range(len(prio))])
 
 
 def nx_greedy(verts, prio, movable):
@@ -157,6 +187,11 @@ def test_greedy_colouring_equals_networkx(seed):
     ref, G = nx_greedy(verts, prio, inv_mass > 0)
     assert np.array_equal(col, ref)
     assert ncol == col.max() + 1
+    lev, nlev = oracle.colouring(verts, prio, inv_mass, kind=1)
+    assert np.array_equal(lev, nx_levels(verts, prio, inv_mass > 0))
+    assert nlev == lev.max() + 1 >= ncol
+    for a, b in G.edges:
+        assert lev[a] != lev[b]
     # valid: no two constraints of one colour share a movable vertex, and a
     # constraint through static vertices only conflicts with nothing
     for a, b in G.edges:
@@ -173,7 +208,7 @@ def test_contact_colouring_of_a_scene_equals_networkx():
     x[x0[:, 1] > 0.002, 1] -= 0.0033  # the layers 0.7 mm apart, within delta
     x += rng.normal(0.0, 0.0001, size=x0.shape)
     osc = oracle.OracleScene(sc)
-    prm = oracle.params_for(sc, seed=99)
+    prm = oracle.params_for(sc, seed=99, colouring=0)
     keys, col = oracle.contact_colours(osc, prm, x, xt)
     assert len(keys) > 50
     verts = []
@@ -189,13 +224,16 @@ def test_contact_colouring_of_a_scene_equals_networkx():
     ref, _ = nx_greedy(np.array(verts), prio, sc.inv_mass > 0)
     assert np.array_equal(col, ref)
     assert col.max() + 1 >= 2
+    keys1, lev = oracle.contact_colours(osc, oracle.params_for(sc, seed=99, colouring=1), x, xt)
+    assert np.array_equal(keys1, keys)
+    assert np.array_equal(lev, nx_levels(np.array(verts), prio, sc.inv_mass > 0))
 
 
 def test_edge_colouring_of_a_cloth_equals_networkx():
     from paper_2211_04045_gb300 import scenes
     sc = scenes.two_cloths(n=12, side=0.1, sep=0.004, omega=0.0, noise=0.0)
     osc = oracle.OracleScene(sc)
-    col, ncol = oracle.edge_colours(osc, oracle.params(seed=5))
+    col, ncol = oracle.edge_colours(osc, oracle.params(seed=5, colouring=0))
     verts = np.concatenate([sc.len_edges, np.full((len(sc.len_edges), 2), -1)], 1)
     prio = [oracle.splitmix64(5 ^ (EDGE_KIND | e)) for e in range(len(sc.len_edges))]
     ref, _ = nx_greedy(verts, prio, sc.inv_mass > 0)
