@@ -199,6 +199,22 @@ def prims(sc):
     return int(len(sc.tris) + len(sc.edges) + len(sc.points)) if len(sc.tris) < 1000 else int(len(sc.tris))
 
 
+def smooth_displacement(sc, rng):
+    """A displacement of every movable vertex by a random smooth field: per
+    axis a sinusoid of x with a random direction, wavelength between a third
+    of the scene's extent and its extent, and phase, with an amplitude drawn
+    log-uniformly from 0.5 to 5 mm."""
+    x = sc.x0
+    ext = float(np.ptp(x, axis=0).max())
+    amp = float(np.exp(rng.uniform(np.log(5e-4), np.log(5e-3))))
+    d = np.zeros_like(x)
+    for a in range(3):
+        k = rng.normal(0.0, 1.0, 3)
+        k *= rng.uniform(1.0, 3.0) / (np.linalg.norm(k) * ext)
+        d[:, a] = amp * np.sin(2.0 * np.pi * (x @ k) + rng.uniform(0.0, 2.0 * np.pi))
+    return d * (sc.inv_mass > 0)[:, None]
+
+
 def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=("mixed", "fp64")):
     """Poisson request stream served with continuous batching, against the
     same requests run one at a time in plain FP64 (each on its own resident
@@ -212,11 +228,12 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
     which = rng.integers(0, len(scs), size=N)
     inputs = []
     for i in range(N):
-        # a seeded random (x^t, x~) pair: the scene's start and a target that
-        # moves every movable vertex by N(0, 1 mm)
+        # a seeded random (x^t, x~) pair: the scene's start and a target
+        # moved by a smooth random displacement field (one time step of a
+        # simulator: neighbouring vertices move alike)
         sc = scs[which[i]]
         x = sc.x0
-        xt = x + rng.normal(0.0, 1e-3, size=x.shape) * (sc.inv_mass > 0)[:, None]
+        xt = x + smooth_displacement(sc, rng)
         inputs.append((torch.tensor(x, device=dev), torch.tensor(xt, device=dev)))
     out = {"requests": N, "rate_per_s": rate, "max_active": max_active, "budget_bytes": 80 << 30,
            "scene_prims": [prims(sc) for sc in scs]}

@@ -320,6 +320,15 @@ __device__ __forceinline__ void child_box(const BVH& B, int child, float4& lo, f
 // ---------------------------------------------------------------------------
 // queries
 // ---------------------------------------------------------------------------
+// FP32 lower bound of an edge-edge distance for the search's filter: the gap
+// along the closest points' difference rejects most distant pairs; a pair it
+// does not reject gets the full separating-axis bound
+__device__ __forceinline__ float ee_lower(fv3 a, fv3 b, fv3 c, fv3 d, float Df) {
+  float t = ftol(a, b, c, d), lo;
+  f_ss_bounds(a, b, c, d, __fadd_ru(Df, t), &lo);
+  return __fsub_rd(lo, t);
+}
+
 // A pair that the FP32 filter could not reject; the exact FP64 distance is
 // evaluated later by k_finalize with one pair per thread (full warps instead
 // of the few lanes still active inside a divergent traversal).
@@ -574,7 +583,7 @@ __global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
           bool qlow = q1 < e2;
           int4 A = qlow ? make_int4(qx, qy, 0, 0) : eb, Bv = qlow ? eb : make_int4(qx, qy, 0, 0);
           fv3 fa0 = fk(P.xf[A.x]), fa1 = fk(P.xf[A.y]), fb0 = fk(P.xf[Bv.x]), fb1 = fk(P.xf[Bv.y]);
-          float lower = __fsub_rd(f_ss_lower(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1));
+          float lower = ee_lower(fa0, fa1, fb0, fb1, Df);
           if (lower >= qD) return;
           push_survivor(P, K_EE, mkkey(K_EE, min(q1, e2) - S.e0, max(q1, e2) - S.e0),
                         make_int4(A.x, A.y, Bv.x, Bv.y), lower);
@@ -663,8 +672,7 @@ __global__ void __launch_bounds__(256) k_query_ee(Pool P, int nxt, int mode, dou
       // edge is the query, so that it does not depend on the tree: in mixed
       // precision it is the pair's distance
       bool qlo = lo_e == e1;
-      float lower = qlo ? __fsub_rd(f_ss_lower(fa0, fa1, fb0, fb1), ftol(fa0, fa1, fb0, fb1))
-                        : __fsub_rd(f_ss_lower(fb0, fb1, fa0, fa1), ftol(fb0, fb1, fa0, fa1));
+      float lower = qlo ? ee_lower(fa0, fa1, fb0, fb1, Df) : ee_lower(fb0, fb1, fa0, fa1, Df);
       if (lower >= Df) return;
       int4 A = qlo ? ea : eb, Bv = qlo ? eb : ea;
       push_survivor(P, K_EE, key, make_int4(A.x, A.y, Bv.x, Bv.y), lower);
@@ -987,28 +995,42 @@ void bvh_build_all(Runtime& R, cudaStream_t st, int gated) {
   for (int c = 0; c < 3; c++) bvh_build(R, c, st, gated);
 }
 
-__global__ void k_refit_guard_reset(Pool P, int c, int force) {
-  // clears the arrival flags when a search is due (or forced)
-  BVH& B = bvh_of(P, c);
-  if (!force && !P.cnt->any_search) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n - 1; i += gridDim.x * blockDim.x) B.flag[i] = 0;
+// All three trees at once: the arrival flags of every internal node, then
+// per leaf its box and the climb (the second child to arrive at a node writes
+// the node's boxes from its children's, which the first wrote before its
+// arrival), so that the three climbs overlap instead of running one after the
+// other.
+__device__ __forceinline__ int class_of(const Pool& P, int i, int& j, bool internal) {
+  int n0 = internal ? max(P.bt.n - 1, 0) : P.bt.n, n1 = internal ? max(P.be.n - 1, 0) : P.be.n;
+  if (i < n0) { j = i; return 0; }
+  if (i < n0 + n1) { j = i - n0; return 1; }
+  j = i - n0 - n1;
+  return 2;
 }
-__global__ void k_leaf_boxes_guard(Pool P, int c, int force) {
+__global__ void k_refit_reset_all(Pool P, int force) {
   if (!force && !P.cnt->any_search) return;
-  BVH& B = bvh_of(P, c);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n; i += gridDim.x * blockDim.x) {
-    dv3 lo, hi;
-    int s;
-    prim_box(P, c, B.ids[i], lo, hi, s);
-    B.leafbox[2 * i] = make_float4(__double2float_rd(lo.x), __double2float_rd(lo.y), __double2float_rd(lo.z), 0.f);
-    B.leafbox[2 * i + 1] = make_float4(__double2float_ru(hi.x), __double2float_ru(hi.y), __double2float_ru(hi.z), 0.f);
+  int n = max(P.bt.n - 1, 0) + max(P.be.n - 1, 0) + max(P.bv.n - 1, 0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int j, c = class_of(P, i, j, true);
+    bvh_of(P, c).flag[j] = 0;
   }
 }
-__global__ void k_refit_guard(Pool P, int c, int force) {
+__global__ void k_refit_all(Pool P, int force) {
   if (!force && !P.cnt->any_search) return;
-  BVH& B = bvh_of(P, c);
-  int n = B.n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  int total = P.bt.n + P.be.n + P.bv.n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int i, c = class_of(P, t, i, false);
+    BVH& B = bvh_of(P, c);
+    int n = B.n;
+    {
+      dv3 lo, hi;
+      int s;
+      prim_box(P, c, B.ids[i], lo, hi, s);
+      B.leafbox[2 * i] = make_float4(__double2float_rd(lo.x), __double2float_rd(lo.y), __double2float_rd(lo.z), 0.f);
+      B.leafbox[2 * i + 1] =
+          make_float4(__double2float_ru(hi.x), __double2float_ru(hi.y), __double2float_ru(hi.z), 0.f);
+    }
+    if (n < 2) continue;
     int node = B.parent[n - 1 + i];
     int climb = 0;
     while (node >= 0) {
@@ -1032,17 +1054,15 @@ __global__ void k_refit_guard(Pool P, int c, int force) {
 
 void bvh_refit_all(Runtime& R, cudaStream_t st, int force) {
   Pool& P = R.pool;
-  for (int c = 0; c < 3; c++) {
-    BVH& B = c == 0 ? P.bt : (c == 1 ? P.be : P.bv);
-    if (B.n == 0) continue;
-    if (B.n > 1) {
-      k_refit_guard_reset<<<grid_for(B.n - 1, 256), 256, 0, st>>>(P, c, force);
-      R.launches++;
-    }
-    k_leaf_boxes_guard<<<grid_for(B.n, 256), 256, 0, st>>>(P, c, force);
-    k_refit_guard<<<grid_for(B.n, 256), 256, 0, st>>>(P, c, force);
-    R.launches += 2;
+  long long ni = (long long)max(P.bt.n - 1, 0) + max(P.be.n - 1, 0) + max(P.bv.n - 1, 0);
+  long long nl = (long long)P.bt.n + P.be.n + P.bv.n;
+  if (nl == 0) return;
+  if (ni > 0) {
+    k_refit_reset_all<<<grid_for(ni, 256), 256, 0, st>>>(P, force);
+    R.launches++;
   }
+  k_refit_all<<<grid_for(nl, 256), 256, 0, st>>>(P, force);
+  R.launches++;
 }
 
 void query_class(Runtime& R, int c, int nxt, int mode, double Dq, cudaStream_t st) {

@@ -175,6 +175,7 @@ cudaError_t alloc_pairs(Runtime& R) {
   if ((e = dalloc_in(L, &P.cons, P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.fdone, (size_t)P.cons_cap + P.nl)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &P.ccol, (size_t)P.cons_cap)) != cudaSuccess) return e;
+  if ((e = dalloc_in(L, &P.corder, (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.iprio, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.iid, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
   if ((e = dalloc_in(L, &R.obuf.rank, 4 * (size_t)P.cons_cap)) != cudaSuccess) return e;
@@ -341,7 +342,8 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
   CK(dalloc(R, &P.vlevel, nv));
   CK(dalloc(R, &P.ccount, 2048));
   CK(cudaMemset(P.ccount, 0, 2048 * sizeof(int)));
-  CK(dalloc(R, &P.tail, 2048));
+  CK(dalloc(R, &P.coff, 2048 + 1));
+  CK(dalloc(R, &P.cfill, 2048));
   CK(dalloc(R, &P.bar, 2));
   CK(cudaMemset(P.bar, 0, 2 * sizeof(unsigned int)));
   CK(dalloc(R, &P.vmin, nv));
@@ -451,6 +453,17 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
       if (c + 1 > P.n_ecol) P.n_ecol = c + 1;
     }
     CK(upload(R, &P.ecol, ecol));
+    // the edges grouped by colour, ascending index within a colour (the
+    // colour-class sweep applies one group per phase)
+    std::vector<int> eoff((size_t)P.n_ecol + 1, 0), eorder(nl);
+    for (int e = 0; e < nl; e++) eoff[ecol[e] + 1]++;
+    for (int c = 0; c < P.n_ecol; c++) eoff[c + 1] += eoff[c];
+    {
+      std::vector<int> fill(eoff.begin(), eoff.end() - 1);
+      for (int e = 0; e < nl; e++) eorder[fill[ecol[e]]++] = e;
+    }
+    CK(upload(R, &P.eorder, eorder));
+    CK(upload(R, &P.eoff, eoff));
     CK(cudaMemcpy(P.sd, R.sd.data(), sizeof(SceneDesc) * R.sd.size(), cudaMemcpyHostToDevice));
     // the level colouring's dataflow sweep waits on each edge's rank among
     // the edges of each of its vertices, by descending priority

@@ -88,7 +88,6 @@ struct Counters {
   int n_ccol;           // colours of this iteration's contact colouring
   int n_exact[2];       // pairs whose exact FP64 distance is due: of the
                         // search's survivors [0], of the refreshed P [1]
-  int n_tail;           // contacts of the sweep's single-block tail
 };
 enum { OV_PAIRS = 1, OV_CONTACTS = 2, OV_QUERY = 16 };
 // error bits of Counters::err (ERR_COLOURS: a contact needed more colours
@@ -192,10 +191,14 @@ struct Pool {
   unsigned long long* cmask;  // per vertex: colours used there so far (CW words)
   int* chw;                // per vertex: mask words in use
   int* ccount;             // contacts per colour of the iteration (MAX_COLOURS)
-  int* tail;               // contacts of the sweep's single-block tail (TAIL_MAX)
+  int* coff;               // start of each colour's contacts in corder (MAX_COLOURS + 1)
+  int* cfill;              // contacts placed per colour so far (MAX_COLOURS)
+  int* corder;             // contacts grouped by colour (cons_cap)
   int* ecol;               // per edge-length constraint: colour class (fixed)
   int n_ecol;              // edge colours (most over the scenes)
-  unsigned int* bar;       // grid barrier of the sweep: arrivals, generation
+  int* eorder;             // edge-length constraints grouped by colour (nl)
+  int* eoff;               // start of each edge colour in eorder (n_ecol + 1)
+  unsigned int* bar;       // grid barrier of the sweep: arrivals since the launch
   double* lam;             // multipliers for gs_sweeps > 1 (contacts then edges)
   double* jdl;             // projected Jacobi: dl per contact, then per edge (cons_cap + nl)
   int* vlstart;            // projected Jacobi: per vertex, start into vllist (nv + 1)
@@ -475,22 +478,28 @@ __device__ __forceinline__ fv3 f_seg_pt(fv3 p, fv3 a, fv3 b) {
   if (ee > 0.f) t = fminf(fmaxf(fdot(w, e) / ee, 0.f), 1.f);
   return {a.x + t * e.x, a.y + t * e.y, a.z + t * e.z};
 }
-__device__ __forceinline__ float f_ss_lower(fv3 a, fv3 b, fv3 c, fv3 d) {
+// Distance of f_ss (returned; an upper estimate of the true distance up to
+// rounding, as the distance of two points of the segments) and, in *lower, a
+// lower bound: the gap along the difference of the closest points found, and
+// unless that gap already reaches `enough`, the larger of it and the gaps
+// along d1 x d2 and the part of c - a orthogonal to d1.  Each gap alone is a
+// valid bound, so a caller that only needs to reject pairs beyond a distance
+// passes it as `enough` and skips the other two for most of them.
+__device__ __forceinline__ float f_ss_bounds(fv3 a, fv3 b, fv3 c, fv3 d, float enough, float* lower) {
   fv3 d1 = fsub(b, a), d2 = fsub(d, c), r = fsub(a, c);
   float A = fdot(d1, d1), E = fdot(d2, d2), B = fdot(d1, d2), C = fdot(d1, r), F = fdot(d2, r);
   // closest points as f_ss finds them: the four endpoint projections and the
   // interior solution, whichever is nearest
-  fv3 p = a, q = f_seg_pt(a, c, d);
-  fv3 z = fsub(p, q);
+  fv3 z = fsub(a, f_seg_pt(a, c, d));
   float bz = fdot(z, z);
   {
-    fv3 q2 = f_seg_pt(b, c, d), z2 = fsub(b, q2);
+    fv3 z2 = fsub(b, f_seg_pt(b, c, d));
     float b2 = fdot(z2, z2);
     if (b2 < bz) { bz = b2; z = z2; }
-    fv3 p3 = f_seg_pt(c, a, b), z3 = fsub(p3, c);
+    fv3 z3 = fsub(f_seg_pt(c, a, b), c);
     float b3 = fdot(z3, z3);
     if (b3 < bz) { bz = b3; z = z3; }
-    fv3 p4 = f_seg_pt(d, a, b), z4 = fsub(p4, d);
+    fv3 z4 = fsub(f_seg_pt(d, a, b), d);
     float b4 = fdot(z4, z4);
     if (b4 < bz) { bz = b4; z = z4; }
   }
@@ -500,17 +509,25 @@ __device__ __forceinline__ float f_ss_lower(fv3 a, fv3 b, fv3 c, fv3 d) {
     if (s >= 0.f && s <= 1.f && t >= 0.f && t <= 1.f) {
       fv3 zi = {r.x + s * d1.x - t * d2.x, r.y + s * d1.y - t * d2.y, r.z + s * d1.z - t * d2.z};
       float bi = fdot(zi, zi);
-      if (bi < bz) z = zi;
+      if (bi < bz) { bz = bi; z = zi; }
     }
   }
   float g = f_gap(z, a, b, c, d);
-  g = fmaxf(g, f_gap(fcross(d1, d2), a, b, c, d));
-  if (A > 0.f) {
-    float sc = C / A;
-    fv3 k = {r.x - sc * d1.x, r.y - sc * d1.y, r.z - sc * d1.z};
-    g = fmaxf(g, f_gap(k, a, b, c, d));
+  if (!(g >= enough)) {
+    g = fmaxf(g, f_gap(fcross(d1, d2), a, b, c, d));
+    if (A > 0.f) {
+      float sc = C / A;
+      fv3 k = {r.x - sc * d1.x, r.y - sc * d1.y, r.z - sc * d1.z};
+      g = fmaxf(g, f_gap(k, a, b, c, d));
+    }
   }
-  return g;
+  *lower = g;
+  return sqrtf(bz);
+}
+__device__ __forceinline__ float f_ss_lower(fv3 a, fv3 b, fv3 c, fv3 d) {
+  float lo;
+  f_ss_bounds(a, b, c, d, __int_as_float(0x7f800000), &lo);
+  return lo;
 }
 // error margin of a float distance over these points
 __device__ __forceinline__ float ftol(fv3 a, fv3 b, fv3 c, fv3 d) {

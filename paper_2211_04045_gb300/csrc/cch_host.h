@@ -159,8 +159,9 @@ __device__ __forceinline__ float2 pair_bounds32(const Pool& P, unsigned long lon
                        __fadd_ru(__fsub_ru(dd, __double2float_rd(r)), t));
   }
   // upper: a distance between two points of the segments; lower: the
-  // separating-axis bound (see f_ss_lower)
-  return make_float2(__fsub_rd(f_ss_lower(a, b, c, d), t), __fadd_ru(f_ss(a, b, c, d), t));
+  // separating-axis bound (see f_ss_bounds)
+  float lo, dd = f_ss_bounds(a, b, c, d, __int_as_float(0x7f800000), &lo);
+  return make_float2(__fsub_rd(lo, t), __fadd_ru(dd, t));
 }
 
 // Exact FP64 distances are needed only where they decide something: a pair

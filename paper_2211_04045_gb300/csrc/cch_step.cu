@@ -579,12 +579,6 @@ __device__ __forceinline__ void pgs_edge(Pool& P, int e, int i, int j, double* l
 constexpr int CW = 32;                  // 64-bit mask words per vertex
 constexpr int MAX_COLOURS = 64 * CW;    // colours one iteration may use
 
-struct SweepCtx {
-  int nc;          // contacts (items [0, nc)); edge-length constraints follow
-  double* lam;     // contact multipliers (gs_sweeps > 1), else null
-  double* elam;    // edge multipliers
-};
-
 // the vertices an item waits on and the counter values it waits for
 struct ItemWait {
   int v[4];
@@ -727,7 +721,9 @@ __global__ void __launch_bounds__(256, 2) k_colour(Pool P, OrderBufs B, int max_
     // its head item; the lanes whose head is ready colour it, and the warp
     // sleeps only when none is (a lane spinning alone would take issue
     // slots from a lane of its warp that could proceed).  The sleep grows
-    // with the smallest number of contacts still ahead of a head item.
+    // by about a microsecond per contact still ahead of the nearest head
+    // item (each of them is at least one dependent hop away), so that
+    // far-from-ready warps do not crowd L2 with counter loads.
     int j = 0;
     ItemWait w;
     bool has = m > 0;
@@ -748,7 +744,7 @@ __global__ void __launch_bounds__(256, 2) k_colour(Pool P, OrderBufs B, int max_
         break;
       }
       int g = __reduce_min_sync(0xffffffffu, gap);
-      __nanosleep(min(32 + 128 * (g - 1), 4096));
+      __nanosleep(min(32 + 1024 * (g - 1), 8192));
     }
   } else {
     // more contacts than that: poll every pending one each round
@@ -802,38 +798,31 @@ __global__ void __launch_bounds__(256) k_colour_stats(Pool P) {
 }
 
 // Grid barrier of a cooperative launch (every block resident): one arrival
-// counter and a generation word.  The last block to arrive resets the
-// counter and publishes the next generation; the others poll it, at most
-// max_polls times, after which the wait sets ERR_POLL.  A block also leaves
-// a wait once another block has given up.  Returns false when the barrier
-// failed; the caller then returns.
-// The release fence before the arrival publishes the block's writes (ordered
-// before thread 0 by the block barrier); a waiting block acquires through the
-// load that sees the new generation, the last block through a fence.
-__device__ __forceinline__ bool grid_barrier(Pool& P, unsigned& gen, int max_polls) {
+// counter, zeroed before the launch.  Each block adds one per barrier, so the
+// k-th barrier is passed once the counter reaches k * gridDim.x; a block
+// polls it at most max_polls times, after which the wait sets ERR_POLL, and
+// leaves a wait once another block has given up.  Returns false when the
+// barrier failed; the caller then returns.  The release fence before the
+// arrival publishes the block's writes (ordered before thread 0 by the block
+// barrier); a waiting block acquires them through the load that sees the
+// count, which the later arrivals' additions carry forward.
+__device__ __forceinline__ bool grid_barrier(Pool& P, unsigned& target, int max_polls) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    unsigned* bar = P.bar;
+    target += gridDim.x;
     fence_acq_rel();
-    unsigned a = atomicAdd(&bar[0], 1u);
-    if (a == gridDim.x - 1) {
-      fence_acq_rel();
-      bar[0] = 0u;
-      st_release_u32(&bar[1], gen + 1);
-    } else {
-      long long polls = 0;
-      while (ld_acquire_u32(&bar[1]) == gen) {
-        if (++polls > max_polls || (ld_relaxed(&P.cnt->err) & ERR_POLL)) {
-          atomicOr(&P.cnt->err, ERR_POLL);
-          ok = 0;
-          break;
-        }
-        __nanosleep(16);
+    red_relaxed_add((int*)P.bar, 1);
+    long long polls = 0;
+    while ((int)(ld_acquire_u32(P.bar) - target) < 0) {
+      if (++polls > max_polls || ((polls & 255) == 0 && (ld_relaxed(&P.cnt->err) & ERR_POLL))) {
+        atomicOr(&P.cnt->err, ERR_POLL);
+        ok = 0;
+        break;
       }
+      __nanosleep(16);
     }
-    gen++;
   }
   __syncthreads();
   return ok != 0;
@@ -843,114 +832,6 @@ __device__ __forceinline__ bool grid_barrier(Pool& P, unsigned& gen, int max_pol
 __device__ __forceinline__ bool edge_live(const Pool& P, int e) {
   const SceneState& S = P.ss[P.lv[e].z];
   return S.active && !S.done;
-}
-
-__device__ __forceinline__ void apply_contact(Pool& P, const SweepCtx& X, int i, bool first) {
-  int4 v = P.mixed ? ((const ContactF*)P.cons)[i].v : P.cons[i].v;
-  int vid[4] = {v.x, v.y, v.z, v.w};
-  if (P.mixed) pgs_contact_f(P, i, vid, X.lam, first);
-  else pgs_contact(P, i, vid, X.lam, first);
-}
-__device__ __forceinline__ void apply_edge(Pool& P, const SweepCtx& X, int e, bool first) {
-  int4 l = P.lv[e];
-  if (P.mixed) pgs_edge_f(P, e, l.x, l.y, X.elam, first);
-  else pgs_edge(P, e, l.x, l.y, X.elam, first);
-}
-
-// insertion of item `it` with sort key `key` into a thread's list (at most 32)
-__device__ __forceinline__ void insert_sorted(int* items, int* keys, int& m, int it, int key) {
-  int j = m++;
-  while (j > 0 && keys[j - 1] > key) {
-    items[j] = items[j - 1];
-    keys[j] = keys[j - 1];
-    j--;
-  }
-  items[j] = it;
-  keys[j] = key;
-}
-
-// The sweep: gs_sweeps times, the contact classes in ascending colour, then
-// the edge classes, one class per phase and a grid barrier after each.  Each
-// thread takes its contacts (i = tid + k * nth) and live edges (e = tid +
-// k * nth), sorted by colour, and applies in phase c the ones of colour c.
-// With more than 32 of either per thread, every thread scans all of its
-// items in every phase instead.  The last contact classes are small: from
-// the first class after which at most TAIL_MAX contacts remain, block 0
-// alone applies the rest, its threads separated by block barriers only,
-// while the other blocks wait at the next grid barrier.
-constexpr int TAIL_MAX = 2048;
-__global__ void __launch_bounds__(256, 1) k_colour_sweep(Pool P, int sweeps, int max_polls) {
-  SweepCtx X;
-  X.nc = min(P.cnt->n_cons, P.cons_cap);
-  X.lam = sweeps > 1 ? P.lam : nullptr;
-  X.elam = X.lam ? P.lam + P.cons_cap : nullptr;
-  int ncc = min(P.cnt->n_ccol, MAX_COLOURS), nec = P.n_ecol;
-  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  unsigned gen = ld_acquire_u32(&P.bar[1]);
-  bool few_c = X.nc <= 32 * nth, few_e = P.nl <= 32 * nth;
-  // first colour of the single-block tail (every block finds the same one)
-  int ctail = ncc;
-  if (few_c && gridDim.x > 1) {
-    int rest = 0;
-    while (ctail > 0 && rest + P.ccount[ctail - 1] <= TAIL_MAX) rest += P.ccount[--ctail];
-  }
-  int ci[32], cc[32], ei[32], ec[32];
-  int mc = 0, me = 0;
-  if (few_c)
-    for (int i = tid; i < X.nc; i += nth) {
-      int c = P.ccol[i];
-      if (c < ctail) insert_sorted(ci, cc, mc, i, c);
-      else {
-        int t = atomicAdd(&P.cnt->n_tail, 1);
-        if (t < TAIL_MAX) P.tail[t] = i;
-      }
-    }
-  if (few_e)
-    for (int e = tid; e < P.nl; e += nth)
-      if (edge_live(P, e)) insert_sorted(ei, ec, me, e, P.ecol[e]);
-  for (int sw = 0; sw < sweeps; sw++) {
-    bool first = sw == 0;
-    int p = 0;
-    for (int c = 0; c < ctail; c++) {
-      if (few_c) {
-        for (; p < mc && cc[p] == c; p++) apply_contact(P, X, ci[p], first);
-      } else {
-        for (int i = tid; i < X.nc; i += nth)
-          if (P.ccol[i] == c) apply_contact(P, X, i, first);
-      }
-      if (!grid_barrier(P, gen, max_polls)) return;
-    }
-    if (ctail < ncc) {
-      // the tail list is complete: every append preceded a grid barrier or
-      // this one
-      if (ctail == 0 && !grid_barrier(P, gen, max_polls)) return;
-      if (blockIdx.x == 0) {
-        int ti[TAIL_MAX / 256], tc[TAIL_MAX / 256];
-        int mt = 0;
-        int nt = min(__ldcg(&P.cnt->n_tail), TAIL_MAX);
-        for (int j = threadIdx.x; j < nt; j += blockDim.x) {
-          int i = __ldcg(&P.tail[j]);
-          insert_sorted(ti, tc, mt, i, P.ccol[i]);
-        }
-        int q = 0;
-        for (int c = ctail; c < ncc; c++) {
-          for (; q < mt && tc[q] == c; q++) apply_contact(P, X, ti[q], first);
-          __syncthreads();
-        }
-      }
-      if (!grid_barrier(P, gen, max_polls)) return;
-    }
-    p = 0;
-    for (int c = 0; c < nec; c++) {
-      if (few_e) {
-        for (; p < me && ec[p] == c; p++) apply_edge(P, X, ei[p], first);
-      } else {
-        for (int e = tid; e < P.nl; e += nth)
-          if (P.ecol[e] == c && edge_live(P, e)) apply_edge(P, X, e, first);
-      }
-      if (!grid_barrier(P, gen, max_polls)) return;
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -983,6 +864,7 @@ struct LevelCtx {
   int sweep;
   double* lam;     // contact multipliers (gs_sweeps > 1), else null
   double* elam;    // edge multipliers
+  bool dataflow;   // level sweep: record levels (first sweep) and advance the vertex counters
 };
 
 __device__ __forceinline__ int contacts_at(const OrderBufs& B, int v) {
@@ -1049,16 +931,211 @@ __device__ __forceinline__ unsigned long long level_prio(const Pool& P, const Le
   return splitmix64(d.seed ^ ((3ULL << 62) | (unsigned long long)(e - d.l0)));
 }
 
+// Quad form of the FP64 sweep.  FP64 runs at 2 lanes per cycle per SM on
+// this part and a warp instruction holds the pipe for all 32 lanes, active or
+// not, so a thread applying a 4-vertex contact alone (about 75 FP64
+// instructions, most lanes of its warp idle) makes the dependent chain long.
+// Here four lanes share one list and apply its head together: lane k owns
+// vertex k of the head constraint, polls that vertex's counter, loads its y,
+// x and gradient block, and computes its term g_k.(y_k - x_k); the quad
+// gathers the four terms and every lane forms w = (((c0 + t0) + t1) + t2) + t3,
+// the same sum in the same order as pgs_contact, then updates its own vertex.
+// Each lane's arithmetic is that of pgs_contact for its vertex, so the result
+// is bit for bit the same, at about 30 FP64 instructions per constraint.  An
+// edge-length constraint is applied by lanes 0 and 1 (vertices i and j).
+//
+// A quad's list is split over its lanes: lane k takes items
+// q + nq * (k + 4 m) and sorts them; the quad's head is the first of the
+// four lanes' heads in the sweep order (contacts, then edges, by descending
+// priority, ties by index), found with two shuffles.
+constexpr int NO_ITEM = 0x7fffffff;  // an exhausted list's head
+constexpr int QWIN = 4;              // items a quad polls at once
+__device__ __forceinline__ bool sweep_before(int ia, unsigned long long ka, int ib, unsigned long long kb, int nc) {
+  bool ea = ia >= nc, eb = ib >= nc;
+  if (ea != eb) return eb;
+  if (ka != kb) return ka < kb;
+  return ia < ib;
+}
+__device__ __forceinline__ int quad_head(unsigned mask, int item, unsigned long long key, int nc) {
+  for (int o = 1; o <= 2; o <<= 1) {
+    int io = __shfl_xor_sync(mask, item, o);
+    unsigned long long ko = __shfl_xor_sync(mask, key, o);
+    if (sweep_before(io, ko, item, key, nc)) {
+      item = io;
+      key = ko;
+    }
+  }
+  return item;
+}
+// lane lk's vertex of item i and the counter value it waits for (-1: none)
+__device__ __forceinline__ void quad_vertex(const Pool& P, const OrderBufs& B, const LevelCtx& X, int i, int lk,
+                                            int& vk, int& tk) {
+  vk = -1;
+  tk = -1;
+  if (i < X.nc) {
+    int4 v = P.cons[i].v;
+    vk = lk == 0 ? v.x : lk == 1 ? v.y : lk == 2 ? v.z : v.w;
+    if (movable(P, vk)) tk = target_at(P, B, vk, X.sweep, __ldg(&B.rank[4 * i + lk]), false);
+  } else if (lk < 2) {
+    int e = i - X.nc;
+    int4 l = P.lv[e];
+    int2 r = __ldg(&P.erank[e]);
+    vk = lk == 0 ? l.x : l.y;
+    if (movable(P, vk)) tk = target_at(P, B, vk, X.sweep, lk == 0 ? r.x : r.y, true);
+  }
+}
+// contact ci, applied by the quads of `mask` (all four lanes of each)
+__device__ __forceinline__ void quad_contact(Pool& P, OrderBufs& B, const LevelCtx& X, unsigned mask, int ci, int lk,
+                                             int vk, int tk) {
+  const Contact& c = P.cons[ci];
+  bool first = X.sweep == 0, rec = first && X.dataflow;
+  dv3 yk = {0.0, 0.0, 0.0}, gk = yk;
+  double tkm = 0.0;
+  if (vk >= 0) {
+    yk = ldy(P, vk);
+    dv3 xk = mk(P.x[vk]);
+    gk = {c.g[3 * lk], c.g[3 * lk + 1], c.g[3 * lk + 2]};
+    tkm = vdot(gk, vsub(yk, xk));
+  }
+  int lv = rec && tk >= 0 ? __ldcg(&P.vlevel[vk]) + 1 : 0;
+  int base = (threadIdx.x & 31) & ~3;
+  double t[4];
+  for (int k = 0; k < 4; k++) t[k] = __shfl_sync(mask, tkm, base + k);
+  lv = max(lv, __shfl_xor_sync(mask, lv, 1));
+  lv = max(lv, __shfl_xor_sync(mask, lv, 2));
+  double den = c.den, w = c.c0;
+  if (den > 0.0) {
+    int nv = c.v.z < 0 ? 2 : 4;
+    for (int k = 0; k < nv; k++) w = w + t[k];
+    double l0 = X.lam && !first ? X.lam[ci] : 0.0;
+    double tl = l0 - w / den;
+    double ln = tl > 0.0 ? tl : 0.0;
+    double dl = ln - l0;
+    if (X.lam && lk == 0) X.lam[ci] = ln;
+    if (dl != 0.0 && vk >= 0) {
+      double sc = P.im[vk] * dl;
+      sty(P, vk, vadd(yk, vscl(sc, gk)));
+    }
+  }
+  if (!X.dataflow) return;
+  if (rec) {
+    if (lk == 0) P.ccol[ci] = lv;
+    if (tk >= 0) __stcg(&P.vlevel[vk], lv);
+  }
+  fence_acq_rel();
+  if (tk >= 0) red_relaxed_add(&B.vdone[vk], 1);
+}
+// edge-length constraint e, applied by lanes 0 (vertex i) and 1 (vertex j)
+__device__ __forceinline__ void quad_edge(Pool& P, OrderBufs& B, const LevelCtx& X, int e, int lk, int vk, int tk) {
+  if (lk < 2) {
+    P4 gd = P.lg[e];
+    int4 l = P.lv[e];
+    dv3 yi = ldy(P, l.x), yj = ldy(P, l.y);
+    double sigma = P.sd[P.vscene[l.x]].sigma;
+    if (gd.w > 0.0) {
+      dv3 g = {gd.x, gd.y, gd.z};
+      double w = sigma - vdot(g, vsub(yi, yj));
+      double l0 = X.elam && X.sweep != 0 ? X.elam[e] : 0.0;
+      double tl = l0 - w / gd.w;
+      double ln = tl > 0.0 ? tl : 0.0;
+      double dl = ln - l0;
+      if (X.elam && lk == 0) X.elam[e] = ln;
+      if (dl != 0.0) {
+        if (lk == 0) sty(P, l.x, vsub(yi, vscl(P.im[l.x] * dl, g)));
+        else sty(P, l.y, vadd(yj, vscl(P.im[l.y] * dl, g)));
+      }
+    }
+  }
+  fence_acq_rel();
+  if (tk >= 0) red_relaxed_add(&B.vdone[vk], 1);
+}
+
 __global__ void __launch_bounds__(256, 2) k_level_sweep(Pool P, OrderBufs B, int sweep, int sweeps, int max_polls) {
   LevelCtx X;
   X.nc = min(P.cnt->n_cons, P.cons_cap);
   X.sweep = sweep;
+  X.dataflow = true;
   X.lam = sweeps > 1 ? P.lam : nullptr;
   X.elam = X.lam ? P.lam + P.cons_cap : nullptr;
   int n = X.nc + P.nl;
   int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   long long polls = 0;
-  if (n <= 32 * nth) {
+  if (!P.mixed && n <= 32 * nth) {
+    const unsigned FULL = 0xffffffffu;
+    int lk = threadIdx.x & 3, nq = nth >> 2, q = tid >> 2;
+    // this lane's share of its quad's items in sweep order (at most 32)
+    int items[32];
+    unsigned long long keys[32];
+    int m = 0;
+    for (int i = q + nq * lk; i < n; i += 4 * nq) {
+      if (!level_live(P, X, i)) continue;
+      unsigned long long key = ~level_prio(P, X, i);
+      int j = m++;
+      while (j > 0 && sweep_before(i, key, items[j - 1], keys[j - 1], X.nc)) {
+        items[j] = items[j - 1];
+        keys[j] = keys[j - 1];
+        j--;
+      }
+      items[j] = i;
+      keys[j] = key;
+    }
+    // The quad keeps a window of the first QWIN unapplied items of its list
+    // and applies any of them whose counters are ready: an item's counters
+    // are ready only once every earlier constraint at its vertices is
+    // applied, so two items found ready in the same round share no movable
+    // vertex and commute.  The earliest pending item of the sweep is in its
+    // quad's window and ready, so the sweep progresses.
+    int j = 0;
+    int wid[QWIN], wv[QWIN], wt[QWIN];
+    for (int s = 0; s < QWIN; s++) {
+      wid[s] = quad_head(FULL, j < m ? items[j] : NO_ITEM, j < m ? keys[j] : ~0ULL, X.nc);
+      if (j < m && items[j] == wid[s]) j++;  // the lane that held the head
+      wv[s] = wt[s] = -1;
+      if (wid[s] != NO_ITEM) quad_vertex(P, B, X, wid[s], lk, wv[s], wt[s]);
+    }
+    // as below: the quads of a warp advance together and the warp sleeps
+    // only when no quad has a ready item
+    for (;;) {
+      bool has = false;
+      for (int s = 0; s < QWIN; s++) has |= wid[s] != NO_ITEM;
+      if (!__any_sync(FULL, has)) break;
+      int gap = 1 << 30;
+      bool ready[QWIN];
+      for (int s = 0; s < QWIN; s++) {
+        int g = wid[s] != NO_ITEM && wt[s] >= 0 ? wt[s] - ld_acquire(&B.vdone[wv[s]]) : 0;
+        g = max(g, __shfl_xor_sync(FULL, g, 1));
+        g = max(g, __shfl_xor_sync(FULL, g, 2));
+        ready[s] = wid[s] != NO_ITEM && g == 0;
+        if (wid[s] != NO_ITEM) gap = min(gap, g);
+      }
+      bool any = false;
+      for (int s = 0; s < QWIN; s++) {
+        unsigned cm = __ballot_sync(FULL, ready[s] && wid[s] < X.nc);
+        unsigned em = __ballot_sync(FULL, ready[s] && wid[s] >= X.nc);
+        if (!(cm | em)) continue;
+        any = true;
+        if (ready[s]) {
+          if (wid[s] < X.nc) quad_contact(P, B, X, cm, wid[s], lk, wv[s], wt[s]);
+          else quad_edge(P, B, X, wid[s] - X.nc, lk, wv[s], wt[s]);
+        }
+        // refill the slot from the list (every lane takes part in the shuffles)
+        int nx = quad_head(FULL, j < m ? items[j] : NO_ITEM, j < m ? keys[j] : ~0ULL, X.nc);
+        if (ready[s]) {
+          if (j < m && items[j] == nx) j++;
+          wid[s] = nx;
+          wv[s] = wt[s] = -1;
+          if (nx != NO_ITEM) quad_vertex(P, B, X, nx, lk, wv[s], wt[s]);
+        }
+      }
+      if (any) continue;
+      if (++polls > max_polls) {  // the same count in every lane
+        if ((threadIdx.x & 31) == 0) atomicOr(&P.cnt->err, ERR_POLL);
+        break;
+      }
+      int g = __reduce_min_sync(FULL, gap);
+      __nanosleep(min(32 + 1024 * (g - 1), 8192));
+    }
+  } else if (n <= 32 * nth) {
     // this thread's items in sweep order (insertion sort, at most 32)
     int items[32];
     unsigned long long keys[32];
@@ -1078,8 +1155,10 @@ __global__ void __launch_bounds__(256, 2) k_level_sweep(Pool P, OrderBufs B, int
     }
     // The lanes of a warp advance together: each round every lane checks
     // its head item; the lanes whose head is ready apply it, and the warp
-    // sleeps only when none is.  The sleep grows with the smallest number of
-    // constraints still ahead of a head item.
+    // sleeps only when none is.  The sleep grows by about a microsecond per
+    // constraint still ahead of the nearest head item (each is at least one
+    // dependent hop away), so that far-from-ready warps do not crowd L2 with
+    // counter loads.
     int j = 0;
     ItemWait w;
     bool has = m > 0;
@@ -1100,7 +1179,7 @@ __global__ void __launch_bounds__(256, 2) k_level_sweep(Pool P, OrderBufs B, int
         break;
       }
       int g = __reduce_min_sync(0xffffffffu, gap);
-      __nanosleep(min(32 + 128 * (g - 1), 4096));
+      __nanosleep(min(32 + 1024 * (g - 1), 8192));
     }
   } else {
     // more items than that: poll every pending item each round
@@ -1126,6 +1205,129 @@ __global__ void __launch_bounds__(256, 2) k_level_sweep(Pool P, OrderBufs B, int
         }
         __nanosleep(32);
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Colour-class sweep of the greedy colouring (colouring = 0).  k_colour_order
+// groups the contacts by colour (a counting sort on the histogram of
+// k_colour_stats; the order within a colour is immaterial, its contacts share
+// no movable vertex); the edge-length constraints were grouped once on the
+// host.  k_colour_sweep then applies, gs_sweeps times, the contact classes
+// in ascending colour and then the edge classes, one class per phase of a
+// persistent kernel with a grid barrier after each.  A class's contacts are
+// contiguous, so its work spreads over the fewest warps: in FP64 a quad of
+// lanes applies each contact (quad_contact, bit for bit pgs_contact), in
+// mixed precision one thread each; edges take one thread each.  The last
+// contact classes are small: from the first class after which at most
+// TAIL_MAX contacts remain, block 0 alone applies the rest, separated by block
+// barriers only, while the other blocks wait at the next grid barrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void apply_contact(Pool& P, const LevelCtx& X, int i) {
+  int4 v = ((const ContactF*)P.cons)[i].v;
+  int vid[4] = {v.x, v.y, v.z, v.w};
+  pgs_contact_f(P, i, vid, X.lam, X.sweep == 0);
+}
+__device__ __forceinline__ void apply_edge(Pool& P, const LevelCtx& X, int e) {
+  int4 l = P.lv[e];
+  if (P.mixed) pgs_edge_f(P, e, l.x, l.y, X.elam, X.sweep == 0);
+  else pgs_edge(P, e, l.x, l.y, X.elam, X.sweep == 0);
+}
+// exclusive prefix of ccount[0, ncc) into off[0, ncc] (one block)
+__device__ __forceinline__ void colour_offsets(const Pool& P, int ncc, int* off) {
+  __shared__ int part[256];
+  int per = (ncc + blockDim.x - 1) / blockDim.x, a = threadIdx.x * per, sum = 0;
+  for (int c = a; c < min(a + per, ncc); c++) sum += P.ccount[c];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < (int)blockDim.x; t++) {
+      int v = part[t];
+      part[t] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  int run = part[threadIdx.x];
+  for (int c = a; c < min(a + per, ncc); c++) {
+    off[c] = run;
+    run += P.ccount[c];
+  }
+  if (threadIdx.x == blockDim.x - 1) off[ncc] = run;
+  __syncthreads();
+}
+__global__ void __launch_bounds__(256) k_colour_order(Pool P) {
+  __shared__ int off[MAX_COLOURS + 1];
+  int ncc = min(P.cnt->n_ccol, MAX_COLOURS);
+  colour_offsets(P, ncc, off);
+  if (blockIdx.x == 0)
+    for (int c = threadIdx.x; c <= ncc; c += blockDim.x) P.coff[c] = off[c];
+  int n = min(P.cnt->n_cons, P.cons_cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c = P.ccol[i];
+    if ((unsigned)c < (unsigned)ncc) P.corder[off[c] + atomicAdd(&P.cfill[c], 1)] = i;
+  }
+}
+
+constexpr int TAIL_MAX = 2048;
+// contacts [a, b) of corder, applied by `quads` quads (quad q of them is this lane's)
+__device__ __forceinline__ void colour_class(Pool& P, OrderBufs& B, const LevelCtx& X, int a, int b, int q, int quads,
+                                             int th, int threads) {
+  if (P.mixed) {
+    for (int k = a + th; k < b; k += threads) apply_contact(P, X, __ldg(&P.corder[k]));
+    return;
+  }
+  int lk = threadIdx.x & 3;
+  for (int base = a; base < b; base += quads) {  // the same trip count in every lane
+    int k = base + q;
+    int ci = k < b ? __ldcg(&P.corder[k]) : -1;
+    unsigned cm = __ballot_sync(0xffffffffu, ci >= 0);
+    if (ci >= 0) {
+      int4 v = P.cons[ci].v;
+      int vk = lk == 0 ? v.x : lk == 1 ? v.y : lk == 2 ? v.z : v.w;
+      quad_contact(P, B, X, cm, ci, lk, vk, -1);
+    }
+  }
+}
+__global__ void __launch_bounds__(256, 1) k_colour_sweep(Pool P, OrderBufs B, int sweeps, int max_polls) {
+  LevelCtx X;
+  X.nc = min(P.cnt->n_cons, P.cons_cap);
+  X.lam = sweeps > 1 ? P.lam : nullptr;
+  X.elam = X.lam ? P.lam + P.cons_cap : nullptr;
+  X.dataflow = false;
+  int ncc = min(P.cnt->n_ccol, MAX_COLOURS), nec = P.n_ecol;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  unsigned target = 0;
+  // first colour of the single-block tail (every block finds the same one)
+  int ctail = ncc;
+  if (gridDim.x > 1) {
+    int rest = 0;
+    while (ctail > 0 && rest + P.ccount[ctail - 1] <= TAIL_MAX) rest += P.ccount[--ctail];
+  }
+  for (int sw = 0; sw < sweeps; sw++) {
+    X.sweep = sw;
+    for (int c = 0; c < ctail; c++) {
+      colour_class(P, B, X, __ldg(&P.coff[c]), __ldg(&P.coff[c + 1]), tid >> 2, nth >> 2, tid, nth);
+      if (!grid_barrier(P, target, max_polls)) return;
+    }
+    if (ctail < ncc) {
+      if (blockIdx.x == 0)
+        for (int c = ctail; c < ncc; c++) {
+          colour_class(P, B, X, __ldg(&P.coff[c]), __ldg(&P.coff[c + 1]), threadIdx.x >> 2, blockDim.x >> 2,
+                       threadIdx.x, blockDim.x);
+          __syncthreads();
+        }
+      if (!grid_barrier(P, target, max_polls)) return;
+    }
+    for (int c = 0; c < nec; c++) {
+      int a = __ldg(&P.eoff[c]), b = __ldg(&P.eoff[c + 1]);
+      for (int k = a + tid; k < b; k += nth) {
+        int e = __ldg(&P.eorder[k]);
+        if (edge_live(P, e)) apply_edge(P, X, e);
+      }
+      if (!grid_barrier(P, target, max_polls)) return;
     }
   }
 }
@@ -1598,7 +1800,6 @@ __global__ void k_control(Pool P, int cur) {
     C->vcontacts = 0;
     C->n_ccol = 0;
     C->n_exact[0] = C->n_exact[1] = 0;
-    C->n_tail = 0;
   }
 }
 
@@ -1636,7 +1837,10 @@ int coop_grid(int threads, int which) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_level_sweep, threads, 0);
     if (per2 < per) per = per2;
   } else {
+    // one block per SM: a class spans a few hundred warps at most, and every
+    // block more is one more arrival at each grid barrier
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_sweep, threads, 0);
+    if (per > 1) per = 1;
   }
   if (per < 1) per = 1;
   return sms * per;
@@ -1755,12 +1959,14 @@ cudaError_t iteration(Runtime& R, int cur, cudaStream_t st) {
       cudaMemsetAsync(P.ccount, 0, sizeof(int) * MAX_COLOURS, st);
       e = coop_launch(k_colour, R.coop_blocks, 256, st, P, B, R.max_polls);
       if (e == cudaSuccess) k_colour_stats<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P);
+      cudaMemsetAsync(P.cfill, 0, sizeof(int) * MAX_COLOURS, st);
+      if (e == cudaSuccess) k_colour_order<<<grid_for(P.cons_cap, 256), 256, 0, st>>>(P);
       prof_mark(R, PG_COLOUR, 1, st);
       prof_mark(R, PG_SWEEP, 0, st);
       cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned int), st);
-      if (e == cudaSuccess) e = coop_launch(k_colour_sweep, R.sweep_blocks, 256, st, P, R.sweeps, R.max_polls);
+      if (e == cudaSuccess) e = coop_launch(k_colour_sweep, R.sweep_blocks, 256, st, P, B, R.sweeps, R.max_polls);
       prof_mark(R, PG_SWEEP, 1, st);
-      R.launches += 7;
+      R.launches += 8;
     }
   }
   if (e != cudaSuccess) return e;

@@ -69,6 +69,27 @@ def test_more_than_32_items_per_thread(cuda, colouring):
     full.close()
 
 
+def test_full_quad_lists_of_the_level_sweep(cuda):
+    # the FP64 level sweep gives each quad of lanes up to 4 x 32 items; with a
+    # one-block grid (64 quads) a scene of 4,096-8,192 items fills them to
+    # 16-32 items per lane, against the same step on the full grid
+    sc = scenes.two_cloths(n=32, side=0.3, sep=0.0012, omega=6.0, noise=0.3, seed=4)
+    kw = dict(max_iters=40)
+    _, _, tr = oracle.handle_step(oracle.OracleScene(sc), oracle.params_for(sc, **kw), *scenes.initial(sc)[:2],
+                                  trace_iters=48)
+    items = np.asarray(tr["n_contacts"]) + len(sc.len_edges)
+    assert 4096 < items.min() and items.max() <= 8192, (items.min(), items.max())
+    one = cch.Scene(sc, cch.params_for(sc, sweep_blocks=1, **kw))
+    full = cch.Scene(sc, cch.params_for(sc, **kw))
+    x, xt, _ = scenes.initial(sc)
+    xn, sg, so = one_step(cuda, sc, x, xt, one, **kw)
+    same_stats(sg, so, "one block")
+    o2, s2 = full.step(T(x, cuda), T(xt, cuda))
+    assert np.array_equal(xn, o2.cpu().numpy()) and s2["iterations"] == sg["iterations"]
+    one.close()
+    full.close()
+
+
 @pytest.mark.parametrize("colouring", [1, 0])
 @pytest.mark.parametrize("sweeps", [2, 3])
 @pytest.mark.parametrize("name", ["cloth_sphere", "two_cloths", "tets"])
