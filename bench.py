@@ -613,7 +613,8 @@ def main():
     log(f"timed {K} steps in {total_ms / 1000:.2f} s: " + ", ".join(f"{m:.0f} ms" for m in step_ms))
     log("per step: iterations " + ", ".join(str(s["iterations"]) for s in stats) + "; final ||r|| "
         + ", ".join(f"{s['final_r_inf']:.3g}" for s in stats) + "; frozen "
-        + ", ".join(str(s["frozen_vertices"]) for s in stats))
+        + ", ".join(str(s["frozen_vertices"]) for s in stats) + "; searches "
+        + ", ".join(str(s["searches"]) for s in stats))
     total_ms = slowest(total_ms, dev)
 
     iters = np.array([s["iterations"] for s in stats])
@@ -729,6 +730,7 @@ def main():
                "iterations_per_step": float(np.mean(iters)), "converged_steps": int(sum(s["converged"] for s in stats)),
                "final_r_inf": [round(s["final_r_inf"], 6) for s in stats],
                "frozen_vertices": [int(s["frozen_vertices"]) for s in stats],
+               "searches_per_step": [int(s["searches"]) for s in stats],
                "intersections": int(sum(s["intersections"] for s in stats)),
                "uncertain": int(sum(s["uncertain"] for s in stats)),
                "sweep_depth": int(pst["gs_depth"]), "contact_colours": int(max(s["contact_colours"] for s in stats)),

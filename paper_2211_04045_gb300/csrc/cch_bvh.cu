@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
           bool qlow = q1 < e2;
           int4 A = qlow ? make_int4(qx, qy, 0, 0) : eb, Bv = qlow ? eb : make_int4(qx, qy, 0, 0);
           fv3 fa0 = fk(P.xf[A.x]), fa1 = fk(P.xf[A.y]), fb0 = fk(P.xf[Bv.x]), fb1 = fk(P.xf[Bv.y]);
-          float lower = ee_lower(fa0, fa1, fb0, fb1, Df);
+          float lower = ee_lower(fa0, fa1, fb0, fb1, qD);
           if (lower >= qD) return;
           push_survivor(P, K_EE, mkkey(K_EE, min(q1, e2) - S.e0, max(q1, e2) - S.e0),
                         make_int4(A.x, A.y, Bv.x, Bv.y), lower);
