@@ -203,10 +203,10 @@ def smooth_displacement(sc, rng):
     """A displacement of every movable vertex by a random smooth field: per
     axis a sinusoid of x with a random direction, wavelength between a third
     of the scene's extent and its extent, and phase, with an amplitude drawn
-    log-uniformly from 0.5 to 5 mm."""
+    log-uniformly from 0.05 to 1 mm (a time step of 1/100 s at up to 10 cm/s)."""
     x = sc.x0
     ext = float(np.ptp(x, axis=0).max())
-    amp = float(np.exp(rng.uniform(np.log(5e-4), np.log(5e-3))))
+    amp = float(np.exp(rng.uniform(np.log(5e-5), np.log(1e-3))))
     d = np.zeros_like(x)
     for a in range(3):
         k = rng.normal(0.0, 1.0, 3)
@@ -245,17 +245,23 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
         g.step(torch.tensor(x, device=dev), torch.tensor(xt, device=dev))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain_ms, plain_out = [], []
+    plain_ms, plain_out, plain_it = [], [], []
     for i in range(N):
         a = time.perf_counter()
-        o, _ = plain[which[i]].step(inputs[i][0], inputs[i][1])
+        o, st = plain[which[i]].step(inputs[i][0], inputs[i][1])
         plain_ms.append(1000.0 * (time.perf_counter() - a))
         plain_out.append(o)
+        plain_it.append(st["iterations"])
     plain_s = time.perf_counter() - t0
     for g in plain:
         g.close()
+    plain_ms, plain_it = np.array(plain_ms), np.array(plain_it)
     out["plain_fp64"] = {"value": N / plain_s, "unit": "steps/s", "p50_ms": float(np.percentile(plain_ms, 50)),
-                         "p99_ms": float(np.percentile(plain_ms, 99))}
+                         "p99_ms": float(np.percentile(plain_ms, 99)),
+                         "per_scene": [{"requests": int(np.sum(which == k)),
+                                        "mean_ms": round(float(np.mean(plain_ms[which == k])), 2) if np.any(which == k) else None,
+                                        "max_iterations": int(np.max(plain_it[which == k])) if np.any(which == k) else None}
+                                       for k in range(len(scs))]}
     for prec in precisions:
         prm = cch.params_for(scs[0], precision=1 if prec == "mixed" else 0, iters_per_launch=8)
         sv = cch.Server(80 << 30, prm, max_active=max_active)

@@ -947,9 +947,9 @@ __device__ __forceinline__ unsigned long long level_prio(const Pool& P, const Le
 // A quad's list is split over its lanes: lane k takes items
 // q + nq * (k + 4 m) and sorts them; the quad's head is the first of the
 // four lanes' heads in the sweep order (contacts, then edges, by descending
-// priority, ties by index), found with two shuffles.
+// priority, ties by index), found with two shuffles.  The quad applies its
+// head once the head's counters are ready, as the thread form below does.
 constexpr int NO_ITEM = 0x7fffffff;  // an exhausted list's head
-constexpr int QWIN = 4;              // items a quad polls at once
 __device__ __forceinline__ bool sweep_before(int ia, unsigned long long ka, int ib, unsigned long long kb, int nc) {
   bool ea = ia >= nc, eb = ib >= nc;
   if (ea != eb) return eb;
@@ -1079,55 +1079,34 @@ __global__ void __launch_bounds__(256, 2) k_level_sweep(Pool P, OrderBufs B, int
       items[j] = i;
       keys[j] = key;
     }
-    // The quad keeps a window of the first QWIN unapplied items of its list
-    // and applies any of them whose counters are ready: an item's counters
-    // are ready only once every earlier constraint at its vertices is
-    // applied, so two items found ready in the same round share no movable
-    // vertex and commute.  The earliest pending item of the sweep is in its
-    // quad's window and ready, so the sweep progresses.
     int j = 0;
-    int wid[QWIN], wv[QWIN], wt[QWIN];
-    for (int s = 0; s < QWIN; s++) {
-      wid[s] = quad_head(FULL, j < m ? items[j] : NO_ITEM, j < m ? keys[j] : ~0ULL, X.nc);
-      if (j < m && items[j] == wid[s]) j++;  // the lane that held the head
-      wv[s] = wt[s] = -1;
-      if (wid[s] != NO_ITEM) quad_vertex(P, B, X, wid[s], lk, wv[s], wt[s]);
-    }
+    int cur = quad_head(FULL, m > 0 ? items[0] : NO_ITEM, m > 0 ? keys[0] : ~0ULL, X.nc);
+    int vk = -1, tk = -1;
+    if (cur != NO_ITEM) quad_vertex(P, B, X, cur, lk, vk, tk);
     // as below: the quads of a warp advance together and the warp sleeps
-    // only when no quad has a ready item
-    for (;;) {
-      bool has = false;
-      for (int s = 0; s < QWIN; s++) has |= wid[s] != NO_ITEM;
-      if (!__any_sync(FULL, has)) break;
-      int gap = 1 << 30;
-      bool ready[QWIN];
-      for (int s = 0; s < QWIN; s++) {
-        int g = wid[s] != NO_ITEM && wt[s] >= 0 ? wt[s] - ld_acquire(&B.vdone[wv[s]]) : 0;
-        g = max(g, __shfl_xor_sync(FULL, g, 1));
-        g = max(g, __shfl_xor_sync(FULL, g, 2));
-        ready[s] = wid[s] != NO_ITEM && g == 0;
-        if (wid[s] != NO_ITEM) gap = min(gap, g);
-      }
-      bool any = false;
-      for (int s = 0; s < QWIN; s++) {
-        unsigned cm = __ballot_sync(FULL, ready[s] && wid[s] < X.nc);
-        unsigned em = __ballot_sync(FULL, ready[s] && wid[s] >= X.nc);
-        if (!(cm | em)) continue;
-        any = true;
-        if (ready[s]) {
-          if (wid[s] < X.nc) quad_contact(P, B, X, cm, wid[s], lk, wv[s], wt[s]);
-          else quad_edge(P, B, X, wid[s] - X.nc, lk, wv[s], wt[s]);
+    // only when no quad's head is ready.  (Polling several items per quad
+    // instead of the head only was measured slower: more counter loads per
+    // round, and the head is the item the sweep waits for.)
+    while (__any_sync(FULL, cur != NO_ITEM)) {
+      bool has = cur != NO_ITEM;
+      int gap = has && tk >= 0 ? tk - ld_acquire(&B.vdone[vk]) : 0;
+      gap = max(gap, __shfl_xor_sync(FULL, gap, 1));
+      gap = max(gap, __shfl_xor_sync(FULL, gap, 2));
+      if (!has) gap = 1 << 30;
+      bool ready = has && gap == 0;
+      unsigned cm = __ballot_sync(FULL, ready && cur < X.nc);
+      unsigned em = __ballot_sync(FULL, ready && cur >= X.nc);
+      if (cm | em) {
+        if (ready) {
+          if (cur < X.nc) quad_contact(P, B, X, cm, cur, lk, vk, tk);
+          else quad_edge(P, B, X, cur - X.nc, lk, vk, tk);
+          if (j < m && items[j] == cur) j++;  // the lane that held the head
+          cur = quad_head(cm | em, j < m ? items[j] : NO_ITEM, j < m ? keys[j] : ~0ULL, X.nc);
+          vk = tk = -1;
+          if (cur != NO_ITEM) quad_vertex(P, B, X, cur, lk, vk, tk);
         }
-        // refill the slot from the list (every lane takes part in the shuffles)
-        int nx = quad_head(FULL, j < m ? items[j] : NO_ITEM, j < m ? keys[j] : ~0ULL, X.nc);
-        if (ready[s]) {
-          if (j < m && items[j] == nx) j++;
-          wid[s] = nx;
-          wv[s] = wt[s] = -1;
-          if (nx != NO_ITEM) quad_vertex(P, B, X, nx, lk, wv[s], wt[s]);
-        }
+        continue;
       }
-      if (any) continue;
       if (++polls > max_polls) {  // the same count in every lane
         if ((threadIdx.x & 31) == 0) atomicOr(&P.cnt->err, ERR_POLL);
         break;
