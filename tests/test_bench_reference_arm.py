@@ -17,9 +17,9 @@ def run(args, env_extra=None):
                           capture_output=True, text=True, timeout=600)
 
 
-def test_reference_line_contract():
+def reference_line(cores):
     p = run(["--impl", "reference", "--config", "cloth_sphere", "--steps", "2", "--warmup", "1",
-             "--ref-budget", "3"])
+             "--ref-budget", "3", "--ref-cores", str(cores)])
     assert p.returncode == 0, p.stderr[-2000:]
     lines = [l for l in p.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -30,8 +30,22 @@ def test_reference_line_contract():
     assert d["value"] > 0 and abs(d["ms_per_step"] - 1000.0 / d["value"]) < 1e-6 * d["ms_per_step"]
     assert d["config"]["workload"] == "cloth32_sphere3_fp64"
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == cores and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    return d
+
+
+def test_reference_line_contract():
+    reference_line(1)
+
+
+def test_reference_line_on_several_cores():
+    # two single-threaded oracles side by side: their steps per second add up
+    import pytest
+    if (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1) < 4:
+        pytest.skip("fewer than four host cores")
+    d1, d2 = reference_line(1), reference_line(2)
+    assert d2["value"] > 1.2 * d1["value"]
 
 
 def test_reference_other_ranks_are_silent():
