@@ -267,8 +267,9 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
     out = {"requests": N, "rate_per_s": rate, "max_active": max_active, "budget_bytes": 80 << 30,
            "scene_prims": [prims(sc) for sc in scs]}
     # plain: one request at a time, FP64, one resident scene per kind
-    base = cch.params_for(scs[0], iters_per_launch=8)
-    plain = [cch.Scene(sc, base) for sc in scs]
+    # every scene with its own physical parameters (Table 2 values, or the
+    # scene's: the tubes take delta = 0.5 mm)
+    plain = [cch.Scene(sc, cch.params_for(sc, iters_per_launch=8)) for sc in scs]
     for g, sc in zip(plain, scs):  # warm-up: builds and graph capture
         x, xt, _ = scenes.initial(sc)
         g.step(torch.tensor(x, device=dev), torch.tensor(xt, device=dev))
@@ -294,7 +295,7 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
     for prec in precisions:
         prm = cch.params_for(scs[0], precision=1 if prec == "mixed" else 0, iters_per_launch=8)
         sv = cch.Server(80 << 30, prm, max_active=max_active)
-        ids = [sv.add_scene(sc) for sc in scs]
+        ids = [sv.add_scene(sc, cch.params_for(sc)) for sc in scs]
         for k, sc in enumerate(scs):  # one warm request per scene (pool build, graph capture)
             x, xt, _ = scenes.initial(sc)
             o = torch.empty((sc.n_verts, 3), dtype=torch.float64, device=dev)

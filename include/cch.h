@@ -200,6 +200,15 @@ cch_status cch_create_scene(const cch_topology* topo, const cch_params* prm, voi
 cch_status cch_create_batch(const cch_topology* topos, int32_t n_scenes, const cch_params* prm, void* cuda_stream,
                             cch_scene** out);
 
+/* As cch_create_batch, with each scene's own physical parameters (Table 2):
+ * d_min, d_max, delta, sigma, gamma, eps, max_iters and seed come from
+ * scene_prm[s] (n_scenes entries, each validated like prm); every other
+ * field, the method and its launch configuration, from prm.  A scene of the
+ * batch then returns what cch_create_scene with scene_prm[s] returns, when
+ * the method fields agree.  scene_prm NULL: cch_create_batch. */
+cch_status cch_create_batch_params(const cch_topology* topos, int32_t n_scenes, const cch_params* prm,
+                                   const cch_params* scene_prm, void* cuda_stream, cch_scene** out);
+
 /* One collision-handling call, Algorithm 1: x^(0) = x_t, y^(0) = x_tilde;
  * x_next receives x^(l+1).  Device pointers, n_verts x 3 float64 each;
  * x_next may alias x_t.  stats may be NULL. */
@@ -351,6 +360,10 @@ cch_status cch_server_create(size_t hbm_budget_bytes, const cch_params* prm, int
                              cch_server** out);
 /* Make a scene resident; CCH_E_BUDGET when it would exceed the budget. */
 cch_status cch_server_add_scene(cch_server* sv, const cch_topology* topo, int32_t* scene_id);
+/* The same, with the scene's own physical parameters (the fields that
+ * cch_create_batch_params takes per scene; the rest from the server's). */
+cch_status cch_server_add_scene_params(cch_server* sv, const cch_topology* topo, const cch_params* scene_prm,
+                                       int32_t* scene_id);
 /* Queue one step of a resident scene; pointers are device pointers that must
  * stay valid until the request completes. */
 cch_status cch_server_submit(cch_server* sv, int32_t scene_id, const double* x_t, const double* x_tilde,

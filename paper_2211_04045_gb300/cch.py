@@ -94,6 +94,8 @@ def lib():
             L.cch_status_string.argtypes = [C.c_int]
             L.cch_create_scene.argtypes = [C.POINTER(Topology), C.POINTER(Params), p, C.POINTER(p)]
             L.cch_create_batch.argtypes = [C.POINTER(Topology), i32, C.POINTER(Params), p, C.POINTER(p)]
+            L.cch_create_batch_params.argtypes = [C.POINTER(Topology), i32, C.POINTER(Params), C.POINTER(Params), p,
+                                                  C.POINTER(p)]
             L.cch_handle_step.argtypes = [p, p, p, p, C.POINTER(StepStats)]
             L.cch_handle_step_host.argtypes = [p, p, p, p, C.POINTER(StepStats)]
             L.cch_batch_handle_step.argtypes = [p, C.POINTER(p), C.POINTER(p), C.POINTER(p), C.POINTER(StepStats)]
@@ -101,6 +103,7 @@ def lib():
             L.cch_query_pairs.argtypes = [p, p, p, d, i32, p, p, i64, C.POINTER(i64)]
             L.cch_server_create.argtypes = [C.c_size_t, C.POINTER(Params), i32, p, C.POINTER(p)]
             L.cch_server_add_scene.argtypes = [p, C.POINTER(Topology), C.POINTER(i32)]
+            L.cch_server_add_scene_params.argtypes = [p, C.POINTER(Topology), C.POINTER(Params), C.POINTER(i32)]
             L.cch_server_submit.argtypes = [p, i32, p, p, p, C.POINTER(C.c_uint64)]
             L.cch_server_wait.argtypes = [p, C.c_uint64, C.POINTER(StepStats), C.POINTER(d)]
             L.cch_server_destroy.argtypes = [p]
@@ -111,7 +114,8 @@ def lib():
             L.cch_set_max_polls.argtypes = [p, i32]
             L.cch_normal_flow_target.argtypes = [p, p, d, d, d, i32, p]
             L.cch_friction_filter.argtypes = [p, p, p, p, d, d, d]
-            for f in ("cch_params_default", "cch_create_scene", "cch_create_batch", "cch_handle_step",
+            for f in ("cch_params_default", "cch_create_scene", "cch_create_batch", "cch_create_batch_params",
+                      "cch_server_add_scene_params", "cch_handle_step",
                       "cch_handle_step_host", "cch_batch_handle_step", "cch_destroy", "cch_query_pairs",
                       "cch_server_create", "cch_server_add_scene", "cch_server_submit", "cch_server_wait",
                       "cch_server_destroy", "cch_set_profiling", "cch_get_profile", "cch_query_pairs_noalloc",
@@ -182,7 +186,10 @@ def _dev_ptr(t, n):
 class Scene:
     """A resident scene (or a batch of scenes) on the current CUDA device."""
 
-    def __init__(self, scenes, prm: Optional[Params] = None, stream=None):
+    def __init__(self, scenes, prm: Optional[Params] = None, stream=None, scene_params=None):
+        """scene_params: optional per-scene Params whose physical fields (d_min,
+        d_max, delta, sigma, gamma, eps, max_iters, seed) replace prm's for
+        that scene (cch_create_batch_params)."""
         single = not isinstance(scenes, (list, tuple))
         self.single = single
         self._scenes = [scenes] if single else list(scenes)
@@ -191,8 +198,15 @@ class Scene:
         self.stream = _stream_ptr(stream)
         arr = (Topology * len(self.topos))(*[t.c for t in self.topos])
         h = C.c_void_p()
-        _check(lib().cch_create_batch(arr, len(self.topos), C.byref(self.prm), C.c_void_p(self.stream), C.byref(h)),
-               "cch_create_batch")
+        if scene_params is None:
+            _check(lib().cch_create_batch(arr, len(self.topos), C.byref(self.prm), C.c_void_p(self.stream),
+                                          C.byref(h)), "cch_create_batch")
+        else:
+            if len(scene_params) != len(self.topos):
+                raise ValueError("one Params per scene")
+            sp = (Params * len(self.topos))(*scene_params)
+            _check(lib().cch_create_batch_params(arr, len(self.topos), C.byref(self.prm), sp,
+                                                 C.c_void_p(self.stream), C.byref(h)), "cch_create_batch_params")
         self.h = h
 
     @property
@@ -351,10 +365,16 @@ class Server:
         self.n = []
         self._keep = {}
 
-    def add_scene(self, scene) -> int:
+    def add_scene(self, scene, prm: Optional[Params] = None) -> int:
+        """Make a scene resident; prm: its own physical parameters (see
+        Scene's scene_params), else the server's."""
         t = _Topo(scene)
         sid = C.c_int32(-1)
-        _check(lib().cch_server_add_scene(self.h, C.byref(t.c), C.byref(sid)), "cch_server_add_scene")
+        if prm is None:
+            _check(lib().cch_server_add_scene(self.h, C.byref(t.c), C.byref(sid)), "cch_server_add_scene")
+        else:
+            _check(lib().cch_server_add_scene_params(self.h, C.byref(t.c), C.byref(prm), C.byref(sid)),
+                   "cch_server_add_scene_params")
         self.n.append(t.n)
         return sid.value
 

@@ -222,7 +222,8 @@ cudaError_t upload(Runtime& R, T** dst, const std::vector<T>& src) {
   return e;
 }
 
-cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, const cch_params* prm, void* stream) {
+cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, const cch_params* prm,
+                      const cch_params* scene_prm, void* stream) {
   Runtime& R = S->R;
   Pool& P = R.pool;
   R.stream = (cudaStream_t)stream;
@@ -243,12 +244,14 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
     d.l0 = nl; d.nl = (int)t.n_len;
     d.q0 = nq; d.nq = (int)t.n_points;
     d.c0 = (int)vc.size();
-    d.d_min = prm->d_min; d.d_max = prm->d_max; d.delta = prm->delta; d.sigma = prm->sigma;
-    d.hgamma = 0.5 * prm->gamma; d.eps = prm->eps; d.omega = prm->jacobi_omega;
+    // the scene's physical parameters (its own when given), the pool's method
+    const cch_params* q = scene_prm ? &scene_prm[s] : prm;
+    d.d_min = q->d_min; d.d_max = q->d_max; d.delta = q->delta; d.sigma = q->sigma;
+    d.hgamma = 0.5 * q->gamma; d.eps = q->eps; d.omega = prm->jacobi_omega;
     d.form = prm->constraint_form;
-    d.max_iters = prm->max_iters; d.gs_sweeps = prm->gs_sweeps; d.solver = prm->solver; d.ccd = prm->ccd_check;
+    d.max_iters = q->max_iters; d.gs_sweeps = prm->gs_sweeps; d.solver = prm->solver; d.ccd = prm->ccd_check;
     d.step_rule = prm->step_rule;
-    d.seed = prm->seed;
+    d.seed = q->seed;
     d.rho_max = 0.0;
     if (t.point_radius)
       for (int64_t v = 0; v < t.n_verts; v++)
@@ -276,7 +279,7 @@ cch_status build_pool(cch_scene* S, const cch_topology* topos, int n_scenes, con
     nv += (int)t.n_verts; nt += (int)t.n_tris; ne += (int)t.n_edges; nl += (int)t.n_len; nq += (int)t.n_points;
     R.sd.push_back(d);
     S->nverts.push_back(t.n_verts);
-    if (prm->max_iters > R.max_iters) R.max_iters = prm->max_iters;
+    if (q->max_iters > R.max_iters) R.max_iters = q->max_iters;
   }
   P.nv = nv; P.nt = nt; P.ne = ne; P.nl = nl; P.nq = nq; P.nvc = (int)vc.size(); P.nscene = n_scenes;
   R.scene_bits = 0;
@@ -720,7 +723,8 @@ const char* cch_status_string(cch_status s) {
   return "unknown status";
 }
 
-cch_status cch_create_batch(const cch_topology* topos, int32_t n_scenes, const cch_params* prm, void* stream,
+cch_status cch_create_batch_params(const cch_topology* topos, int32_t n_scenes, const cch_params* prm,
+                                   const cch_params* scene_prm, void* stream,
                             cch_scene** out) {
   if (!out || !topos || n_scenes <= 0 || n_scenes > (1 << 20)) return CCH_E_INVALID_ARG;
   *out = nullptr;
@@ -731,10 +735,11 @@ cch_status cch_create_batch(const cch_topology* topos, int32_t n_scenes, const c
     v = validate_topology(&topos[s]);
     if (v != CCH_OK) return v;
     tot += topos[s].n_verts;
+    if (scene_prm && (v = validate_params(&scene_prm[s])) != CCH_OK) return v;
   }
   if (tot >= (1LL << 30)) return CCH_E_INVALID_ARG;
   cch_scene* S = new cch_scene();
-  cch_status r = build_pool(S, topos, n_scenes, prm, stream);
+  cch_status r = build_pool(S, topos, n_scenes, prm, scene_prm, stream);
   if (r != CCH_OK) {
     free_all(S->R);
     delete S;
@@ -742,6 +747,11 @@ cch_status cch_create_batch(const cch_topology* topos, int32_t n_scenes, const c
   }
   *out = S;
   return CCH_OK;
+}
+
+cch_status cch_create_batch(const cch_topology* topos, int32_t n_scenes, const cch_params* prm, void* stream,
+                            cch_scene** out) {
+  return cch_create_batch_params(topos, n_scenes, prm, nullptr, stream, out);
 }
 
 cch_status cch_create_scene(const cch_topology* topo, const cch_params* prm, void* stream, cch_scene** out) {
@@ -1202,6 +1212,7 @@ struct cch_server {
   int max_active = 1;
   cudaStream_t stream = nullptr;
   std::vector<OwnedTopo> topos;
+  std::vector<cch_params> sprm;   // per resident scene: its parameters
   cch_scene* pool = nullptr;      // built from every resident scene
   int pool_scenes = 0;            // scenes the pool was built with
   std::mutex mu;
@@ -1236,7 +1247,7 @@ void server_loop(cch_server* sv) {
       int ns = (int)views.size();
       lk.unlock();
       cch_scene* p = nullptr;
-      cch_status st = cch_create_batch(views.data(), ns, &sv->prm, sv->stream, &p);
+      cch_status st = cch_create_batch_params(views.data(), ns, &sv->prm, sv->sprm.data(), sv->stream, &p);
       lk.lock();
       if (st != CCH_OK) {
         sv->fatal = st;
@@ -1389,9 +1400,16 @@ cch_status cch_server_create(size_t hbm_budget_bytes, const cch_params* prm, int
 }
 
 cch_status cch_server_add_scene(cch_server* sv, const cch_topology* topo, int32_t* scene_id) {
-  if (!sv || !scene_id) return CCH_E_INVALID_ARG;
+  if (!sv) return CCH_E_INVALID_ARG;
+  return cch_server_add_scene_params(sv, topo, &sv->prm, scene_id);
+}
+
+cch_status cch_server_add_scene_params(cch_server* sv, const cch_topology* topo, const cch_params* scene_prm,
+                                       int32_t* scene_id) {
+  if (!sv || !scene_id || !scene_prm) return CCH_E_INVALID_ARG;
   cch_status v = validate_topology(topo);
   if (v != CCH_OK) return v;
+  if ((v = validate_params(scene_prm)) != CCH_OK) return v;
   size_t need = scene_bytes(*topo);
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->used + need > sv->budget) return CCH_E_BUDGET;
@@ -1403,6 +1421,7 @@ cch_status cch_server_add_scene(cch_server* sv, const cch_topology* topo, int32_
   t.len_edges.assign(topo->len_edges, topo->len_edges + 2 * topo->n_len);
   t.points.assign(topo->points, topo->points + topo->n_points);
   sv->topos.push_back(std::move(t));
+  sv->sprm.push_back(*scene_prm);
   sv->used += need;
   *scene_id = (int32_t)sv->topos.size() - 1;
   sv->cv_work.notify_all();
