@@ -354,40 +354,54 @@ __device__ __forceinline__ void add_candidates(Pool& P, int s, long long n) {
 // ---------------------------------------------------------------------------
 // Packet traversal for the step's searches.  The 32 lanes of a warp take 32
 // consecutive queries in Morton order (close in space) and descend the tree
-// together: a node is entered when the box of any lane is near it, and every
-// lane keeps its own tests, so each lane reaches exactly the leaves that its
-// own traversal would.  The node loads are shared and the box tests run on
-// all lanes at once (a thread-per-query traversal kept ~5 of 32 lanes busy).
-// The stack lives in shared memory, one per warp; lanes of different scenes
-// descend in turn, each from its scene's root.
+// together as a wavefront: every stack entry is a node and the mask of the
+// queries whose traversal reaches it.  Each step pops up to 32 entries, one
+// per lane; a lane loads its node's two child boxes and tests them against
+// each query of its mask, so a child is reached by exactly the queries whose
+// own traversal would reach it (box test and, for the edge-edge search, the
+// later-leaves rule applied per query).  A step thus has up to 32 node loads
+// in flight instead of one, and the number of steps is about the depth of
+// the traversed region rather than its node count.  Lanes of different
+// scenes descend in turn, each from its scene's root.
 // ---------------------------------------------------------------------------
-constexpr int PACKET_STACK = 64;
+constexpr int WAVE_STACK = 512;    // entries per warp: (node, query mask)
+constexpr int WAVE_RESERVE = 128;  // kept free for depth-first steps (deeper than any tree here)
 
-// Leaf work runs from a per-warp queue: a lane that reaches a leaf first runs
-// the cheap checks (pre), and the pairs that pass are queued; whenever 32 are
-// queued, the whole warp evaluates them at once (work), each lane fetching
-// its entry's query data from the lane that queued it.  The distance bounds
-// thus run with all lanes busy instead of on the few lanes at a leaf.
-constexpr int PACKET_QUEUE = 96;  // a node adds at most 64 entries to at most 31 pending
+// a query of the wavefront: its box, D (lo.w) and the last sorted leaf
+// position it skips (hi.w, as int bits; -1: none)
+struct WaveQuery {
+  float4 lo, hi;
+};
 
+// Leaf work runs from a per-warp queue: a (query, leaf) pair reached by the
+// traversal first passes the cheap checks (pre), and the pairs that pass are
+// queued; whenever 32 are queued, the whole warp evaluates them at once
+// (work), each lane fetching its entry's query data from the query's lane.
+// The distance bounds thus run with all lanes busy.
+constexpr int PACKET_QUEUE = 96;  // at most 31 pending plus 32 per round
+
+// pre(valid, q, leaf) and work(valid, q, leaf) are called by all 32 lanes
+// together (they may shuffle query data from lane q); valid marks the lanes
+// that hold a pair.  Returns the warp's number of pairs that passed pre.
 template <class PreFn, class WorkFn>
-__device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, float3 qlo, float3 qhi, float Df,
-                                              int min_pos, int* stack, int* qlane, int* qleaf, Counters* cnt,
-                                              PreFn pre, WorkFn work) {
+__device__ __forceinline__ long long traverse_wave(const BVH& B, int root, bool act, float3 qlo, float3 qhi, float Df,
+                                                   int min_pos, WaveQuery* qs, int2* stack, int* qlane, int* qleaf,
+                                                   Counters* cnt, PreFn pre, WorkFn work) {
   const unsigned FULL = 0xffffffffu;
   int lane = threadIdx.x & 31;
-  if (root < 0) return;
+  if (root < 0) return 0;
   int qn = 0;  // identical in every lane
-  auto enqueue = [&](bool hit, int l) {
-    bool want = hit && pre(l);
+  long long passed = 0;
+  auto enqueue = [&](bool want, int q, int l) {
     unsigned m = __ballot_sync(FULL, want);
     if (!m) return;
     if (want) {
       int at = qn + __popc(m & ((1u << lane) - 1u));
-      qlane[at] = lane;
+      qlane[at] = q;
       qleaf[at] = l;
     }
     qn += __popc(m);
+    passed += want;
     __syncwarp();
   };
   auto drain = [&](bool all) {
@@ -410,67 +424,103 @@ __device__ __forceinline__ void traverse_warp(const BVH& B, int root, bool act, 
     qn = rest > 0 ? rest : 0;
     __syncwarp();
   };
-  if (root & LEAF) {
+  auto reduce = [&](long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+  };
+  if (root & LEAF) {  // a scene of one primitive: each lane tests the leaf itself
     int l = root & ~LEAF;
     bool hit = false;
     if (act && l > min_pos) {
       float4 lo = B.leafbox[2 * l], hi = B.leafbox[2 * l + 1];
       hit = fbox_near(lo, hi, qlo, qhi, Df);
     }
-    enqueue(hit, l);
+    enqueue(hit && pre(hit, lane, l), lane, l);
     drain(true);
-    return;
+    return reduce(passed);
   }
+  qs[lane].lo = make_float4(qlo.x, qlo.y, qlo.z, Df);
+  qs[lane].hi = make_float4(qhi.x, qhi.y, qhi.z, __int_as_float(min_pos));
+  unsigned amask = __ballot_sync(FULL, act);
   __syncwarp();
-  if (lane == 0) stack[0] = root;
+  if (!amask) return 0;
+  if (lane == 0) stack[0] = make_int2(root, (int)amask);
   int sp = 1;  // identical in every lane
   int budget = B.n + 2;
   __syncwarp();
   while (sp > 0) {
-    if (--budget < 0) {
-      if (lane == 0) atomicOr(&cnt->err, ERR_BUDGET);
+    // A popped entry pushes at most two, so popping k grows the stack by at
+    // most k: up to WAVE_STACK - WAVE_RESERVE entries the warp pops up to 32
+    // at once, beyond that one at a time (depth first, growing the stack by
+    // at most the depth of the subtree under way before it shrinks again).
+    int room = WAVE_STACK - WAVE_RESERVE - sp;
+    int k = room > 0 ? min(min(sp, 32), room) : (sp < WAVE_STACK ? 1 : 0);
+    if (k <= 0 || (budget -= k) < 0) {
+      if (lane == 0) atomicOr(&cnt->err, k <= 0 ? ERR_STACK : ERR_BUDGET);
       break;
     }
-    int node = stack[--sp];
+    int2 ent = lane < k ? stack[sp - k + lane] : make_int2(0, 0);
+    sp -= k;
     __syncwarp();
-    bool ok = act && B.range_hi[node] > min_pos;
-    float4 a = B.box[3 * node], b = B.box[3 * node + 1], d = B.box[3 * node + 2];
-    float4 llo = make_float4(a.x, a.y, a.z, 0.f), lhi = make_float4(a.w, b.x, b.y, 0.f);
-    float4 rlo = make_float4(b.z, b.w, d.x, 0.f), rhi = make_float4(d.y, d.z, d.w, 0.f);
-    int L = B.left[node], R = B.right[node];
-    bool hr = ok && fbox_near(rlo, rhi, qlo, qhi, Df) && (!(R & LEAF) || (R & ~LEAF) > min_pos);
-    bool hl = ok && fbox_near(llo, lhi, qlo, qhi, Df) && (!(L & LEAF) || (L & ~LEAF) > min_pos);
-    unsigned mr = __ballot_sync(FULL, hr), ml = __ballot_sync(FULL, hl);
-    if (mr) {
-      if (R & LEAF) {
-        enqueue(hr, R & ~LEAF);
-      } else if (sp < PACKET_STACK) {
-        if (lane == 0) stack[sp] = R;
-        sp++;
-      } else if (lane == 0) {
-        atomicOr(&cnt->err, ERR_STACK);
+    unsigned ml = 0u, mr = 0u;
+    int L = 0, R = 0;
+    if (lane < k) {
+      int node = ent.x;
+      unsigned m = (unsigned)ent.y;
+      float4 a = B.box[3 * node], b = B.box[3 * node + 1], d = B.box[3 * node + 2];
+      float4 llo = make_float4(a.x, a.y, a.z, 0.f), lhi = make_float4(a.w, b.x, b.y, 0.f);
+      float4 rlo = make_float4(b.z, b.w, d.x, 0.f), rhi = make_float4(d.y, d.z, d.w, 0.f);
+      L = B.left[node];
+      R = B.right[node];
+      int rh = B.range_hi[node];
+      while (m) {
+        int q = __ffs(m) - 1;
+        m &= m - 1u;
+        WaveQuery Q = qs[q];
+        int qmin = __float_as_int(Q.hi.w);
+        if (!(rh > qmin)) continue;
+        float3 lo3 = make_float3(Q.lo.x, Q.lo.y, Q.lo.z), hi3 = make_float3(Q.hi.x, Q.hi.y, Q.hi.z);
+        if (fbox_near(rlo, rhi, lo3, hi3, Q.lo.w) && (!(R & LEAF) || (R & ~LEAF) > qmin)) mr |= 1u << q;
+        if (fbox_near(llo, lhi, lo3, hi3, Q.lo.w) && (!(L & LEAF) || (L & ~LEAF) > qmin)) ml |= 1u << q;
       }
     }
-    if (ml) {
-      if (L & LEAF) {
-        enqueue(hl, L & ~LEAF);
-      } else if (sp < PACKET_STACK) {
-        if (lane == 0) stack[sp] = L;
-        sp++;
-      } else if (lane == 0) {
-        atomicOr(&cnt->err, ERR_STACK);
+    // inner children with queries go on the stack
+    bool pr = mr && !(R & LEAF), pl = ml && !(L & LEAF);
+    unsigned br = __ballot_sync(FULL, pr), bl = __ballot_sync(FULL, pl);
+    unsigned lt = (1u << lane) - 1u;
+    int at = sp + __popc(br & lt) + __popc(bl & lt);
+    if (pr) stack[at] = make_int2(R, (int)mr);
+    if (pl) stack[at + (pr ? 1 : 0)] = make_int2(L, (int)ml);
+    sp += __popc(br) + __popc(bl);
+    // leaf children: one (query, leaf) pair per lane and round
+    unsigned lr = (R & LEAF) ? mr : 0u, ll = (L & LEAF) ? ml : 0u;
+    while (__any_sync(FULL, lr | ll)) {
+      int q = -1, l = 0;
+      if (lr) {
+        q = __ffs(lr) - 1;
+        lr &= lr - 1u;
+        l = R & ~LEAF;
+      } else if (ll) {
+        q = __ffs(ll) - 1;
+        ll &= ll - 1u;
+        l = L & ~LEAF;
       }
+      bool v = q >= 0;
+      bool want = pre(v, v ? q : 0, l) && v;
+      enqueue(want, q, l);
+      if (qn >= 32) drain(false);
     }
-    if (qn >= 32) drain(false);
     __syncwarp();
   }
   drain(true);
+  return reduce(passed);
 }
 
 // vertex-triangle pairs of the step's searches, queries in the Morton order
 // of the collision vertices
 __global__ void __launch_bounds__(256) k_pquery_vt(Pool P) {
-  __shared__ int stacks[8][PACKET_STACK];
+  __shared__ int2 stacks[8][WAVE_STACK];
+  __shared__ WaveQuery wq[8][32];
   __shared__ int qlanes[8][PACKET_QUEUE], qleaves[8][PACKET_QUEUE];
   if (!P.cnt->any_search) return;
   const unsigned FULL = 0xffffffffu;
@@ -494,19 +544,21 @@ __global__ void __launch_bounds__(256) k_pquery_vt(Pool P) {
     float raf = __double2float_ru(ra);  // rounded up: the bound stays below the distance
     fv3 fa = a >= 0 ? fk(P.xf[a]) : fv3{0.f, 0.f, 0.f};
     bool sa = a >= 0 && is_static(P, a);
-    long long ncand = 0;
     while (__any_sync(FULL, pend)) {
       int leader = __ffs(__ballot_sync(FULL, pend)) - 1;
       int sc = __shfl_sync(FULL, s, leader);
       bool mine = pend && s == sc;
       const SceneDesc& S = P.sd[sc];
-      traverse_warp(P.bt, P.bt.sroot[sc], mine, qlo, qhi, Df, -1, stacks[warp], qlanes[warp], qleaves[warp], P.cnt,
-        [&](int pos) {
+      long long nc = traverse_wave(P.bt, P.bt.sroot[sc], mine, qlo, qhi, Df, -1, wq[warp], stacks[warp],
+                                   qlanes[warp], qleaves[warp], P.cnt,
+        [&](bool valid, int q, int pos) {
+          // the query's vertex; a triangle at it or a static pair is skipped
+          int qa = __shfl_sync(FULL, a, q);
+          bool qs = __shfl_sync(FULL, sa, q);
+          if (!valid) return false;
           int4 tv = P.tv[P.bt.ids[pos]];
-          if (a == tv.x || a == tv.y || a == tv.z) return false;
-          if (sa && is_static(P, tv.x) && is_static(P, tv.y) && is_static(P, tv.z)) return false;
-          ncand++;
-          return true;
+          if (qa == tv.x || qa == tv.y || qa == tv.z) return false;
+          return !(qs && is_static(P, tv.x) && is_static(P, tv.y) && is_static(P, tv.z));
         },
         [&](bool valid, int src, int pos) {
           // the queuing lane's query: the vertex, its float position and radius bound, D
@@ -522,16 +574,17 @@ __global__ void __launch_bounds__(256) k_pquery_vt(Pool P) {
           if (lower >= qD) return;
           push_survivor(P, K_VT, mkkey(K_VT, qa - S.v0, t - S.t0), make_int4(qa, tv.x, tv.y, tv.z), lower);
         });
+      if (lane == 0 && nc) atomicAdd((unsigned long long*)&P.ss[sc].candidates, (unsigned long long)nc);
       if (mine) pend = false;
     }
-    if (s >= 0 && ncand) add_candidates(P, s, ncand);
   }
 }
 
 // edge-edge pairs of the step's searches: each edge (at sorted leaf position
 // i) against the later leaves of its scene
 __global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
-  __shared__ int stacks[8][PACKET_STACK];
+  __shared__ int2 stacks[8][WAVE_STACK];
+  __shared__ WaveQuery wq[8][32];
   __shared__ int qlanes[8][PACKET_QUEUE], qleaves[8][PACKET_QUEUE];
   if (!P.cnt->any_search) return;
   const unsigned FULL = 0xffffffffu;
@@ -557,19 +610,21 @@ __global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
     float3 qlo = f3rd(alo), qhi = f3ru(ahi);
     float Df = s >= 0 ? __double2float_ru(P.sd[s].d_max) : 0.f;
     bool sa = e1 >= 0 && is_static(P, ea.x) && is_static(P, ea.y);
-    long long ncand = 0;
     while (__any_sync(FULL, pend)) {
       int leader = __ffs(__ballot_sync(FULL, pend)) - 1;
       int sc = __shfl_sync(FULL, s, leader);
       bool mine = pend && s == sc;
       const SceneDesc& S = P.sd[sc];
-      traverse_warp(B, B.sroot[sc], mine, qlo, qhi, Df, i, stacks[warp], qlanes[warp], qleaves[warp], P.cnt,
-        [&](int pos) {
+      long long nc = traverse_wave(B, B.sroot[sc], mine, qlo, qhi, Df, i, wq[warp], stacks[warp], qlanes[warp],
+                                   qleaves[warp], P.cnt,
+        [&](bool valid, int q, int pos) {
+          // the query edge; an edge sharing a vertex with it or a static pair is skipped
+          int qx = __shfl_sync(FULL, ea.x, q), qy = __shfl_sync(FULL, ea.y, q);
+          bool qs = __shfl_sync(FULL, sa, q);
+          if (!valid) return false;
           int4 eb = P.ev[B.ids[pos]];
-          if (ea.x == eb.x || ea.x == eb.y || ea.y == eb.x || ea.y == eb.y) return false;
-          if (sa && is_static(P, eb.x) && is_static(P, eb.y)) return false;
-          ncand++;
-          return true;
+          if (qx == eb.x || qx == eb.y || qy == eb.x || qy == eb.y) return false;
+          return !(qs && is_static(P, eb.x) && is_static(P, eb.y));
         },
         [&](bool valid, int src, int pos) {
           // the queuing lane's query edge and D
@@ -588,9 +643,9 @@ __global__ void __launch_bounds__(256) k_pquery_ee(Pool P) {
           push_survivor(P, K_EE, mkkey(K_EE, min(q1, e2) - S.e0, max(q1, e2) - S.e0),
                         make_int4(A.x, A.y, Bv.x, Bv.y), lower);
         });
+      if (lane == 0 && nc) atomicAdd((unsigned long long*)&P.ss[sc].candidates, (unsigned long long)nc);
       if (mine) pend = false;
     }
-    if (s >= 0 && ncand) add_candidates(P, s, ncand);
   }
 }
 
