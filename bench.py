@@ -244,7 +244,7 @@ def smooth_displacement(sc, rng):
     return d * (sc.inv_mass > 0)[:, None]
 
 
-def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=("mixed", "fp64")):
+def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=("mixed", "fp64"), group: int = 8):
     """Poisson request stream served with continuous batching, against the
     same requests run one at a time in plain FP64 (each on its own resident
     scene).  Returns the comparison as a dict."""
@@ -269,7 +269,7 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
     # plain: one request at a time, FP64, one resident scene per kind
     # every scene with its own physical parameters (Table 2 values, or the
     # scene's: the tubes take delta = 0.5 mm)
-    plain = [cch.Scene(sc, cch.params_for(sc, iters_per_launch=8)) for sc in scs]
+    plain = [cch.Scene(sc, cch.params_for(sc, iters_per_launch=group)) for sc in scs]
     for g, sc in zip(plain, scs):  # warm-up: builds and graph capture
         x, xt, _ = scenes.initial(sc)
         g.step(torch.tensor(x, device=dev), torch.tensor(xt, device=dev))
@@ -293,7 +293,7 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
                                         "max_iterations": int(np.max(plain_it[which == k])) if np.any(which == k) else None}
                                        for k in range(len(scs))]}
     for prec in precisions:
-        prm = cch.params_for(scs[0], precision=1 if prec == "mixed" else 0, iters_per_launch=8)
+        prm = cch.params_for(scs[0], precision=1 if prec == "mixed" else 0, iters_per_launch=group)
         sv = cch.Server(80 << 30, prm, max_active=max_active)
         ids = [sv.add_scene(sc, cch.params_for(sc)) for sc in scs]
         for k, sc in enumerate(scs):  # one warm request per scene (pool build, graph capture)
@@ -328,7 +328,8 @@ def run_serving(args):
     """The serving workload on its own: one JSON line."""
     import torch
     dev = torch.device("cuda:0")
-    r = serve_compare(dev, args.requests, args.rate, args.max_active, precisions=(args.precision,))
+    r = serve_compare(dev, args.requests, args.rate, args.max_active, precisions=(args.precision,),
+                      group=args.serve_group)
     srv = r[f"served_{args.precision}"]
     out = {"metric": METRIC, "value": srv["value"], "unit": "steps/s", "n_gpus": 1, "steps": args.requests,
            "warmup": len(r["scene_prims"]), "ms_per_step": 1000.0 / srv["value"], "higher_is_better": True,
@@ -540,6 +541,7 @@ def main():
     ap.add_argument("--requests", type=int, default=None, help="serving: requests in the stream (512)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving: requests batched at once")
+    ap.add_argument("--serve-group", type=int, default=8, help="serving: iterations per graph launch (both arms)")
     ap.add_argument("--ncu-warm", type=int, default=0, help="full chain steps before the --ncu-case step")
     ap.add_argument("--ncu-case", type=int, default=0,
                     help="profiling aid: run one step of the workload capped at this many iterations and exit "
@@ -751,7 +753,8 @@ def main():
             compare["batched"] = batch_compare(dev, stream, args.batch_scenes, 2, flush)
             log(f"batched: {compare['batched']}")
         if args.requests:
-            compare["served"] = serve_compare(dev, args.requests, args.rate, args.max_active, precisions=("mixed",))
+            compare["served"] = serve_compare(dev, args.requests, args.rate, args.max_active, precisions=("mixed",),
+                                              group=args.serve_group)
             log(f"served: {compare['served']}")
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
