@@ -274,22 +274,32 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
         x, xt, _ = scenes.initial(sc)
         g.step(torch.tensor(x, device=dev), torch.tensor(xt, device=dev))
     torch.cuda.synchronize()
+    # the same Poisson stream served one request at a time, in arrival order:
+    # a request waits for its arrival and for the one before it; latency runs
+    # from arrival to completion, as for the served requests
     t0 = time.perf_counter()
-    plain_ms, plain_out, plain_it = [], [], []
+    plain_lat, plain_svc, plain_out, plain_it = [], [], [], []
     for i in range(N):
+        delay = arrivals[i] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
         a = time.perf_counter()
         o, st = plain[which[i]].step(inputs[i][0], inputs[i][1])
-        plain_ms.append(1000.0 * (time.perf_counter() - a))
+        b = time.perf_counter()
+        plain_svc.append(1000.0 * (b - a))
+        plain_lat.append(1000.0 * (b - t0 - arrivals[i]))
         plain_out.append(o)
         plain_it.append(st["iterations"])
     plain_s = time.perf_counter() - t0
     for g in plain:
         g.close()
-    plain_ms, plain_it = np.array(plain_ms), np.array(plain_it)
-    out["plain_fp64"] = {"value": N / plain_s, "unit": "steps/s", "p50_ms": float(np.percentile(plain_ms, 50)),
-                         "p99_ms": float(np.percentile(plain_ms, 99)),
+    plain_svc, plain_it = np.array(plain_svc), np.array(plain_it)
+    plain_cap = N / (float(np.sum(plain_svc)) / 1000.0)
+    out["plain_fp64"] = {"value": N / plain_s, "unit": "steps/s", "p50_ms": float(np.percentile(plain_lat, 50)),
+                         "p99_ms": float(np.percentile(plain_lat, 99)), "capacity": plain_cap,
+                         "service_p50_ms": float(np.percentile(plain_svc, 50)),
                          "per_scene": [{"requests": int(np.sum(which == k)),
-                                        "mean_ms": round(float(np.mean(plain_ms[which == k])), 2) if np.any(which == k) else None,
+                                        "mean_ms": round(float(np.mean(plain_svc[which == k])), 2) if np.any(which == k) else None,
                                         "max_iterations": int(np.max(plain_it[which == k])) if np.any(which == k) else None}
                                        for k in range(len(scs))]}
     for prec in precisions:
@@ -314,11 +324,18 @@ def serve_compare(dev, requests: int, rate: float, max_active: int, precisions=(
             lat.append(ms)
             iters.append(st["iterations"])
         served_s = time.perf_counter() - t0
-        sv.close()
         # FP64 served results equal the plain ones bitwise; mixed: max deviation
         dev_max = max(float((o - p).abs().max().item()) for o, p in zip(outs, plain_out))
+        # capacity: the whole stream submitted at once
+        t0 = time.perf_counter()
+        tickets = [sv.submit(ids[which[i]], inputs[i][0], inputs[i][1], outs[i]) for i in range(N)]
+        for tk in tickets:
+            sv.wait(tk)
+        cap = N / (time.perf_counter() - t0)
+        sv.close()
         out[f"served_{prec}"] = {"value": N / served_s, "unit": "steps/s", "p50_ms": float(np.percentile(lat, 50)),
                                  "p99_ms": float(np.percentile(lat, 99)), "speedup_vs_plain": plain_s / served_s,
+                                 "capacity": cap, "capacity_vs_plain": cap / plain_cap,
                                  "iterations_per_step": float(np.mean(iters)),
                                  "max_abs_diff_vs_plain_m": dev_max}
     return out
