@@ -1442,7 +1442,9 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
     /* forward step, Eq. forward2 (R2).  The CCD-based rule (Sec. 5.1's
      * comparison scheme) caps every vertex by the global bound D^(l) instead
      * of its own D_i and lets the CCD below decide the step: a pair outside P
-     * is at least D^(l) apart and its two sides close at most 0.9 D^(l) */
+     * is at least D^(l) apart and its two sides close at most 0.9 D^(l).  A
+     * vertex whose own D_i is below the floor (R2b) stays under either rule:
+     * at that distance the CCD's roots are rounding noise */
     const int ccd_rule = prm->step_rule == 1;
     double Dcap = D;
     if (!(Dcap >= ORC_D_FLOOR)) Dcap = 0.0;
@@ -1451,7 +1453,7 @@ int orc_handle_step(const orc_topology* t, const orc_params* prm, const double* 
       v3 xv = ld3(x, v), yv = ld3(y, v);
       v3 dx = sub3(yv, xv);
       double nd = norm3(dx), a = 1.0;
-      double bound = ccd_rule ? Dcap : Di[v];
+      double bound = ccd_rule ? (Di[v] == 0.0 ? 0.0 : Dcap) : Di[v];
       if (nd > 0.0) {
         double q = (hg * bound) / nd;
         a = q < 1.0 ? q : 1.0;

@@ -1578,16 +1578,19 @@ __global__ void k_forward(Pool P) {
     int s = P.vscene[v];
     const SceneState& S = P.ss[s];
     if (!S.active || S.done) continue;
-    // CCD-based rule: the global bound D^(l) caps every vertex, the CCD
-    // rounds decide the rest
+    // CCD-based rule: the global bound D^(l) caps every vertex that is not
+    // floored, the CCD rounds decide the rest
     unsigned long long dvb = P.Dv[v];
     if (dvb != 0x7ff0000000000000ULL) {
       // a vertex of a pair of P (statistics)
       scene_count(P, s, [&](int n) { atomicAdd((unsigned long long*)&P.ss[s].pverts, (unsigned long long)n); });
     }
-    double Di = P.sd[s].step_rule ? S.D : bitsd(dvb);
-    if (S.D < Di) Di = S.D;
-    bool floored = !(Di >= D_FLOOR);
+    // the vertex's own D_i; below the floor (R2b) the vertex does not move,
+    // under either rule
+    double own = bitsd(dvb);
+    if (S.D < own) own = S.D;
+    double Di = P.sd[s].step_rule ? S.D : own;
+    bool floored = !(Di >= D_FLOOR) || !(own >= D_FLOOR);
     if (floored) Di = 0.0;
     P.Dv[v] = 0x7ff0000000000000ULL;
     P4 xv4 = P.x[v];

@@ -143,3 +143,25 @@ def test_distance_rule_segments_certified_apart(case):
             assert not oracle.ccd_conservative(kind, xl[vs], xl1[vs], rho, tol=0.05 * d), (name, l, k, d)
             checked += 1
     assert checked > 100
+
+
+def test_floor_keeps_collapsed_pairs_still_under_the_ccd_rule():
+    # a 32 x 32 cloth falling onto a subdivision-3 sphere, three chain steps of
+    # 2,049 iterations under the CCD-based rule: the rule collapses some pairs
+    # to about 1e-17 m, where the root-finding CCD no longer sees a crossing;
+    # with the R2b floor on each vertex's own D_i those vertices stay, and
+    # every step ends intersection-free under the exact test
+    torch = pytest.importorskip("torch")
+    sc = scenes.cloth_over_sphere(n=32)
+    osc = oracle.OracleScene(sc)
+    prm = oracle.params_for(sc, step_rule=1)
+    dyn = scenes.TorchDynamics(sc, "cpu")
+    x, xt, _ = scenes.initial(sc)
+    frozen = 0
+    for _ in range(3):
+        xn, st, _ = oracle.handle_step(osc, prm, x, xt)
+        assert oracle.count_intersections(osc, xn) == 0
+        frozen += st["frozen_vertices"]
+        v = dyn.next_velocity(torch.tensor(xn), torch.tensor(x)).numpy()
+        x, xt = xn, dyn.predict(torch.tensor(xn), torch.tensor(v)).numpy()
+    assert frozen > 0  # the floor did hold vertices
