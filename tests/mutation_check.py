@@ -62,7 +62,8 @@ M = [
     ("colouring without classes (priority order only)", "  qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_colour);", "  qsort(cc, (size_t)nc, sizeof(cons), cmp_cons_prio_desc);"),
     ("contact multipliers kept (equivalent: rebuilt at 0)", "  for (int64_t i = 0; i < nc; i++) cc[i].lambda = 0.0;\n", ""),
     ("forward step uses gamma not gamma/2", "double q = (hg * bound) / nd;", "double q = (2.0 * hg * bound) / nd;"),
-    ("CCD rule uses D_i", "double bound = ccd_rule ? Dcap : Di[v];", "double bound = ccd_rule ? Di[v] : Di[v];"),
+    ("CCD rule uses D_i", "double bound = ccd_rule ? (Di[v] == 0.0 ? 0.0 : Dcap) : Di[v];", "double bound = ccd_rule ? Di[v] : Di[v];"),
+    ("CCD rule ignores the D_i floor", "double bound = ccd_rule ? (Di[v] == 0.0 ? 0.0 : Dcap) : Di[v];", "double bound = ccd_rule ? Dcap : Di[v];"),
     ("r update", "r[v] = r[v] * (1.0 - alpha[v]);", "r[v] = r[v] * alpha[v];"),
     ("D update halves the move", "D = nextafter(D - 2.0 * mmax, -INFINITY);", "D = nextafter(D - mmax, -INFINITY);"),
     ("D_i from the first vertex only", "if (P.d[i] < Di[v4[k]]) Di[v4[k]] = P.d[i];", "if (P.d[i] < Di[v4[0]]) Di[v4[0]] = P.d[i];"),

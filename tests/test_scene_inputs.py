@@ -32,3 +32,33 @@ def test_generators_are_seeded():
     assert np.array_equal(S.initial(a)[1], S.initial(b)[1])
     c = S.two_cloths(n=32, seed=6)
     assert not np.array_equal(S.initial(a)[1], S.initial(c)[1])
+
+
+def test_serving_requests_are_smooth_small_steps():
+    # the serving stream's targets: a smooth field of at most 1 mm that moves
+    # no fixed vertex, reproducible from its seed; on the small tube pair,
+    # with the scene's own parameters, such a request converges in a few
+    # oracle iterations and stays intersection-free
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    sc = S.tube_knot(around=16, rings=65, r=0.004, helix_r=0.0055, pitch=0.03, ring_dz=0.002)
+    d1 = bench.smooth_displacement(sc, np.random.default_rng(3))
+    d2 = bench.smooth_displacement(sc, np.random.default_rng(3))
+    assert np.array_equal(d1, d2)
+    assert np.abs(d1).max() <= 1e-3 and np.abs(d1).max() > 0.0
+    assert not np.any(d1[sc.inv_mass == 0.0])
+    # neighbouring vertices move alike: each component is a sinusoid of
+    # amplitude at most 1 mm and wavelength at least a third of the extent,
+    # so along an edge between movable vertices it changes by at most
+    # 1 mm * 2 pi * 3 / extent * edge length
+    e = np.asarray(sc.edges)
+    e = e[(sc.inv_mass[e[:, 0]] > 0.0) & (sc.inv_mass[e[:, 1]] > 0.0)]
+    ext = float(np.ptp(sc.x0, axis=0).max())
+    length = np.linalg.norm(sc.x0[e[:, 0]] - sc.x0[e[:, 1]], axis=1)
+    assert np.all(np.abs(d1[e[:, 0]] - d1[e[:, 1]]).max(axis=1) <= 1e-3 * 2 * np.pi * 3 / ext * length * (1 + 1e-9))
+    osc = oracle.OracleScene(sc)
+    xn, st, _ = oracle.handle_step(osc, oracle.params_for(sc), sc.x0, sc.x0 + d1)
+    assert st["converged"] == 1 and st["iterations"] < 64
+    assert oracle.count_intersections(osc, xn) == 0
