@@ -524,11 +524,6 @@ __device__ __forceinline__ float f_ss_bounds(fv3 a, fv3 b, fv3 c, fv3 d, float e
   *lower = g;
   return sqrtf(bz);
 }
-__device__ __forceinline__ float f_ss_lower(fv3 a, fv3 b, fv3 c, fv3 d) {
-  float lo;
-  f_ss_bounds(a, b, c, d, __int_as_float(0x7f800000), &lo);
-  return lo;
-}
 // error margin of a float distance over these points
 __device__ __forceinline__ float ftol(fv3 a, fv3 b, fv3 c, fv3 d) {
   float X = fmaxf(fmaxf(fmaxabs(a), fmaxabs(b)), fmaxf(fmaxabs(c), fmaxabs(d)));

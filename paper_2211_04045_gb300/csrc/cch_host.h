@@ -110,11 +110,6 @@ __device__ __forceinline__ void scene_count(const Pool& P, int s, Done done) {
   if (part.thread_rank() == 0) done((int)part.size());
 }
 
-// per-scene candidate counts, aggregated over the lanes of one scene
-__device__ __forceinline__ void count_candidate(Pool& P, int s) {
-  scene_count(P, s, [&](int n) { atomicAdd((unsigned long long*)&P.ss[s].candidates, (unsigned long long)n); });
-}
-
 __device__ __forceinline__ int append_idx(int* ctr) {
   cg::coalesced_group g = cg::coalesced_threads();
   int base = 0;
@@ -137,7 +132,7 @@ __device__ __forceinline__ int claim(int* ctr, int cap) {
 // FP32 bounds (lower, upper) of a pair's FP64 distance from the float copy of
 // the positions: d32 -/+ FILTER_TOL * (|x|max + extent), rounded outward.
 // VT: point-triangle minus the point's radius; EE: segment-segment, whose
-// lower bound is the separating-axis gap of f_ss_lower; VV: centre distance
+// lower bound is the separating-axis gap of f_ss_bounds; VV: centre distance
 // minus both radii.  The lower bound is the one the search's FP32 filter
 // uses.
 __device__ __forceinline__ float2 pair_bounds32(const Pool& P, unsigned long long key, int4 v) {
