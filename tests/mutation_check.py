@@ -93,6 +93,7 @@ def run(i):
         for sub in ("oracle", "tests", "paper_2211_04045_gb300"):
             shutil.copytree(os.path.join(ROOT, sub), os.path.join(d, sub),
                             ignore=shutil.ignore_patterns("_build", "__pycache__", "*.so", "*.o"))
+        shutil.copy(os.path.join(ROOT, "bench.py"), d)  # the serving inputs' generator
         src = os.path.join(d, "oracle", "cch_oracle.c")
         s = open(src).read()
         if old not in s:
