@@ -90,3 +90,21 @@ def test_server_admission_by_budget():
         sv.add_scene(big)
     assert e.value.code == 3
     sv.close()
+
+
+@pytest.mark.parametrize("field,value", [("d_min", 0.0), ("delta", 3e-3), ("gamma", 1.0), ("max_iters", -1)])
+def test_invalid_scene_params_rejected(field, value):
+    # per-scene physical parameters are validated like the pool's, before
+    # any device work, in batches and in the server
+    good, bad = cch.params(), cch.params()
+    setattr(bad, field, value)
+    with pytest.raises(cch.CchError) as e:
+        cch.Scene([topo(), topo()], cch.params(), stream=0, scene_params=[good, bad])
+    assert e.value.code == 1
+    with pytest.raises(ValueError):
+        cch.Scene([topo(), topo()], cch.params(), stream=0, scene_params=[good])
+    sv = cch.Server(1 << 20, cch.params(), max_active=2, stream=0)
+    with pytest.raises(cch.CchError) as e:
+        sv.add_scene(topo(), bad)
+    assert e.value.code == 1
+    sv.close()
