@@ -205,7 +205,9 @@ cch_status cch_create_batch(const cch_topology* topos, int32_t n_scenes, const c
  * scene_prm[s] (n_scenes entries, each validated like prm); every other
  * field, the method and its launch configuration, from prm.  A scene of the
  * batch then returns what cch_create_scene with scene_prm[s] returns, when
- * the method fields agree.  scene_prm NULL: cch_create_batch. */
+ * the method fields agree.  scene_prm NULL: cch_create_batch.  The arrays are
+ * read during the call only; an invalid entry returns CCH_E_INVALID_ARG
+ * before any device work. */
 cch_status cch_create_batch_params(const cch_topology* topos, int32_t n_scenes, const cch_params* prm,
                                    const cch_params* scene_prm, void* cuda_stream, cch_scene** out);
 
@@ -231,9 +233,9 @@ cch_status cch_batch_handle_step(cch_scene* s, const double* const* x_t, const d
  * iterations (1..4096), run twice per candidate.  Coordinate descent over:
  * iterations per graph launch group G in {4, 8, 16, 32, 64}; threads per block
  * of the BVH queries in {64, 128, 256}; BVH refit at later searches against a
- * rebuild at every search; warp-packet traversal (the 32 lanes of a warp
- * descend together, each keeping its own tests) against one traversal per
- * thread.  The fastest configuration is kept for the scene's
+ * rebuild at every search; packet traversal (32 queries per warp descend as
+ * a wavefront, each stack entry holding the queries that reach its node)
+ * against one traversal per thread.  The fastest configuration is kept for the scene's
  * later steps.  Results never depend on the configuration: each probe's output
  * is compared bitwise with the first (consistent = 1).  Allocates one scratch
  * output of n_verts x 3 doubles for the duration of the call. */
@@ -243,7 +245,7 @@ typedef struct {
   int32_t bvh_refit_only;    /* chosen: 1 refit, 0 rebuild at every search    */
   int32_t trials;            /* configurations timed                          */
   int32_t consistent;        /* 1: every probe gave the same x_next bitwise    */
-  int32_t packet_traversal;  /* chosen: 1 warp-packet, 0 thread-per-query      */
+  int32_t packet_traversal;  /* chosen: 1 packet (wavefront), 0 thread-per-query */
   double best_ms;            /* probe time with the chosen configuration      */
   double default_ms;         /* probe time with the configuration at entry    */
 } cch_tune_result;
@@ -361,7 +363,8 @@ cch_status cch_server_create(size_t hbm_budget_bytes, const cch_params* prm, int
 /* Make a scene resident; CCH_E_BUDGET when it would exceed the budget. */
 cch_status cch_server_add_scene(cch_server* sv, const cch_topology* topo, int32_t* scene_id);
 /* The same, with the scene's own physical parameters (the fields that
- * cch_create_batch_params takes per scene; the rest from the server's). */
+ * cch_create_batch_params takes per scene; the rest from the server's).
+ * scene_prm is copied; an invalid one returns CCH_E_INVALID_ARG. */
 cch_status cch_server_add_scene_params(cch_server* sv, const cch_topology* topo, const cch_params* scene_prm,
                                        int32_t* scene_id);
 /* Queue one step of a resident scene; pointers are device pointers that must
